@@ -1,0 +1,420 @@
+"""Seeded synthetic inputs for the SimInf split-step method.
+
+This module only builds input data: model tables (the matrices S, G, E, N and
+the data vectors ldata / gdata that the paper's model slots hold, Sec. 3.2),
+initial states and scheduled-event tables (Sec. 3.3).  It does none of the
+method's arithmetic.  Both the CUDA path and the CPU oracle consume what it
+returns, so their results can be compared on identical inputs.
+
+The paper's datasets (Swedish cattle data, Sec. 1; the package's ``nodes``,
+``u0_SISe`` and ``events_SISe`` data, Sec. 4.2) are not available, so the
+cattle-shaped workloads are synthetic: log-normal herd sizes, a directed
+heavy-tailed movement network, and daily enter / exit / internal-transfer /
+external-transfer events whose sizes are geometric with mean 3.  The
+generator tracks every node's per-age-class totals through the event order
+the solver uses, which the SSA leaves unchanged, so every generated event is
+valid whatever the stochastic trajectory.
+
+All layouts are 0-based: ``node``, ``dest``, ``select`` and ``shift`` index
+from 0 and ``shift = -1`` means "no shift".
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SIR, SIS, SISE, SISE3 = 0, 1, 2, 3
+EXIT, ENTER, INTERNAL, EXTERNAL = 0, 1, 2, 3
+KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3"}
+
+
+@dataclass
+class Workload:
+    name: str
+    kind: int
+    S: np.ndarray          # (n_comp, n_trans) int32
+    G: np.ndarray          # (n_trans, n_trans) int32
+    E: np.ndarray          # (n_comp, n_select) int32
+    N: np.ndarray          # (n_comp, n_shift) int32
+    gdata: np.ndarray      # (n_gdata,) float64
+    ldata: np.ndarray      # (n_ldata, n_nodes) float64
+    n_v: int
+    u0: np.ndarray         # (n_rep, n_nodes, n_comp) int32
+    v0: np.ndarray         # (n_rep, n_nodes, n_v) float64
+    tspan: np.ndarray      # (M,) int32, strictly increasing
+    events: dict | None    # event table, see empty_events()
+    seed: int
+    n_rep: int = 1
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self) -> int:
+        return int(self.u0.shape[1])
+
+    @property
+    def n_comp(self) -> int:
+        return int(self.S.shape[0])
+
+    @property
+    def n_days(self) -> int:
+        return int(self.tspan[-1] - self.tspan[0])
+
+    @property
+    def n_events(self) -> int:
+        return 0 if self.events is None else int(len(self.events["event"]))
+
+
+def empty_events():
+    return {k: np.zeros(0, dtype=np.float64 if k == "proportion" else np.int32)
+            for k in ("event", "time", "node", "dest", "n", "proportion",
+                      "select", "shift")} | {"rep": None}
+
+
+def make_events(rows, rep=None):
+    """Event table from rows (event, time, node, dest, n, proportion, select,
+    shift), all 0-based."""
+    ev = empty_events()
+    if rows:
+        cols = list(zip(*rows))
+        for k, c in zip(("event", "time", "node", "dest", "n", "proportion",
+                         "select", "shift"), cols):
+            ev[k] = np.asarray(c, dtype=np.float64 if k == "proportion"
+                               else np.int32)
+    ev["rep"] = None if rep is None else np.asarray(rep, dtype=np.int32)
+    return ev
+
+
+# --------------------------------------------------------------------------
+# Model tables (Sec. 3.2 slots).  G[k, j] != 0 marks that rate k must be
+# recomputed after transition j.
+# --------------------------------------------------------------------------
+
+def sir_tables():
+    """SIR, Eq. (SIR): S -> I, I -> R.  E columns: {S}, {I}, {R}, {S,I,R}
+    as in the SIR event example of Sec. 4.1."""
+    S = np.array([[-1, 0], [1, -1], [0, 1]], dtype=np.int32)
+    G = np.array([[1, 1], [1, 1]], dtype=np.int32)
+    E = np.array([[1, 0, 0, 1], [0, 1, 0, 1], [0, 0, 1, 1]], dtype=np.int32)
+    N = np.zeros((3, 1), dtype=np.int32)
+    return S, G, E, N
+
+
+def sis_tables():
+    """SIS of Sec. 2.1: S + I -> 2I, I -> S.  E columns: {S}, {I}, {S,I}."""
+    S = np.array([[-1, 1], [1, -1]], dtype=np.int32)
+    G = np.array([[1, 1], [1, 1]], dtype=np.int32)
+    E = np.array([[1, 0, 1], [0, 1, 1]], dtype=np.int32)
+    N = np.zeros((2, 1), dtype=np.int32)
+    return S, G, E, N
+
+
+def sise_tables():
+    """SISe (Sec. 4.2 without spatial coupling): S -> I at upsilon phi S,
+    I -> S at gamma I.  Each rate depends only on its own source
+    compartment."""
+    S = np.array([[-1, 1], [1, -1]], dtype=np.int32)
+    G = np.array([[1, 1], [1, 1]], dtype=np.int32)
+    E = np.array([[1, 0, 1], [0, 1, 1]], dtype=np.int32)
+    N = np.zeros((2, 1), dtype=np.int32)
+    return S, G, E, N
+
+
+def sise3_tables():
+    """SISe3: compartments [S1, I1, S2, I2, S3, I3], transitions
+    S_a -> I_a (2a) and I_a -> S_a (2a + 1).  E columns 0-2 = {S_a} (enter),
+    3-5 = {S_a, I_a} (exit, transfers), as in the event table of Appendix B.
+    N column 0 ages {S1, I1} into {S2, I2}; column 1 ages {S2, I2} into
+    {S3, I3}."""
+    S = np.zeros((6, 6), dtype=np.int32)
+    G = np.zeros((6, 6), dtype=np.int32)
+    for a in range(3):
+        S[2 * a, 2 * a], S[2 * a + 1, 2 * a] = -1, 1
+        S[2 * a, 2 * a + 1], S[2 * a + 1, 2 * a + 1] = 1, -1
+        for j in (2 * a, 2 * a + 1):
+            G[2 * a, j] = 1
+            G[2 * a + 1, j] = 1
+    E = np.zeros((6, 6), dtype=np.int32)
+    for a in range(3):
+        E[2 * a, a] = 1
+        E[2 * a, 3 + a] = 1
+        E[2 * a + 1, 3 + a] = 1
+    N = np.zeros((6, 2), dtype=np.int32)
+    N[0, 0] = N[1, 0] = 2
+    N[2, 1] = N[3, 1] = 2
+    return S, G, E, N
+
+
+def seasons_ldata(n_nodes, ends=(91, 182, 273, 365)):
+    return np.tile(np.asarray(ends, dtype=np.float64)[:, None], (1, n_nodes))
+
+
+def sise_gdata(upsilon=0.0173, gamma=0.1, alpha=1.0, betas=(0.1,) * 4):
+    return np.array([upsilon, gamma, alpha, *betas], dtype=np.float64)
+
+
+def sise3_gdata(upsilons=(0.0173,) * 3, gammas=(0.1,) * 3, alpha=1.0,
+                betas=(0.10, 0.12, 0.12, 0.10)):
+    return np.array([*upsilons, *gammas, alpha, *betas], dtype=np.float64)
+
+
+def _tile_rep(a, n_rep):
+    return np.ascontiguousarray(np.broadcast_to(a[None], (n_rep,) + a.shape))
+
+
+def plain_model(kind, u0, tspan, gdata, seed=42, n_rep=1, events=None,
+                ldata=None, v0=None, name=None):
+    """A workload on explicit initial state ``u0`` (n_nodes, n_comp) or
+    (n_rep, n_nodes, n_comp)."""
+    tables = {SIR: sir_tables, SIS: sis_tables, SISE: sise_tables,
+              SISE3: sise3_tables}[kind]()
+    S, G, E, N = tables
+    u0 = np.asarray(u0, dtype=np.int32)
+    if u0.ndim == 2:
+        u0 = _tile_rep(u0, n_rep)
+    n_nodes = u0.shape[1]
+    n_v = 1 if kind in (SISE, SISE3) else 0
+    if ldata is None:
+        ldata = (seasons_ldata(n_nodes) if n_v
+                 else np.zeros((0, n_nodes), dtype=np.float64))
+    if v0 is None:
+        v0 = np.zeros((n_rep, n_nodes, n_v), dtype=np.float64)
+    v0 = np.asarray(v0, dtype=np.float64)
+    if v0.ndim == 2:
+        v0 = _tile_rep(v0, n_rep)
+    return Workload(name or KIND_NAMES[kind], kind, S, G, E, N,
+                    np.asarray(gdata, dtype=np.float64),
+                    np.asarray(ldata, dtype=np.float64), n_v, u0, v0,
+                    np.asarray(tspan, dtype=np.int32),
+                    events if events is not None else empty_events(),
+                    int(seed), int(n_rep))
+
+
+# --------------------------------------------------------------------------
+# Synthetic cattle-shaped populations and event streams.
+# --------------------------------------------------------------------------
+
+def lognormal_herds(rng, n, median, sigma, lo, hi):
+    z = rng.standard_normal(n)
+    return np.clip(np.rint(np.exp(np.log(median) + sigma * z)), lo, hi
+                   ).astype(np.int64)
+
+
+def split_ages(herd, fracs=(0.2, 0.2, 0.6)):
+    """Largest-remainder split of each herd into age classes."""
+    fr = np.asarray(fracs, dtype=np.float64)
+    raw = herd[:, None] * fr[None, :]
+    base = np.floor(raw).astype(np.int64)
+    rem = raw - base
+    short = herd - base.sum(axis=1)
+    order = np.argsort(-rem, axis=1, kind="stable")
+    for i in range(len(fr)):
+        add = short > i
+        base[np.arange(len(herd))[add], order[add, i]] += 1
+    return base
+
+
+def powerlaw_network(rng, n_nodes, exponent=2.2, kmax=1000):
+    """Directed graph: out-degree k in [1, kmax] with P(k) ~ k^-exponent,
+    out-neighbours uniform without self-loops.  Returns CSR (ptr, adj)."""
+    kmax = max(1, min(kmax, n_nodes - 1))
+    ks = np.arange(1, kmax + 1, dtype=np.float64)
+    p = ks ** (-exponent)
+    p /= p.sum()
+    deg = rng.choice(np.arange(1, kmax + 1), size=n_nodes, p=p)
+    ptr = np.zeros(n_nodes + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum(deg)
+    adj = np.empty(ptr[-1], dtype=np.int64)
+    for i in range(n_nodes):
+        d = int(deg[i])
+        nb = rng.choice(n_nodes - 1, size=d, replace=False)
+        nb[nb >= i] += 1
+        adj[ptr[i]:ptr[i + 1]] = nb
+    return ptr, adj, deg
+
+
+def _geometric3(rng, size):
+    # Geometric on {1, 2, ...} with mean 3.
+    return rng.geometric(1.0 / 3.0, size=size).astype(np.int64)
+
+
+def _cattle_events(rng, totals, n_days, t0, rate, mix, n_ages, net, enter_sel,
+                   exit_sel, ages_shift):
+    """Daily events with exact tracking of per-age totals.
+
+    totals: (n_nodes, n_ages) int64, modified in place.
+    mix: fractions (exit, enter, internal, external).
+    Within a day the solver runs exits, then enters, then internal
+    transfers, then external transfers in list order, so the totals are
+    tracked in that order.  The final list is shuffled, keeping the relative
+    order of each day's external transfers.
+    """
+    n_nodes = totals.shape[0]
+    ptr, adj, deg = net
+    src_p = deg / deg.sum()
+    rows = []          # (event, time, node, dest, n, select, shift)
+    for d in range(n_days):
+        T = t0 + 1 + d
+        n_today = rng.poisson(rate * n_nodes)
+        n_exit, n_enter, n_int, n_ext = rng.multinomial(n_today, mix)
+        # exits: clamp cumulatively per (node, age) group
+        if n_exit:
+            nodes = rng.integers(0, n_nodes, n_exit)
+            ages = rng.integers(0, n_ages, n_exit)
+            want = _geometric3(rng, n_exit)
+            key = nodes * n_ages + ages
+            order = np.argsort(key, kind="stable")
+            k_s, w_s = key[order], want[order]
+            starts = np.r_[True, k_s[1:] != k_s[:-1]]
+            grp = np.cumsum(starts) - 1
+            cs = np.cumsum(w_s)
+            base = np.r_[0, cs][np.flatnonzero(starts)][grp]
+            cum = cs - base
+            avail = totals.reshape(-1)[k_s]
+            capped = np.minimum(cum, avail)
+            got = capped - np.r_[0, capped[:-1]]
+            got[starts] = capped[starts]
+            np.subtract.at(totals.reshape(-1), k_s, got)
+            ok = got > 0
+            for i in np.flatnonzero(ok):
+                nd, ag = divmod(int(k_s[i]), n_ages)
+                rows.append((EXIT, T, nd, 0, int(got[i]), exit_sel[ag], -1))
+        if n_enter:
+            nodes = rng.integers(0, n_nodes, n_enter)
+            want = _geometric3(rng, n_enter)
+            np.add.at(totals[:, 0], nodes, want)
+            for nd, w in zip(nodes.tolist(), want.tolist()):
+                rows.append((ENTER, T, nd, 0, w, enter_sel, -1))
+        if n_int and ages_shift:
+            for _ in range(n_int):
+                nd = int(rng.integers(0, n_nodes))
+                a = int(rng.integers(0, len(ages_shift)))
+                sel, q = ages_shift[a]
+                avail = int(totals[nd, a])
+                w = min(int(_geometric3(rng, 1)[0]), avail)
+                if w <= 0:
+                    continue
+                totals[nd, a] -= w
+                totals[nd, a + 1] += w
+                rows.append((INTERNAL, T, nd, 0, w, sel, q))
+        if n_ext:
+            srcs = rng.choice(n_nodes, size=n_ext, p=src_p)
+            picks = rng.random(n_ext)
+            want = _geometric3(rng, n_ext)
+            ages = rng.integers(0, n_ages, n_ext)
+            for s, pk, w, a in zip(srcs.tolist(), picks.tolist(),
+                                   want.tolist(), ages.tolist()):
+                nb = adj[ptr[s]:ptr[s + 1]]
+                dst = int(nb[int(pk * len(nb))])
+                avail = int(totals[s, a])
+                w = min(w, avail)
+                if w <= 0:
+                    continue
+                totals[s, a] -= w
+                totals[dst, a] += w
+                rows.append((EXTERNAL, T, s, dst, w, exit_sel[a], -1))
+    if not rows:
+        return empty_events()
+    arr = np.asarray(rows, dtype=np.int64)
+    n = len(arr)
+    perm = rng.permutation(n)
+    shuffled = arr[perm]
+    # Internal and external transfers may depend on earlier ones of the same
+    # day and type (the solver runs them in list order), so each day keeps
+    # their relative order: the positions that a day's events of one such
+    # type occupy receive those events in generation order.
+    for etype in (INTERNAL, EXTERNAL):
+        pos = np.flatnonzero(shuffled[:, 0] == etype)
+        if pos.size == 0:
+            continue
+        orig = perm[pos]
+        tday = shuffled[pos, 1]
+        o_pos = np.lexsort((pos, tday))
+        o_orig = np.lexsort((orig, tday))
+        shuffled[pos[o_pos]] = arr[orig[o_orig]]
+    ev = empty_events()
+    ev["event"] = shuffled[:, 0].astype(np.int32)
+    ev["time"] = shuffled[:, 1].astype(np.int32)
+    ev["node"] = shuffled[:, 2].astype(np.int32)
+    ev["dest"] = shuffled[:, 3].astype(np.int32)
+    ev["n"] = shuffled[:, 4].astype(np.int32)
+    ev["proportion"] = np.zeros(n, dtype=np.float64)
+    ev["select"] = shuffled[:, 5].astype(np.int32)
+    ev["shift"] = shuffled[:, 6].astype(np.int32)
+    return ev
+
+
+def config_sir(n_nodes=100, days=99, seed=42):
+    """SIR without events: every node S=99 I=1 R=0, beta 0.16, gamma 0.077,
+    tspan = 1..days+1 (the first-example parameters of Sec. 4.1)."""
+    u0 = np.tile(np.array([[99, 1, 0]], dtype=np.int32), (n_nodes, 1))
+    return plain_model(SIR, u0, np.arange(1, days + 2), [0.16, 0.077],
+                       seed=seed, name=f"SIR {n_nodes} nodes x {days} days")
+
+
+def config_sise(n_nodes=1600, days=365, gen_seed=1002, seed=42,
+                events_per_node_day=0.41, median=50, sigma=1.0, hi=5000):
+    """SISe with scheduled events: log-normal herds (median 50, sigma 1.0,
+    clamp 1..5000), 1% of nodes seeded with 10% infected, phi updated daily
+    (alpha 1.0, decay 0.1), upsilon 0.0173, gamma 0.1; one year of enter /
+    exit / external-transfer events (thirds), ~0.34 events per node-day."""
+    rng = np.random.default_rng(gen_seed)
+    herd = lognormal_herds(rng, n_nodes, median, sigma, 1, hi)
+    I = np.zeros(n_nodes, dtype=np.int64)
+    seeded = rng.choice(n_nodes, size=max(1, n_nodes // 100), replace=False)
+    I[seeded] = np.maximum(1, np.rint(0.1 * herd[seeded])).astype(np.int64)
+    S = herd - I
+    u0 = np.stack([S, I], axis=1).astype(np.int32)
+    net = powerlaw_network(rng, n_nodes)
+    totals = herd[:, None].copy()
+    ev = _cattle_events(rng, totals, days, 0, events_per_node_day,
+                        (1 / 3, 1 / 3, 0.0, 1 / 3), 1, net, enter_sel=0,
+                        exit_sel=[2], ages_shift=None)
+    w = plain_model(SISE, u0, np.arange(0, days + 1), sise_gdata(),
+                    seed=seed, events=ev,
+                    name=f"SISe {n_nodes} nodes x {days} days with events")
+    w.meta = {"gen_seed": gen_seed}
+    return w
+
+
+def config_sise3(n_nodes=37000, days=3650, gen_seed=1003, seed=42,
+                 events_per_node_day=0.111, median=60, sigma=1.2, hi=10000,
+                 n_rep=1, per_rep_events=False):
+    """SISe3 (three age classes): log-normal herds split 0.2/0.2/0.6 by age,
+    1% of nodes seeded with 10% infected per age class, seasonal decay per
+    quarter; events: exit 30%, enter 30%, internal transfer (ageing) 20%,
+    external transfer 20% on a power-law network."""
+    rng = np.random.default_rng(gen_seed)
+    herd = lognormal_herds(rng, n_nodes, median, sigma, 1, hi)
+    ages = split_ages(herd)
+    I = np.zeros_like(ages)
+    seeded = rng.choice(n_nodes, size=max(1, n_nodes // 100), replace=False)
+    I[seeded] = np.rint(0.1 * ages[seeded]).astype(np.int64)
+    S = ages - I
+    u0 = np.stack([S[:, 0], I[:, 0], S[:, 1], I[:, 1], S[:, 2], I[:, 2]],
+                  axis=1).astype(np.int32)
+    net = powerlaw_network(rng, n_nodes)
+    mix = (0.3, 0.3, 0.2, 0.2)
+    evs = []
+    reps = n_rep if per_rep_events else 1
+    for r in range(reps):
+        totals = ages.copy()
+        ev = _cattle_events(rng, totals, days, 0, events_per_node_day, mix, 3,
+                            net, enter_sel=0, exit_sel=[3, 4, 5],
+                            ages_shift=[(3, 0), (4, 1)])
+        if per_rep_events:
+            ev["rep"] = np.full(len(ev["event"]), r, dtype=np.int32)
+        evs.append(ev)
+    if per_rep_events:
+        ev = empty_events()
+        for k in ("event", "time", "node", "dest", "n", "proportion",
+                  "select", "shift", "rep"):
+            ev[k] = np.concatenate([e[k] for e in evs])
+    else:
+        ev = evs[0]
+    w = plain_model(SISE3, u0, np.arange(0, days + 1), sise3_gdata(),
+                    seed=seed, n_rep=n_rep, events=ev,
+                    name=f"SISe3 {n_nodes} nodes x {days} days"
+                         + (f" x {n_rep} replicates" if n_rep > 1 else ""))
+    w.meta = {"gen_seed": gen_seed}
+    return w
