@@ -1,0 +1,341 @@
+"""Benchmark of the SimInf split-step engine on one GB300.
+
+One step = one complete simulation of the SISe workload with scheduled
+events (1,600 nodes, log-normal herds, 365 days, ~200k enter / exit /
+external-transfer events): per-node direct SSA, E1 and E2 events, post time
+step (phi) and recording of U and V at every day, all through the C ABI.
+
+Prints one JSON line.  `value` is node-days/s over the timed steps (inputs
+resident in HBM); `e2e` is the same metric through the public host-buffer
+call (model creation, event upload and planning, host-to-device copy of the
+initial state, run, device-to-host copy of U and V).  `--impl reference`
+times the CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+_ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, _ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "node-days/s (direct-method SSA + scheduled events + post time step + recording)"
+UNIT = "node-days/s"
+L2_BYTES = 129 * 2 ** 20
+# FP64 ops (adds, multiplies, divides, conversions each counted once) of one
+# SSA draw in the SISe rate loop: two uniforms (6), logarithm (34), waiting
+# time (1 divide), rate sum (2), time update and comparison (1); a draw that
+# fires a transition adds the inversion (3) and two rate recomputations (6).
+FP64_PER_DRAW = 44
+FP64_PER_REACTION = 9
+FP64_PER_NODE_DAY = 14  # day-start rates (6) + post time step (8)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal table figure)
+
+
+def _workload(name):
+    from paper_1605_01421_gb300 import workloads as W
+    if name == "sise":
+        return W.config_sise()
+    if name == "sir":
+        return W.config_sir()
+    if name == "sise3":
+        return W.config_sise3()
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def time_oracle(w, budget_s=10.0, max_runs=50):
+    """Run the CPU oracle on the whole workload repeatedly for ~budget_s
+    (at least once); node-days/s and reactions/s."""
+    import oracle
+    oracle.build()
+    node_days = w.n_nodes * w.n_days * w.n_rep
+    runs, t_total, reactions = 0, 0.0, 0
+    while runs < max_runs and (runs == 0 or t_total < budget_s):
+        t = time.perf_counter()
+        code, U, V, R, err = oracle.run(w)
+        t_total += time.perf_counter() - t
+        assert code == 0, err
+        reactions += int(R.sum())
+        runs += 1
+    return {"value": node_days * runs / t_total, "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "reactions_per_s": reactions / t_total,
+            "sample": f"{runs} complete run(s) of the workload ({node_days} node-days each), "
+                      f"serial C oracle, 1 thread, {t_total:.2f} s"}
+
+
+def bench_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = _workload(args.workload)
+    node_days = w.n_nodes * w.n_days * w.n_rep
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.run(w)
+    times, reactions = [], 0
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        code, U, V, R, err = oracle.run(w)
+        times.append(time.perf_counter() - t)
+        assert code == 0, err
+        reactions += int(R.sum())
+    total = sum(times)
+    value = node_days * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
+            "data": "synthetic", "reactions_per_s": reactions / total,
+            "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
+                       "replicates": w.n_rep, "events": w.n_events, "seed": w.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} complete run(s) of the workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def bench_gpu(args):
+    import torch
+    from paper_1605_01421_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    binding.build()
+    w = _workload(args.workload)
+    n_rep = w.n_rep
+    M = len(w.tspan)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    model = binding.Model(w)
+    u0 = torch.as_tensor(np.ascontiguousarray(w.u0), device=dev)
+    v0 = torch.as_tensor(np.ascontiguousarray(w.v0), device=dev)
+    U = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32, device=dev)
+    V = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    # replicas only: every rank runs the same workload with its own seed
+    seed = w.seed + rank
+
+    def step():
+        return model.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    reactions = draws = launches = 0
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed interval of the step
+        starts[i].record(stream)
+        rc, st, er = step()
+        ends[i].record(stream)
+        reactions += st["reactions"]
+        draws += st["draws"]
+        launches += st["kernel_launches"]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    node_days = w.n_nodes * w.n_days * n_rep
+    value = node_days * args.steps * world / (total_ms * 1e-3)
+
+    # per-kernel device time in a second pass with timing events around every
+    # launch (kept out of the timed region above)
+    model.set_kernel_timing(True)
+    kt = {"ms_ssa": 0.0, "ms_e1": 0.0, "ms_e2": 0.0, "launches_ssa": 0,
+          "launches_e1": 0, "launches_e2": 0, "draws": 0, "reactions": 0,
+          "node_days": 0}
+    for _ in range(args.steps):
+        flush.zero_()
+        rc, st, er = step()
+        for k in kt:
+            kt[k] += st[k]
+    model.set_kernel_timing(False)
+    shares = {k: kt[f"ms_{k}"] for k in ("ssa", "e1", "e2")}
+    dominant = max(shares, key=shares.get)
+    fp64_measured = binding.fp64_fma_probe()
+    ssa_flops = (FP64_PER_DRAW * kt["draws"] + FP64_PER_REACTION * kt["reactions"]
+                 + FP64_PER_NODE_DAY * kt["node_days"])
+    if dominant == "ssa":
+        achieved = ssa_flops / (kt["ms_ssa"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": "k_days (SSA + post time step + recording)",
+                "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s)",
+                "fp64_fma_measured_tflops": fp64_measured,
+                "frac_of_measured_fp64": achieved / fp64_measured,
+                "avg_launch_ms": kt["ms_ssa"] / max(1, kt["launches_ssa"])}
+    else:
+        # event kernels: algorithmic bytes = event record (35 B) + read/write of
+        # the touched node states (2 x 4 C B per node, 2 nodes for E2)
+        C = w.n_comp
+        ev_bytes = w.n_events * n_rep * (35 + (2 * 2 * 4 * C if dominant == "e2" else 2 * 4 * C))
+        ms_k = kt[f"ms_{dominant}"]
+        from_peaks = _measured_peaks()
+        achieved = ev_bytes / (ms_k * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": from_peaks,
+                "unit": "GB/s", "frac": achieved / from_peaks, "traffic": None,
+                "kernel": f"k_events_{dominant}",
+                "avg_launch_ms": ms_k / max(1, kt[f"launches_{dominant}"])}
+    roof["kernel_ms_share"] = {k: v / max(1e-9, sum(shares.values())) for k, v in shares.items()}
+
+    # end to end through the public host-buffer call
+    e2e = None
+    if True:
+        u0h = torch.as_tensor(np.ascontiguousarray(w.u0)).pin_memory().numpy()
+        v0h = torch.as_tensor(np.ascontiguousarray(w.v0)).pin_memory().numpy()
+        Uh = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32).pin_memory().numpy()
+        Vh = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64).pin_memory().numpy()
+        t_e2e = 0.0
+        for i in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            m2 = binding.Model(w)  # tables + events: host validation, plan, upload
+            m2.run_host(w.tspan, seed, n_rep, u0h, v0h, Uh, Vh, stream=stream)
+            t_e2e += time.perf_counter() - t
+            m2.close()
+        ev_bytes_h2d = w.n_events * 35
+        e2e = {"value": node_days * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(u0h.nbytes + v0h.nbytes + ev_bytes_h2d),
+               "d2h_bytes_per_step": int(Uh.nbytes + Vh.nbytes)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = time_oracle(w, budget_s=args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
+            "data": "synthetic",
+            "reactions_per_s": reactions * world / (total_ms * 1e-3),
+            "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
+                       "replicates": n_rep, "events": w.n_events, "seed": w.seed,
+                       "l2": "flushed between steps (512 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "gpu_launches": launches,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+    print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(_ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="sise", choices=["sise", "sir", "sise3"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

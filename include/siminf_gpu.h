@@ -1,0 +1,216 @@
+/*
+ * siminf_gpu.h -- C ABI of the GB300 (sm_103a) engine for the SimInf
+ * split-step method (Widgren, Bauer, Eriksson, Engblom, arXiv 1605.01421).
+ *
+ * The library runs, for every replicate and node, the direct-method SSA
+ * between unit time points (Sec. 2.3 Eq. numstep1, Appendix A), the scheduled
+ * events (Sec. 2.3 Eq. numstep2, Sec. 3.3), the post time step update of the
+ * continuous state (Eq. numstep3) and the recording of U and V at the tspan
+ * points (Sec. 3.2).  Every step runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every call:
+ *   - Indices are 0-based: node, dest, select and shift columns.  shift < 0
+ *     means "no shift" (the paper's 1-based shift = 0).
+ *   - Matrices S, G, E, N and ldata are column-major, as the paper's model
+ *     slots (Sec. 3.2 table of SimInf_model slots): column j of S is the
+ *     state change of transition j; ldata column i is node i's local data.
+ *   - Return value: SG_OK (0) or a negative SG_ERR_* code.  No call aborts
+ *     the process; a failed call leaves the model usable.
+ *   - Host arrays passed to sg_model_create / sg_set_events are copied; the
+ *     caller may free them after the call.  Device pointers passed to sg_run
+ *     stay owned by the caller; the library never frees them.
+ *   - The library owns the sg_model and the device memory behind it (model
+ *     tables, event plan, working state); sg_model_destroy releases it.
+ *   - One sg_model must not be used from two threads at once.
+ */
+#ifndef SIMINF_GPU_H
+#define SIMINF_GPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_MAX_COMP 16   /* compartments per node */
+#define SG_MAX_TRANS 16  /* transitions per node */
+#define SG_MAX_SELECT 32 /* columns of E */
+#define SG_MAX_SHIFT 32  /* columns of N */
+
+/* Built-in models.  Transition-rate functions (TRFun) and the post time step
+ * (PTSFun) of Sec. 3.4.1 are compiled device functions, one set per kind;
+ * the model tables S, G, E, N are data.
+ *   SG_SIR   Eq. (SIR) and the rate listing of Appendix C: S -> I at
+ *            beta S I / (S + I + R), I -> R at gamma I.  gdata = [beta,
+ *            gamma].  No continuous state.
+ *   SG_SIS   Sec. 2.1 example: R(x) = [beta S I, gamma I].  gdata = [beta,
+ *            gamma].
+ *   SG_SISE  Sec. 4.2 without spatial coupling: S -> I at upsilon phi S,
+ *            I -> S at gamma I; phi' = alpha I / N - beta(t) phi.  gdata =
+ *            [upsilon, gamma, alpha, beta_t1..beta_t4]; ldata = [end_t1..
+ *            end_t4] per node; v = [phi].
+ *   SG_SISE3 SISe per age class, compartments [S1,I1,S2,I2,S3,I3]; gdata =
+ *            [upsilon_1..3, gamma_1..3, alpha, beta_t1..beta_t4]; ldata and
+ *            v as SG_SISE.                                                  */
+typedef enum { SG_SIR = 0, SG_SIS = 1, SG_SISE = 2, SG_SISE3 = 3 } sg_model_kind;
+
+/* Event types, coded as in the event table of Sec. 3.3. */
+typedef enum {
+  SG_EXIT = 0,
+  SG_ENTER = 1,
+  SG_INTERNAL_TRANSFER = 2,
+  SG_EXTERNAL_TRANSFER = 3
+} sg_event_type;
+
+enum {
+  SG_OK = 0,
+  SG_ERR_ARG = -1,             /* invalid argument or table entry          */
+  SG_ERR_EVENT_UNDERFLOW = -2, /* an event moves more individuals than the
+                                  selected compartments hold (Sec. 4.1)     */
+  SG_ERR_SHIFT_RANGE = -3,     /* p + N[p, q] outside the compartments     */
+  SG_ERR_RATE = -4,            /* negative or non-finite transition rate   */
+  SG_ERR_PTS = -5,             /* post time step returned an error         */
+  SG_ERR_TIMEOUT = -6,         /* a bounded device wait gave up            */
+  SG_ERR_CUDA = -7,            /* a CUDA runtime call failed               */
+  SG_ERR_NOMEM = -8,           /* host or device allocation failed         */
+  SG_ERR_STEP_LIMIT = -9       /* a node needed more than SG_MAX_DRAWS draws
+                                  in one unit step (rates far too large)    */
+};
+
+/* Draws one node may take in one unit step before the run stops with
+ * SG_ERR_STEP_LIMIT: a bound on kernel run time, not part of the method. */
+#define SG_MAX_DRAWS (1u << 24)
+
+typedef struct sg_model sg_model; /* opaque, library-owned */
+
+/* Model description: the slots of the SimInf_model class (Sec. 3.2). */
+typedef struct {
+  int32_t kind;     /* sg_model_kind                                        */
+  int32_t n_nodes;  /* Nnodes >= 0                                          */
+  int32_t n_comp;   /* Ncomp: must equal the kind's compartment count       */
+  int32_t n_trans;  /* Ntrans: must equal the kind's transition count       */
+  const int32_t *S; /* n_comp x n_trans state-change matrix (column-major)  */
+  const int32_t *G; /* n_trans x n_trans dependency graph: G[k, j] != 0
+                       means rate k is recomputed after transition j         */
+  int32_t n_select; /* columns of E                                         */
+  const int32_t *E; /* n_comp x n_select select matrix; non-zero = selected */
+  int32_t n_shift;  /* columns of N (may be 0)                              */
+  const int32_t *N; /* n_comp x n_shift shift matrix (compartment offsets)  */
+  int32_t n_v;      /* continuous states per node: the kind's count         */
+  int32_t n_ldata;  /* local data per node (>= the kind's requirement)      */
+  const double *ldata; /* n_ldata x n_nodes                                 */
+  int32_t n_gdata;  /* global data entries (>= the kind's requirement)      */
+  const double *gdata;
+} sg_desc;
+
+/* First error seen by a run (code 0 if none); -1 marks "not applicable". */
+typedef struct {
+  int32_t code;
+  int32_t rep;
+  int32_t node;
+  int32_t day; /* the unit time point T being simulated toward */
+  int64_t event; /* index of the event in the list given to sg_set_events */
+} sg_error;
+
+typedef struct {
+  int64_t reactions;      /* SSA transitions fired, all replicates         */
+  int64_t draws;          /* SSA random draws (Philox calls), all replicates*/
+  int64_t node_days;      /* replicates x nodes x unit time steps           */
+  int64_t events_applied; /* scheduled events run, all replicates           */
+  int64_t kernel_launches;/* kernels this run launched                      */
+  int32_t e2_waves;       /* external-transfer waves over the run           */
+  int32_t days;           /* unit time steps simulated                      */
+  /* Per-kernel device time, filled only when kernel timing is enabled
+   * (sg_set_kernel_timing): CUDA events around every launch.               */
+  double ms_ssa;          /* SSA + post time step + recording kernels       */
+  double ms_e1;           /* exit / enter / internal-transfer kernels       */
+  double ms_e2;           /* external-transfer wave kernels                 */
+  int64_t launches_ssa, launches_e1, launches_e2;
+} sg_stats;
+
+/* Create a model from its tables (Sec. 3.2).  Validates the sizes against
+ * the kind, copies every table to the device and returns the handle in
+ * *out.  Errors: SG_ERR_ARG, SG_ERR_NOMEM, SG_ERR_CUDA. */
+int sg_model_create(const sg_desc *desc, sg_model **out);
+
+/* Replace the model's scheduled events (event table of Sec. 3.3): n_events
+ * entries of type event[e] at integer time[e] on node[e] (and dest[e] for
+ * external transfers), moving n[e] individuals, or, when n[e] == 0 and the
+ * type samples, round(proportion[e] * selected total) (half away from zero),
+ * sampled without replacement from the compartments of column select[e] of E
+ * and shifted by column shift[e] of N.  rep may be NULL (every replicate runs
+ * every event) or give each event's replicate.  The events are validated
+ * (types, node and dest ranges, select / shift columns, n >= 0, 0 <=
+ * proportion <= 1, internal transfers need a shift, shifts must keep every
+ * selectable compartment in range), sorted and planned on the host, and
+ * copied to the device.  Errors: SG_ERR_ARG, SG_ERR_SHIFT_RANGE,
+ * SG_ERR_NOMEM, SG_ERR_CUDA. */
+int sg_set_events(sg_model *m, int64_t n_events, const int32_t *event,
+                  const int32_t *time, const int32_t *node, const int32_t *dest,
+                  const int32_t *n, const double *proportion,
+                  const int32_t *select, const int32_t *shift,
+                  const int32_t *rep);
+
+/* Run n_rep independent trajectories over tspan (n_tspan >= 1 strictly
+ * increasing integers; the simulation covers unit steps T = tspan[0] + 1 ..
+ * tspan[n_tspan - 1]) with Philox key `seed`, on the caller's CUDA stream
+ * (cudaStream_t passed as void*, NULL = legacy default stream).
+ *   d_u0 [n_rep][n_nodes][n_comp] int32   device, read
+ *   d_v0 [n_rep][n_nodes][n_v]    double  device, read (NULL if n_v == 0)
+ *   d_U  [n_rep][n_tspan][n_nodes][n_comp] int32  device, written: U[r][m]
+ *        is column m of the paper's U (node-major, compartments contiguous)
+ *   d_V  [n_rep][n_tspan][n_nodes][n_v]    double device, written (NULL if
+ *        n_v == 0)
+ * Events dated tspan[0] or earlier run at the first step; events after the
+ * last tspan point never run.  The call enqueues all work, then waits for
+ * the stream and reads back the error word and counters.  stats and err may
+ * be NULL.  Errors: any SG_ERR_* (err says where). */
+int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+           int32_t n_rep, const int32_t *d_u0, const double *d_v0,
+           int32_t *d_U, double *d_V, void *stream, sg_stats *stats,
+           sg_error *err);
+
+/* sg_run on host buffers (same shapes): copies u0 / v0 to the device,
+ * runs, and copies U / V back, all on `stream`.  Device buffers for the
+ * copies are allocated by the library and kept for reuse.  Host buffers in
+ * page-locked memory give full copy bandwidth. */
+int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan,
+                uint64_t seed, int32_t n_rep, const int32_t *u0,
+                const double *v0, int32_t *U, double *V, void *stream,
+                sg_stats *stats, sg_error *err);
+
+/* Enable (1) or disable (0) per-kernel timing: sg_run then brackets every
+ * kernel launch with CUDA events on its stream and fills the ms_* fields of
+ * sg_stats.  Off by default (the events add host work per launch). */
+int sg_set_kernel_timing(sg_model *m, int enable);
+
+/* Release the model and all its device memory. */
+void sg_model_destroy(sg_model *m);
+
+/* Static description of an error code. */
+const char *sg_strerror(int code);
+
+/* Device-side primitives, exported for parity checks of the random stream
+ * and arithmetic (each fills a caller-owned device buffer on `stream` and
+ * waits for it):
+ *   sg_philox_batch: out[4 i .. 4 i + 3] = Philox4x32-10(ctr[4 i ..], key)
+ *                    for i < n  (Salmon et al., SC'11)
+ *   sg_log_batch:    y[i] = the library's natural logarithm of x[i]
+ *   sg_u01_batch:    y[i] = open-interval uniform of words w[2 i], w[2 i+1]
+ * All pointers are device pointers. */
+int sg_philox_batch(const uint32_t *d_ctr, uint64_t key, uint32_t *d_out,
+                    int64_t n, void *stream);
+int sg_log_batch(const double *d_x, double *d_y, int64_t n, void *stream);
+int sg_u01_batch(const uint32_t *d_w, double *d_y, int64_t n, void *stream);
+
+/* FP64 throughput probe for roofline statements: runs independent chains of
+ * fused multiply-adds on every SM for about `iters` steps and returns the
+ * achieved rate in *tflops (2 flops per fused multiply-add). */
+int sg_fp64_fma_probe(int32_t iters, double *tflops, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMINF_GPU_H */

@@ -33,6 +33,7 @@ ERR_NAMES = {
     -4: "negative or non-finite transition rate",
     -5: "post time step error",
     -8: "out of memory",
+    -9: "more than 2^24 draws in one node-day",
 }
 
 _lock = threading.Lock()

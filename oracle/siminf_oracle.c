@@ -523,6 +523,9 @@ static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
         /* Reading: with lambda = 0 no transition can fire; the node jumps
          * to T without consuming a draw. */
         if (!(lambda > 0.0)) break;
+        /* Guard (not in the paper): rates so large that a node-day needs more
+         * than 2^24 draws end the run with an error instead of running on. */
+        if (ctr[0] >= ORACLE_MAX_DRAWS_PER_NODE_DAY) return ORACLE_ERR_STEP_LIMIT;
         oracle_philox4x32_10(ctr, key, x);
         ctr[0] += 1;
         r1 = oracle_u01(x[0], x[1]);

@@ -37,8 +37,12 @@ enum {
     ORACLE_ERR_SHIFT_RANGE = -3,
     ORACLE_ERR_RATE = -4,
     ORACLE_ERR_PTS = -5,
-    ORACLE_ERR_NOMEM = -8
+    ORACLE_ERR_NOMEM = -8,
+    ORACLE_ERR_STEP_LIMIT = -9
 };
+
+/* A node-day stops with ORACLE_ERR_STEP_LIMIT before its 2^24 + 1-th draw. */
+#define ORACLE_MAX_DRAWS_PER_NODE_DAY (1u << 24)
 
 typedef struct {
     int kind;

@@ -1,0 +1,328 @@
+"""Thin ctypes binding of the C ABI in include/siminf_gpu.h.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``libsiminf_gpu.so``.  Device buffers are torch tensors (torch is
+used for device memory and streams).  There is no CPU fallback: if the
+library is missing, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INCLUDE = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_PKG, "_build")
+LIB_PATH = os.path.join(_BUILD, "libsiminf_gpu.so")
+
+SOURCES = ["sg_engine.cu", "sg_plan.cpp"]
+HEADERS = ["sg_common.h", "sg_device.cuh", "sg_plan.h"]
+ARCH = "-gencode=arch=compute_103a,code=sm_103a"
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", ARCH,
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-I" + _INCLUDE, "-I" + _CSRC]
+
+OK = 0
+ERR_NAMES = {0: "ok", -1: "invalid argument",
+             -2: "event moves more individuals than exist",
+             -3: "shift moves outside the compartments",
+             -4: "negative or non-finite transition rate",
+             -5: "post time step error", -6: "device wait timed out",
+             -7: "CUDA runtime error", -8: "out of memory",
+             -9: "more than 2^24 draws in one node-day"}
+
+
+class SimInfError(RuntimeError):
+    def __init__(self, code, err=None):
+        self.code = code
+        self.err = err or {}
+        super().__init__(f"siminf_gpu error {code}: {ERR_NAMES.get(code, '?')} {self.err}")
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library for sm_103a into ``_build/libsiminf_gpu.so``."""
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = ([os.path.join(_CSRC, s) for s in SOURCES + HEADERS]
+            + [os.path.join(_INCLUDE, "siminf_gpu.h")])
+    newest = max(os.path.getmtime(p) for p in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+    objs = []
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, "-c", os.path.join(_CSRC, src), "-o", obj] + NVCC_FLAGS
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + ".tmp%d" % os.getpid()
+    cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-Xcompiler", "-fPIC"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_nodes", ctypes.c_int32),
+                ("n_comp", ctypes.c_int32), ("n_trans", ctypes.c_int32),
+                ("S", ctypes.c_void_p), ("G", ctypes.c_void_p),
+                ("n_select", ctypes.c_int32), ("E", ctypes.c_void_p),
+                ("n_shift", ctypes.c_int32), ("N", ctypes.c_void_p),
+                ("n_v", ctypes.c_int32), ("n_ldata", ctypes.c_int32),
+                ("ldata", ctypes.c_void_p), ("n_gdata", ctypes.c_int32),
+                ("gdata", ctypes.c_void_p)]
+
+
+class Error(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_int32), ("rep", ctypes.c_int32),
+                ("node", ctypes.c_int32), ("day", ctypes.c_int32),
+                ("event", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("reactions", ctypes.c_int64), ("draws", ctypes.c_int64),
+                ("node_days", ctypes.c_int64),
+                ("events_applied", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64),
+                ("e2_waves", ctypes.c_int32), ("days", ctypes.c_int32),
+                ("ms_ssa", ctypes.c_double), ("ms_e1", ctypes.c_double),
+                ("ms_e2", ctypes.c_double), ("launches_ssa", ctypes.c_int64),
+                ("launches_e1", ctypes.c_int64), ("launches_e2", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
+           "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
+           "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe"]
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library {p} is missing: build it with "
+                "paper_1605_01421_gb300.binding.build() (there is no CPU fallback)")
+        L = ctypes.CDLL(p)
+        vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+        L.sg_model_create.argtypes = [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]
+        L.sg_model_create.restype = ctypes.c_int
+        L.sg_set_events.argtypes = [vp, i64] + [vp] * 9
+        L.sg_set_events.restype = ctypes.c_int
+        run_args = [vp, vp, i32, u64, i32, vp, vp, vp, vp, vp,
+                    ctypes.POINTER(Stats), ctypes.POINTER(Error)]
+        L.sg_run.argtypes = run_args
+        L.sg_run.restype = ctypes.c_int
+        L.sg_run_host.argtypes = run_args
+        L.sg_run_host.restype = ctypes.c_int
+        L.sg_model_destroy.argtypes = [vp]
+        L.sg_model_destroy.restype = None
+        L.sg_strerror.argtypes = [ctypes.c_int]
+        L.sg_strerror.restype = ctypes.c_char_p
+        L.sg_philox_batch.argtypes = [vp, u64, vp, i64, vp]
+        L.sg_philox_batch.restype = ctypes.c_int
+        L.sg_log_batch.argtypes = [vp, vp, i64, vp]
+        L.sg_log_batch.restype = ctypes.c_int
+        L.sg_u01_batch.argtypes = [vp, vp, i64, vp]
+        L.sg_u01_batch.restype = ctypes.c_int
+        L.sg_set_kernel_timing.argtypes = [vp, ctypes.c_int]
+        L.sg_set_kernel_timing.restype = ctypes.c_int
+        L.sg_fp64_fma_probe.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
+        L.sg_fp64_fma_probe.restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _colmajor(M):
+    return np.ascontiguousarray(np.asarray(M, dtype=np.int32).ravel(order="F"))
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
+
+
+def _dev_ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Model:
+    """A model handle (sg_model): tables of Sec. 3.2 plus scheduled events.
+
+    ``w`` is any object with the attributes of ``workloads.Workload``:
+    kind, S, G, E, N, gdata, ldata, n_v, u0 (for the node count) and events.
+    """
+
+    def __init__(self, w):
+        L = lib()
+        S, G = _colmajor(w.S), _colmajor(w.G)
+        E, N = _colmajor(w.E), _colmajor(w.N)
+        ldata = np.ascontiguousarray(np.asarray(w.ldata, np.float64).ravel(order="F"))
+        gdata = np.ascontiguousarray(w.gdata, dtype=np.float64)
+        n_nodes = int(np.asarray(w.u0).shape[-2])
+        self.n_nodes, self.n_comp, self.n_v = n_nodes, int(w.S.shape[0]), int(w.n_v)
+        d = _Desc(int(w.kind), n_nodes, int(w.S.shape[0]), int(w.S.shape[1]),
+                  _p(S), _p(G), int(w.E.shape[1]), _p(E), int(w.N.shape[1]), _p(N),
+                  int(w.n_v), int(np.asarray(w.ldata).shape[0]), _p(ldata),
+                  int(gdata.size), _p(gdata))
+        h = ctypes.c_void_p()
+        rc = L.sg_model_create(ctypes.byref(d), ctypes.byref(h))
+        if rc:
+            raise SimInfError(rc)
+        self._h = h
+        if getattr(w, "events", None) is not None:
+            self.set_events(w.events)
+
+    def set_events(self, ev):
+        L = lib()
+        n = len(ev["event"])
+        arrs = [_i32(ev[k]) for k in ("event", "time", "node", "dest", "n")]
+        prop = np.ascontiguousarray(ev["proportion"], dtype=np.float64)
+        sel, sh = _i32(ev["select"]), _i32(ev["shift"])
+        rep = _i32(ev["rep"]) if ev.get("rep") is not None else None
+        rc = L.sg_set_events(self._h, n, *[_p(a) for a in arrs], _p(prop), _p(sel),
+                             _p(sh), _p(rep) if rep is not None else None)
+        if rc:
+            raise SimInfError(rc)
+
+    def run(self, tspan, seed, n_rep, u0, v0, U, V, stream=None, check=True):
+        """Run on device tensors: u0 (R, Nn, C) int32, v0 (R, Nn, Nv) float64,
+        U (R, M, Nn, C) int32, V (R, M, Nn, Nv) float64, all on the GPU."""
+        L = lib()
+        ts = _i32(tspan)
+        st, er = Stats(), Error()
+        rc = L.sg_run(self._h, _p(ts), int(ts.size), int(seed), int(n_rep),
+                      _dev_ptr(u0), _dev_ptr(v0), _dev_ptr(U), _dev_ptr(V),
+                      _stream_handle(stream), ctypes.byref(st), ctypes.byref(er))
+        if rc and check:
+            raise SimInfError(rc, er.as_dict())
+        return rc, st.as_dict(), er.as_dict()
+
+    def run_host(self, tspan, seed, n_rep, u0, v0, U, V, stream=None, check=True):
+        """Run on host numpy arrays (pinned memory for full copy speed)."""
+        L = lib()
+        ts = _i32(tspan)
+        st, er = Stats(), Error()
+        rc = L.sg_run_host(self._h, _p(ts), int(ts.size), int(seed), int(n_rep),
+                           _p(u0), _p(v0), _p(U), _p(V), _stream_handle(stream),
+                           ctypes.byref(st), ctypes.byref(er))
+        if rc and check:
+            raise SimInfError(rc, er.as_dict())
+        return rc, st.as_dict(), er.as_dict()
+
+    def set_kernel_timing(self, enable=True):
+        rc = lib().sg_set_kernel_timing(self._h, 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sg_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def simulate(w, device="cuda", seed=None, n_rep=None, stream=None):
+    """Convenience: run a workload on the GPU and return numpy (U, V, stats)."""
+    import torch
+    n_rep = w.n_rep if n_rep is None else n_rep
+    seed = w.seed if seed is None else seed
+    m = Model(w)
+    try:
+        u0 = torch.as_tensor(np.ascontiguousarray(w.u0[:n_rep]), device=device)
+        v0 = torch.as_tensor(np.ascontiguousarray(w.v0[:n_rep]), device=device)
+        M = len(w.tspan)
+        U = torch.empty((n_rep, M, m.n_nodes, m.n_comp), dtype=torch.int32, device=device)
+        V = torch.empty((n_rep, M, m.n_nodes, m.n_v), dtype=torch.float64, device=device)
+        rc, st, er = m.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
+        return U.cpu().numpy(), V.cpu().numpy(), st
+    finally:
+        m.close()
+
+
+def fp64_fma_probe(iters=20000, stream=None):
+    """Measured FP64 fused multiply-add throughput of this GPU, TFLOP/s."""
+    out = ctypes.c_double()
+    rc = lib().sg_fp64_fma_probe(int(iters), ctypes.byref(out), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return out.value
+
+
+def philox_batch(ctr, key, stream=None):
+    import torch
+    c = torch.as_tensor(np.ascontiguousarray(ctr, dtype=np.uint32).view(np.int32),
+                        device="cuda")
+    out = torch.empty_like(c)
+    rc = lib().sg_philox_batch(_dev_ptr(c), int(key), _dev_ptr(out), c.numel() // 4,
+                               _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return out.cpu().numpy().view(np.uint32)
+
+
+def log_batch(x, stream=None):
+    import torch
+    t = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+    y = torch.empty_like(t)
+    rc = lib().sg_log_batch(_dev_ptr(t), _dev_ptr(y), t.numel(), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return y.cpu().numpy()
+
+
+def u01_batch(words, stream=None):
+    import torch
+    w = torch.as_tensor(np.ascontiguousarray(words, dtype=np.uint32).view(np.int32),
+                        device="cuda")
+    y = torch.empty(w.numel() // 2, dtype=torch.float64, device="cuda")
+    rc = lib().sg_u01_batch(_dev_ptr(w), _dev_ptr(y), y.numel(), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return y.cpu().numpy()

@@ -1,0 +1,238 @@
+// sg_device.cuh -- device primitives of the SimInf GB300 engine: the
+// counter-based random stream, the open-interval uniform, the logarithm, the
+// bounded integers, the transition-rate functions and the post time step.
+//
+// Every double expression is written in a fixed evaluation order and the
+// library is compiled with -fmad=false, so no multiply-add is contracted:
+// the results are the correctly rounded IEEE results of each written
+// operation, in that order.
+#pragma once
+
+#include <stdint.h>
+
+#include "sg_common.h"
+
+namespace sg {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
+// easy as 1, 2, 3", SC'11): ten rounds of two 32x32 -> 64-bit products whose
+// halves are xor-ed with the other counter words and the round key; the key
+// is advanced by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform on (0, 1) from 52 random bits: k = (hi << 20) | (lo >> 12),
+// r = (k + 1/2) 2^-52.  Exact; the range is [2^-53, 1 - 2^-53].
+__device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
+  const unsigned long long k =
+      ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  return ((double)k + 0.5) * 0x1.0p-52;
+}
+
+// ---------------------------------------------------------------------------
+// Natural logarithm from the argument reduction x = 2^k m, m in
+// (sqrt(2)/2, sqrt(2)], and log(m) = 2 atanh(s), s = f / (2 + f), f = m - 1,
+// evaluated as f - (h - s (h + R(s^2))) with h = f^2 / 2 and the atanh
+// Taylor polynomial R(z) = sum_{j=1}^{10} 2 z^j / (2 j + 1) in Horner form;
+// k ln 2 is added through a split ln 2 = L_hi + L_lo whose high part has 33
+// significant bits (k L_hi exact).  Accuracy: within 1 ulp of the correctly
+// rounded logarithm.  Only positive finite arguments reach it here.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double log_pos(double x) {
+  long long bits = __double_as_longlong(x);
+  int k = 0;
+  if (bits < 0x0010000000000000LL) {  // subnormal: scale by 2^54
+    x = x * 0x1.0p54;
+    bits = __double_as_longlong(x);
+    k = -54;
+  }
+  k += (int)(bits >> 52) - 1023;
+  double m = __longlong_as_double((bits & 0x000fffffffffffffLL) |
+                                  0x3ff0000000000000LL);
+  if (m > 0x1.6a09e667f3bcdp+0) {  // sqrt(2) rounded to nearest
+    m = m * 0.5;
+    k = k + 1;
+  }
+  const double f = m - 1.0;
+  const double h = (0.5 * f) * f;
+  const double s = f / (2.0 + f);
+  const double z = s * s;
+  const double R =
+      z * (0x1.5555555555555p-1 +
+      z * (0x1.999999999999ap-2 +
+      z * (0x1.2492492492492p-2 +
+      z * (0x1.c71c71c71c71cp-3 +
+      z * (0x1.745d1745d1746p-3 +
+      z * (0x1.3b13b13b13b14p-3 +
+      z * (0x1.1111111111111p-3 +
+      z * (0x1.e1e1e1e1e1e1ep-4 +
+      z * (0x1.af286bca1af28p-4 +
+      z * 0x1.8618618618618p-4)))))))));
+  const double dk = (double)k;
+  return dk * 0x1.62e42fefp-1 + (f - (h - (s * (h + R) + dk * 0x1.473de6af278edp-34)));
+}
+
+// ---------------------------------------------------------------------------
+// Event word stream: Philox counter (c, index_lo, index_hi,
+// (SG_STREAM_EVENTS << 24) | rep), four words per call, consumed in order.
+// ---------------------------------------------------------------------------
+struct WordStream {
+  uint32_t k0, k1, idx_lo, idx_hi, tag, c;
+  U4 buf;
+  int pos;
+  __device__ __forceinline__ void init(uint64_t seed, long long index, int rep) {
+    k0 = (uint32_t)seed;
+    k1 = (uint32_t)(seed >> 32);
+    idx_lo = (uint32_t)(unsigned long long)index;
+    idx_hi = (uint32_t)((unsigned long long)index >> 32);
+    tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
+    c = 0;
+    pos = 4;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    if (pos == 4) {
+      buf = philox10(U4{c, idx_lo, idx_hi, tag}, k0, k1);
+      ++c;
+      pos = 0;
+    }
+    const uint32_t r = pos == 0 ? buf.x : pos == 1 ? buf.y : pos == 2 ? buf.z : buf.w;
+    ++pos;
+    return r;
+  }
+  // Uniform integer on [0, s), s >= 1: Lemire's multiply-shift with
+  // rejection of the low product words below 2^32 mod s (unbiased).
+  __device__ __forceinline__ uint32_t below(uint32_t s) {
+    unsigned long long m = (unsigned long long)next() * s;
+    uint32_t lo = (uint32_t)m;
+    if (lo < s) {
+      const uint32_t thr = (0u - s) % s;
+      while (lo < thr) {
+        m = (unsigned long long)next() * s;
+        lo = (uint32_t)m;
+      }
+    }
+    return (uint32_t)(m >> 32);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Transition-rate functions (TRFun, Sec. 3.4.1), one set per kind.
+// ---------------------------------------------------------------------------
+template <int KIND> struct ModelTraits;
+
+// SIR, Eq. (SIR); operation order of the SIR rate listing (Appendix C).
+template <> struct ModelTraits<SG_SIR> {
+  static constexpr int C = 3, T = 2, NV = 0;
+  __device__ static __forceinline__ double rate(int j, const int *u, const double *,
+                                                const double *g) {
+    if (j == 0) {
+      const double Sn = (double)u[0], In = (double)u[1];
+      const double n = Sn + In + (double)u[2];
+      return n > 0.0 ? (g[0] * Sn * In) / n : 0.0;
+    }
+    return g[1] * (double)u[1];
+  }
+};
+
+// SIS of Sec. 2.1: [beta S I, gamma I].
+template <> struct ModelTraits<SG_SIS> {
+  static constexpr int C = 2, T = 2, NV = 0;
+  __device__ static __forceinline__ double rate(int j, const int *u, const double *,
+                                                const double *g) {
+    return j == 0 ? g[0] * (double)u[0] * (double)u[1] : g[1] * (double)u[1];
+  }
+};
+
+// SISe (Sec. 4.2, no coupling): [upsilon phi S, gamma I].
+template <> struct ModelTraits<SG_SISE> {
+  static constexpr int C = 2, T = 2, NV = 1;
+  __device__ static __forceinline__ double rate(int j, const int *u, const double *v,
+                                                const double *g) {
+    return j == 0 ? g[0] * v[0] * (double)u[0] : g[1] * (double)u[1];
+  }
+};
+
+// SISe3: transition 2a is S_a -> I_a at upsilon_a phi S_a, 2a + 1 is
+// I_a -> S_a at gamma_a I_a.
+template <> struct ModelTraits<SG_SISE3> {
+  static constexpr int C = 6, T = 6, NV = 1;
+  __device__ static __forceinline__ double rate(int j, const int *u, const double *v,
+                                                const double *g) {
+    const int a = j >> 1;
+    return (j & 1) == 0 ? g[a] * v[0] * (double)u[2 * a] : g[3 + a] * (double)u[2 * a + 1];
+  }
+};
+
+__device__ __forceinline__ bool bad_rate(double w) { return !(w >= 0.0) || isinf(w); }
+
+// beta(t) of Sec. 4.2: season of day-of-year ((t - 1) mod 365) + 1 against
+// the node's season ends.
+__device__ __forceinline__ double season_decay(int t, const double *ld, const double *b4) {
+  int d = (t - 1) % 365;
+  if (d < 0) d += 365;
+  const double doy = (double)(d + 1);
+  return doy <= ld[0] ? b4[0] : doy <= ld[1] ? b4[1] : doy <= ld[2] ? b4[2] : b4[3];
+}
+
+// Post time step (PTSFun; Eq. numstep3 as one Euler step of length 1) for
+// the SISe kinds: phi_new = phi + (alpha I / N - beta(t) phi), shedding 0 in
+// an empty node.  Returns 1 if phi changed, 0 if not, SG_ERR_PTS if the new
+// value is not finite.
+template <int KIND>
+__device__ __forceinline__ int post_step(double *v, const int *u, const double *ld,
+                                         const double *g, int t) {
+  double I_tot, N_tot;
+  const double *pg;
+  if (KIND == SG_SISE) {
+    I_tot = (double)u[1];
+    N_tot = (double)u[0] + (double)u[1];
+    pg = g + 2;
+  } else if (KIND == SG_SISE3) {
+    I_tot = 0.0;
+    N_tot = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      I_tot = I_tot + (double)u[2 * a + 1];
+      N_tot = N_tot + (double)u[2 * a] + (double)u[2 * a + 1];
+    }
+    pg = g + 6;
+  } else {
+    return 0;
+  }
+  const double phi = v[0];
+  const double shed = N_tot > 0.0 ? (pg[0] * I_tot) / N_tot : 0.0;
+  const double beta = season_decay(t, ld, pg + 1);
+  const double nv = phi + (shed - beta * phi);
+  v[0] = nv;
+  if (!isfinite(nv)) return SG_ERR_PTS;
+  return nv != phi ? 1 : 0;
+}
+
+__device__ __forceinline__ void report(SgDevError *err, int code, int rep, int node,
+                                       int day, long long event) {
+  if (atomicCAS(&err->code, 0, code) == 0) {
+    err->rep = rep;
+    err->node = node;
+    err->day = day;
+    err->event = event;
+  }
+}
+
+}  // namespace sg

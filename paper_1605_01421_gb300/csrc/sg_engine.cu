@@ -1,0 +1,939 @@
+// sg_engine.cu -- kernels and C ABI of the SimInf GB300 engine.
+//
+// The split-step method of Sec. 2.3 runs as a chain of kernels on the
+// caller's stream:
+//   k_days<KIND>   one thread per (replicate, node): finishes the previous
+//                  unit step (post time step + recording), then runs the
+//                  direct SSA toward the next unit time point (Appendix A),
+//                  for a whole run of days that carry no scheduled events;
+//   k_events_e1    the exit / enter / internal-transfer events of a day, one
+//                  thread per (replicate, node) that has any, in the order of
+//                  Sec. 3.3;
+//   k_events_e2    the external transfers of a day, one block per replicate,
+//                  wave by wave (a block barrier between waves);
+// and a last k_days launch finishes the final unit step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sg_common.h"
+#include "sg_device.cuh"
+#include "sg_plan.h"
+
+using namespace sg;
+
+namespace {
+
+constexpr int kDayBlock = 128;
+constexpr int kE1Block = 128;
+constexpr int kE2Block = 256;
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+struct DayArgs {
+  int *u;              // [R][Nn][C] working counts
+  double *v;           // [R][Nn][NV] working continuous state
+  const double *ldata; // [Nn][n_ldata]
+  int32_t *U;          // [R][M][Nn][C]
+  double *V;           // [R][M][Nn][NV]
+  const int32_t *rec;  // [days + 1]: tspan slot of T = t0 + i, or -1
+  int32_t t0, M, n_rep;
+  int32_t T_begin, T_end;  // SSA toward T = T_begin .. T_end - 1
+  int32_t finish_first;    // finish unit step T_begin - 1 before the SSA
+  int32_t finish_last;     // finish unit step T_end - 1 after the SSA
+  uint32_t k0, k1;         // Philox key (seed)
+  SgDevError *err;
+  SgCounters *cnt;
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(kDayBlock)
+k_days(const SgTables tb, const DayArgs a) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NV = M::NV;
+  const int Nn = tb.n_nodes;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)Nn * a.n_rep;
+  unsigned long long fired = 0, drawn = 0;
+  if (gid < total && *(volatile int32_t *)&a.err->code == 0) {
+    const int rep = (int)(gid / Nn);
+    const int node = (int)(gid - (long long)rep * Nn);
+    int u[C];
+    double v[NV > 0 ? NV : 1];
+    double ld[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+    if (NV > 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) ld[i] = a.ldata[(long long)node * tb.n_ldata + i];
+    }
+    const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
+    int code = 0, bad_day = 0;
+
+    // finish unit step Tf: post time step on the state after its events,
+    // then record if Tf is a tspan point
+    auto finish = [&](int Tf) {
+      if (NV > 0) {
+        const int r = post_step<KIND>(v, u, ld, tb.gdata, Tf);
+        if (r < 0 && code == 0) { code = r; bad_day = Tf; }
+      }
+      const int m = a.rec[Tf - a.t0];
+      if (m >= 0) {
+        const long long base = ((long long)rep * a.M + m) * Nn + node;
+#pragma unroll
+        for (int p = 0; p < C; ++p) a.U[base * C + p] = u[p];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) a.V[base * NV + q] = v[q];
+      }
+    };
+
+    if (a.finish_first) finish(a.T_begin - 1);
+    for (int Td = a.T_begin; Td < a.T_end && code == 0; ++Td) {
+      // rates at the start of the day (Appendix A step "compute transition
+      // rates"); recomputed every day so events and the post time step are
+      // always seen
+      double w[T];
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        w[j] = M::rate(j, u, v, tb.gdata);
+        if (bad_rate(w[j])) code = SG_ERR_RATE;
+      }
+      if (code) { bad_day = Td; break; }
+      double t = (double)(Td - 1);
+      const double Tn = (double)Td;
+      uint32_t c = 0;
+      for (;;) {
+        double lam = 0.0;
+#pragma unroll
+        for (int j = 0; j < T; ++j) lam = lam + w[j];
+        if (!(lam > 0.0)) break;  // nothing can fire: jump to Td
+        if (c >= SG_MAX_DRAWS) {  // bound on run time, see SG_ERR_STEP_LIMIT
+          code = SG_ERR_STEP_LIMIT;
+          bad_day = Td;
+          break;
+        }
+        const U4 x = philox10(U4{c, (uint32_t)node, (uint32_t)Td, tag}, a.k0, a.k1);
+        ++c;
+        const double r1 = u01_open(x.x, x.y);
+        const double r2 = u01_open(x.z, x.w);
+        const double tau = -log_pos(r1) / lam;
+        if (t + tau >= Tn) break;
+        t = t + tau;
+        // inversion over the positive rates in index order
+        const double target = lam * r2;
+        double cum = 0.0;
+        int n = -1, last = -1;
+#pragma unroll
+        for (int j = 0; j < T; ++j) {
+          if (n < 0 && w[j] > 0.0) {
+            cum = cum + w[j];
+            last = j;
+            if (target <= cum) n = j;
+          }
+        }
+        if (n < 0) n = last;
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] += tb.S[n][p];
+        const uint32_t dep = tb.dep[n];
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          if ((dep >> k) & 1u) {
+            w[k] = M::rate(k, u, v, tb.gdata);
+            if (bad_rate(w[k])) code = SG_ERR_RATE;
+          }
+        }
+        ++fired;
+        if (code) { bad_day = Td; break; }
+      }
+      drawn += c;
+      if (code) break;
+      if (Td + 1 < a.T_end || a.finish_last) finish(Td);
+      if (code) break;
+    }
+    if (code) report(a.err, code, rep, node, bad_day, -1);
+#pragma unroll
+    for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.v[gid * NV + q] = v[q];
+  }
+  // one atomic per warp for the reaction and draw counts
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fired += __shfl_down_sync(0xffffffffu, fired, off);
+    drawn += __shfl_down_sync(0xffffffffu, drawn, off);
+  }
+  if ((threadIdx.x & 31) == 0 && drawn) {
+    atomicAdd(&a.cnt->reactions, fired);
+    atomicAdd(&a.cnt->draws, drawn);
+  }
+}
+
+struct EvArgs {
+  SgEventsDev ev;
+  int *u;
+  int32_t n_rep;
+  uint32_t k0, k1;
+  int32_t day;  // unit time point T the events run at
+  SgDevError *err;
+  SgCounters *cnt;
+};
+
+// Apply event j for replicate rep.  `atomic_dest` selects atomic additions
+// into the destination (several external transfers of one wave may share a
+// destination).  Returns 0 or an error code.
+__device__ int apply_event(const SgTables &tb, const EvArgs &a, long long j, int rep,
+                           bool atomic_dest) {
+  const int C = tb.n_comp;
+  const int type = a.ev.type[j];
+  const uint32_t mask = tb.Emask[a.ev.select[j]];
+  int *un = a.u + ((long long)rep * tb.n_nodes + a.ev.node[j]) * C;
+  if (type == SG_ENTER) {
+    un[__ffs(mask) - 1] += a.ev.n[j];  // first selected compartment
+    return 0;
+  }
+  long long total = 0;
+  for (int p = 0; p < C; ++p)
+    if ((mask >> p) & 1u) total += un[p];
+  const long long k = a.ev.n[j] > 0 ? (long long)a.ev.n[j]
+                                    : (long long)round(a.ev.proportion[j] * (double)total);
+  if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
+  int moved[SG_MAX_COMP];
+  for (int p = 0; p < C; ++p) moved[p] = 0;
+  if (k > 0) {
+    // urn: one uniform position among the remaining individuals per draw,
+    // resolved in compartment order
+    WordStream ws;
+    ws.init(((uint64_t)a.k1 << 32) | a.k0, a.ev.index[j], rep);
+    for (long long i = 0; i < k; ++i) {
+      uint32_t x = ws.below((uint32_t)(total - i));
+      for (int p = 0; p < C; ++p) {
+        if (!((mask >> p) & 1u)) continue;
+        const uint32_t rem = (uint32_t)(un[p] - moved[p]);
+        if (x < rem) {
+          ++moved[p];
+          break;
+        }
+        x -= rem;
+      }
+    }
+  }
+  for (int p = 0; p < C; ++p) un[p] -= moved[p];
+  if (type == SG_EXIT) return 0;
+  const int q = a.ev.shift[j];
+  int *ut = type == SG_INTERNAL_TRANSFER
+                ? un
+                : a.u + ((long long)rep * tb.n_nodes + a.ev.dest[j]) * C;
+  for (int p = 0; p < C; ++p) {
+    if (moved[p] == 0) continue;
+    const int to = q >= 0 ? p + tb.Nsh[q][p] : p;
+    if (atomic_dest && type == SG_EXTERNAL_TRANSFER)
+      atomicAdd(ut + to, moved[p]);
+    else
+      ut[to] += moved[p];
+  }
+  return 0;
+}
+
+// E1 events of one day: positions [begin, begin + count) of the planned
+// order, sorted by (slot, node, time, type, index).  Thread (r, i) handles
+// position i for replicate r (r only varies when every replicate runs the
+// same events) if i starts a node's run, and then walks that run.
+__global__ void __launch_bounds__(kE1Block)
+k_events_e1(const SgTables tb, const EvArgs a, long long begin, long long count,
+            int rep_threads) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= count * rep_threads) return;
+  if (*(volatile int32_t *)&a.err->code != 0) return;
+  const int rthread = (int)(gid / count);
+  const long long i = begin + (gid - (long long)rthread * count);
+  const int node = a.ev.node[i];
+  const int erep = a.ev.rep[i];
+  if (i > begin && a.ev.node[i - 1] == node && a.ev.rep[i - 1] == erep) return;
+  const int rep = erep >= 0 ? erep : rthread;
+  const long long end = begin + count;
+  unsigned long long applied = 0;
+  for (long long j = i; j < end && a.ev.node[j] == node && a.ev.rep[j] == erep; ++j) {
+    const int rc = apply_event(tb, a, j, rep, false);
+    if (rc) {
+      report(a.err, rc, rep, node, a.day, a.ev.index[j]);
+      break;
+    }
+    ++applied;
+  }
+  atomicAdd(&a.cnt->events, applied);
+}
+
+// E2 events of one day: block r runs replicate r's waves in order.
+__global__ void __launch_bounds__(kE2Block)
+k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_ev,
+            long long w_begin_shared, long long w_end_shared,
+            const int64_t *__restrict__ wave_off, int day_index, int slots) {
+  const int rep = blockIdx.x;
+  long long w0 = w_begin_shared, w1 = w_end_shared;
+  if (slots > 1) {
+    w0 = wave_off[(long long)day_index * slots + rep];
+    w1 = wave_off[(long long)day_index * slots + rep + 1];
+  }
+  unsigned long long applied = 0;
+  for (long long w = w0; w < w1; ++w) {
+    const long long e0 = wave_ev[w], e1 = wave_ev[w + 1];
+    for (long long j = e0 + threadIdx.x; j < e1; j += blockDim.x) {
+      if (*(volatile int32_t *)&a.err->code != 0) break;
+      const int rc = apply_event(tb, a, j, rep, true);
+      if (rc)
+        report(a.err, rc, rep, a.ev.node[j], a.day, a.ev.index[j]);
+      else
+        ++applied;
+    }
+    __syncthreads();
+  }
+  if (applied) atomicAdd(&a.cnt->events, applied);
+}
+
+// U[r][0] = u0[r], V[r][0] = v0[r], working state = initial state.
+__global__ void k_init(const int32_t *__restrict__ u0, const double *__restrict__ v0, int *u,
+                       double *v, int32_t *U, double *V, long long per_rep_u,
+                       long long per_rep_v, int M, int n_rep) {
+  const long long nu = per_rep_u * n_rep, nv = per_rep_v * n_rep;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nu + nv;
+       i += (long long)gridDim.x * blockDim.x) {
+    if (i < nu) {
+      const long long r = i / per_rep_u, k = i - r * per_rep_u;
+      const int32_t x = u0[i];
+      u[i] = x;
+      U[r * M * per_rep_u + k] = x;
+    } else {
+      const long long ii = i - nu;
+      const long long r = ii / per_rep_v, k = ii - r * per_rep_v;
+      const double x = v0[ii];
+      v[ii] = x;
+      V[r * M * per_rep_v + k] = x;
+    }
+  }
+}
+
+__global__ void k_philox_batch(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
+                               long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const U4 c = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+    const U4 r = philox10(c, k0, k1);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+  }
+}
+
+__global__ void k_log_batch(const double *x, double *y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double a = x[i];
+    double r;
+    if (!(a > 0.0)) r = a == 0.0 ? -INFINITY : NAN;
+    else if (isinf(a)) r = a;
+    else r = log_pos(a);
+    y[i] = r;
+  }
+}
+
+__global__ void k_u01_batch(const uint32_t *w, double *y, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] = u01_open(w[2 * i], w[2 * i + 1]);
+}
+
+// Independent fused multiply-add chains (8 per thread) for the FP64
+// throughput probe; the result is stored so the chains are not removed.
+__global__ void k_fp64_fma(double *out, int iters) {
+  double a0 = threadIdx.x * 1e-9, a1 = a0 + 1e-9, a2 = a0 + 2e-9, a3 = a0 + 3e-9;
+  double a4 = a0 + 4e-9, a5 = a0 + 5e-9, a6 = a0 + 6e-9, a7 = a0 + 7e-9;
+  const double m = 0.999999, c = 1e-7;
+  for (int i = 0; i < iters; ++i) {
+    a0 = __fma_rn(a0, m, c); a1 = __fma_rn(a1, m, c);
+    a2 = __fma_rn(a2, m, c); a3 = __fma_rn(a3, m, c);
+    a4 = __fma_rn(a4, m, c); a5 = __fma_rn(a5, m, c);
+    a6 = __fma_rn(a6, m, c); a7 = __fma_rn(a7, m, c);
+  }
+  out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+// ---------------------------------------------------------------------------
+// Host runtime
+// ---------------------------------------------------------------------------
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  int ensure(size_t want) {
+    if (want <= n && p) return SG_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    if (want == 0) want = 1;
+    if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      return SG_ERR_NOMEM;
+    }
+    n = want;
+    return SG_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+template <typename T>
+int upload(DevBuf<T> &b, const std::vector<T> &h) {
+  int rc = b.ensure(h.size());
+  if (rc) return rc;
+  if (!h.empty() &&
+      cudaMemcpy(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+}  // namespace
+
+struct sg_model {
+  SgTables tb;
+  DevBuf<double> ldata;
+  EventTable ev;
+  // planned events for the cached window
+  bool plan_ok = false;
+  Plan plan;
+  DevBuf<int8_t> e_type, e_shift;
+  DevBuf<uint8_t> e_select;
+  DevBuf<int32_t> e_node, e_dest, e_n, e_rep;
+  DevBuf<double> e_prop;
+  DevBuf<int64_t> e_index, wave_ev, wave_off;
+  // working memory
+  DevBuf<int> u;
+  DevBuf<double> v;
+  DevBuf<int32_t> rec;
+  DevBuf<SgDevError> err;
+  DevBuf<SgCounters> cnt;
+  SgDevError *h_err = nullptr;
+  SgCounters *h_cnt = nullptr;
+  // per-kernel timing (sg_set_kernel_timing)
+  bool timing = false;
+  std::vector<cudaEvent_t> evpool;
+  std::vector<int> ev_kind;  // per launch: 0 SSA, 1 E1, 2 E2
+  size_t ev_used = 0;
+  // buffers of sg_run_host
+  DevBuf<int32_t> hu0, hU;
+  DevBuf<double> hv0, hV;
+};
+
+extern "C" const char *sg_strerror(int code) {
+  switch (code) {
+    case SG_OK: return "ok";
+    case SG_ERR_ARG: return "invalid argument";
+    case SG_ERR_EVENT_UNDERFLOW: return "event moves more individuals than exist";
+    case SG_ERR_SHIFT_RANGE: return "shift moves outside the compartments";
+    case SG_ERR_RATE: return "negative or non-finite transition rate";
+    case SG_ERR_PTS: return "post time step error";
+    case SG_ERR_TIMEOUT: return "device wait timed out";
+    case SG_ERR_CUDA: return "CUDA runtime error";
+    case SG_ERR_NOMEM: return "out of memory";
+    case SG_ERR_STEP_LIMIT: return "more than SG_MAX_DRAWS draws in one node-day";
+    default: return "unknown error";
+  }
+}
+
+static const int kKindComp[4] = {3, 2, 2, 6};
+static const int kKindTrans[4] = {2, 2, 2, 6};
+static const int kKindNv[4] = {0, 0, 1, 1};
+static const int kKindGdata[4] = {2, 2, 7, 11};
+static const int kKindLdata[4] = {0, 0, 4, 4};
+
+extern "C" int sg_model_create(const sg_desc *d, sg_model **out) {
+  if (!d || !out) return SG_ERR_ARG;
+  *out = nullptr;
+  const int k = d->kind;
+  if (k < SG_SIR || k > SG_SISE3) return SG_ERR_ARG;
+  if (d->n_nodes < 0 || d->n_comp != kKindComp[k] || d->n_trans != kKindTrans[k] ||
+      d->n_v != kKindNv[k] || d->n_gdata < kKindGdata[k] || d->n_gdata > SG_MAX_GDATA ||
+      d->n_ldata < kKindLdata[k] || d->n_select < 0 || d->n_select > SG_MAX_SELECT ||
+      d->n_shift < 0 || d->n_shift > SG_MAX_SHIFT || !d->S || !d->G ||
+      (d->n_select > 0 && !d->E) || (d->n_shift > 0 && !d->N) ||
+      (d->n_gdata > 0 && !d->gdata) ||
+      (d->n_ldata > 0 && d->n_nodes > 0 && !d->ldata))
+    return SG_ERR_ARG;
+  sg_model *m = new (std::nothrow) sg_model();
+  if (!m) return SG_ERR_NOMEM;
+  SgTables &tb = m->tb;
+  std::memset(&tb, 0, sizeof tb);
+  tb.kind = k;
+  tb.n_nodes = d->n_nodes;
+  tb.n_comp = d->n_comp;
+  tb.n_trans = d->n_trans;
+  tb.n_v = d->n_v;
+  tb.n_ldata = d->n_ldata;
+  tb.n_select = d->n_select;
+  tb.n_shift = d->n_shift;
+  const int C = d->n_comp, T = d->n_trans;
+  for (int j = 0; j < T; ++j) {
+    for (int p = 0; p < C; ++p) {
+      const int s = d->S[(size_t)j * C + p];
+      if (s < -127 || s > 127) { delete m; return SG_ERR_ARG; }
+      tb.S[j][p] = (int8_t)s;
+    }
+    uint32_t dep = 0;
+    for (int kk = 0; kk < T; ++kk)
+      if (d->G[(size_t)j * T + kk] != 0) dep |= 1u << kk;
+    tb.dep[j] = dep;
+  }
+  for (int s = 0; s < d->n_select; ++s) {
+    uint32_t mask = 0;
+    for (int p = 0; p < C; ++p)
+      if (d->E[(size_t)s * C + p] != 0) mask |= 1u << p;
+    tb.Emask[s] = mask;
+  }
+  for (int q = 0; q < d->n_shift; ++q)
+    for (int p = 0; p < C; ++p) {
+      const int x = d->N[(size_t)q * C + p];
+      if (x < -127 || x > 127) { delete m; return SG_ERR_ARG; }
+      tb.Nsh[q][p] = (int8_t)x;
+    }
+  for (int i = 0; i < d->n_gdata; ++i) tb.gdata[i] = d->gdata[i];
+  const size_t nl = (size_t)d->n_ldata * d->n_nodes;
+  std::vector<double> ld(d->ldata ? d->ldata : nullptr, d->ldata ? d->ldata + nl : nullptr);
+  int rc = upload(m->ldata, ld);
+  if (!rc) rc = m->err.ensure(1);
+  if (!rc) rc = m->cnt.ensure(1);
+  if (!rc && cudaMallocHost(&m->h_err, sizeof(SgDevError)) != cudaSuccess) rc = SG_ERR_NOMEM;
+  if (!rc && cudaMallocHost(&m->h_cnt, sizeof(SgCounters)) != cudaSuccess) rc = SG_ERR_NOMEM;
+  if (rc) {
+    cudaGetLastError();
+    sg_model_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return SG_OK;
+}
+
+extern "C" void sg_model_destroy(sg_model *m) {
+  if (!m) return;
+  m->ldata.release();
+  m->e_type.release(); m->e_shift.release(); m->e_select.release();
+  m->e_node.release(); m->e_dest.release(); m->e_n.release(); m->e_rep.release();
+  m->e_prop.release(); m->e_index.release(); m->wave_ev.release(); m->wave_off.release();
+  m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
+  m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
+  if (m->h_err) cudaFreeHost(m->h_err);
+  if (m->h_cnt) cudaFreeHost(m->h_cnt);
+  for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
+  delete m;
+}
+
+extern "C" int sg_set_events(sg_model *m, int64_t n_events, const int32_t *event,
+                             const int32_t *time, const int32_t *node, const int32_t *dest,
+                             const int32_t *n, const double *proportion,
+                             const int32_t *select, const int32_t *shift,
+                             const int32_t *rep) {
+  if (!m || n_events < 0) return SG_ERR_ARG;
+  if (n_events > 0 && (!event || !time || !node || !dest || !n || !proportion || !select ||
+                       !shift))
+    return SG_ERR_ARG;
+  EventTable ev;
+  try {
+    ev.type.assign(event, event + n_events);
+    ev.time.assign(time, time + n_events);
+    ev.node.assign(node, node + n_events);
+    ev.dest.assign(dest, dest + n_events);
+    ev.n.assign(n, n + n_events);
+    ev.proportion.assign(proportion, proportion + n_events);
+    ev.select.assign(select, select + n_events);
+    ev.shift.assign(shift, shift + n_events);
+    if (rep) {
+      ev.rep.assign(rep, rep + n_events);
+      ev.per_rep = true;
+      for (int64_t e = 0; e < n_events; ++e) ev.max_rep = std::max(ev.max_rep, rep[e]);
+    }
+  } catch (const std::bad_alloc &) {
+    return SG_ERR_NOMEM;
+  }
+  int64_t bad = -1;
+  const int rc = validate_events(m->tb, ev, &bad);
+  if (rc) return rc;
+  m->ev = std::move(ev);
+  m->plan_ok = false;
+  return SG_OK;
+}
+
+// Build (or reuse) the device schedule of the events for a window.
+static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
+  if (m->plan_ok && m->plan.t0 == t0 && m->plan.t_end == t_end && m->plan.slots == slots)
+    return SG_OK;
+  m->plan_ok = false;
+  Plan &P = m->plan;
+  int rc = build_plan(m->ev, m->tb.n_nodes, t0, t_end, slots, &P);
+  if (rc) return rc;
+  const size_t n = P.order.size();
+  std::vector<int8_t> type(n), shift(n);
+  std::vector<uint8_t> sel(n);
+  std::vector<int32_t> nd(n), ds(n), cnt(n), rp(n);
+  std::vector<double> prop(n);
+  std::vector<int64_t> idx(n);
+  const EventTable &ev = m->ev;
+  for (size_t i = 0; i < n; ++i) {
+    const int64_t e = P.order[i];
+    type[i] = (int8_t)ev.type[e];
+    shift[i] = (int8_t)(ev.shift[e] < 0 ? -1 : ev.shift[e]);
+    sel[i] = (uint8_t)ev.select[e];
+    nd[i] = ev.node[e];
+    ds[i] = ev.dest[e];
+    cnt[i] = ev.n[e];
+    rp[i] = ev.per_rep ? ev.rep[e] : -1;
+    prop[i] = ev.proportion[e];
+    idx[i] = e;
+  }
+  if ((rc = upload(m->e_type, type)) || (rc = upload(m->e_shift, shift)) ||
+      (rc = upload(m->e_select, sel)) || (rc = upload(m->e_node, nd)) ||
+      (rc = upload(m->e_dest, ds)) || (rc = upload(m->e_n, cnt)) ||
+      (rc = upload(m->e_rep, rp)) || (rc = upload(m->e_prop, prop)) ||
+      (rc = upload(m->e_index, idx)) || (rc = upload(m->wave_ev, P.wave_ev)) ||
+      (rc = upload(m->wave_off, P.e2_wave_off)))
+    return rc;
+  m->plan_ok = true;
+  return SG_OK;
+}
+
+template <int KIND>
+static void launch_days(sg_model *m, const DayArgs &a, cudaStream_t st) {
+  const long long threads = (long long)m->tb.n_nodes * a.n_rep;
+  const unsigned grid = (unsigned)std::max<long long>(1, (threads + kDayBlock - 1) / kDayBlock);
+  k_days<KIND><<<grid, kDayBlock, 0, st>>>(m->tb, a);
+}
+
+static void launch_days_kind(sg_model *m, const DayArgs &a, cudaStream_t st) {
+  switch (m->tb.kind) {
+    case SG_SIR: launch_days<SG_SIR>(m, a, st); break;
+    case SG_SIS: launch_days<SG_SIS>(m, a, st); break;
+    case SG_SISE: launch_days<SG_SISE>(m, a, st); break;
+    default: launch_days<SG_SISE3>(m, a, st); break;
+  }
+}
+
+// Bracket one kernel launch with timing events (no-op unless timing is on).
+struct LaunchTimer {
+  sg_model *m;
+  cudaStream_t st;
+  int kind;
+  bool on;
+  LaunchTimer(sg_model *m_, cudaStream_t s_, int k_) : m(m_), st(s_), kind(k_), on(m_->timing) {
+    if (!on) return;
+    while (m->evpool.size() < m->ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); on = false; return; }
+      m->evpool.push_back(e);
+    }
+    cudaEventRecord(m->evpool[m->ev_used], st);
+  }
+  ~LaunchTimer() {
+    if (!on) return;
+    cudaEventRecord(m->evpool[m->ev_used + 1], st);
+    m->ev_kind.push_back(kind);
+    m->ev_used += 2;
+  }
+};
+
+static void fill_error(sg_error *err, int code, int rep, int node, int day, int64_t ev) {
+  if (!err) return;
+  err->code = code;
+  err->rep = rep;
+  err->node = node;
+  err->day = day;
+  err->event = ev;
+}
+
+extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+                      int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
+                      double *d_V, void *stream, sg_stats *stats, sg_error *err) {
+  fill_error(err, 0, -1, -1, -1, -1);
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (!m || !tspan || n_tspan < 1 || n_rep < 1 || n_rep >= (1 << 24)) return SG_ERR_ARG;
+  for (int i = 1; i < n_tspan; ++i)
+    if (tspan[i] <= tspan[i - 1]) return SG_ERR_ARG;
+  const SgTables &tb = m->tb;
+  const int C = tb.n_comp, NV = tb.n_v, Nn = tb.n_nodes;
+  if (Nn > 0 && (!d_u0 || !d_U || (NV > 0 && (!d_v0 || !d_V)))) return SG_ERR_ARG;
+  if (m->ev.per_rep && m->ev.max_rep >= n_rep) {
+    fill_error(err, SG_ERR_ARG, m->ev.max_rep, -1, -1, -1);
+    return SG_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t t0 = tspan[0], t_end = tspan[n_tspan - 1];
+  const int32_t days = t_end - t0;
+  const int32_t slots = m->ev.per_rep ? n_rep : 1;
+  int rc = ensure_plan(m, t0, t_end, slots);
+  if (rc) return rc;
+  const Plan &P = m->plan;
+
+  const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
+  if ((rc = m->u.ensure((size_t)(per_rep_u * n_rep))) ||
+      (rc = m->v.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))) ||
+      (rc = m->rec.ensure((size_t)days + 1)))
+    return rc;
+  std::vector<int32_t> rec(days + 1, -1);
+  for (int i = 0; i < n_tspan; ++i) rec[tspan[i] - t0] = i;
+  if (cudaMemcpyAsync(m->rec.p, rec.data(), rec.size() * sizeof(int32_t),
+                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st) != cudaSuccess ||
+      cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  long long launches = 0;
+  m->ev_used = 0;
+  m->ev_kind.clear();
+  if (Nn > 0) {
+    const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
+    const unsigned g = (unsigned)std::min<long long>(4096, (nthreads + 255) / 256);
+    k_init<<<std::max(1u, g), 256, 0, st>>>(d_u0, NV ? d_v0 : nullptr, m->u.p,
+                                            NV ? m->v.p : nullptr, d_U, NV ? d_V : nullptr,
+                                            per_rep_u, per_rep_v, n_tspan, n_rep);
+    ++launches;
+  }
+
+  DayArgs da;
+  da.u = m->u.p;
+  da.v = m->v.p;
+  da.ldata = m->ldata.p;
+  da.U = d_U;
+  da.V = d_V;
+  da.rec = m->rec.p;
+  da.t0 = t0;
+  da.M = n_tspan;
+  da.n_rep = n_rep;
+  da.k0 = (uint32_t)seed;
+  da.k1 = (uint32_t)(seed >> 32);
+  da.err = m->err.p;
+  da.cnt = m->cnt.p;
+
+  EvArgs ea;
+  ea.ev = SgEventsDev{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
+                      m->e_n.p, m->e_prop.p, m->e_index.p, m->e_rep.p};
+  ea.u = m->u.p;
+  ea.n_rep = n_rep;
+  ea.k0 = da.k0;
+  ea.k1 = da.k1;
+  ea.err = m->err.p;
+  ea.cnt = m->cnt.p;
+
+  int32_t waves = 0;
+  if (Nn > 0 && days > 0) {
+    bool pending = false;  // the previous unit step still needs finishing
+    int32_t d = 0;
+    while (d < days) {
+      int32_t last = d;
+      while (last < days - 1 && !P.day_has_events[last]) ++last;
+      const bool ev_today = P.day_has_events[last] != 0;
+      da.T_begin = t0 + 1 + d;
+      da.T_end = t0 + 1 + last + 1;
+      da.finish_first = pending ? 1 : 0;
+      da.finish_last = ev_today ? 0 : 1;
+      {
+        LaunchTimer lt(m, st, 0);
+        launch_days_kind(m, da, st);
+      }
+      ++launches;
+      if (ev_today) {
+        ea.day = t0 + 1 + last;
+        const long long b0 = (long long)last * slots, b1 = b0 + slots;
+        const long long e1b = P.e1_off[b0], e1n = P.e1_off[b1] - e1b;
+        if (e1n > 0) {
+          const int rep_threads = slots > 1 ? 1 : n_rep;
+          const long long th = e1n * rep_threads;
+          LaunchTimer lt(m, st, 1);
+          k_events_e1<<<(unsigned)((th + kE1Block - 1) / kE1Block), kE1Block, 0, st>>>(
+              tb, ea, e1b, e1n, rep_threads);
+          ++launches;
+        }
+        const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
+        if (we > wb) {
+          LaunchTimer lt(m, st, 2);
+          k_events_e2<<<(unsigned)n_rep, kE2Block, 0, st>>>(
+              tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, last, slots);
+          ++launches;
+          waves += (int32_t)(we - wb);
+        }
+      }
+      pending = ev_today;
+      d = last + 1;
+    }
+    if (pending) {
+      da.T_begin = t_end + 1;
+      da.T_end = t_end + 1;
+      da.finish_first = 1;
+      da.finish_last = 0;
+      {
+        LaunchTimer lt(m, st, 0);
+        launch_days_kind(m, da, st);
+      }
+      ++launches;
+    }
+  }
+  if (cudaMemcpyAsync(m->h_err, m->err.p, sizeof(SgDevError), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(m->h_cnt, m->cnt.p, sizeof(SgCounters), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    fill_error(err, SG_ERR_CUDA, -1, -1, -1, -1);
+    return SG_ERR_CUDA;
+  }
+  if (stats) {
+    for (size_t i = 0; i < m->ev_kind.size(); ++i) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, m->evpool[2 * i], m->evpool[2 * i + 1]);
+      const int k = m->ev_kind[i];
+      (k == 0 ? stats->ms_ssa : k == 1 ? stats->ms_e1 : stats->ms_e2) += ms;
+      ++(k == 0 ? stats->launches_ssa : k == 1 ? stats->launches_e1 : stats->launches_e2);
+    }
+    cudaGetLastError();
+    stats->draws = (int64_t)m->h_cnt->draws;
+    stats->reactions = (int64_t)m->h_cnt->reactions;
+    stats->events_applied = (int64_t)m->h_cnt->events;
+    stats->node_days = (int64_t)Nn * n_rep * days;
+    stats->kernel_launches = launches;
+    stats->e2_waves = waves;
+    stats->days = days;
+  }
+  const SgDevError &e = *m->h_err;
+  if (e.code) {
+    fill_error(err, e.code, e.rep, e.node, e.day, e.event);
+    return e.code;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+                           int32_t n_rep, const int32_t *u0, const double *v0, int32_t *U,
+                           double *V, void *stream, sg_stats *stats, sg_error *err) {
+  if (!m || !tspan || n_tspan < 1 || n_rep < 1) return SG_ERR_ARG;
+  const SgTables &tb = m->tb;
+  const size_t nu = (size_t)n_rep * tb.n_nodes * tb.n_comp;
+  const size_t nv = (size_t)n_rep * tb.n_nodes * tb.n_v;
+  const size_t M = (size_t)n_tspan;
+  if (tb.n_nodes > 0 && (!u0 || !U || (tb.n_v > 0 && (!v0 || !V)))) return SG_ERR_ARG;
+  int rc;
+  if ((rc = m->hu0.ensure(nu)) || (rc = m->hU.ensure(nu * M)) ||
+      (rc = m->hv0.ensure(std::max<size_t>(1, nv))) || (rc = m->hV.ensure(std::max<size_t>(1, nv * M))))
+    return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if ((nu && cudaMemcpyAsync(m->hu0.p, u0, nu * sizeof(int32_t), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess) ||
+      (nv && cudaMemcpyAsync(m->hv0.p, v0, nv * sizeof(double), cudaMemcpyHostToDevice, st) !=
+                 cudaSuccess)) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  rc = sg_run(m, tspan, n_tspan, seed, n_rep, m->hu0.p, nv ? m->hv0.p : nullptr, m->hU.p,
+              nv ? m->hV.p : nullptr, stream, stats, err);
+  if (rc) return rc;
+  if ((nu && cudaMemcpyAsync(U, m->hU.p, nu * M * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             st) != cudaSuccess) ||
+      (nv && cudaMemcpyAsync(V, m->hV.p, nv * M * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+                 cudaSuccess) ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+static unsigned grid_for(long long n) {
+  return (unsigned)std::max<long long>(1, std::min<long long>(8192, (n + 255) / 256));
+}
+
+extern "C" int sg_philox_batch(const uint32_t *d_ctr, uint64_t key, uint32_t *d_out, int64_t n,
+                               void *stream) {
+  if (n < 0 || (n > 0 && (!d_ctr || !d_out))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n) k_philox_batch<<<grid_for(n), 256, 0, st>>>(d_ctr, (uint32_t)key, (uint32_t)(key >> 32),
+                                                     d_out, n);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_log_batch(const double *d_x, double *d_y, int64_t n, void *stream) {
+  if (n < 0 || (n > 0 && (!d_x || !d_y))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n) k_log_batch<<<grid_for(n), 256, 0, st>>>(d_x, d_y, n);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_u01_batch(const uint32_t *d_w, double *d_y, int64_t n, void *stream) {
+  if (n < 0 || (n > 0 && (!d_w || !d_y))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n) k_u01_batch<<<grid_for(n), 256, 0, st>>>(d_w, d_y, n);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_set_kernel_timing(sg_model *m, int enable) {
+  if (!m) return SG_ERR_ARG;
+  m->timing = enable != 0;
+  return SG_OK;
+}
+
+extern "C" int sg_fp64_fma_probe(int32_t iters, double *tflops, void *stream) {
+  if (iters < 1 || !tflops) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  const int threads = 256, blocks = sms * 8;
+  double *out = nullptr;
+  cudaEvent_t e0, e1;
+  if (cudaMallocAsync(&out, sizeof(double) * threads * blocks, st) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_NOMEM;
+  }
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  k_fp64_fma<<<blocks, threads, 0, st>>>(out, 16);  // warm-up
+  cudaEventRecord(e0, st);
+  k_fp64_fma<<<blocks, threads, 0, st>>>(out, iters);
+  cudaEventRecord(e1, st);
+  float ms = 0.f;
+  const bool ok = cudaEventSynchronize(e1) == cudaSuccess &&
+                  cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  cudaFreeAsync(out, st);
+  cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
+  const double flops = 2.0 * 8.0 * (double)iters * threads * blocks;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return SG_OK;
+}

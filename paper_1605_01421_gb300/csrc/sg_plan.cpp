@@ -1,0 +1,153 @@
+// sg_plan.cpp -- host-side validation and scheduling of the scheduled events
+// (Sec. 3.3, Appendix A "Process E1 events" / "Process E2 events").
+#include "sg_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+namespace sg {
+
+int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad) {
+  const int64_t n = ev.size();
+  for (int64_t e = 0; e < n; ++e) {
+    const int type = ev.type[e], s = ev.select[e], q = ev.shift[e];
+    bool ok = type >= SG_EXIT && type <= SG_EXTERNAL_TRANSFER;
+    ok = ok && ev.node[e] >= 0 && ev.node[e] < tb.n_nodes;
+    if (type == SG_EXTERNAL_TRANSFER)
+      ok = ok && ev.dest[e] >= 0 && ev.dest[e] < tb.n_nodes;
+    ok = ok && s >= 0 && s < tb.n_select;
+    ok = ok && ev.n[e] >= 0;
+    ok = ok && ev.proportion[e] >= 0.0 && ev.proportion[e] <= 1.0;
+    // Reading: an internal transfer without a shift column is an error.
+    if (type == SG_INTERNAL_TRANSFER) ok = ok && q >= 0;
+    if (type != SG_ENTER) ok = ok && q < tb.n_shift;
+    if (ev.per_rep) ok = ok && ev.rep[e] >= 0;
+    if (ok && type == SG_ENTER) ok = tb.Emask[s] != 0;
+    if (!ok) {
+      *bad = e;
+      return SG_ERR_ARG;
+    }
+    // a shift must keep every selectable compartment inside the node
+    if (q >= 0 && (type == SG_INTERNAL_TRANSFER || type == SG_EXTERNAL_TRANSFER)) {
+      for (int p = 0; p < tb.n_comp; ++p) {
+        if (!((tb.Emask[s] >> p) & 1u)) continue;
+        const int to = p + tb.Nsh[q][p];
+        if (to < 0 || to >= tb.n_comp) {
+          *bad = e;
+          return SG_ERR_SHIFT_RANGE;
+        }
+      }
+    }
+  }
+  *bad = -1;
+  return SG_OK;
+}
+
+int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
+               int32_t slots, Plan *out) {
+  Plan &P = *out;
+  P = Plan();
+  P.t0 = t0;
+  P.t_end = t_end;
+  P.slots = slots;
+  P.days = std::max(0, t_end - t0);
+  const int64_t nb = (int64_t)P.days * slots;
+  P.e1_off.assign(nb + 1, 0);
+  P.e2_wave_off.assign(nb + 1, 0);
+  P.day_has_events.assign(P.days, 0);
+  P.wave_ev.assign(1, 0);
+  if (P.days == 0) return SG_OK;
+
+  // 1. stable bucketing by (day, slot); events after t_end never run, and
+  //    events dated t0 or earlier run at the first step.
+  const int64_t n = ev.size();
+  std::vector<int64_t> bucket_of(n, -1);
+  std::vector<int64_t> count(nb + 1, 0);
+  for (int64_t e = 0; e < n; ++e) {
+    if (ev.time[e] > t_end) continue;
+    const int64_t d = std::max<int64_t>(0, (int64_t)ev.time[e] - t0 - 1);
+    const int64_t s = slots > 1 ? ev.rep[e] : 0;
+    if (s >= slots) return SG_ERR_ARG;
+    bucket_of[e] = d * slots + s;
+    ++count[bucket_of[e] + 1];
+  }
+  std::partial_sum(count.begin(), count.end(), count.begin());
+  std::vector<int64_t> bucketed(count[nb]);
+  {
+    std::vector<int64_t> fill(count.begin(), count.end() - 1);
+    for (int64_t e = 0; e < n; ++e)
+      if (bucket_of[e] >= 0) bucketed[fill[bucket_of[e]]++] = e;
+  }
+
+  // 2. per bucket: E1 part sorted by (node, time, type, index); E2 part in
+  //    (time, index) order split into waves.
+  std::vector<int64_t> e1, e2;
+  e1.reserve(bucketed.size());
+  e2.reserve(bucketed.size());
+  std::vector<int32_t> last_sample(n_nodes, 0), last_add(n_nodes, 0);
+  std::vector<int64_t> stamp(n_nodes, -1);
+  std::vector<int64_t> tmp1, tmp2;
+  std::vector<int32_t> wave_of;
+  for (int64_t b = 0; b < nb; ++b) {
+    tmp1.clear();
+    tmp2.clear();
+    for (int64_t i = count[b]; i < count[b + 1]; ++i) {
+      const int64_t e = bucketed[i];
+      (ev.type[e] == SG_EXTERNAL_TRANSFER ? tmp2 : tmp1).push_back(e);
+    }
+    std::sort(tmp1.begin(), tmp1.end(), [&](int64_t a, int64_t c) {
+      if (ev.node[a] != ev.node[c]) return ev.node[a] < ev.node[c];
+      if (ev.time[a] != ev.time[c]) return ev.time[a] < ev.time[c];
+      if (ev.type[a] != ev.type[c]) return ev.type[a] < ev.type[c];
+      return a < c;
+    });
+    e1.insert(e1.end(), tmp1.begin(), tmp1.end());
+    P.e1_off[b + 1] = (int64_t)e1.size();
+
+    // E2: list order within the bucket is already (index); only the first
+    // day can mix times, so order by (time, index) there.
+    std::stable_sort(tmp2.begin(), tmp2.end(), [&](int64_t a, int64_t c) {
+      return ev.time[a] < ev.time[c];
+    });
+    wave_of.assign(tmp2.size(), 0);
+    int32_t n_w = 0;
+    for (size_t i = 0; i < tmp2.size(); ++i) {
+      const int64_t e = tmp2[i];
+      const int32_t s = ev.node[e], d = ev.dest[e];
+      if (stamp[s] != b) { stamp[s] = b; last_sample[s] = 0; last_add[s] = 0; }
+      if (stamp[d] != b) { stamp[d] = b; last_sample[d] = 0; last_add[d] = 0; }
+      const int32_t w = std::max(std::max(last_sample[s], last_add[s]), last_sample[d]) + 1;
+      last_sample[s] = w;
+      last_add[d] = std::max(last_add[d], w);
+      wave_of[i] = w;
+      n_w = std::max(n_w, w);
+    }
+    // counting sort by wave, list order kept inside a wave
+    std::vector<int64_t> wc(n_w + 2, 0);
+    for (size_t i = 0; i < tmp2.size(); ++i) ++wc[wave_of[i] + 1];
+    std::partial_sum(wc.begin(), wc.end(), wc.begin());
+    std::vector<int64_t> sorted(tmp2.size());
+    {
+      std::vector<int64_t> fill(wc.begin(), wc.end() - 1);
+      for (size_t i = 0; i < tmp2.size(); ++i) sorted[fill[wave_of[i]]++] = tmp2[i];
+    }
+    const int64_t base = (int64_t)e2.size();
+    e2.insert(e2.end(), sorted.begin(), sorted.end());
+    for (int32_t w = 1; w <= n_w; ++w) P.wave_ev.push_back(base + wc[w + 1]);
+    P.e2_wave_off[b + 1] = (int64_t)P.wave_ev.size() - 1;
+    if (count[b + 1] > count[b]) P.day_has_events[b / slots] = 1;
+    P.max_waves_per_day = std::max(P.max_waves_per_day, n_w);
+  }
+  P.n_e1 = (int64_t)e1.size();
+  P.n_e2 = (int64_t)e2.size();
+  P.n_waves = (int64_t)P.wave_ev.size() - 1;
+  // wave_ev holds positions within the E2 part; shift them past the E1 part
+  for (auto &x : P.wave_ev) x += P.n_e1;
+  P.order.reserve(P.n_e1 + P.n_e2);
+  P.order.insert(P.order.end(), e1.begin(), e1.end());
+  P.order.insert(P.order.end(), e2.begin(), e2.end());
+  return SG_OK;
+}
+
+}  // namespace sg

@@ -1,0 +1,57 @@
+// sg_plan.h -- host-side validation and scheduling of the scheduled events
+// (Sec. 3.3) for the SimInf GB300 engine.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "sg_common.h"
+
+namespace sg {
+
+// The caller's event table, copied (0-based; shift < 0 = no shift).
+struct EventTable {
+  std::vector<int32_t> type, time, node, dest, n, select, shift, rep;
+  std::vector<double> proportion;
+  bool per_rep = false;  // rep[] given
+  int32_t max_rep = -1;
+  int64_t size() const { return (int64_t)type.size(); }
+};
+
+// Checks of the event table against the model (Sec. 3.3 constraints and the
+// readings of the engine): returns SG_OK or the error code, and the index of
+// the first offending event in *bad.
+int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad);
+
+// The device-ready schedule of the events for one simulation window
+// (unit steps T = t0 + 1 .. t_end) and one number of replicate slots
+// (1 when every replicate runs the same events, else n_rep).
+//
+// Day d (T = t0 + 1 + d) runs the events with time in (T - 1, T]; for d = 0
+// also every earlier time.  E1 events (exit, enter, internal transfer) are
+// grouped per (day, slot) and, inside, sorted by (node, time, type, list
+// index): a node's events run in the order of Sec. 3.3.  E2 events
+// (external transfers) of a (day, slot) keep their (time, list index) order
+// and are split into waves: an event goes one wave after the last earlier
+// event that sampled its source, added to its source, or sampled its
+// destination.  So no two events of a wave touch the same node except as
+// destinations (additions commute), and every node sees its samples and
+// additions in list order.
+struct Plan {
+  int32_t t0 = 0, t_end = 0, slots = 1;
+  int32_t days = 0;
+  // sorted events, E1 part first then E2 part (indices into EventTable)
+  std::vector<int64_t> order;
+  std::vector<int64_t> e1_off;   // [days * slots + 1] into order
+  std::vector<int64_t> e2_wave_off;  // [days * slots + 1] into wave_ev
+  std::vector<int64_t> wave_ev;  // [n_waves + 1] into order
+  std::vector<uint8_t> day_has_events;  // [days]
+  int64_t n_e1 = 0, n_e2 = 0, n_waves = 0;
+  int32_t max_waves_per_day = 0;
+};
+
+int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
+               int32_t slots, Plan *out);
+
+}  // namespace sg
