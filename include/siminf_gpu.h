@@ -74,8 +74,10 @@ enum {
   SG_ERR_TIMEOUT = -6,         /* a bounded device wait gave up            */
   SG_ERR_CUDA = -7,            /* a CUDA runtime call failed               */
   SG_ERR_NOMEM = -8,           /* host or device allocation failed         */
-  SG_ERR_STEP_LIMIT = -9       /* a node needed more than SG_MAX_DRAWS draws
+  SG_ERR_STEP_LIMIT = -9,      /* a node needed more than SG_MAX_DRAWS draws
                                   in one unit step (rates far too large)    */
+  SG_ERR_TOO_LARGE = -10       /* the problem does not fit the fixed scratch
+                                  of sg_run_noalloc                         */
 };
 
 /* Draws one node may take in one unit step before the run stops with
@@ -190,6 +192,42 @@ void sg_model_destroy(sg_model *m);
 
 /* Static description of an error code. */
 const char *sg_strerror(int code);
+
+/* sg_run without any allocation, for callers that cannot allocate memory.
+ *
+ * Some callers cannot call cudaMalloc (or anything that allocates): code that
+ * runs inside a host framework which owns the device memory pool and forbids
+ * private allocations, services that must not allocate after start-up so
+ * that their memory footprint stays fixed, and pipelines that may run while a
+ * CUDA stream is being captured, where allocation calls are not allowed.
+ * This entry point needs neither an sg_model nor any allocation: the model
+ * tables come from `desc` (host memory, read during the call; desc->ldata is
+ * ignored and `d_ldata` gives the local data on the device, n_ldata x
+ * n_nodes column-major), the caller passes every input and output buffer,
+ * and the working memory (node states, tspan table, error word, counters)
+ * lives in one fixed array of SG_NOALLOC_SCRATCH_BYTES bytes inside this
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  It runs the model without scheduled events (the event schedule
+ * needs memory proportional to the event table).
+ *
+ * Limits and behaviour:
+ *   - needed scratch = 1024 + 4 (days + 1) + 4 n_tspan + 4 n_rep n_nodes
+ *     n_comp + 8 n_rep n_nodes n_v bytes, each part rounded up to 256 bytes;
+ *     a larger problem returns SG_ERR_TOO_LARGE before any device work;
+ *   - the first call on a device (per process) looks up the array's device
+ *     address with that device current; make that first call before any
+ *     stream capture;
+ *   - every call on a device uses the same array, which keeps the previous
+ *     call's contents (each call clears what must start at zero); calls whose
+ *     work overlaps on the GPU (several host threads, or several streams
+ *     without ordering) race on it and must be serialised by the caller;
+ *   - otherwise as sg_run: same results bit for bit, same errors; the call
+ *     waits for its stream before it returns. */
+#define SG_NOALLOC_SCRATCH_BYTES (8u << 20)
+int sg_run_noalloc(const sg_desc *desc, const double *d_ldata, const int32_t *tspan,
+                   int32_t n_tspan, uint64_t seed, int32_t n_rep, const int32_t *d_u0,
+                   const double *d_v0, int32_t *d_U, double *d_V, void *stream,
+                   sg_stats *stats, sg_error *err);
 
 /* Device-side primitives, exported for parity checks of the random stream
  * and arithmetic (each fills a caller-owned device buffer on `stream` and

@@ -36,7 +36,8 @@ ERR_NAMES = {0: "ok", -1: "invalid argument",
              -4: "negative or non-finite transition rate",
              -5: "post time step error", -6: "device wait timed out",
              -7: "CUDA runtime error", -8: "out of memory",
-             -9: "more than 2^24 draws in one node-day"}
+             -9: "more than 2^24 draws in one node-day",
+             -10: "problem exceeds the fixed scratch of sg_run_noalloc"}
 
 
 class SimInfError(RuntimeError):
@@ -117,7 +118,8 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
-           "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe"]
+           "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe",
+           "sg_run_noalloc"]
 
 _lock = threading.Lock()
 _lib = None
@@ -160,6 +162,10 @@ def lib(path: str | None = None):
         L.sg_set_kernel_timing.restype = ctypes.c_int
         L.sg_fp64_fma_probe.argtypes = [i32, ctypes.POINTER(ctypes.c_double), vp]
         L.sg_fp64_fma_probe.restype = ctypes.c_int
+        L.sg_run_noalloc.argtypes = [ctypes.POINTER(_Desc), vp, vp, i32, u64, i32, vp, vp,
+                                     vp, vp, vp, ctypes.POINTER(Stats),
+                                     ctypes.POINTER(Error)]
+        L.sg_run_noalloc.restype = ctypes.c_int
         _lib = L
         return L
 

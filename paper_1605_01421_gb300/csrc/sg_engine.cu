@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -451,6 +452,7 @@ extern "C" const char *sg_strerror(int code) {
     case SG_ERR_CUDA: return "CUDA runtime error";
     case SG_ERR_NOMEM: return "out of memory";
     case SG_ERR_STEP_LIMIT: return "more than SG_MAX_DRAWS draws in one node-day";
+    case SG_ERR_TOO_LARGE: return "problem exceeds the fixed scratch of sg_run_noalloc";
     default: return "unknown error";
   }
 }
@@ -935,5 +937,194 @@ extern "C" int sg_fp64_fma_probe(int32_t iters, double *tflops, void *stream) {
   if (!ok || cudaGetLastError() != cudaSuccess) return SG_ERR_CUDA;
   const double flops = 2.0 * 8.0 * (double)iters * threads * blocks;
   *tflops = flops / (ms * 1e-3) / 1e12;
+  return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sg_run_noalloc: the event-free run with its working memory in a fixed
+// device array instead of allocated buffers (see include/siminf_gpu.h for
+// which callers need this and its limits).
+// ---------------------------------------------------------------------------
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[kNoallocMaxDevices] = {};
+
+// The array's device address for the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up once per
+// device, with that device current.
+int noalloc_base(unsigned char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SG_ERR_CUDA;
+    }
+    g_noalloc_base[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_base[dev];
+  return SG_OK;
+}
+
+constexpr size_t round256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// rec[i] = tspan slot of unit time t0 + i, or -1
+__global__ void k_noalloc_rec(const int32_t *tspan, int32_t n_tspan, int32_t *rec, int32_t days) {
+  const int32_t t0 = tspan[0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= days; i += gridDim.x * blockDim.x)
+    rec[i] = -1;
+  __syncthreads();
+  if (blockIdx.x == 0)
+    for (int i = threadIdx.x; i < n_tspan; i += blockDim.x) rec[tspan[i] - t0] = i;
+}
+
+}  // namespace
+
+extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int32_t *tspan,
+                              int32_t n_tspan, uint64_t seed, int32_t n_rep,
+                              const int32_t *d_u0, const double *d_v0, int32_t *d_U,
+                              double *d_V, void *stream, sg_stats *stats, sg_error *err) {
+  fill_error(err, 0, -1, -1, -1, -1);
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (!d || !tspan || n_tspan < 1 || n_rep < 1 || n_rep >= (1 << 24)) return SG_ERR_ARG;
+  const int k = d->kind;
+  if (k < SG_SIR || k > SG_SISE3) return SG_ERR_ARG;
+  if (d->n_nodes < 0 || d->n_comp != kKindComp[k] || d->n_trans != kKindTrans[k] ||
+      d->n_v != kKindNv[k] || d->n_gdata < kKindGdata[k] || d->n_gdata > SG_MAX_GDATA ||
+      d->n_ldata < kKindLdata[k] || !d->S || !d->G || (d->n_gdata > 0 && !d->gdata) ||
+      (d->n_ldata > 0 && d->n_nodes > 0 && !d_ldata))
+    return SG_ERR_ARG;
+  for (int i = 1; i < n_tspan; ++i)
+    if (tspan[i] <= tspan[i - 1]) return SG_ERR_ARG;
+  const int C = d->n_comp, T = d->n_trans, NV = d->n_v, Nn = d->n_nodes;
+  if (Nn > 0 && (!d_u0 || !d_U || (NV > 0 && (!d_v0 || !d_V)))) return SG_ERR_ARG;
+
+  // tables passed by value to the kernels (no allocation)
+  SgTables tb;
+  std::memset(&tb, 0, sizeof tb);
+  tb.kind = k;
+  tb.n_nodes = Nn;
+  tb.n_comp = C;
+  tb.n_trans = T;
+  tb.n_v = NV;
+  tb.n_ldata = d->n_ldata;
+  for (int j = 0; j < T; ++j) {
+    for (int p = 0; p < C; ++p) {
+      const int sv = d->S[(size_t)j * C + p];
+      if (sv < -127 || sv > 127) return SG_ERR_ARG;
+      tb.S[j][p] = (int8_t)sv;
+    }
+    uint32_t dep = 0;
+    for (int kk = 0; kk < T; ++kk)
+      if (d->G[(size_t)j * T + kk] != 0) dep |= 1u << kk;
+    tb.dep[j] = dep;
+  }
+  for (int i = 0; i < d->n_gdata; ++i) tb.gdata[i] = d->gdata[i];
+
+  // scratch layout: error word | counters | tspan | rec | u | v
+  const int32_t t0 = tspan[0], t_end = tspan[n_tspan - 1], days = t_end - t0;
+  const size_t units = (size_t)n_rep * (size_t)Nn;
+  const size_t off_cnt = 256, off_tspan = 512;
+  const size_t off_rec = off_tspan + round256(sizeof(int32_t) * (size_t)n_tspan);
+  const size_t off_u = off_rec + round256(sizeof(int32_t) * ((size_t)days + 1));
+  const size_t off_v = off_u + round256(sizeof(int32_t) * units * C);
+  const size_t need = off_v + round256(sizeof(double) * units * NV) + 512;
+  if (need > SG_NOALLOC_SCRATCH_BYTES) {
+    fill_error(err, SG_ERR_TOO_LARGE, -1, -1, -1, -1);
+    return SG_ERR_TOO_LARGE;
+  }
+  unsigned char *base = nullptr;
+  int rc = noalloc_base(&base);
+  if (rc) {
+    fill_error(err, rc, -1, -1, -1, -1);
+    return rc;
+  }
+  SgDevError *d_err = (SgDevError *)base;
+  SgCounters *d_cnt = (SgCounters *)(base + off_cnt);
+  int32_t *d_tspan = (int32_t *)(base + off_tspan);
+  int32_t *d_rec = (int32_t *)(base + off_rec);
+  int *d_u = (int *)(base + off_u);
+  double *d_v = (double *)(base + off_v);
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // clear what must start at zero; the rest is overwritten before use
+  if (cudaMemsetAsync(d_err, 0, sizeof(SgDevError), st) != cudaSuccess ||
+      cudaMemsetAsync(d_cnt, 0, sizeof(SgCounters), st) != cudaSuccess ||
+      cudaMemcpyAsync(d_tspan, tspan, sizeof(int32_t) * (size_t)n_tspan,
+                      cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    cudaGetLastError();
+    fill_error(err, SG_ERR_CUDA, -1, -1, -1, -1);
+    return SG_ERR_CUDA;
+  }
+  k_noalloc_rec<<<1, 256, 0, st>>>(d_tspan, n_tspan, d_rec, days);
+  long long launches = 1;
+  const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
+  if (Nn > 0) {
+    const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
+    const unsigned g = (unsigned)std::min<long long>(4096, (nthreads + 255) / 256);
+    k_init<<<std::max(1u, g), 256, 0, st>>>(d_u0, NV ? d_v0 : nullptr, d_u, NV ? d_v : nullptr,
+                                            d_U, NV ? d_V : nullptr, per_rep_u, per_rep_v,
+                                            n_tspan, n_rep);
+    ++launches;
+    if (days > 0) {
+      DayArgs da;
+      da.u = d_u;
+      da.v = d_v;
+      da.ldata = d_ldata;
+      da.U = d_U;
+      da.V = d_V;
+      da.rec = d_rec;
+      da.t0 = t0;
+      da.M = n_tspan;
+      da.n_rep = n_rep;
+      da.T_begin = t0 + 1;
+      da.T_end = t_end + 1;
+      da.finish_first = 0;
+      da.finish_last = 1;
+      da.k0 = (uint32_t)seed;
+      da.k1 = (uint32_t)(seed >> 32);
+      da.err = d_err;
+      da.cnt = d_cnt;
+      const long long threads = (long long)Nn * n_rep;
+      const unsigned grid = (unsigned)std::max<long long>(1, (threads + kDayBlock - 1) / kDayBlock);
+      switch (k) {
+        case SG_SIR: k_days<SG_SIR><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        case SG_SIS: k_days<SG_SIS><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        case SG_SISE: k_days<SG_SISE><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        default: k_days<SG_SISE3><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+      }
+      ++launches;
+    }
+  }
+  SgDevError h_err;
+  SgCounters h_cnt;
+  if (cudaMemcpyAsync(&h_err, d_err, sizeof h_err, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaMemcpyAsync(&h_cnt, d_cnt, sizeof h_cnt, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    fill_error(err, SG_ERR_CUDA, -1, -1, -1, -1);
+    return SG_ERR_CUDA;
+  }
+  if (stats) {
+    stats->reactions = (int64_t)h_cnt.reactions;
+    stats->draws = (int64_t)h_cnt.draws;
+    stats->node_days = (int64_t)Nn * n_rep * days;
+    stats->kernel_launches = launches;
+    stats->days = days;
+  }
+  if (h_err.code) {
+    fill_error(err, h_err.code, h_err.rep, h_err.node, h_err.day, h_err.event);
+    return h_err.code;
+  }
   return SG_OK;
 }
