@@ -190,8 +190,8 @@ def bench_gpu(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     model = binding.Model(w)
-    u0 = torch.as_tensor(np.ascontiguousarray(w.u0), device=dev)
-    v0 = torch.as_tensor(np.ascontiguousarray(w.v0), device=dev)
+    u0 = torch.as_tensor(np.array(w.u0, dtype=np.int32, order="C"), device=dev)
+    v0 = torch.as_tensor(np.array(w.v0, dtype=np.float64, order="C"), device=dev)
     U = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32, device=dev)
     V = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
@@ -200,6 +200,11 @@ def bench_gpu(args):
 
     def step():
         return model.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
+
+    tuned = None
+    if args.autotune:
+        # the work split changes speed only, never results
+        tuned = model.autotune(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -308,6 +313,8 @@ def bench_gpu(args):
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches,
+            "tuning": {"nodes_per_block": tuned[0], "heavy_after": tuned[1],
+                       "autotune_best_ms": tuned[2]} if tuned else None,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
     print(json.dumps(line))
     if dist:
@@ -330,6 +337,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sise", choices=["sise", "sir", "sise3"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

@@ -187,6 +187,25 @@ int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan,
  * sg_stats.  Off by default (the events add host work per launch). */
 int sg_set_kernel_timing(sg_model *m, int enable);
 
+/* Work split of the SSA day kernel.  Each block of 128 threads owns
+ * nodes_per_block (1..128) (replicate, node) pairs, one per thread; a node
+ * whose SSA needs more than heavy_after draws in a day is handed to one of
+ * the block's warps, whose 32 lanes compute 32 draws' random numbers at
+ * once.  Results are identical for every setting (the random stream is a
+ * function of replicate, node, day and draw index only); only speed changes.
+ * nodes_per_block <= 0 or heavy_after < 0 restore the size-based defaults. */
+int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
+
+/* Autotuner: runs the given workload (arguments as sg_run) once for each of
+ * nodes_per_block in {16, 32, 64, 128} x heavy_after in {0, 1, 2, 4, 8},
+ * keeps the fastest setting in the model and reports it (outputs may be
+ * NULL).  U and V hold the last run's (identical) results.  A shorter tspan
+ * tunes a long workload on a prefix. */
+int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+                int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
+                double *d_V, void *stream, int32_t *nodes_per_block,
+                int32_t *heavy_after, double *ms);
+
 /* Release the model and all its device memory. */
 void sg_model_destroy(sg_model *m);
 

@@ -119,7 +119,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
            "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe",
-           "sg_run_noalloc"]
+           "sg_run_noalloc", "sg_set_tuning", "sg_autotune"]
 
 _lock = threading.Lock()
 _lib = None
@@ -166,6 +166,12 @@ def lib(path: str | None = None):
                                      vp, vp, vp, ctypes.POINTER(Stats),
                                      ctypes.POINTER(Error)]
         L.sg_run_noalloc.restype = ctypes.c_int
+        L.sg_set_tuning.argtypes = [vp, i32, i32]
+        L.sg_set_tuning.restype = ctypes.c_int
+        ip32 = ctypes.POINTER(ctypes.c_int32)
+        L.sg_autotune.argtypes = [vp, vp, i32, u64, i32, vp, vp, vp, vp, vp, ip32, ip32,
+                                  ctypes.POINTER(ctypes.c_double)]
+        L.sg_autotune.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -182,8 +188,20 @@ def _p(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else None
 
 
-def _dev_ptr(t):
-    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else None
+def _dev_ptr(t, dtype=None, shape=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (checked: the C ABI reads
+    plain row-major buffers)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous (row-major)")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, not {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else None
 
 
 def _stream_handle(stream):
@@ -235,11 +253,16 @@ class Model:
     def run(self, tspan, seed, n_rep, u0, v0, U, V, stream=None, check=True):
         """Run on device tensors: u0 (R, Nn, C) int32, v0 (R, Nn, Nv) float64,
         U (R, M, Nn, C) int32, V (R, M, Nn, Nv) float64, all on the GPU."""
+        import torch
         L = lib()
         ts = _i32(tspan)
         st, er = Stats(), Error()
-        rc = L.sg_run(self._h, _p(ts), int(ts.size), int(seed), int(n_rep),
-                      _dev_ptr(u0), _dev_ptr(v0), _dev_ptr(U), _dev_ptr(V),
+        R, Nn, C, Nv, M = int(n_rep), self.n_nodes, self.n_comp, self.n_v, int(ts.size)
+        rc = L.sg_run(self._h, _p(ts), M, int(seed), R,
+                      _dev_ptr(u0, torch.int32, (R, Nn, C), "u0"),
+                      _dev_ptr(v0, torch.float64, (R, Nn, Nv), "v0"),
+                      _dev_ptr(U, torch.int32, (R, M, Nn, C), "U"),
+                      _dev_ptr(V, torch.float64, (R, M, Nn, Nv), "V"),
                       _stream_handle(stream), ctypes.byref(st), ctypes.byref(er))
         if rc and check:
             raise SimInfError(rc, er.as_dict())
@@ -250,12 +273,37 @@ class Model:
         L = lib()
         ts = _i32(tspan)
         st, er = Stats(), Error()
-        rc = L.sg_run_host(self._h, _p(ts), int(ts.size), int(seed), int(n_rep),
+        R, Nn, C, Nv, M = int(n_rep), self.n_nodes, self.n_comp, self.n_v, int(ts.size)
+        for a, dt, shp, nm in ((u0, np.int32, (R, Nn, C), "u0"), (v0, np.float64, (R, Nn, Nv), "v0"),
+                               (U, np.int32, (R, M, Nn, C), "U"), (V, np.float64, (R, M, Nn, Nv), "V")):
+            if (a.dtype != dt or a.shape != shp or not a.flags.c_contiguous
+                    or (nm in ("U", "V") and not a.flags.writeable)):
+                raise ValueError(f"{nm} must be a C-contiguous {np.dtype(dt).name} array "
+                                 f"of shape {shp}")
+        rc = L.sg_run_host(self._h, _p(ts), M, int(seed), R,
                            _p(u0), _p(v0), _p(U), _p(V), _stream_handle(stream),
                            ctypes.byref(st), ctypes.byref(er))
         if rc and check:
             raise SimInfError(rc, er.as_dict())
         return rc, st.as_dict(), er.as_dict()
+
+    def set_tuning(self, nodes_per_block=-1, heavy_after=-1):
+        rc = lib().sg_set_tuning(self._h, int(nodes_per_block), int(heavy_after))
+        if rc:
+            raise SimInfError(rc)
+
+    def autotune(self, tspan, seed, n_rep, u0, v0, U, V, stream=None):
+        """Pick the fastest work split on this workload; returns
+        (nodes_per_block, heavy_after, ms)."""
+        ts = _i32(tspan)
+        npb, ha, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+        rc = lib().sg_autotune(self._h, _p(ts), int(ts.size), int(seed), int(n_rep),
+                               _dev_ptr(u0), _dev_ptr(v0), _dev_ptr(U), _dev_ptr(V),
+                               _stream_handle(stream), ctypes.byref(npb), ctypes.byref(ha),
+                               ctypes.byref(ms))
+        if rc:
+            raise SimInfError(rc)
+        return npb.value, ha.value, ms.value
 
     def set_kernel_timing(self, enable=True):
         rc = lib().sg_set_kernel_timing(self._h, 1 if enable else 0)
@@ -274,15 +322,18 @@ class Model:
             pass
 
 
-def simulate(w, device="cuda", seed=None, n_rep=None, stream=None):
-    """Convenience: run a workload on the GPU and return numpy (U, V, stats)."""
+def simulate(w, device="cuda", seed=None, n_rep=None, stream=None, tuning=None):
+    """Convenience: run a workload on the GPU and return numpy (U, V, stats).
+    tuning = (nodes_per_block, heavy_after) or None for the defaults."""
     import torch
     n_rep = w.n_rep if n_rep is None else n_rep
     seed = w.seed if seed is None else seed
     m = Model(w)
+    if tuning is not None:
+        m.set_tuning(*tuning)
     try:
-        u0 = torch.as_tensor(np.ascontiguousarray(w.u0[:n_rep]), device=device)
-        v0 = torch.as_tensor(np.ascontiguousarray(w.v0[:n_rep]), device=device)
+        u0 = torch.as_tensor(np.array(w.u0[:n_rep], dtype=np.int32, order="C"), device=device)
+        v0 = torch.as_tensor(np.array(w.v0[:n_rep], dtype=np.float64, order="C"), device=device)
         M = len(w.tspan)
         U = torch.empty((n_rep, M, m.n_nodes, m.n_comp), dtype=torch.int32, device=device)
         V = torch.empty((n_rep, M, m.n_nodes, m.n_v), dtype=torch.float64, device=device)

@@ -39,11 +39,47 @@ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1) {
 }
 
 // Uniform on (0, 1) from 52 random bits: k = (hi << 20) | (lo >> 12),
-// r = (k + 1/2) 2^-52.  Exact; the range is [2^-53, 1 - 2^-53].
+// r = (k + 1/2) 2^-52 = (2k + 1) 2^-53.  The value is exact, so it is built
+// directly from its bits with integer instructions (normalise the odd 53-bit
+// integer 2k + 1): no floating-point operation, same value as the product.
+// The range is [2^-53, 1 - 2^-53].
 __device__ __forceinline__ double u01_open(uint32_t lo, uint32_t hi) {
-  const unsigned long long k =
-      ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
-  return ((double)k + 0.5) * 0x1.0p-52;
+  const unsigned long long m =
+      (((unsigned long long)hi << 21) | (unsigned long long)((lo >> 12) << 1)) | 1ull;
+  const int p = 63 - __clzll((long long)m);  // msb position, 0..52
+  const unsigned long long frac = (m << (52 - p)) & 0x000fffffffffffffull;
+  const unsigned long long ex = (unsigned long long)(p + 970);  // 2^(p - 53)
+  return __longlong_as_double((long long)((ex << 52) | frac));
+}
+
+// ---------------------------------------------------------------------------
+// Exact helpers that replace FP64 instructions (each FP64 instruction costs
+// tens of cycles of latency on GB300) by integer ones with identical results.
+// ---------------------------------------------------------------------------
+
+// (double)n for a 32-bit integer: positive values are normalised from their
+// bits; zero and negatives (which counts never are) use the conversion.
+__device__ __forceinline__ double i2d(int n) {
+  if (n <= 0) return (double)n;
+  const int p = 31 - __clz(n);
+  const unsigned long long frac =
+      ((unsigned long long)(unsigned)n << (52 - p)) & 0x000fffffffffffffull;
+  return __longlong_as_double((long long)(((unsigned long long)(p + 1023) << 52) | frac));
+}
+
+// Order-preserving integer key of a double (for non-NaN values, including
+// negatives): a < b  <=>  key(a) < key(b), except that -0 orders below +0.
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// x > 0 for a value that is not NaN (negative zero is not > 0).
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+
+// a <= b for two values that are not NaN and not negative.
+__device__ __forceinline__ bool le_nonneg(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -106,6 +142,14 @@ struct WordStream {
     c = 0;
     pos = 4;
   }
+  // Same stream with the first Philox block already computed (c = 0).
+  __device__ __forceinline__ void init_with_first(uint64_t seed, long long index, int rep,
+                                                  U4 first) {
+    init(seed, index, rep);
+    buf = first;
+    c = 1;
+    pos = 0;
+  }
   __device__ __forceinline__ uint32_t next() {
     if (pos == 4) {
       buf = philox10(U4{c, idx_lo, idx_hi, tag}, k0, k1);
@@ -137,32 +181,55 @@ struct WordStream {
 // ---------------------------------------------------------------------------
 template <int KIND> struct ModelTraits;
 
+// Each kind also has `prepare`, which evaluates once per node and day the
+// factors of its rates that do not change within the day (they depend on v
+// and gdata only), and `rate_k`, the same rate from those factors.  The
+// factors are the leftmost products of the written expressions, so the
+// values are identical to `rate`.
+
 // SIR, Eq. (SIR); operation order of the SIR rate listing (Appendix C).
 template <> struct ModelTraits<SG_SIR> {
-  static constexpr int C = 3, T = 2, NV = 0;
+  static constexpr int C = 3, T = 2, NV = 0, NK = 1;
+  __device__ static __forceinline__ void prepare(const double *, const double *, double *) {}
+  __device__ static __forceinline__ double rate_k(int j, const int *u, const double *,
+                                                  const double *g) {
+    return rate(j, u, nullptr, g);
+  }
   __device__ static __forceinline__ double rate(int j, const int *u, const double *,
                                                 const double *g) {
     if (j == 0) {
-      const double Sn = (double)u[0], In = (double)u[1];
-      const double n = Sn + In + (double)u[2];
-      return n > 0.0 ? (g[0] * Sn * In) / n : 0.0;
+      const double Sn = i2d(u[0]), In = i2d(u[1]);
+      const double n = Sn + In + i2d(u[2]);
+      return gt0(n) ? (g[0] * Sn * In) / n : 0.0;
     }
-    return g[1] * (double)u[1];
+    return g[1] * i2d(u[1]);
   }
 };
 
 // SIS of Sec. 2.1: [beta S I, gamma I].
 template <> struct ModelTraits<SG_SIS> {
-  static constexpr int C = 2, T = 2, NV = 0;
+  static constexpr int C = 2, T = 2, NV = 0, NK = 1;
+  __device__ static __forceinline__ void prepare(const double *, const double *, double *) {}
+  __device__ static __forceinline__ double rate_k(int j, const int *u, const double *,
+                                                  const double *g) {
+    return rate(j, u, nullptr, g);
+  }
   __device__ static __forceinline__ double rate(int j, const int *u, const double *,
                                                 const double *g) {
-    return j == 0 ? g[0] * (double)u[0] * (double)u[1] : g[1] * (double)u[1];
+    return j == 0 ? g[0] * i2d(u[0]) * i2d(u[1]) : g[1] * i2d(u[1]);
   }
 };
 
 // SISe (Sec. 4.2, no coupling): [upsilon phi S, gamma I].
 template <> struct ModelTraits<SG_SISE> {
-  static constexpr int C = 2, T = 2, NV = 1;
+  static constexpr int C = 2, T = 2, NV = 1, NK = 1;
+  __device__ static __forceinline__ void prepare(const double *v, const double *g, double *k) {
+    k[0] = g[0] * v[0];
+  }
+  __device__ static __forceinline__ double rate_k(int j, const int *u, const double *k,
+                                                  const double *g) {
+    return j == 0 ? k[0] * i2d(u[0]) : g[1] * i2d(u[1]);
+  }
   __device__ static __forceinline__ double rate(int j, const int *u, const double *v,
                                                 const double *g) {
     return j == 0 ? g[0] * v[0] * (double)u[0] : g[1] * (double)u[1];
@@ -172,7 +239,17 @@ template <> struct ModelTraits<SG_SISE> {
 // SISe3: transition 2a is S_a -> I_a at upsilon_a phi S_a, 2a + 1 is
 // I_a -> S_a at gamma_a I_a.
 template <> struct ModelTraits<SG_SISE3> {
-  static constexpr int C = 6, T = 6, NV = 1;
+  static constexpr int C = 6, T = 6, NV = 1, NK = 3;
+  __device__ static __forceinline__ void prepare(const double *v, const double *g, double *k) {
+    k[0] = g[0] * v[0];
+    k[1] = g[1] * v[0];
+    k[2] = g[2] * v[0];
+  }
+  __device__ static __forceinline__ double rate_k(int j, const int *u, const double *k,
+                                                  const double *g) {
+    const int a = j >> 1;
+    return (j & 1) == 0 ? k[a] * i2d(u[2 * a]) : g[3 + a] * i2d(u[2 * a + 1]);
+  }
   __device__ static __forceinline__ double rate(int j, const int *u, const double *v,
                                                 const double *g) {
     const int a = j >> 1;
@@ -180,15 +257,28 @@ template <> struct ModelTraits<SG_SISE3> {
   }
 };
 
-__device__ __forceinline__ bool bad_rate(double w) { return !(w >= 0.0) || isinf(w); }
+// !(w >= 0) || isinf(w) from the bits: bad unless w is -0 or a finite
+// value >= +0.
+__device__ __forceinline__ bool bad_rate(double w) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  return !(b == 0x8000000000000000ull || b < 0x7ff0000000000000ull);
+}
+
+// Season ends as integers: for an integer day d, d <= e exactly when
+// d <= floor(e) (any finite e); NaN ends never hold.
+__device__ __forceinline__ int season_end_int(double e) {
+  if (e >= 2147483647.0) return 0x7fffffff;
+  if (!(e >= -2147483648.0)) return (int)0x80000000;
+  return (int)floor(e);
+}
 
 // beta(t) of Sec. 4.2: season of day-of-year ((t - 1) mod 365) + 1 against
 // the node's season ends.
-__device__ __forceinline__ double season_decay(int t, const double *ld, const double *b4) {
+__device__ __forceinline__ double season_decay(int t, const int *ends, const double *b4) {
   int d = (t - 1) % 365;
   if (d < 0) d += 365;
-  const double doy = (double)(d + 1);
-  return doy <= ld[0] ? b4[0] : doy <= ld[1] ? b4[1] : doy <= ld[2] ? b4[2] : b4[3];
+  const int doy = d + 1;
+  return doy <= ends[0] ? b4[0] : doy <= ends[1] ? b4[1] : doy <= ends[2] ? b4[2] : b4[3];
 }
 
 // Post time step (PTSFun; Eq. numstep3 as one Euler step of length 1) for
@@ -196,33 +286,33 @@ __device__ __forceinline__ double season_decay(int t, const double *ld, const do
 // an empty node.  Returns 1 if phi changed, 0 if not, SG_ERR_PTS if the new
 // value is not finite.
 template <int KIND>
-__device__ __forceinline__ int post_step(double *v, const int *u, const double *ld,
+__device__ __forceinline__ int post_step(double *v, const int *u, const int *ends,
                                          const double *g, int t) {
   double I_tot, N_tot;
   const double *pg;
   if (KIND == SG_SISE) {
-    I_tot = (double)u[1];
-    N_tot = (double)u[0] + (double)u[1];
+    I_tot = i2d(u[1]);
+    N_tot = i2d(u[0]) + i2d(u[1]);
     pg = g + 2;
   } else if (KIND == SG_SISE3) {
     I_tot = 0.0;
     N_tot = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      I_tot = I_tot + (double)u[2 * a + 1];
-      N_tot = N_tot + (double)u[2 * a] + (double)u[2 * a + 1];
+      I_tot = I_tot + i2d(u[2 * a + 1]);
+      N_tot = N_tot + i2d(u[2 * a]) + i2d(u[2 * a + 1]);
     }
     pg = g + 6;
   } else {
     return 0;
   }
   const double phi = v[0];
-  const double shed = N_tot > 0.0 ? (pg[0] * I_tot) / N_tot : 0.0;
-  const double beta = season_decay(t, ld, pg + 1);
+  const double shed = gt0(N_tot) ? (pg[0] * I_tot) / N_tot : 0.0;
+  const double beta = season_decay(t, ends, pg + 1);
   const double nv = phi + (shed - beta * phi);
   v[0] = nv;
   if (!isfinite(nv)) return SG_ERR_PTS;
-  return nv != phi ? 1 : 0;
+  return __double_as_longlong(nv) != __double_as_longlong(phi) ? 1 : 0;
 }
 
 __device__ __forceinline__ void report(SgDevError *err, int code, int rep, int node,

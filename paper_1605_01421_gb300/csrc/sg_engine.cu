@@ -3,12 +3,11 @@
 // The split-step method of Sec. 2.3 runs as a chain of kernels on the
 // caller's stream:
 //   k_days<KIND>   one thread per (replicate, node): finishes the previous
-//                  unit step (post time step + recording), then runs the
-//                  direct SSA toward the next unit time point (Appendix A),
-//                  for a whole run of days that carry no scheduled events;
-//   k_events_e1    the exit / enter / internal-transfer events of a day, one
-//                  thread per (replicate, node) that has any, in the order of
-//                  Sec. 3.3;
+//                  unit step (post time step + recording), then per day runs
+//                  the direct SSA toward the next unit time point (Appendix A;
+//                  a warp takes over nodes that need many draws) and the
+//                  node's own exit / enter / internal-transfer events, for a
+//                  whole run of days without external transfers;
 //   k_events_e2    the external transfers of a day, one block per replicate,
 //                  wave by wave (a block barrier between waves);
 // and a last k_days launch finishes the final unit step.
@@ -31,12 +30,23 @@ using namespace sg;
 namespace {
 
 constexpr int kDayBlock = 128;
-constexpr int kE1Block = 128;
 constexpr int kE2Block = 256;
 
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
+
+// Events of the plan, structure of arrays in planned order (E1 part first).
+struct EvDev {
+  const int8_t *type;
+  const uint8_t *select;
+  const int8_t *shift;       // -1 = no shift
+  const int32_t *node, *dest, *n;
+  const double *proportion;
+  const int64_t *index;      // position in the caller's list (random stream key)
+  const int32_t *e1_day;     // day index of each E1 event
+  const int64_t *e1_node_off;  // [slots * Nn + 1]; nullptr when there are none
+};
 
 struct DayArgs {
   int *u;              // [R][Nn][C] working counts
@@ -45,141 +55,417 @@ struct DayArgs {
   int32_t *U;          // [R][M][Nn][C]
   double *V;           // [R][M][Nn][NV]
   const int32_t *rec;  // [days + 1]: tspan slot of T = t0 + i, or -1
-  int32_t t0, M, n_rep;
+  int32_t *e1_cur;     // [R][Nn]: next E1 event, relative to the node's list
+  EvDev ev;
+  int32_t t0, M, n_rep, slots;
   int32_t T_begin, T_end;  // SSA toward T = T_begin .. T_end - 1
   int32_t finish_first;    // finish unit step T_begin - 1 before the SSA
   int32_t finish_last;     // finish unit step T_end - 1 after the SSA
+  int32_t heavy_after;     // draws a thread takes before its warp takes over
+  int32_t npb;             // nodes per block (<= kDayBlock); the other
+                           // threads of the block only serve heavy nodes
   uint32_t k0, k1;         // Philox key (seed)
   SgDevError *err;
   SgCounters *cnt;
 };
 
+// One transition (Appendix A, inversion and update): the smallest n with
+// target <= running sum of the positive rates (last positive one if rounding
+// leaves none), u += S[, n], and the rates that column n of G marks are
+// recomputed.  Returns 0 or SG_ERR_RATE.
+template <int KIND>
+__device__ __forceinline__ int fire(int *u, double *w, double target, const double *kf,
+                                    const SgTables &tb) {
+  using M = ModelTraits<KIND>;
+  // running sum over the positive rates in index order; the first term is
+  // taken as is (0 + w == w exactly), the comparisons are exact integer
+  // comparisons of non-negative doubles
+  double cum = 0.0;
+  int n = -1, last = -1;
+#pragma unroll
+  for (int j = 0; j < M::T; ++j) {
+    if (n < 0 && gt0(w[j])) {
+      cum = last < 0 ? w[j] : cum + w[j];
+      last = j;
+      if (le_nonneg(target, cum)) n = j;
+    }
+  }
+  if (n < 0) n = last;
+#pragma unroll
+  for (int p = 0; p < M::C; ++p) u[p] += tb.S[n][p];
+  const uint32_t dep = tb.dep[n];
+  int code = 0;
+#pragma unroll
+  for (int k = 0; k < M::T; ++k) {
+    if ((dep >> k) & 1u) {
+      w[k] = M::rate_k(k, u, kf, tb.gdata);
+      if (bad_rate(w[k])) code = SG_ERR_RATE;
+    }
+  }
+  return code;
+}
+
+enum { SSA_DONE = 0, SSA_HEAVY = 1 };
+
+// Direct SSA of one node toward the unit time Tn in its own thread, for at
+// most `budget` draws (Appendix A, one iteration per draw).  Returns SSA_DONE,
+// SSA_HEAVY (budget spent, state and counter ready for the warp) or an error.
+template <int KIND>
+__device__ __forceinline__ int ssa_thread(int *u, double *w, const double *kf, double &t,
+                                          uint32_t &c, double Tn, uint32_t node, uint32_t Td,
+                                          uint32_t tag, uint32_t k0, uint32_t k1, int budget,
+                                          const SgTables &tb, unsigned long long &fired) {
+  using M = ModelTraits<KIND>;
+  const long long Tkey = order_key(Tn);
+  for (int b = 0;; ++b) {
+    // lambda = ((0 + w_1) + w_2) + ...; the leading 0 + w_1 changes no
+    // decision or value, so the sum starts at w_1
+    double lam = w[0];
+#pragma unroll
+    for (int j = 1; j < M::T; ++j) lam = lam + w[j];
+    if (!gt0(lam)) return SSA_DONE;  // nothing can fire: jump to Tn
+    if (c >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+    if (b == budget) return SSA_HEAVY;
+    const U4 x = philox10(U4{c, node, Td, tag}, k0, k1);
+    ++c;
+    const double r1 = u01_open(x.x, x.y);
+    const double r2 = u01_open(x.z, x.w);
+    const double tau = -log_pos(r1) / lam;
+    const double tt = t + tau;
+    if (order_key(tt) >= Tkey) return SSA_DONE;
+    t = tt;
+    const int rc = fire<KIND>(u, w, lam * r2, kf, tb);
+    ++fired;
+    if (rc) return rc;
+  }
+}
+
+// A node handed from its thread to a warp.
+template <int C, int NK>
+struct HeavySlot {
+  double t;
+  double kf[NK];
+  uint32_t c;
+  int32_t node, rep, code;
+  int32_t u[C];
+};
+
+// Direct SSA of one heavy node by a whole warp.  The draws depend only on
+// (seed, replicate, node, day, draw index), so lane l computes the Philox
+// words, uniforms and logarithm of draw c0 + l for 32 draws at once; the
+// sequential part (waiting time, boundary test, transition) then runs on all
+// lanes in step, reading draw j from lane j.  The transition for a draw is
+// evaluated alongside the waiting-time division and kept only if the draw
+// falls before Tn.  Same operations, in the same order, as ssa_thread.
+template <int KIND>
+__device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> &hs, double Tn,
+                         uint32_t Td, uint32_t k0, uint32_t k1, const SgTables &tb,
+                         unsigned long long &fired, unsigned long long &drawn) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NK = M::NK;
+  const int lane = threadIdx.x & 31;
+  int u[C];
+  double kf[NK], w[T];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = hs.u[p];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) kf[i] = hs.kf[i];
+  double t = hs.t;
+  uint32_t c = hs.c;
+  const uint32_t c_in = c, node = (uint32_t)hs.node;
+  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)hs.rep;
+  int code = 0;
+#pragma unroll
+  for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
+  uint32_t c0 = c;
+  double nE = 0.0, r2 = 0.0;
+  bool have = false;
+  unsigned long long f = 0;
+  const long long Tkey = order_key(Tn);
+  for (;;) {
+    double lam = w[0];
+#pragma unroll
+    for (int j = 1; j < T; ++j) lam = lam + w[j];
+    if (!gt0(lam)) break;
+    if (c >= SG_MAX_DRAWS) {
+      code = SG_ERR_STEP_LIMIT;
+      break;
+    }
+    if (!have || c - c0 >= 32u) {
+      c0 = c;
+      const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+      nE = -log_pos(u01_open(x.x, x.y));
+      r2 = u01_open(x.z, x.w);
+      have = true;
+    }
+    const int jj = (int)(c - c0);
+    const double E = __shfl_sync(0xffffffffu, nE, jj);
+    const double R2 = __shfl_sync(0xffffffffu, r2, jj);
+    ++c;
+    const double tau = E / lam;
+    int u2[C];
+    double w2[T];
+#pragma unroll
+    for (int p = 0; p < C; ++p) u2[p] = u[p];
+#pragma unroll
+    for (int j = 0; j < T; ++j) w2[j] = w[j];
+    const int rc = fire<KIND>(u2, w2, lam * R2, kf, tb);
+    const double tt = t + tau;
+    if (order_key(tt) >= Tkey) break;
+    t = tt;
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = u2[p];
+#pragma unroll
+    for (int j = 0; j < T; ++j) w[j] = w2[j];
+    ++f;
+    if (rc) {
+      code = rc;
+      break;
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+    hs.c = c;
+    hs.code = code;
+    fired += f;
+    drawn += c - c_in;
+  }
+  __syncwarp();
+}
+
+// One E1 event (exit, enter or internal transfer, Sec. 3.3) on a node whose
+// counts are in the calling thread's registers.  Returns 0 or an error.
+template <int C>
+__device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const EvDev &ev, long long j,
+                                        int rep, uint32_t k0, uint32_t k1) {
+  const int type = ev.type[j];
+  const uint32_t mask = tb.Emask[ev.select[j]];
+  const int n = ev.n[j];
+  if (type == SG_ENTER) {
+    const int first = __ffs(mask) - 1;  // first selected compartment
+#pragma unroll
+    for (int p = 0; p < C; ++p)
+      if (p == first) u[p] += n;
+    return 0;
+  }
+  long long total = 0;
+#pragma unroll
+  for (int p = 0; p < C; ++p)
+    if ((mask >> p) & 1u) total += u[p];
+  const long long k = n > 0 ? (long long)n : (long long)round(ev.proportion[j] * (double)total);
+  if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
+  int moved[C];
+#pragma unroll
+  for (int p = 0; p < C; ++p) moved[p] = 0;
+  if (k > 0) {
+    WordStream ws;
+    ws.init(((uint64_t)k1 << 32) | k0, ev.index[j], rep);
+    for (long long i = 0; i < k; ++i) {
+      uint32_t x = ws.below((uint32_t)(total - i));
+      bool taken = false;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        if (taken || !((mask >> p) & 1u)) continue;
+        const uint32_t rem = (uint32_t)(u[p] - moved[p]);
+        if (x < rem) {
+          ++moved[p];
+          taken = true;
+        } else {
+          x -= rem;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] -= moved[p];
+  if (type == SG_EXIT) return 0;
+  const int q = ev.shift[j];  // internal transfer: validated q >= 0
+#pragma unroll
+  for (int dst = 0; dst < C; ++dst) {
+    int add = 0;
+#pragma unroll
+    for (int p = 0; p < C; ++p)
+      if (p + tb.Nsh[q][p] == dst) add += moved[p];
+    u[dst] += add;
+  }
+  return 0;
+}
+
+// Post time step and recording for unit time Tf (the state after its
+// events).  Returns 0 or SG_ERR_PTS.
+template <int KIND>
+__device__ __forceinline__ int finish_step(int Tf, const int *u, double *v, const int *ends,
+                                           const SgTables &tb, const DayArgs &a, int rep,
+                                           int node) {
+  using M = ModelTraits<KIND>;
+  int code = 0;
+  if (M::NV > 0) {
+    const int r = post_step<KIND>(v, u, ends, tb.gdata, Tf);
+    if (r < 0) code = r;
+  }
+  const int m = a.rec[Tf - a.t0];
+  if (m >= 0) {
+    const long long base = ((long long)rep * a.M + m) * tb.n_nodes + node;
+#pragma unroll
+    for (int p = 0; p < M::C; ++p) a.U[base * M::C + p] = u[p];
+#pragma unroll
+    for (int q = 0; q < M::NV; ++q) a.V[base * M::NV + q] = v[q];
+  }
+  return code;
+}
+
+// The day kernel: one thread per (replicate, node) for a run of days
+// T_begin .. T_end - 1 with no external transfers before T_end - 1.  Per day:
+// rates, SSA (thread, then warp for heavy nodes), the node's E1 events, and
+// (unless a kernel boundary follows) the post time step and recording.
 template <int KIND>
 __global__ void __launch_bounds__(kDayBlock)
 k_days(const SgTables tb, const DayArgs a) {
   using M = ModelTraits<KIND>;
-  constexpr int C = M::C, T = M::T, NV = M::NV;
+  constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
+  __shared__ HeavySlot<C, NK> s_heavy[kDayBlock];
+  __shared__ int s_nheavy;
   const int Nn = tb.n_nodes;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gid = (long long)blockIdx.x * a.npb + threadIdx.x;
   const long long total = (long long)Nn * a.n_rep;
-  unsigned long long fired = 0, drawn = 0;
-  if (gid < total && *(volatile int32_t *)&a.err->code == 0) {
-    const int rep = (int)(gid / Nn);
-    const int node = (int)(gid - (long long)rep * Nn);
-    int u[C];
-    double v[NV > 0 ? NV : 1];
-    double ld[4] = {0.0, 0.0, 0.0, 0.0};
+  const bool live = (int)threadIdx.x < a.npb && gid < total &&
+                    *(volatile int32_t *)&a.err->code == 0;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  unsigned long long fired = 0, drawn = 0, applied = 0;
+  int rep = 0, node = 0, code = 0, bad_day = 0;
+  long long bad_event = -1;
+  int u[C];
+  double v[NV > 0 ? NV : 1];
+  int ld[4] = {0, 0, 0, 0};  // season ends of the node (integer form)
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = 0;
+  v[0] = 0.0;
+  long long ecur = 0, ebase = 0, eend = 0;
+  int next_day = 0x7fffffff;
+  if (live) {
+    rep = (int)(gid / Nn);
+    node = (int)(gid - (long long)rep * Nn);
 #pragma unroll
     for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
     if (NV > 0) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) ld[i] = a.ldata[(long long)node * tb.n_ldata + i];
+      for (int i = 0; i < 4; ++i)
+        ld[i] = season_end_int(a.ldata[(long long)node * tb.n_ldata + i]);
     }
-    const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
-    int code = 0, bad_day = 0;
-
-    // finish unit step Tf: post time step on the state after its events,
-    // then record if Tf is a tspan point
-    auto finish = [&](int Tf) {
-      if (NV > 0) {
-        const int r = post_step<KIND>(v, u, ld, tb.gdata, Tf);
-        if (r < 0 && code == 0) { code = r; bad_day = Tf; }
-      }
-      const int m = a.rec[Tf - a.t0];
-      if (m >= 0) {
-        const long long base = ((long long)rep * a.M + m) * Nn + node;
-#pragma unroll
-        for (int p = 0; p < C; ++p) a.U[base * C + p] = u[p];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) a.V[base * NV + q] = v[q];
-      }
-    };
-
-    if (a.finish_first) finish(a.T_begin - 1);
-    for (int Td = a.T_begin; Td < a.T_end && code == 0; ++Td) {
-      // rates at the start of the day (Appendix A step "compute transition
-      // rates"); recomputed every day so events and the post time step are
-      // always seen
-      double w[T];
+    if (a.ev.e1_node_off) {
+      const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
+      ebase = a.ev.e1_node_off[key];
+      eend = a.ev.e1_node_off[key + 1];
+      ecur = ebase + a.e1_cur[gid];
+      if (ecur < eend) next_day = a.ev.e1_day[ecur];
+    }
+    if (a.finish_first) {
+      code = finish_step<KIND>(a.T_begin - 1, u, v, ld, tb, a, rep, node);
+      if (code) bad_day = a.T_begin - 1;
+    }
+  }
+  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
+  for (int Td = a.T_begin; Td < a.T_end; ++Td) {
+    const double Tn = (double)Td;
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
+    int my = -1;
+    if (live && code == 0) {
+      double kf[NK], w[T];
+      M::prepare(v, tb.gdata, kf);
 #pragma unroll
       for (int j = 0; j < T; ++j) {
-        w[j] = M::rate(j, u, v, tb.gdata);
+        w[j] = M::rate_k(j, u, kf, tb.gdata);
         if (bad_rate(w[j])) code = SG_ERR_RATE;
       }
-      if (code) { bad_day = Td; break; }
-      double t = (double)(Td - 1);
-      const double Tn = (double)Td;
-      uint32_t c = 0;
-      for (;;) {
-        double lam = 0.0;
+      if (code == 0) {
+        double t = (double)(Td - 1);
+        uint32_t c = 0;
+        const int r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag,
+                                       a.k0, a.k1, a.heavy_after, tb, fired);
+        drawn += c;
+        if (r == SSA_HEAVY) {
+          my = atomicAdd(&s_nheavy, 1);
+          HeavySlot<C, NK> &hs = s_heavy[my];
+          hs.t = t;
 #pragma unroll
-        for (int j = 0; j < T; ++j) lam = lam + w[j];
-        if (!(lam > 0.0)) break;  // nothing can fire: jump to Td
-        if (c >= SG_MAX_DRAWS) {  // bound on run time, see SG_ERR_STEP_LIMIT
-          code = SG_ERR_STEP_LIMIT;
+          for (int i = 0; i < NK; ++i) hs.kf[i] = kf[i];
+          hs.c = c;
+          hs.node = node;
+          hs.rep = rep;
+          hs.code = 0;
+#pragma unroll
+          for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+        } else if (r < 0) {
+          code = r;
+        }
+      }
+      if (code) bad_day = Td;
+    }
+    __syncthreads();
+    const int nh = s_nheavy;
+    for (int h = warp; h < nh; h += nwarps)
+      ssa_warp<KIND>(s_heavy[h], Tn, (uint32_t)Td, a.k0, a.k1, tb, fired, drawn);
+    __syncthreads();
+    if (my >= 0) {
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = s_heavy[my].u[p];
+      if (s_heavy[my].code) {
+        code = s_heavy[my].code;
+        bad_day = Td;
+      }
+    }
+    // this node's E1 events of day Td, in (time, type, list index) order
+    const int d = Td - a.t0 - 1;
+    if (live && code == 0 && next_day == d) {
+      while (ecur < eend && a.ev.e1_day[ecur] == d) {
+        const int rc = apply_e1<C>(u, tb, a.ev, ecur, rep, a.k0, a.k1);
+        if (rc) {
+          code = rc;
           bad_day = Td;
+          bad_event = a.ev.index[ecur];
           break;
         }
-        const U4 x = philox10(U4{c, (uint32_t)node, (uint32_t)Td, tag}, a.k0, a.k1);
-        ++c;
-        const double r1 = u01_open(x.x, x.y);
-        const double r2 = u01_open(x.z, x.w);
-        const double tau = -log_pos(r1) / lam;
-        if (t + tau >= Tn) break;
-        t = t + tau;
-        // inversion over the positive rates in index order
-        const double target = lam * r2;
-        double cum = 0.0;
-        int n = -1, last = -1;
-#pragma unroll
-        for (int j = 0; j < T; ++j) {
-          if (n < 0 && w[j] > 0.0) {
-            cum = cum + w[j];
-            last = j;
-            if (target <= cum) n = j;
-          }
-        }
-        if (n < 0) n = last;
-#pragma unroll
-        for (int p = 0; p < C; ++p) u[p] += tb.S[n][p];
-        const uint32_t dep = tb.dep[n];
-#pragma unroll
-        for (int k = 0; k < T; ++k) {
-          if ((dep >> k) & 1u) {
-            w[k] = M::rate(k, u, v, tb.gdata);
-            if (bad_rate(w[k])) code = SG_ERR_RATE;
-          }
-        }
-        ++fired;
-        if (code) { bad_day = Td; break; }
+        ++applied;
+        ++ecur;
       }
-      drawn += c;
-      if (code) break;
-      if (Td + 1 < a.T_end || a.finish_last) finish(Td);
-      if (code) break;
+      next_day = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
     }
-    if (code) report(a.err, code, rep, node, bad_day, -1);
+    if (live && code == 0 && (Td + 1 < a.T_end || a.finish_last)) {
+      code = finish_step<KIND>(Td, u, v, ld, tb, a, rep, node);
+      if (code) bad_day = Td;
+    }
+  }
+  if (live) {
+    if (code) report(a.err, code, rep, node, bad_day, bad_event);
 #pragma unroll
     for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
 #pragma unroll
     for (int q = 0; q < NV; ++q) a.v[gid * NV + q] = v[q];
+    if (a.ev.e1_node_off) a.e1_cur[gid] = (int32_t)(ecur - ebase);
   }
-  // one atomic per warp for the reaction and draw counts
+  // one atomic per warp for the counters
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     fired += __shfl_down_sync(0xffffffffu, fired, off);
     drawn += __shfl_down_sync(0xffffffffu, drawn, off);
+    applied += __shfl_down_sync(0xffffffffu, applied, off);
   }
-  if ((threadIdx.x & 31) == 0 && drawn) {
-    atomicAdd(&a.cnt->reactions, fired);
-    atomicAdd(&a.cnt->draws, drawn);
+  if ((threadIdx.x & 31) == 0) {
+    if (drawn) {
+      atomicAdd(&a.cnt->reactions, fired);
+      atomicAdd(&a.cnt->draws, drawn);
+    }
+    if (applied) atomicAdd(&a.cnt->events, applied);
   }
 }
 
 struct EvArgs {
-  SgEventsDev ev;
+  EvDev ev;
   int *u;
   int32_t n_rep;
   uint32_t k0, k1;
@@ -188,114 +474,165 @@ struct EvArgs {
   SgCounters *cnt;
 };
 
-// Apply event j for replicate rep.  `atomic_dest` selects atomic additions
-// into the destination (several external transfers of one wave may share a
-// destination).  Returns 0 or an error code.
-__device__ int apply_event(const SgTables &tb, const EvArgs &a, long long j, int rep,
-                           bool atomic_dest) {
-  const int C = tb.n_comp;
-  const int type = a.ev.type[j];
-  const uint32_t mask = tb.Emask[a.ev.select[j]];
-  int *un = a.u + ((long long)rep * tb.n_nodes + a.ev.node[j]) * C;
-  if (type == SG_ENTER) {
-    un[__ffs(mask) - 1] += a.ev.n[j];  // first selected compartment
-    return 0;
+// Block-wide copy of n 32-bit words with 16-byte accesses where both ends
+// are aligned, several loads in flight per thread.
+__device__ __forceinline__ void copy_words(int *dst, const int *src, int n) {
+  int head = 0;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const int n4 = n >> 2;
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+    head = n4 << 2;
   }
-  long long total = 0;
-  for (int p = 0; p < C; ++p)
-    if ((mask >> p) & 1u) total += un[p];
-  const long long k = a.ev.n[j] > 0 ? (long long)a.ev.n[j]
-                                    : (long long)round(a.ev.proportion[j] * (double)total);
-  if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
-  int moved[SG_MAX_COMP];
-  for (int p = 0; p < C; ++p) moved[p] = 0;
-  if (k > 0) {
-    // urn: one uniform position among the remaining individuals per draw,
-    // resolved in compartment order
-    WordStream ws;
-    ws.init(((uint64_t)a.k1 << 32) | a.k0, a.ev.index[j], rep);
-    for (long long i = 0; i < k; ++i) {
-      uint32_t x = ws.below((uint32_t)(total - i));
-      for (int p = 0; p < C; ++p) {
-        if (!((mask >> p) & 1u)) continue;
-        const uint32_t rem = (uint32_t)(un[p] - moved[p]);
-        if (x < rem) {
-          ++moved[p];
-          break;
-        }
-        x -= rem;
-      }
-    }
-  }
-  for (int p = 0; p < C; ++p) un[p] -= moved[p];
-  if (type == SG_EXIT) return 0;
-  const int q = a.ev.shift[j];
-  int *ut = type == SG_INTERNAL_TRANSFER
-                ? un
-                : a.u + ((long long)rep * tb.n_nodes + a.ev.dest[j]) * C;
-  for (int p = 0; p < C; ++p) {
-    if (moved[p] == 0) continue;
-    const int to = q >= 0 ? p + tb.Nsh[q][p] : p;
-    if (atomic_dest && type == SG_EXTERNAL_TRANSFER)
-      atomicAdd(ut + to, moved[p]);
-    else
-      ut[to] += moved[p];
-  }
-  return 0;
+#pragma unroll 4
+  for (int i = head + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
-// E1 events of one day: positions [begin, begin + count) of the planned
-// order, sorted by (slot, node, time, type, index).  Thread (r, i) handles
-// position i for replicate r (r only varies when every replicate runs the
-// same events) if i starts a node's run, and then walks that run.
-__global__ void __launch_bounds__(kE1Block)
-k_events_e1(const SgTables tb, const EvArgs a, long long begin, long long count,
-            int rep_threads) {
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= count * rep_threads) return;
-  if (*(volatile int32_t *)&a.err->code != 0) return;
-  const int rthread = (int)(gid / count);
-  const long long i = begin + (gid - (long long)rthread * count);
-  const int node = a.ev.node[i];
-  const int erep = a.ev.rep[i];
-  if (i > begin && a.ev.node[i - 1] == node && a.ev.rep[i - 1] == erep) return;
-  const int rep = erep >= 0 ? erep : rthread;
-  const long long end = begin + count;
-  unsigned long long applied = 0;
-  for (long long j = i; j < end && a.ev.node[j] == node && a.ev.rep[j] == erep; ++j) {
-    const int rc = apply_event(tb, a, j, rep, false);
-    if (rc) {
-      report(a.err, rc, rep, node, a.day, a.ev.index[j]);
-      break;
-    }
-    ++applied;
-  }
-  atomicAdd(&a.cnt->events, applied);
-}
+constexpr int kE2Cap = 512;      // events staged in shared memory per chunk
+constexpr int kE2WaveCap = 128;  // wave bounds staged per chunk
 
-// E2 events of one day: block r runs replicate r's waves in order.
+// E2 events of one day: block r runs replicate r's external transfers
+// (Sec. 3.3) wave by wave, with a block barrier between waves.  The block
+// first stages a chunk of events in shared memory together with the first
+// Philox block of each event's random stream (which does not depend on the
+// state); with SMEM_STATE the replicate's whole node state is also held in
+// shared memory for the day.  Several transfers of one wave may share a
+// destination, so additions are atomic; a wave never samples a node that
+// another event of the wave touches.
+template <int KIND, bool SMEM_STATE>
 __global__ void __launch_bounds__(kE2Block)
 k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_ev,
             long long w_begin_shared, long long w_end_shared,
             const int64_t *__restrict__ wave_off, int day_index, int slots) {
+  constexpr int C = ModelTraits<KIND>::C;
+  extern __shared__ __align__(16) int s_state[];
+  __shared__ int32_t s_node[kE2Cap], s_dest[kE2Cap], s_n[kE2Cap];
+  __shared__ uint8_t s_sel[kE2Cap];
+  __shared__ int8_t s_shift[kE2Cap];
+  __shared__ long long s_idx[kE2Cap];
+  __shared__ double s_prop[kE2Cap];
+  __shared__ uint4 s_w[kE2Cap];
+  __shared__ long long s_wave[kE2WaveCap + 1];
+  __shared__ int s_stop;
   const int rep = blockIdx.x;
+  const int Nn = tb.n_nodes;
   long long w0 = w_begin_shared, w1 = w_end_shared;
   if (slots > 1) {
     w0 = wave_off[(long long)day_index * slots + rep];
     w1 = wave_off[(long long)day_index * slots + rep + 1];
   }
+  if (w0 >= w1 || *(volatile int32_t *)&a.err->code != 0) return;
+  int *gstate = a.u + (long long)rep * Nn * C;
+  int *state = gstate;
+  if (SMEM_STATE) {
+    copy_words(s_state, gstate, Nn * C);
+    state = s_state;
+  }
+  if (threadIdx.x == 0) s_stop = 0;
+  const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
+  const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
   unsigned long long applied = 0;
-  for (long long w = w0; w < w1; ++w) {
-    const long long e0 = wave_ev[w], e1 = wave_ev[w + 1];
-    for (long long j = e0 + threadIdx.x; j < e1; j += blockDim.x) {
-      if (*(volatile int32_t *)&a.err->code != 0) break;
-      const int rc = apply_event(tb, a, j, rep, true);
-      if (rc)
-        report(a.err, rc, rep, a.ev.node[j], a.day, a.ev.index[j]);
-      else
-        ++applied;
+  long long w = w0;
+  long long pos = wave_ev[w0];
+  const long long pos_end = wave_ev[w1];
+  while (pos < pos_end) {
+    // stage the bounds of the next waves, then the events [pos, pend) they
+    // hold (at most kE2Cap; a wave may continue into the next chunk)
+    const long long wn = min(w1 - w, (long long)kE2WaveCap);
+    __syncthreads();
+    for (long long i = threadIdx.x; i <= wn; i += blockDim.x) s_wave[i] = wave_ev[w + i];
+    __syncthreads();
+    const long long pend = min(pos + (long long)kE2Cap, s_wave[wn]);
+    for (long long i = threadIdx.x; i < pend - pos; i += blockDim.x) {
+      const long long j = pos + i;
+      s_node[i] = a.ev.node[j];
+      s_dest[i] = a.ev.dest[j];
+      s_n[i] = a.ev.n[j];
+      s_sel[i] = a.ev.select[j];
+      s_shift[i] = a.ev.shift[j];
+      s_prop[i] = a.ev.proportion[j];
+      const long long idx = a.ev.index[j];
+      s_idx[i] = idx;
+      const U4 f = philox10(U4{0u, (uint32_t)(unsigned long long)idx,
+                               (uint32_t)((unsigned long long)idx >> 32), tag},
+                            a.k0, a.k1);
+      s_w[i] = make_uint4(f.x, f.y, f.z, f.w);
     }
     __syncthreads();
+    // waves w .. (staged) intersecting [pos, pend)
+    long long wi = 0;
+    while (wi < wn && s_wave[wi] < pend) {
+      const long long lo = max(pos, s_wave[wi]), hi = min(pend, s_wave[wi + 1]);
+      for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+        const int i = (int)(q - pos);
+        const int src = s_node[i];
+        int *un = state + (long long)src * C;
+        const uint32_t mask = tb.Emask[s_sel[i]];
+        int cur[C];
+        long long total = 0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          cur[p] = un[p];
+          if ((mask >> p) & 1u) total += cur[p];
+        }
+        const long long k = s_n[i] > 0 ? (long long)s_n[i]
+                                       : (long long)round(s_prop[i] * (double)total);
+        if (k < 0 || k > total) {
+          report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, a.day, s_idx[i]);
+          s_stop = 1;
+          continue;
+        }
+        int moved[C];
+#pragma unroll
+        for (int p = 0; p < C; ++p) moved[p] = 0;
+        if (k > 0) {
+          WordStream ws;
+          const uint4 f = s_w[i];
+          ws.init_with_first(seed, s_idx[i], rep, U4{f.x, f.y, f.z, f.w});
+          for (long long d = 0; d < k; ++d) {
+            uint32_t x = ws.below((uint32_t)(total - d));
+            bool taken = false;
+#pragma unroll
+            for (int p = 0; p < C; ++p) {
+              if (taken || !((mask >> p) & 1u)) continue;
+              const uint32_t rem = (uint32_t)(cur[p] - moved[p]);
+              if (x < rem) {
+                ++moved[p];
+                taken = true;
+              } else {
+                x -= rem;
+              }
+            }
+          }
+        }
+        const int q_sh = s_shift[i];
+        int *ud = state + (long long)s_dest[i] * C;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          if (moved[p] == 0) continue;
+          un[p] = cur[p] - moved[p];
+        }
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          if (moved[p] == 0) continue;
+          atomicAdd(ud + (q_sh >= 0 ? p + tb.Nsh[q_sh][p] : p), moved[p]);
+        }
+        ++applied;
+      }
+      __syncthreads();
+      if (s_stop) break;
+      if (s_wave[wi + 1] <= pend) ++wi;
+      else break;  // the wave continues in the next chunk
+    }
+    if (s_stop) break;
+    w += wi;
+    pos = pend;
+  }
+  if (SMEM_STATE) {
+    __syncthreads();
+    copy_words(gstate, s_state, Nn * C);
   }
   if (applied) atomicAdd(&a.cnt->events, applied);
 }
@@ -419,10 +756,13 @@ struct sg_model {
   Plan plan;
   DevBuf<int8_t> e_type, e_shift;
   DevBuf<uint8_t> e_select;
-  DevBuf<int32_t> e_node, e_dest, e_n, e_rep;
+  DevBuf<int32_t> e_node, e_dest, e_n, e1_day;
   DevBuf<double> e_prop;
-  DevBuf<int64_t> e_index, wave_ev, wave_off;
+  DevBuf<int64_t> e_index, wave_ev, wave_off, e1_node_off;
+  int32_t heavy_after = -1;  // draws a thread takes before its warp takes
+  int32_t npb = -1;          // nodes per block; -1 = chosen from the size
   // working memory
+  DevBuf<int32_t> e1_cur;
   DevBuf<int> u;
   DevBuf<double> v;
   DevBuf<int32_t> rec;
@@ -533,7 +873,8 @@ extern "C" void sg_model_destroy(sg_model *m) {
   if (!m) return;
   m->ldata.release();
   m->e_type.release(); m->e_shift.release(); m->e_select.release();
-  m->e_node.release(); m->e_dest.release(); m->e_n.release(); m->e_rep.release();
+  m->e_node.release(); m->e_dest.release(); m->e_n.release(); m->e1_day.release();
+  m->e1_node_off.release(); m->e1_cur.release();
   m->e_prop.release(); m->e_index.release(); m->wave_ev.release(); m->wave_off.release();
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
@@ -589,7 +930,7 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
   const size_t n = P.order.size();
   std::vector<int8_t> type(n), shift(n);
   std::vector<uint8_t> sel(n);
-  std::vector<int32_t> nd(n), ds(n), cnt(n), rp(n);
+  std::vector<int32_t> nd(n), ds(n), cnt(n);
   std::vector<double> prop(n);
   std::vector<int64_t> idx(n);
   const EventTable &ev = m->ev;
@@ -601,25 +942,33 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
     nd[i] = ev.node[e];
     ds[i] = ev.dest[e];
     cnt[i] = ev.n[e];
-    rp[i] = ev.per_rep ? ev.rep[e] : -1;
     prop[i] = ev.proportion[e];
     idx[i] = e;
   }
   if ((rc = upload(m->e_type, type)) || (rc = upload(m->e_shift, shift)) ||
       (rc = upload(m->e_select, sel)) || (rc = upload(m->e_node, nd)) ||
       (rc = upload(m->e_dest, ds)) || (rc = upload(m->e_n, cnt)) ||
-      (rc = upload(m->e_rep, rp)) || (rc = upload(m->e_prop, prop)) ||
-      (rc = upload(m->e_index, idx)) || (rc = upload(m->wave_ev, P.wave_ev)) ||
-      (rc = upload(m->wave_off, P.e2_wave_off)))
+      (rc = upload(m->e_prop, prop)) || (rc = upload(m->e_index, idx)) ||
+      (rc = upload(m->wave_ev, P.wave_ev)) || (rc = upload(m->wave_off, P.e2_wave_off)) ||
+      (rc = upload(m->e1_day, P.e1_day)) || (rc = upload(m->e1_node_off, P.e1_node_off)))
     return rc;
   m->plan_ok = true;
   return SG_OK;
 }
 
+// Nodes per block when not tuned: fill about two blocks per SM for small
+// problems (so heavy nodes spread over many SMs and warps), full blocks
+// otherwise.
+static int32_t default_npb(long long units) {
+  int32_t npb = kDayBlock;
+  while (npb > 16 && (units + npb - 1) / npb < 2 * 152) npb >>= 1;
+  return npb;
+}
+
 template <int KIND>
 static void launch_days(sg_model *m, const DayArgs &a, cudaStream_t st) {
-  const long long threads = (long long)m->tb.n_nodes * a.n_rep;
-  const unsigned grid = (unsigned)std::max<long long>(1, (threads + kDayBlock - 1) / kDayBlock);
+  const long long units = (long long)m->tb.n_nodes * a.n_rep;
+  const unsigned grid = (unsigned)std::max<long long>(1, (units + a.npb - 1) / a.npb);
   k_days<KIND><<<grid, kDayBlock, 0, st>>>(m->tb, a);
 }
 
@@ -654,6 +1003,41 @@ struct LaunchTimer {
     m->ev_used += 2;
   }
 };
+
+// The E2 kernel keeps the replicate's node state in shared memory when it
+// is at most this large.
+constexpr size_t kE2SmemStateMax = 64 * 1024;
+
+template <int KIND>
+static void launch_e2(sg_model *m, const EvArgs &ea, long long wb, long long we, int day,
+                      int slots, int n_rep, cudaStream_t st) {
+  const size_t bytes = sizeof(int) * (size_t)m->tb.n_nodes * ModelTraits<KIND>::C;
+  if (bytes <= kE2SmemStateMax) {
+    static unsigned long long attr_set = 0;  // one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !((attr_set >> dev) & 1ull)) {
+      cudaFuncSetAttribute(k_events_e2<KIND, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kE2SmemStateMax);
+      attr_set |= 1ull << dev;
+    }
+    k_events_e2<KIND, true><<<(unsigned)n_rep, kE2Block, bytes, st>>>(
+        m->tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, day, slots);
+  } else {
+    k_events_e2<KIND, false><<<(unsigned)n_rep, kE2Block, 0, st>>>(
+        m->tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, day, slots);
+  }
+}
+
+static void launch_e2_kind(sg_model *m, const EvArgs &ea, long long wb, long long we, int day,
+                           int slots, int n_rep, cudaStream_t st) {
+  switch (m->tb.kind) {
+    case SG_SIR: launch_e2<SG_SIR>(m, ea, wb, we, day, slots, n_rep, st); break;
+    case SG_SIS: launch_e2<SG_SIS>(m, ea, wb, we, day, slots, n_rep, st); break;
+    case SG_SISE: launch_e2<SG_SISE>(m, ea, wb, we, day, slots, n_rep, st); break;
+    default: launch_e2<SG_SISE3>(m, ea, wb, we, day, slots, n_rep, st); break;
+  }
+}
 
 static void fill_error(sg_error *err, int code, int rep, int node, int day, int64_t ev) {
   if (!err) return;
@@ -690,14 +1074,15 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
   if ((rc = m->u.ensure((size_t)(per_rep_u * n_rep))) ||
       (rc = m->v.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))) ||
-      (rc = m->rec.ensure((size_t)days + 1)))
+      (rc = m->e1_cur.ensure((size_t)Nn * n_rep)) || (rc = m->rec.ensure((size_t)days + 1)))
     return rc;
   std::vector<int32_t> rec(days + 1, -1);
   for (int i = 0; i < n_tspan; ++i) rec[tspan[i] - t0] = i;
   if (cudaMemcpyAsync(m->rec.p, rec.data(), rec.size() * sizeof(int32_t),
                       cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st) != cudaSuccess ||
-      cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st) != cudaSuccess) {
+      cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st) != cudaSuccess ||
+      cudaMemsetAsync(m->e1_cur.p, 0, sizeof(int32_t) * (size_t)Nn * n_rep, st) != cudaSuccess) {
     cudaGetLastError();
     return SG_ERR_CUDA;
   }
@@ -713,6 +1098,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     ++launches;
   }
 
+  const EvDev evd{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
+                  m->e_n.p,    m->e_prop.p,   m->e_index.p, m->e1_day.p,
+                  P.n_e1 > 0 ? m->e1_node_off.p : nullptr};
   DayArgs da;
   da.u = m->u.p;
   da.v = m->v.p;
@@ -720,17 +1108,21 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.U = d_U;
   da.V = d_V;
   da.rec = m->rec.p;
+  da.e1_cur = m->e1_cur.p;
+  da.ev = evd;
   da.t0 = t0;
   da.M = n_tspan;
   da.n_rep = n_rep;
+  da.slots = slots;
+  da.heavy_after = m->heavy_after >= 0 ? m->heavy_after : 2;
+  da.npb = m->npb > 0 ? m->npb : default_npb((long long)Nn * n_rep);
   da.k0 = (uint32_t)seed;
   da.k1 = (uint32_t)(seed >> 32);
   da.err = m->err.p;
   da.cnt = m->cnt.p;
 
   EvArgs ea;
-  ea.ev = SgEventsDev{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
-                      m->e_n.p, m->e_prop.p, m->e_index.p, m->e_rep.p};
+  ea.ev = evd;
   ea.u = m->u.p;
   ea.n_rep = n_rep;
   ea.k0 = da.k0;
@@ -743,40 +1135,30 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     bool pending = false;  // the previous unit step still needs finishing
     int32_t d = 0;
     while (d < days) {
+      // days d .. last run in one kernel; only `last` may have external
+      // transfers, which need every node's state first
       int32_t last = d;
-      while (last < days - 1 && !P.day_has_events[last]) ++last;
-      const bool ev_today = P.day_has_events[last] != 0;
+      while (last < days - 1 && !P.day_has_e2[last]) ++last;
+      const bool e2_today = P.day_has_e2[last] != 0;
       da.T_begin = t0 + 1 + d;
       da.T_end = t0 + 1 + last + 1;
       da.finish_first = pending ? 1 : 0;
-      da.finish_last = ev_today ? 0 : 1;
+      da.finish_last = e2_today ? 0 : 1;
       {
         LaunchTimer lt(m, st, 0);
         launch_days_kind(m, da, st);
       }
       ++launches;
-      if (ev_today) {
+      if (e2_today) {
         ea.day = t0 + 1 + last;
         const long long b0 = (long long)last * slots, b1 = b0 + slots;
-        const long long e1b = P.e1_off[b0], e1n = P.e1_off[b1] - e1b;
-        if (e1n > 0) {
-          const int rep_threads = slots > 1 ? 1 : n_rep;
-          const long long th = e1n * rep_threads;
-          LaunchTimer lt(m, st, 1);
-          k_events_e1<<<(unsigned)((th + kE1Block - 1) / kE1Block), kE1Block, 0, st>>>(
-              tb, ea, e1b, e1n, rep_threads);
-          ++launches;
-        }
         const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
-        if (we > wb) {
-          LaunchTimer lt(m, st, 2);
-          k_events_e2<<<(unsigned)n_rep, kE2Block, 0, st>>>(
-              tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, last, slots);
-          ++launches;
-          waves += (int32_t)(we - wb);
-        }
+        LaunchTimer lt(m, st, 2);
+        launch_e2_kind(m, ea, wb, we, last, slots, n_rep, st);
+        ++launches;
+        waves += (int32_t)(we - wb);
       }
-      pending = ev_today;
+      pending = e2_today;
       d = last + 1;
     }
     if (pending) {
@@ -1084,9 +1466,14 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.U = d_U;
       da.V = d_V;
       da.rec = d_rec;
+      da.e1_cur = nullptr;
+      da.ev = EvDev{};
       da.t0 = t0;
       da.M = n_tspan;
       da.n_rep = n_rep;
+      da.slots = 1;
+      da.heavy_after = 2;
+      da.npb = default_npb((long long)Nn * n_rep);
       da.T_begin = t0 + 1;
       da.T_end = t_end + 1;
       da.finish_first = 0;
@@ -1095,8 +1482,8 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.k1 = (uint32_t)(seed >> 32);
       da.err = d_err;
       da.cnt = d_cnt;
-      const long long threads = (long long)Nn * n_rep;
-      const unsigned grid = (unsigned)std::max<long long>(1, (threads + kDayBlock - 1) / kDayBlock);
+      const long long units = (long long)Nn * n_rep;
+      const unsigned grid = (unsigned)std::max<long long>(1, (units + da.npb - 1) / da.npb);
       switch (k) {
         case SG_SIR: k_days<SG_SIR><<<grid, kDayBlock, 0, st>>>(tb, da); break;
         case SG_SIS: k_days<SG_SIS><<<grid, kDayBlock, 0, st>>>(tb, da); break;
@@ -1126,5 +1513,67 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
     fill_error(err, h_err.code, h_err.rep, h_err.node, h_err.day, h_err.event);
     return h_err.code;
   }
+  return SG_OK;
+}
+
+extern "C" int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after) {
+  if (!m || nodes_per_block > kDayBlock || heavy_after > (1 << 20)) return SG_ERR_ARG;
+  m->npb = nodes_per_block > 0 ? nodes_per_block : -1;
+  m->heavy_after = heavy_after >= 0 ? heavy_after : -1;
+  return SG_OK;
+}
+
+extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+                           int32_t n_rep, const int32_t *d_u0, const double *d_v0,
+                           int32_t *d_U, double *d_V, void *stream, int32_t *npb_out,
+                           int32_t *heavy_after_out, double *ms_out) {
+  if (!m) return SG_ERR_ARG;
+  static const int32_t kNpb[] = {16, 32, 64, 128};
+  static const int32_t kHeavy[] = {0, 1, 2, 4, 8};
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  const int32_t old_npb = m->npb, old_heavy = m->heavy_after;
+  const bool old_timing = m->timing;
+  m->timing = false;
+  double best = 1e300;
+  int32_t best_npb = -1, best_heavy = -1;
+  int rc = SG_OK;
+  for (int32_t npb : kNpb) {
+    for (int32_t h : kHeavy) {
+      m->npb = npb;
+      m->heavy_after = h;
+      cudaEventRecord(e0, st);
+      rc = sg_run(m, tspan, n_tspan, seed, n_rep, d_u0, d_v0, d_U, d_V, stream, nullptr,
+                  nullptr);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      float ms = 0.f;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_npb = npb;
+        best_heavy = h;
+      }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  m->timing = old_timing;
+  if (rc) {
+    m->npb = old_npb;
+    m->heavy_after = old_heavy;
+    return rc;
+  }
+  m->npb = best_npb;
+  m->heavy_after = best_heavy;
+  if (npb_out) *npb_out = best_npb;
+  if (heavy_after_out) *heavy_after_out = best_heavy;
+  if (ms_out) *ms_out = best;
   return SG_OK;
 }

@@ -51,69 +51,91 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   P.t0 = t0;
   P.t_end = t_end;
   P.slots = slots;
+  P.n_nodes = n_nodes;
   P.days = std::max(0, t_end - t0);
   const int64_t nb = (int64_t)P.days * slots;
-  P.e1_off.assign(nb + 1, 0);
+  const int64_t nk = (int64_t)slots * n_nodes;
+  P.e1_node_off.assign(nk + 1, 0);
   P.e2_wave_off.assign(nb + 1, 0);
-  P.day_has_events.assign(P.days, 0);
+  P.day_has_e2.assign(P.days, 0);
   P.wave_ev.assign(1, 0);
   if (P.days == 0) return SG_OK;
 
-  // 1. stable bucketing by (day, slot); events after t_end never run, and
-  //    events dated t0 or earlier run at the first step.
+  // Events after t_end never run; events dated t0 or earlier run at the
+  // first step.
   const int64_t n = ev.size();
-  std::vector<int64_t> bucket_of(n, -1);
+  auto day_of = [&](int64_t e) {
+    return (int32_t)std::max<int64_t>(0, (int64_t)ev.time[e] - t0 - 1);
+  };
+  auto slot_of = [&](int64_t e) -> int64_t { return slots > 1 ? ev.rep[e] : 0; };
+
+  // 1. E1: stable counting sort by (slot, node), then (day, time, type,
+  //    index) inside each node's list.
+  std::vector<int64_t> e1_count(nk + 1, 0);
+  int64_t n_e1 = 0;
+  for (int64_t e = 0; e < n; ++e) {
+    if (ev.time[e] > t_end || ev.type[e] == SG_EXTERNAL_TRANSFER) continue;
+    const int64_t s = slot_of(e);
+    if (s >= slots) return SG_ERR_ARG;
+    ++e1_count[s * n_nodes + ev.node[e] + 1];
+    ++n_e1;
+  }
+  std::partial_sum(e1_count.begin(), e1_count.end(), e1_count.begin());
+  std::vector<int64_t> e1(n_e1);
+  {
+    std::vector<int64_t> fill(e1_count.begin(), e1_count.end() - 1);
+    for (int64_t e = 0; e < n; ++e) {
+      if (ev.time[e] > t_end || ev.type[e] == SG_EXTERNAL_TRANSFER) continue;
+      e1[fill[slot_of(e) * n_nodes + ev.node[e]]++] = e;
+    }
+  }
+  for (int64_t k = 0; k < nk; ++k) {
+    auto b = e1.begin() + e1_count[k], en = e1.begin() + e1_count[k + 1];
+    if (en - b > 1)
+      std::sort(b, en, [&](int64_t a, int64_t c) {
+        const int32_t da = day_of(a), dc = day_of(c);
+        if (da != dc) return da < dc;
+        if (ev.time[a] != ev.time[c]) return ev.time[a] < ev.time[c];
+        if (ev.type[a] != ev.type[c]) return ev.type[a] < ev.type[c];
+        return a < c;
+      });
+  }
+  P.e1_node_off = e1_count;
+  P.e1_day.resize(n_e1);
+  for (int64_t i = 0; i < n_e1; ++i) P.e1_day[i] = day_of(e1[i]);
+
+  // 2. E2: stable bucketing by (day, slot), waves inside each bucket.
   std::vector<int64_t> count(nb + 1, 0);
   for (int64_t e = 0; e < n; ++e) {
-    if (ev.time[e] > t_end) continue;
-    const int64_t d = std::max<int64_t>(0, (int64_t)ev.time[e] - t0 - 1);
-    const int64_t s = slots > 1 ? ev.rep[e] : 0;
+    if (ev.time[e] > t_end || ev.type[e] != SG_EXTERNAL_TRANSFER) continue;
+    const int64_t s = slot_of(e);
     if (s >= slots) return SG_ERR_ARG;
-    bucket_of[e] = d * slots + s;
-    ++count[bucket_of[e] + 1];
+    ++count[(int64_t)day_of(e) * slots + s + 1];
   }
   std::partial_sum(count.begin(), count.end(), count.begin());
   std::vector<int64_t> bucketed(count[nb]);
   {
     std::vector<int64_t> fill(count.begin(), count.end() - 1);
-    for (int64_t e = 0; e < n; ++e)
-      if (bucket_of[e] >= 0) bucketed[fill[bucket_of[e]]++] = e;
+    for (int64_t e = 0; e < n; ++e) {
+      if (ev.time[e] > t_end || ev.type[e] != SG_EXTERNAL_TRANSFER) continue;
+      bucketed[fill[(int64_t)day_of(e) * slots + slot_of(e)]++] = e;
+    }
   }
-
-  // 2. per bucket: E1 part sorted by (node, time, type, index); E2 part in
-  //    (time, index) order split into waves.
-  std::vector<int64_t> e1, e2;
-  e1.reserve(bucketed.size());
+  std::vector<int64_t> e2;
   e2.reserve(bucketed.size());
   std::vector<int32_t> last_sample(n_nodes, 0), last_add(n_nodes, 0);
   std::vector<int64_t> stamp(n_nodes, -1);
-  std::vector<int64_t> tmp1, tmp2;
+  std::vector<int64_t> tmp;
   std::vector<int32_t> wave_of;
   for (int64_t b = 0; b < nb; ++b) {
-    tmp1.clear();
-    tmp2.clear();
-    for (int64_t i = count[b]; i < count[b + 1]; ++i) {
-      const int64_t e = bucketed[i];
-      (ev.type[e] == SG_EXTERNAL_TRANSFER ? tmp2 : tmp1).push_back(e);
-    }
-    std::sort(tmp1.begin(), tmp1.end(), [&](int64_t a, int64_t c) {
-      if (ev.node[a] != ev.node[c]) return ev.node[a] < ev.node[c];
-      if (ev.time[a] != ev.time[c]) return ev.time[a] < ev.time[c];
-      if (ev.type[a] != ev.type[c]) return ev.type[a] < ev.type[c];
-      return a < c;
-    });
-    e1.insert(e1.end(), tmp1.begin(), tmp1.end());
-    P.e1_off[b + 1] = (int64_t)e1.size();
-
-    // E2: list order within the bucket is already (index); only the first
-    // day can mix times, so order by (time, index) there.
-    std::stable_sort(tmp2.begin(), tmp2.end(), [&](int64_t a, int64_t c) {
-      return ev.time[a] < ev.time[c];
-    });
-    wave_of.assign(tmp2.size(), 0);
+    tmp.assign(bucketed.begin() + count[b], bucketed.begin() + count[b + 1]);
+    // list order is kept by the bucketing; only the first day can mix times
+    std::stable_sort(tmp.begin(), tmp.end(),
+                     [&](int64_t a, int64_t c) { return ev.time[a] < ev.time[c]; });
+    wave_of.assign(tmp.size(), 0);
     int32_t n_w = 0;
-    for (size_t i = 0; i < tmp2.size(); ++i) {
-      const int64_t e = tmp2[i];
+    for (size_t i = 0; i < tmp.size(); ++i) {
+      const int64_t e = tmp[i];
       const int32_t s = ev.node[e], d = ev.dest[e];
       if (stamp[s] != b) { stamp[s] = b; last_sample[s] = 0; last_add[s] = 0; }
       if (stamp[d] != b) { stamp[d] = b; last_sample[d] = 0; last_add[d] = 0; }
@@ -125,25 +147,24 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     }
     // counting sort by wave, list order kept inside a wave
     std::vector<int64_t> wc(n_w + 2, 0);
-    for (size_t i = 0; i < tmp2.size(); ++i) ++wc[wave_of[i] + 1];
+    for (size_t i = 0; i < tmp.size(); ++i) ++wc[wave_of[i] + 1];
     std::partial_sum(wc.begin(), wc.end(), wc.begin());
-    std::vector<int64_t> sorted(tmp2.size());
+    std::vector<int64_t> sorted(tmp.size());
     {
       std::vector<int64_t> fill(wc.begin(), wc.end() - 1);
-      for (size_t i = 0; i < tmp2.size(); ++i) sorted[fill[wave_of[i]]++] = tmp2[i];
+      for (size_t i = 0; i < tmp.size(); ++i) sorted[fill[wave_of[i]]++] = tmp[i];
     }
     const int64_t base = (int64_t)e2.size();
     e2.insert(e2.end(), sorted.begin(), sorted.end());
     for (int32_t w = 1; w <= n_w; ++w) P.wave_ev.push_back(base + wc[w + 1]);
     P.e2_wave_off[b + 1] = (int64_t)P.wave_ev.size() - 1;
-    if (count[b + 1] > count[b]) P.day_has_events[b / slots] = 1;
+    if (!tmp.empty()) P.day_has_e2[b / slots] = 1;
     P.max_waves_per_day = std::max(P.max_waves_per_day, n_w);
   }
-  P.n_e1 = (int64_t)e1.size();
+  P.n_e1 = n_e1;
   P.n_e2 = (int64_t)e2.size();
   P.n_waves = (int64_t)P.wave_ev.size() - 1;
-  // wave_ev holds positions within the E2 part; shift them past the E1 part
-  for (auto &x : P.wave_ev) x += P.n_e1;
+  for (auto &x : P.wave_ev) x += P.n_e1;  // positions past the E1 part
   P.order.reserve(P.n_e1 + P.n_e2);
   P.order.insert(P.order.end(), e1.begin(), e1.end());
   P.order.insert(P.order.end(), e2.begin(), e2.end());

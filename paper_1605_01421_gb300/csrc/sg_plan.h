@@ -29,24 +29,26 @@ int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad);
 // (1 when every replicate runs the same events, else n_rep).
 //
 // Day d (T = t0 + 1 + d) runs the events with time in (T - 1, T]; for d = 0
-// also every earlier time.  E1 events (exit, enter, internal transfer) are
-// grouped per (day, slot) and, inside, sorted by (node, time, type, list
-// index): a node's events run in the order of Sec. 3.3.  E2 events
-// (external transfers) of a (day, slot) keep their (time, list index) order
-// and are split into waves: an event goes one wave after the last earlier
-// event that sampled its source, added to its source, or sampled its
+// also every earlier time.
+//
+// E1 events (exit, enter, internal transfer) are grouped per (slot, node) and
+// sorted inside by (day, time, type, list index): the thread that owns a node
+// walks its own list with a cursor, in the order of Sec. 3.3.
+//
+// E2 events (external transfers) of a (day, slot) keep their (time, list
+// index) order and are split into waves: an event goes one wave after the last
+// earlier event that sampled its source, added to its source, or sampled its
 // destination.  So no two events of a wave touch the same node except as
 // destinations (additions commute), and every node sees its samples and
 // additions in list order.
 struct Plan {
-  int32_t t0 = 0, t_end = 0, slots = 1;
-  int32_t days = 0;
-  // sorted events, E1 part first then E2 part (indices into EventTable)
-  std::vector<int64_t> order;
-  std::vector<int64_t> e1_off;   // [days * slots + 1] into order
+  int32_t t0 = 0, t_end = 0, slots = 1, days = 0, n_nodes = 0;
+  std::vector<int64_t> order;        // E1 part, then E2 part (EventTable indices)
+  std::vector<int32_t> e1_day;       // [n_e1] day index of each E1 event
+  std::vector<int64_t> e1_node_off;  // [slots * n_nodes + 1] into order
   std::vector<int64_t> e2_wave_off;  // [days * slots + 1] into wave_ev
-  std::vector<int64_t> wave_ev;  // [n_waves + 1] into order
-  std::vector<uint8_t> day_has_events;  // [days]
+  std::vector<int64_t> wave_ev;      // [n_waves + 1] positions in order
+  std::vector<uint8_t> day_has_e2;   // [days]
   int64_t n_e1 = 0, n_e2 = 0, n_waves = 0;
   int32_t max_waves_per_day = 0;
 };

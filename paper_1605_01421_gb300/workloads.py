@@ -159,7 +159,8 @@ def sise3_gdata(upsilons=(0.0173,) * 3, gammas=(0.1,) * 3, alpha=1.0,
 
 
 def _tile_rep(a, n_rep):
-    return np.ascontiguousarray(np.broadcast_to(a[None], (n_rep,) + a.shape))
+    # a C-ordered, writable copy (np.array would keep the broadcast's order)
+    return np.broadcast_to(a[None], (n_rep,) + a.shape).copy(order="C")
 
 
 def plain_model(kind, u0, tspan, gdata, seed=42, n_rep=1, events=None,

@@ -239,3 +239,28 @@ def test_full_size_sise3_prefix(orc, gpu):
     d_exit = np.bincount(ev["time"][ev["event"] == EXIT],
                          weights=ev["n"][ev["event"] == EXIT], minlength=3651)
     assert np.array_equal(np.diff(tot), (d_enter - d_exit)[1:3651].astype(np.int64))
+
+
+@pytest.mark.parametrize("tuning", [(1, 0), (16, 0), (32, 1), (64, 4), (128, 2), (128, 1 << 20)])
+def test_work_split_never_changes_results(orc, gpu, tuning):
+    # nodes per block and the thread-to-warp hand-off point change speed only
+    w = W.config_sise(n_nodes=700, days=120, gen_seed=21)
+    w.u0[0, :40, 1] = np.maximum(w.u0[0, :40, 1], w.u0[0, :40, 0] // 2)
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == 0
+    U1, V1, st = gpu.simulate(w, tuning=tuning)
+    assert np.array_equal(U0, U1)
+    assert np.array_equal(V0.view(np.uint64), V1.view(np.uint64))
+    assert st["reactions"] == int(R0.sum())
+
+
+def test_one_wave_larger_than_a_staging_chunk(orc, gpu):
+    # 1,500 transfers between disjoint node pairs on one day form one wave,
+    # larger than the 512 events the E2 kernel stages at a time
+    n = 3000
+    rows = [(EXTERNAL, 1, 2 * i, 2 * i + 1, 2, 0.0, 2, -1) for i in range(n // 2)]
+    rows += [(EXTERNAL, 2, 2 * i + 1, 2 * i, 1, 0.0, 2, -1) for i in range(n // 2)]
+    u0 = np.tile([[20, 3]], (n, 1))
+    w = W.plain_model(W.SISE, u0, np.arange(0, 4), W.sise_gdata(), seed=13,
+                      events=W.make_events(rows), v0=np.full((n, 1), 0.2))
+    _compare(orc, gpu, w)
