@@ -32,6 +32,18 @@ namespace {
 constexpr int kDayBlock = 128;
 constexpr int kE2Block = 256;
 
+// Programmatic dependent launch: the day kernels and the E2 kernels are
+// launched so that the next kernel in the stream may start while the
+// previous one finishes.  Each kernel lets its successor launch at once,
+// reads only static inputs (model tables, event plan) before pdl_wait, and
+// waits for its predecessor (completion and memory) before it touches state.
+// Every such kernel executes pdl_wait on all paths, so its completion implies
+// its predecessor's.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -182,6 +194,93 @@ __device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> 
   bool have = false;
   unsigned long long f = 0;
   const long long Tkey = order_key(Tn);
+  if (T == 2 && tb.dep[0] == 3u && tb.dep[1] == 3u) {
+    // Two transitions, every rate recomputed after every transition: the
+    // states reachable within the next J = 7 draws are u + (j - b) S0 + b S1,
+    // 0 <= b <= j < 7 (28 of them).  Lane l = j (j + 1) / 2 + b evaluates
+    // draw c + j at state (j, b): rates, lambda, waiting time, inversion.
+    // The walk then follows the fired transitions through the table, so each
+    // draw costs one addition (t + tau) and a branch.  Rates from scratch
+    // equal the incrementally kept ones (pure functions of the counts).
+    constexpr int J = 7;
+    int lj = 0, lb = 0;
+    {
+      int l = lane < J * (J + 1) / 2 ? lane : 0;
+      while (l > lj) { l -= lj + 1; ++lj; }
+      lb = l;
+    }
+    bool done = false;
+    while (!done && code == 0) {
+      if (!have || c + (uint32_t)J - c0 > 32u) {
+        c0 = c;
+        const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+        nE = -log_pos(u01_open(x.x, x.y));
+        r2 = u01_open(x.z, x.w);
+        have = true;
+      }
+      // this lane's state and draw
+      int us[C];
+#pragma unroll
+      for (int p = 0; p < C; ++p) us[p] = u[p] + (lj - lb) * tb.S[0][p] + lb * tb.S[1][p];
+      double ws[T];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ws[j] = M::rate_k(j, us, kf, tb.gdata);
+        bad = bad || bad_rate(ws[j]);
+      }
+      const int src = (int)(c - c0) + lj;  // lane holding draw c + lj
+      const double E = __shfl_sync(0xffffffffu, nE, src);
+      const double R2 = __shfl_sync(0xffffffffu, r2, src);
+      const double lam = ws[0] + ws[1];
+      const double tau = E / lam;
+      const double target = lam * R2;
+      const int fire0 = gt0(ws[0]) && le_nonneg(target, ws[0]);
+      // inversion: transition 0 if target <= w0 (w0 > 0), else 1 if w1 > 0,
+      // else the last positive one (w0)
+      const int nsel = fire0 ? 0 : (gt0(ws[1]) ? 1 : 0);
+      const unsigned pos_mask = __ballot_sync(0xffffffffu, gt0(lam));
+      const unsigned bad_mask = __ballot_sync(0xffffffffu, bad);
+      const unsigned n1_mask = __ballot_sync(0xffffffffu, nsel == 1);
+      int j = 0, b = 0;
+      for (; j < J; ++j) {
+        const int L = j * (j + 1) / 2 + b;
+        if (j > 0 && ((bad_mask >> L) & 1u)) {
+          code = SG_ERR_RATE;  // the transition into this state gave a bad rate
+          break;
+        }
+        if (!((pos_mask >> L) & 1u)) {
+          done = true;  // nothing can fire: jump to Tn
+          break;
+        }
+        if (c >= SG_MAX_DRAWS) {
+          code = SG_ERR_STEP_LIMIT;
+          break;
+        }
+        const double tauL = __shfl_sync(0xffffffffu, tau, L);
+        ++c;
+        const double tt = t + tauL;
+        if (order_key(tt) >= Tkey) {
+          done = true;
+          break;
+        }
+        t = tt;
+        b += (int)((n1_mask >> L) & 1u);
+        ++f;
+      }
+      // move to the state reached
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = u[p] + (j - b) * tb.S[0][p] + b * tb.S[1][p];
+      if (!done && code == 0) {
+        // j == J: a new window starts from the state after J transitions
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          w[k] = M::rate_k(k, u, kf, tb.gdata);
+          if (bad_rate(w[k])) code = SG_ERR_RATE;
+        }
+      }
+    }
+  } else {
   for (;;) {
     double lam = w[0];
 #pragma unroll
@@ -222,6 +321,7 @@ __device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> 
       code = rc;
       break;
     }
+  }
   }
   __syncwarp();
   if (lane == 0) {
@@ -327,11 +427,11 @@ k_days(const SgTables tb, const DayArgs a) {
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
   __shared__ HeavySlot<C, NK> s_heavy[kDayBlock];
   __shared__ int s_nheavy;
+  pdl_trigger();
   const int Nn = tb.n_nodes;
   const long long gid = (long long)blockIdx.x * a.npb + threadIdx.x;
   const long long total = (long long)Nn * a.n_rep;
-  const bool live = (int)threadIdx.x < a.npb && gid < total &&
-                    *(volatile int32_t *)&a.err->code == 0;
+  const bool in_range = (int)threadIdx.x < a.npb && gid < total;
   const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   unsigned long long fired = 0, drawn = 0, applied = 0;
   int rep = 0, node = 0, code = 0, bad_day = 0;
@@ -344,13 +444,10 @@ k_days(const SgTables tb, const DayArgs a) {
   v[0] = 0.0;
   long long ecur = 0, ebase = 0, eend = 0;
   int next_day = 0x7fffffff;
-  if (live) {
+  // static inputs first (they overlap the previous kernel's tail)
+  if (in_range) {
     rep = (int)(gid / Nn);
     node = (int)(gid - (long long)rep * Nn);
-#pragma unroll
-    for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
     if (NV > 0) {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -360,6 +457,16 @@ k_days(const SgTables tb, const DayArgs a) {
       const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
       ebase = a.ev.e1_node_off[key];
       eend = a.ev.e1_node_off[key + 1];
+    }
+  }
+  pdl_wait();
+  const bool live = in_range && *(volatile int32_t *)&a.err->code == 0;
+  if (live) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+    if (a.ev.e1_node_off) {
       ecur = ebase + a.e1_cur[gid];
       if (ecur < eend) next_day = a.ev.e1_day[ecur];
     }
@@ -516,6 +623,7 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   __shared__ uint4 s_w[kE2Cap];
   __shared__ long long s_wave[kE2WaveCap + 1];
   __shared__ int s_stop;
+  pdl_trigger();
   const int rep = blockIdx.x;
   const int Nn = tb.n_nodes;
   long long w0 = w_begin_shared, w1 = w_end_shared;
@@ -523,13 +631,13 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
     w0 = wave_off[(long long)day_index * slots + rep];
     w1 = wave_off[(long long)day_index * slots + rep + 1];
   }
-  if (w0 >= w1 || *(volatile int32_t *)&a.err->code != 0) return;
-  int *gstate = a.u + (long long)rep * Nn * C;
-  int *state = gstate;
-  if (SMEM_STATE) {
-    copy_words(s_state, gstate, Nn * C);
-    state = s_state;
+  if (w0 >= w1) {
+    pdl_wait();
+    return;
   }
+  int *gstate = a.u + (long long)rep * Nn * C;
+  int *state = SMEM_STATE ? s_state : gstate;
+  bool waited = false;
   if (threadIdx.x == 0) s_stop = 0;
   const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
   const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
@@ -560,7 +668,15 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
                             a.k0, a.k1);
       s_w[i] = make_uint4(f.x, f.y, f.z, f.w);
     }
+    if (!waited) {
+      // the first chunk is staged: now wait for the day kernel's state
+      pdl_wait();
+      waited = true;
+      if (*(volatile int32_t *)&a.err->code != 0) s_stop = 1;
+      if (SMEM_STATE) copy_words(s_state, gstate, Nn * C);
+    }
     __syncthreads();
+    if (s_stop) break;
     // waves w .. (staged) intersecting [pos, pend)
     long long wi = 0;
     while (wi < wn && s_wave[wi] < pend) {
@@ -630,7 +746,8 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
     w += wi;
     pos = pend;
   }
-  if (SMEM_STATE) {
+  if (!waited) pdl_wait();
+  if (SMEM_STATE && waited) {
     __syncthreads();
     copy_words(gstate, s_state, Nn * C);
   }
@@ -956,6 +1073,23 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
   return SG_OK;
 }
 
+// Launch with programmatic stream serialization (see pdl_wait).
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Nodes per block when not tuned: fill about two blocks per SM for small
 // problems (so heavy nodes spread over many SMs and warps), full blocks
 // otherwise.
@@ -969,7 +1103,7 @@ template <int KIND>
 static void launch_days(sg_model *m, const DayArgs &a, cudaStream_t st) {
   const long long units = (long long)m->tb.n_nodes * a.n_rep;
   const unsigned grid = (unsigned)std::max<long long>(1, (units + a.npb - 1) / a.npb);
-  k_days<KIND><<<grid, kDayBlock, 0, st>>>(m->tb, a);
+  launch_pdl(k_days<KIND>, grid, kDayBlock, 0, st, m->tb, a);
 }
 
 static void launch_days_kind(sg_model *m, const DayArgs &a, cudaStream_t st) {
@@ -1021,11 +1155,11 @@ static void launch_e2(sg_model *m, const EvArgs &ea, long long wb, long long we,
                            (int)kE2SmemStateMax);
       attr_set |= 1ull << dev;
     }
-    k_events_e2<KIND, true><<<(unsigned)n_rep, kE2Block, bytes, st>>>(
-        m->tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, day, slots);
+    launch_pdl(k_events_e2<KIND, true>, (unsigned)n_rep, kE2Block, bytes, st, m->tb, ea,
+               (const int64_t *)m->wave_ev.p, wb, we, (const int64_t *)m->wave_off.p, day, slots);
   } else {
-    k_events_e2<KIND, false><<<(unsigned)n_rep, kE2Block, 0, st>>>(
-        m->tb, ea, m->wave_ev.p, wb, we, m->wave_off.p, day, slots);
+    launch_pdl(k_events_e2<KIND, false>, (unsigned)n_rep, kE2Block, 0, st, m->tb, ea,
+               (const int64_t *)m->wave_ev.p, wb, we, (const int64_t *)m->wave_off.p, day, slots);
   }
 }
 
