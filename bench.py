@@ -48,7 +48,32 @@ def _workload(name):
         return W.config_sir()
     if name == "sise3":
         return W.config_sise3()
+    if name == "batched":
+        return W.config_batched()
     raise SystemExit(f"unknown workload {name}")
+
+
+def _oracle_sample(w, max_node_days):
+    """A bounded sample of the workload for the CPU oracle: one replicate
+    (with its own events), then a prefix of days, so that it holds at most
+    max_node_days node-days."""
+    from paper_1605_01421_gb300 import workloads as W
+    desc = []
+    if w.n_rep > 1:
+        ev = w.events
+        if ev.get("rep") is not None:
+            keep = ev["rep"] == 0
+            ev = {k: (v[keep] if v is not None else None) for k, v in ev.items()}
+            ev["rep"] = None
+        w = W.Workload(**{**w.__dict__, "events": ev, "n_rep": 1,
+                          "u0": w.u0[:1].copy(), "v0": w.v0[:1].copy()})
+        desc.append("replicate 0 only")
+    days = w.n_days
+    if w.n_nodes * days > max_node_days:
+        days = max(1, int(max_node_days // w.n_nodes))
+        w = W.Workload(**{**w.__dict__, "tspan": w.tspan[:days + 1].copy()})
+        desc.append(f"first {days} days")
+    return w, desc
 
 
 class ClockSampler:
@@ -118,10 +143,11 @@ def _cpu_cores():
 
 
 def time_oracle(w, budget_s=10.0, max_runs=50):
-    """Run the CPU oracle on the whole workload repeatedly for ~budget_s
-    (at least once); node-days/s and reactions/s."""
+    """Run the CPU oracle on (a bounded sample of) the workload repeatedly for
+    ~budget_s (at least once); node-days/s and reactions/s."""
     import oracle
     oracle.build()
+    w, desc = _oracle_sample(w, max_node_days=1.5e6 * budget_s)
     node_days = w.n_nodes * w.n_days * w.n_rep
     runs, t_total, reactions = 0, 0.0, 0
     while runs < max_runs and (runs == 0 or t_total < budget_s):
@@ -134,15 +160,17 @@ def time_oracle(w, budget_s=10.0, max_runs=50):
     return {"value": node_days * runs / t_total, "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "reactions_per_s": reactions / t_total,
-            "sample": f"{runs} complete run(s) of the workload ({node_days} node-days each), "
-                      f"serial C oracle, 1 thread, {t_total:.2f} s"}
+            "sample": f"{runs} run(s) of " + (", ".join(desc) if desc else "the whole workload")
+                      + f" ({node_days} node-days each), serial C oracle, 1 thread, "
+                      f"{t_total:.2f} s"}
 
 
 def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w = _workload(args.workload)
+    w_full = _workload(args.workload)
+    w, desc = _oracle_sample(w_full, max_node_days=3e6)
     node_days = w.n_nodes * w.n_days * w.n_rep
     import oracle
     oracle.build()
@@ -162,10 +190,12 @@ def bench_reference(args):
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
             "data": "synthetic", "reactions_per_s": reactions / total,
-            "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
-                       "replicates": w.n_rep, "events": w.n_events, "seed": w.seed},
+            "config": {"workload": w_full.name, "nodes": w_full.n_nodes,
+                       "days": w_full.n_days, "replicates": w_full.n_rep,
+                       "events": w_full.n_events, "seed": w_full.seed},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} complete run(s) of the workload"},
+                             "sample": f"{args.steps} run(s) of "
+                                       + (", ".join(desc) if desc else "the whole workload")},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -188,7 +218,9 @@ def bench_gpu(args):
     n_rep = w.n_rep
     M = len(w.tspan)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # a non-default stream, so that each run is one replayed CUDA graph
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     model = binding.Model(w)
     u0 = torch.as_tensor(np.array(w.u0, dtype=np.int32, order="C"), device=dev)
     v0 = torch.as_tensor(np.array(w.v0, dtype=np.float64, order="C"), device=dev)
@@ -289,6 +321,7 @@ def bench_gpu(args):
             torch.cuda.synchronize()
             t = time.perf_counter()
             m2 = binding.Model(w)  # tables + events: host validation, plan, upload
+            m2.set_graphs(False)  # a single run: capturing a graph would not pay
             m2.run_host(w.tspan, seed, n_rep, u0h, v0h, Uh, Vh, stream=stream)
             t_e2e += time.perf_counter() - t
             m2.close()
@@ -335,7 +368,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sise", choices=["sise", "sir", "sise3"])
+    ap.add_argument("--workload", default="sise", choices=["sise", "sir", "sise3", "batched"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()

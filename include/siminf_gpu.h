@@ -206,6 +206,14 @@ int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t see
                 double *d_V, void *stream, int32_t *nodes_per_block,
                 int32_t *heavy_after, double *ms);
 
+/* CUDA graphs (on by default): sg_run captures its whole launch sequence
+ * (counter resets, initial copy, every day and event kernel) into one CUDA
+ * graph the first time, and replays it while the buffers, tspan window,
+ * seed, replicate count, work split and events stay the same.  Runs on the
+ * legacy default stream (stream NULL) or with kernel timing on are launched
+ * directly.  enable = 0 turns capture off. */
+int sg_set_graphs(sg_model *m, int enable);
+
 /* Release the model and all its device memory. */
 void sg_model_destroy(sg_model *m);
 

@@ -119,7 +119,7 @@ class Stats(ctypes.Structure):
 EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
            "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe",
-           "sg_run_noalloc", "sg_set_tuning", "sg_autotune"]
+           "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs"]
 
 _lock = threading.Lock()
 _lib = None
@@ -172,6 +172,8 @@ def lib(path: str | None = None):
         L.sg_autotune.argtypes = [vp, vp, i32, u64, i32, vp, vp, vp, vp, vp, ip32, ip32,
                                   ctypes.POINTER(ctypes.c_double)]
         L.sg_autotune.restype = ctypes.c_int
+        L.sg_set_graphs.argtypes = [vp, ctypes.c_int]
+        L.sg_set_graphs.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -304,6 +306,11 @@ class Model:
         if rc:
             raise SimInfError(rc)
         return npb.value, ha.value, ms.value
+
+    def set_graphs(self, enable=True):
+        rc = lib().sg_set_graphs(self._h, 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
 
     def set_kernel_timing(self, enable=True):
         rc = lib().sg_set_kernel_timing(self._h, 1 if enable else 0)

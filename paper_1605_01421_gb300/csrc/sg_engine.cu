@@ -864,6 +864,23 @@ int upload(DevBuf<T> &b, const std::vector<T> &h) {
 
 }  // namespace
 
+// What a captured run depends on besides the model's tables and plan.
+// Every pointer the captured kernels use is part of the key, so a buffer
+// that was reallocated in between (by any call) forces a new capture.
+struct GraphKey {
+  const void *u0, *v0, *U, *V;
+  const void *u, *v, *cur, *rec;
+  uint64_t seed;
+  int32_t n_rep, n_tspan, t0, t_end, npb, heavy_after;
+  uint64_t plan_version;
+  bool operator==(const GraphKey &o) const {
+    return u0 == o.u0 && v0 == o.v0 && U == o.U && V == o.V && u == o.u && v == o.v &&
+           cur == o.cur && rec == o.rec && seed == o.seed && n_rep == o.n_rep &&
+           n_tspan == o.n_tspan && t0 == o.t0 && t_end == o.t_end && npb == o.npb &&
+           heavy_after == o.heavy_after && plan_version == o.plan_version;
+  }
+};
+
 struct sg_model {
   SgTables tb;
   DevBuf<double> ldata;
@@ -895,6 +912,16 @@ struct sg_model {
   // buffers of sg_run_host
   DevBuf<int32_t> hu0, hU;
   DevBuf<double> hv0, hV;
+  // the tspan table on the device, as last uploaded
+  std::vector<int32_t> rec_host;
+  // the captured run (CUDA graph)
+  bool graphs = true;
+  bool graph_ok = false;
+  GraphKey graph_key{};
+  cudaGraphExec_t graph_exec = nullptr;
+  long long graph_launches = 0;
+  int32_t graph_waves = 0;
+  uint64_t plan_version = 0;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -998,6 +1025,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
+  if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   delete m;
 }
 
@@ -1070,6 +1098,7 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
       (rc = upload(m->e1_day, P.e1_day)) || (rc = upload(m->e1_node_off, P.e1_node_off)))
     return rc;
   m->plan_ok = true;
+  ++m->plan_version;
   return SG_OK;
 }
 
@@ -1182,47 +1211,22 @@ static void fill_error(sg_error *err, int code, int rep, int node, int day, int6
   err->event = ev;
 }
 
-extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
-                      int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
-                      double *d_V, void *stream, sg_stats *stats, sg_error *err) {
-  fill_error(err, 0, -1, -1, -1, -1);
-  if (stats) std::memset(stats, 0, sizeof *stats);
-  if (!m || !tspan || n_tspan < 1 || n_rep < 1 || n_rep >= (1 << 24)) return SG_ERR_ARG;
-  for (int i = 1; i < n_tspan; ++i)
-    if (tspan[i] <= tspan[i - 1]) return SG_ERR_ARG;
+// Everything one run puts on the stream after the host set-up: counters and
+// cursors cleared, initial state copied, then the day loop (day kernels and
+// E2 kernels).  Returns the number of kernels and E2 waves enqueued.
+static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int32_t days,
+                        int32_t t0, int32_t t_end, int32_t slots, int32_t n_rep, int32_t n_tspan,
+                        const int32_t *d_u0, const double *d_v0, int32_t *d_U, double *d_V,
+                        cudaStream_t st, long long *launches_out, int32_t *waves_out) {
   const SgTables &tb = m->tb;
-  const int C = tb.n_comp, NV = tb.n_v, Nn = tb.n_nodes;
-  if (Nn > 0 && (!d_u0 || !d_U || (NV > 0 && (!d_v0 || !d_V)))) return SG_ERR_ARG;
-  if (m->ev.per_rep && m->ev.max_rep >= n_rep) {
-    fill_error(err, SG_ERR_ARG, m->ev.max_rep, -1, -1, -1);
-    return SG_ERR_ARG;
-  }
-  cudaStream_t st = (cudaStream_t)stream;
-  const int32_t t0 = tspan[0], t_end = tspan[n_tspan - 1];
-  const int32_t days = t_end - t0;
-  const int32_t slots = m->ev.per_rep ? n_rep : 1;
-  int rc = ensure_plan(m, t0, t_end, slots);
-  if (rc) return rc;
   const Plan &P = m->plan;
-
+  const int C = tb.n_comp, NV = tb.n_v, Nn = tb.n_nodes;
   const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
-  if ((rc = m->u.ensure((size_t)(per_rep_u * n_rep))) ||
-      (rc = m->v.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))) ||
-      (rc = m->e1_cur.ensure((size_t)Nn * n_rep)) || (rc = m->rec.ensure((size_t)days + 1)))
-    return rc;
-  std::vector<int32_t> rec(days + 1, -1);
-  for (int i = 0; i < n_tspan; ++i) rec[tspan[i] - t0] = i;
-  if (cudaMemcpyAsync(m->rec.p, rec.data(), rec.size() * sizeof(int32_t),
-                      cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st) != cudaSuccess ||
-      cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st) != cudaSuccess ||
-      cudaMemsetAsync(m->e1_cur.p, 0, sizeof(int32_t) * (size_t)Nn * n_rep, st) != cudaSuccess) {
-    cudaGetLastError();
-    return SG_ERR_CUDA;
-  }
   long long launches = 0;
-  m->ev_used = 0;
-  m->ev_kind.clear();
+  int32_t waves = 0;
+  cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st);
+  cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st);
+  cudaMemsetAsync(m->e1_cur.p, 0, sizeof(int32_t) * (size_t)std::max(1, Nn * n_rep), st);
   if (Nn > 0) {
     const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
     const unsigned g = (unsigned)std::min<long long>(4096, (nthreads + 255) / 256);
@@ -1231,40 +1235,8 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                                             per_rep_u, per_rep_v, n_tspan, n_rep);
     ++launches;
   }
-
-  const EvDev evd{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
-                  m->e_n.p,    m->e_prop.p,   m->e_index.p, m->e1_day.p,
-                  P.n_e1 > 0 ? m->e1_node_off.p : nullptr};
-  DayArgs da;
-  da.u = m->u.p;
-  da.v = m->v.p;
-  da.ldata = m->ldata.p;
-  da.U = d_U;
-  da.V = d_V;
-  da.rec = m->rec.p;
-  da.e1_cur = m->e1_cur.p;
-  da.ev = evd;
-  da.t0 = t0;
-  da.M = n_tspan;
-  da.n_rep = n_rep;
-  da.slots = slots;
-  da.heavy_after = m->heavy_after >= 0 ? m->heavy_after : 2;
-  da.npb = m->npb > 0 ? m->npb : default_npb((long long)Nn * n_rep);
-  da.k0 = (uint32_t)seed;
-  da.k1 = (uint32_t)(seed >> 32);
-  da.err = m->err.p;
-  da.cnt = m->cnt.p;
-
-  EvArgs ea;
-  ea.ev = evd;
-  ea.u = m->u.p;
-  ea.n_rep = n_rep;
-  ea.k0 = da.k0;
-  ea.k1 = da.k1;
-  ea.err = m->err.p;
-  ea.cnt = m->cnt.p;
-
-  int32_t waves = 0;
+  DayArgs da = da0;
+  EvArgs ea = ea0;
   if (Nn > 0 && days > 0) {
     bool pending = false;  // the previous unit step still needs finishing
     int32_t d = 0;
@@ -1306,6 +1278,135 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
       }
       ++launches;
     }
+  }
+  *launches_out = launches;
+  *waves_out = waves;
+}
+
+extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
+                      int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
+                      double *d_V, void *stream, sg_stats *stats, sg_error *err) {
+  fill_error(err, 0, -1, -1, -1, -1);
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (!m || !tspan || n_tspan < 1 || n_rep < 1 || n_rep >= (1 << 24)) return SG_ERR_ARG;
+  for (int i = 1; i < n_tspan; ++i)
+    if (tspan[i] <= tspan[i - 1]) return SG_ERR_ARG;
+  const SgTables &tb = m->tb;
+  const int C = tb.n_comp, NV = tb.n_v, Nn = tb.n_nodes;
+  if (Nn > 0 && (!d_u0 || !d_U || (NV > 0 && (!d_v0 || !d_V)))) return SG_ERR_ARG;
+  if (m->ev.per_rep && m->ev.max_rep >= n_rep) {
+    fill_error(err, SG_ERR_ARG, m->ev.max_rep, -1, -1, -1);
+    return SG_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int32_t t0 = tspan[0], t_end = tspan[n_tspan - 1];
+  const int32_t days = t_end - t0;
+  const int32_t slots = m->ev.per_rep ? n_rep : 1;
+  int rc = ensure_plan(m, t0, t_end, slots);
+  if (rc) return rc;
+  const Plan &P = m->plan;
+
+  const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
+  if ((rc = m->u.ensure((size_t)(per_rep_u * n_rep))) ||
+      (rc = m->v.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))) ||
+      (rc = m->e1_cur.ensure((size_t)std::max(1, Nn * n_rep))) ||
+      (rc = m->rec.ensure((size_t)days + 1)))
+    return rc;
+  // tspan slot of every unit time, uploaded when it changes
+  std::vector<int32_t> rec(days + 1, -1);
+  for (int i = 0; i < n_tspan; ++i) rec[tspan[i] - t0] = i;
+  if (rec != m->rec_host) {
+    if (cudaMemcpy(m->rec.p, rec.data(), rec.size() * sizeof(int32_t),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return SG_ERR_CUDA;
+    }
+    m->rec_host.swap(rec);
+    m->graph_ok = false;
+  }
+
+  const EvDev evd{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
+                  m->e_n.p,    m->e_prop.p,   m->e_index.p, m->e1_day.p,
+                  P.n_e1 > 0 ? m->e1_node_off.p : nullptr};
+  DayArgs da;
+  da.u = m->u.p;
+  da.v = m->v.p;
+  da.ldata = m->ldata.p;
+  da.U = d_U;
+  da.V = d_V;
+  da.rec = m->rec.p;
+  da.e1_cur = m->e1_cur.p;
+  da.ev = evd;
+  da.t0 = t0;
+  da.M = n_tspan;
+  da.n_rep = n_rep;
+  da.slots = slots;
+  da.heavy_after = m->heavy_after >= 0 ? m->heavy_after : 2;
+  da.npb = m->npb > 0 ? m->npb : default_npb((long long)Nn * n_rep);
+  da.k0 = (uint32_t)seed;
+  da.k1 = (uint32_t)(seed >> 32);
+  da.err = m->err.p;
+  da.cnt = m->cnt.p;
+  da.T_begin = da.T_end = da.finish_first = da.finish_last = 0;
+
+  EvArgs ea;
+  ea.ev = evd;
+  ea.u = m->u.p;
+  ea.n_rep = n_rep;
+  ea.k0 = da.k0;
+  ea.k1 = da.k1;
+  ea.day = 0;
+  ea.err = m->err.p;
+  ea.cnt = m->cnt.p;
+
+  m->ev_used = 0;
+  m->ev_kind.clear();
+  long long launches = 0;
+  int32_t waves = 0;
+  // The whole run is one CUDA graph, captured the first time and replayed
+  // while nothing it depends on changes (not on the legacy default stream,
+  // which cannot be captured, and not while kernels are being timed).
+  const bool use_graph = m->graphs && st != nullptr && !m->timing;
+  const GraphKey key{d_u0,      d_v0,     d_U,          d_V,       m->u.p,
+                     m->v.p,    m->e1_cur.p, m->rec.p,  seed,      n_rep,
+                     n_tspan,   t0,        t_end,        da.npb,    da.heavy_after,
+                     m->plan_version};
+  if (use_graph) {
+    if (!(m->graph_ok && m->graph_key == key)) {
+      if (m->graph_exec) {
+        cudaGraphExecDestroy(m->graph_exec);
+        m->graph_exec = nullptr;
+      }
+      m->graph_ok = false;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SG_ERR_CUDA;
+      }
+      enqueue_run(m, da, ea, days, t0, t_end, slots, n_rep, n_tspan, d_u0, d_v0, d_U, d_V,
+                  st, &launches, &waves);
+      if (cudaStreamEndCapture(st, &g) != cudaSuccess ||
+          cudaGraphInstantiate(&m->graph_exec, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        m->graph_exec = nullptr;
+        return SG_ERR_CUDA;
+      }
+      cudaGraphDestroy(g);
+      m->graph_key = key;
+      m->graph_launches = launches;
+      m->graph_waves = waves;
+      m->graph_ok = true;
+    }
+    launches = m->graph_launches;
+    waves = m->graph_waves;
+    if (cudaGraphLaunch(m->graph_exec, st) != cudaSuccess) {
+      cudaGetLastError();
+      return SG_ERR_CUDA;
+    }
+  } else {
+    enqueue_run(m, da, ea, days, t0, t_end, slots, n_rep, n_tspan, d_u0, d_v0, d_U, d_V, st,
+                &launches, &waves);
   }
   if (cudaMemcpyAsync(m->h_err, m->err.p, sizeof(SgDevError), cudaMemcpyDeviceToHost, st) !=
           cudaSuccess ||
@@ -1709,5 +1810,12 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
   if (npb_out) *npb_out = best_npb;
   if (heavy_after_out) *heavy_after_out = best_heavy;
   if (ms_out) *ms_out = best;
+  return SG_OK;
+}
+
+extern "C" int sg_set_graphs(sg_model *m, int enable) {
+  if (!m) return SG_ERR_ARG;
+  m->graphs = enable != 0;
+  if (!m->graphs) m->graph_ok = false;
   return SG_OK;
 }

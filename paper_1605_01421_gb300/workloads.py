@@ -419,3 +419,113 @@ def config_sise3(n_nodes=37000, days=3650, gen_seed=1003, seed=42,
                          + (f" x {n_rep} replicates" if n_rep > 1 else ""))
     w.meta = {"gen_seed": gen_seed}
     return w
+
+
+def config_batched(n_rep=256, n_nodes=5000, days=365, gen_seed=1004, seed=42,
+                   events_per_node_day=0.111, median=50, sigma=1.0, hi=5000):
+    """Batched replicates: SISe3 on `n_nodes` log-normal herds (median 50,
+    sigma 1.0, clamp 1..5000), `n_rep` independent replicates, each with its
+    own event list at the SISe3 density (exit 30%, enter 30%, ageing 20%,
+    external transfer 20%) on one shared power-law movement network.  The
+    lists are generated for all replicates at once (each day's events of a
+    given position in the day are drawn for every replicate in one vector
+    step); totals are tracked per replicate in the solver's order."""
+    rng = np.random.default_rng(gen_seed)
+    herd = lognormal_herds(rng, n_nodes, median, sigma, 1, hi)
+    ages = split_ages(herd)
+    I = np.zeros_like(ages)
+    seeded = rng.choice(n_nodes, size=max(1, n_nodes // 100), replace=False)
+    I[seeded] = np.rint(0.1 * ages[seeded]).astype(np.int64)
+    S = ages - I
+    u0 = np.stack([S[:, 0], I[:, 0], S[:, 1], I[:, 1], S[:, 2], I[:, 2]],
+                  axis=1).astype(np.int32)
+    ptr, adj, deg = powerlaw_network(rng, n_nodes)
+    src_cdf = np.cumsum(deg / deg.sum())
+    R, Nn = n_rep, n_nodes
+    totals = np.broadcast_to(ages[None], (R, Nn, 3)).copy()
+    flat = totals.reshape(-1)
+    cols = {k: [] for k in ("rep", "event", "time", "node", "dest", "n", "select", "shift",
+                            "order")}
+
+    def emit(rep, etype, T, node, dest, n, sel, shift, order):
+        k = len(rep)
+        cols["rep"].append(rep.astype(np.int32))
+        cols["event"].append(np.full(k, etype, np.int32))
+        cols["time"].append(np.full(k, T, np.int32))
+        cols["node"].append(node.astype(np.int32))
+        cols["dest"].append(np.asarray(dest, dtype=np.int32) * np.ones(k, np.int32))
+        cols["n"].append(n.astype(np.int32))
+        cols["select"].append(np.asarray(sel, dtype=np.int32) * np.ones(k, np.int32))
+        cols["shift"].append(np.asarray(shift, dtype=np.int32) * np.ones(k, np.int32))
+        cols["order"].append(np.full(k, order, np.int64))
+
+    reps = np.arange(R)
+    for d in range(days):
+        T = 1 + d
+        n_today = rng.poisson(events_per_node_day * Nn, size=R)
+        mix = rng.multinomial(n_today, [0.3, 0.3, 0.2, 0.2])
+        # exits: cumulative clamp per (rep, node, age)
+        ne = mix[:, 0]
+        rep_e = np.repeat(reps, ne)
+        if rep_e.size:
+            nodes = rng.integers(0, Nn, rep_e.size)
+            ag = rng.integers(0, 3, rep_e.size)
+            want = _geometric3(rng, rep_e.size)
+            key = (rep_e * Nn + nodes) * 3 + ag
+            o = np.argsort(key, kind="stable")
+            k_s, w_s, r_s = key[o], want[o], rep_e[o]
+            starts = np.r_[True, k_s[1:] != k_s[:-1]]
+            grp = np.cumsum(starts) - 1
+            cs = np.cumsum(w_s)
+            base = np.r_[0, cs][np.flatnonzero(starts)][grp]
+            capped = np.minimum(cs - base, flat[k_s])
+            got = capped - np.r_[0, capped[:-1]]
+            got[starts] = capped[starts]
+            np.subtract.at(flat, k_s, got)
+            ok = got > 0
+            nd = (k_s[ok] // 3) % Nn
+            emit(r_s[ok], EXIT, T, nd, 0, got[ok], 3 + k_s[ok] % 3, -1, 0)
+        # enters into S1
+        rep_n = np.repeat(reps, mix[:, 1])
+        if rep_n.size:
+            nodes = rng.integers(0, Nn, rep_n.size)
+            want = _geometric3(rng, rep_n.size)
+            np.add.at(totals[:, :, 0], (rep_n, nodes), want)
+            emit(rep_n, ENTER, T, nodes, 0, want, 0, -1, 1)
+        # ageing, one position of the day at a time for every replicate
+        for k in range(int(mix[:, 2].max(initial=0))):
+            act = reps[mix[:, 2] > k]
+            nodes = rng.integers(0, Nn, act.size)
+            a = rng.integers(0, 2, act.size)
+            w = np.minimum(_geometric3(rng, act.size), totals[act, nodes, a])
+            ok = w > 0
+            act, nodes, a, w = act[ok], nodes[ok], a[ok], w[ok]
+            totals[act, nodes, a] -= w
+            totals[act, nodes, a + 1] += w
+            emit(act, INTERNAL, T, nodes, 0, w, 3 + a, a, 2 + k)
+        # external transfers, in list order within each replicate
+        for k in range(int(mix[:, 3].max(initial=0))):
+            act = reps[mix[:, 3] > k]
+            src = np.minimum(np.searchsorted(src_cdf, rng.random(act.size)), Nn - 1)
+            pick = rng.random(act.size)
+            dst = adj[ptr[src] + (pick * deg[src]).astype(np.int64)]
+            a = rng.integers(0, 3, act.size)
+            w = np.minimum(_geometric3(rng, act.size), totals[act, src, a])
+            ok = w > 0
+            act, src, dst, a, w = act[ok], src[ok], dst[ok], a[ok], w[ok]
+            totals[act, src, a] -= w
+            totals[act, dst, a] += w
+            emit(act, EXTERNAL, T, src, dst, w, 3 + a, -1, 10_000 + k)
+    cat = {k: np.concatenate(v) if v else np.zeros(0, np.int64) for k, v in cols.items()}
+    o = np.lexsort((cat["order"], cat["time"], cat["rep"]))
+    ev = empty_events()
+    for k in ("event", "time", "node", "dest", "n", "select", "shift"):
+        ev[k] = np.ascontiguousarray(cat[k][o], dtype=np.int32)
+    ev["proportion"] = np.zeros(len(o), dtype=np.float64)
+    ev["rep"] = np.ascontiguousarray(cat["rep"][o], dtype=np.int32)
+    w = plain_model(SISE3, u0, np.arange(0, days + 1), sise3_gdata(), seed=seed,
+                    n_rep=n_rep, events=ev,
+                    name=f"SISe3 {n_rep} replicates x {n_nodes} nodes x {days} days, "
+                         f"own events per replicate")
+    w.meta = {"gen_seed": gen_seed}
+    return w

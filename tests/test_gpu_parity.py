@@ -264,3 +264,53 @@ def test_one_wave_larger_than_a_staging_chunk(orc, gpu):
     w = W.plain_model(W.SISE, u0, np.arange(0, 4), W.sise_gdata(), seed=13,
                       events=W.make_events(rows), v0=np.full((n, 1), 0.2))
     _compare(orc, gpu, w)
+
+
+def _dev(w, n_rep=None):
+    import torch
+    n_rep = w.n_rep if n_rep is None else n_rep
+    u0 = torch.as_tensor(np.ascontiguousarray(w.u0[:n_rep]), device="cuda")
+    v0 = torch.as_tensor(np.ascontiguousarray(w.v0[:n_rep]), device="cuda")
+    M = len(w.tspan)
+    U = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32, device="cuda")
+    V = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64, device="cuda")
+    return u0, v0, U, V
+
+
+def test_graph_capture_and_replay(orc, gpu):
+    # on a non-default stream the run is captured into a CUDA graph once and
+    # replayed; a new seed forces a new capture
+    import torch
+    w = W.config_sise(n_nodes=400, days=50, gen_seed=31)
+    code, U0, V0, R0, err = orc.run(w)
+    code2, U2, V2, R2, err2 = orc.run(w, seed=7)
+    m = gpu.Model(w)
+    u0, v0, U, V = _dev(w)
+    s = torch.cuda.Stream()
+    for seed, (Ue, Ve, Re) in ((w.seed, (U0, V0, R0)), (w.seed, (U0, V0, R0)),
+                               (7, (U2, V2, R2)), (w.seed, (U0, V0, R0))):
+        U.fill_(-1)
+        rc, st, er = m.run(w.tspan, seed, 1, u0, v0, U, V, stream=s)
+        s.synchronize()
+        assert np.array_equal(U.cpu().numpy(), Ue)
+        assert np.array_equal(V.cpu().numpy().view(np.uint64), Ve.view(np.uint64))
+        assert st["reactions"] == int(Re.sum())
+
+
+def test_graph_recaptured_after_buffers_change(orc, gpu):
+    import torch
+    w = W.config_sise3(n_nodes=300, days=40, gen_seed=8, n_rep=3)
+    code, U0, V0, R0, err = orc.run(w, n_rep=1)
+    m = gpu.Model(w)
+    s = torch.cuda.Stream()
+    u0, v0, U, V = _dev(w, 1)
+    m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=s)
+    # a run with more replicates on the default stream reallocates the
+    # model's working buffers
+    u3, v3, U3, V3 = _dev(w, 3)
+    m.run(w.tspan, w.seed, 3, u3, v3, U3, V3)
+    U.fill_(-1)
+    m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=s)
+    s.synchronize()
+    assert np.array_equal(U.cpu().numpy(), U0)
+    assert np.array_equal(U3.cpu().numpy()[:1], U0)
