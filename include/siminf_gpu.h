@@ -256,6 +256,22 @@ int sg_run_noalloc(const sg_desc *desc, const double *d_ldata, const int32_t *ts
                    const double *d_v0, int32_t *d_U, double *d_V, void *stream,
                    sg_stats *stats, sg_error *err);
 
+/* Dense layer on the tensor cores (tcgen05, FP32 accumulators in tensor
+ * memory), the building block of the learned one-day emulator (an extension
+ * of the method; the paper has no emulator):
+ *   C = act(A . Bt^T + bias)
+ * A: M x K BF16 row-major (leading dimension lda), Bt: N x K BF16 row-major
+ * (ldb), i.e. the weight in "out x in" layout; bias: N floats or NULL;
+ * act: 0 identity, 1 GELU (erf form).  C32 (FP32, before the activation,
+ * ldc32) and / or C16 (BF16, after it, ldc16) are written; either may be
+ * NULL but not both.  K, lda and ldb must be multiples of 8 and A / Bt
+ * 16-byte aligned (SG_ERR_ARG otherwise).  All pointers are device pointers;
+ * the call waits for its stream.  SG_ERR_TIMEOUT if a tensor-core wait gave
+ * up (the kernel bounds every wait). */
+int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t ldb, int32_t M,
+                 int32_t N, int32_t K, const float *bias, int32_t act, float *C32,
+                 int32_t ldc32, void *C16, int32_t ldc16, void *stream);
+
 /* Device-side primitives, exported for parity checks of the random stream
  * and arithmetic (each fills a caller-owned device buffer on `stream` and
  * waits for it):

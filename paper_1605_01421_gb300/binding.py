@@ -22,8 +22,8 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsiminf_gpu.so")
 
-SOURCES = ["sg_engine.cu", "sg_plan.cpp"]
-HEADERS = ["sg_common.h", "sg_device.cuh", "sg_plan.h"]
+SOURCES = ["sg_engine.cu", "sg_plan.cpp", "sg_mlp.cu"]
+HEADERS = ["sg_common.h", "sg_device.cuh", "sg_plan.h", "sg_mlp.h", "sg_tc.cuh"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", ARCH,
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
@@ -119,7 +119,8 @@ class Stats(ctypes.Structure):
 EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
            "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe",
-           "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs"]
+           "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs",
+           "sg_gemm_bf16"]
 
 _lock = threading.Lock()
 _lib = None
@@ -174,6 +175,9 @@ def lib(path: str | None = None):
         L.sg_autotune.restype = ctypes.c_int
         L.sg_set_graphs.argtypes = [vp, ctypes.c_int]
         L.sg_set_graphs.restype = ctypes.c_int
+        L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
+                                   i32, vp]
+        L.sg_gemm_bf16.restype = ctypes.c_int
         _lib = L
         return L
 
@@ -348,6 +352,25 @@ def simulate(w, device="cuda", seed=None, n_rep=None, stream=None, tuning=None):
         return U.cpu().numpy(), V.cpu().numpy(), st
     finally:
         m.close()
+
+
+def gemm_bf16(A, Bt, bias=None, act=0, out32=True, out16=False, stream=None):
+    """C = act(A @ Bt.T + bias) on the tensor cores.  A (M, K) and Bt (N, K)
+    are contiguous BF16 CUDA tensors; returns (C32 or None, C16 or None)."""
+    import torch
+    M, K = A.shape
+    N = Bt.shape[0]
+    C32 = torch.empty((M, N), dtype=torch.float32, device=A.device) if out32 else None
+    C16 = torch.empty((M, N), dtype=torch.bfloat16, device=A.device) if out16 else None
+    rc = lib().sg_gemm_bf16(
+        _dev_ptr(A, torch.bfloat16, (M, K), "A"), int(K),
+        _dev_ptr(Bt, torch.bfloat16, (N, K), "Bt"), int(K), int(M), int(N), int(K),
+        _dev_ptr(bias, torch.float32, (N,), "bias") if bias is not None else None, int(act),
+        _dev_ptr(C32) if C32 is not None else None, int(N),
+        _dev_ptr(C16) if C16 is not None else None, int(N), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return C32, C16
 
 
 def fp64_fma_probe(iters=20000, stream=None):

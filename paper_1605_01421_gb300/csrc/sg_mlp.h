@@ -1,0 +1,33 @@
+// sg_mlp.h -- internal interface of the emulator's tensor-core kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "siminf_gpu.h"
+
+namespace sg {
+
+// C = act(A . Bt^T + bias): A is M x K, Bt is N x K (row-major BF16, K
+// contiguous); C32 (FP32, before the activation) and / or C16 (BF16, after
+// it) are written.  act: 0 identity, 1 GELU.
+struct GemmArgs {
+  const __nv_bfloat16 *A;
+  int lda;
+  const __nv_bfloat16 *Bt;
+  int ldb;
+  int M, N, K;
+  const float *bias;
+  int act;
+  float *C32;
+  int ldc32;
+  __nv_bfloat16 *C16;
+  int ldc16;
+  int *err;  // device error word (SG_ERR_TIMEOUT if a wait gave up)
+};
+
+int gemm_bf16(const GemmArgs &g, cudaStream_t st);
+int gemm_check(cudaStream_t st);
+
+}  // namespace sg
