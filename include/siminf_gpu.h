@@ -272,6 +272,59 @@ int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t ldb, int32_
                  int32_t N, int32_t K, const float *bias, int32_t act, float *C32,
                  int32_t ldc32, void *C16, int32_t ldc16, void *stream);
 
+/* ---- Learned one-day emulator (an extension of the method: the paper has
+ * no emulator).  For SISe3 nodes inside a validity range, a small MLP
+ * predicts the distribution of each age class's one-day increment of I
+ * (S moves opposite, so every age class keeps its size, as under the SSA),
+ * and a sample from it replaces the node's SSA for that day; other nodes run
+ * the SSA.  Network: 16 features -> 256 -> 256 -> 256 (GELU) -> 392 logits
+ * (three heads of 129 bins for increments -64..64, 5 padding columns), BF16
+ * weights and activations, FP32 accumulation on the tensor cores.
+ * Features of a node: log1p of S1, I1, S2, I2, S3, I3; phi; 50 upsilon_1..3;
+ * 10 gamma_1..3; three zeros.
+ * All pointers below are device pointers; every call waits for its stream. */
+
+/* Cross-entropy of the three 129-way heads of `B` rows of logits (FP32,
+ * leading dimension ldl >= 387) against target bins (int32, B x 3, 0..128):
+ * adds the summed loss to *loss_sum (device double) and writes
+ * d loss / d logits / B as BF16 (leading dimension ldd; columns 387.. are 0). */
+int sg_mlp_ce_loss(const float *logits, int32_t ldl, const int32_t *targets, int32_t B,
+                   void *dlogits, int32_t ldd, double *loss_sum, void *stream);
+/* dpre[i] = dpost[i] * GELU'(pre[i]) (BF16 out), n elements. */
+int sg_gelu_backward(const float *dpost, const float *pre, int64_t n, void *dpre, void *stream);
+/* dst (cols x rows) = src (rows x cols) transposed, BF16. */
+int sg_transpose_bf16(const void *src, int32_t rows, int32_t cols, void *dst, void *stream);
+/* out[c] = sum over rows of src[r][c] (BF16 in, FP32 out). */
+int sg_colsum_bf16(const void *src, int32_t rows, int32_t cols, float *out, void *stream);
+/* One Adam step (Kingma and Ba) on n FP32 parameters with bias correction
+ * for `step` (>= 1); params_bf16 (may be NULL) receives the BF16 copy. */
+int sg_adam_step(float *params, const float *grads, float *m, float *v, int64_t n, float lr,
+                 float beta1, float beta2, float eps, int32_t step, void *params_bf16,
+                 void *stream);
+/* Emulator features (units x 16 BF16) of SISe3 states u (units x 6 int32)
+ * and phi (units doubles) with the model's gdata (11 host doubles); flag[i]
+ * = 1 when herd <= max_herd and phi_lo <= phi <= phi_hi, else 0. */
+int sg_emu_features(const int32_t *u, const double *v, int64_t units, const double *gdata,
+                    int32_t max_herd, double phi_lo, double phi_hi, void *feat,
+                    int32_t *flag, void *stream);
+/* Training targets: bins clamp(I_a(after) - I_a(before) + 64, 0, 128). */
+int sg_emu_targets(const int32_t *u_before, const int32_t *u_after, int64_t units,
+                   int32_t *targets, void *stream);
+/* Sample increments for the flagged units from the logits: delta[i] =
+ * (dI_1, dI_2, dI_3, used), each clamped to -I_a .. S_a; the uniforms come
+ * from Philox with counter (0, node, day, (2 << 24) | replicate), unit i =
+ * replicate * n_nodes + node. */
+int sg_emu_sample(const float *logits, int32_t ldl, const int32_t *u, const int32_t *flag,
+                  int64_t units, int32_t n_nodes, uint64_t seed, int32_t day, int32_t *delta,
+                  void *stream);
+/* Use the emulator in sg_run (enable != 0; SISe3 models only): W[l] are the
+ * BF16 weights in "out x in" layout (256 x 16, 256 x 256, 256 x 256,
+ * 392 x 256) and b[l] the FP32 biases; both stay owned by the caller and
+ * must outlive the runs.  Nodes with herd > max_herd (-1: every node) or phi outside
+ * [phi_lo, phi_hi] fall back to the SSA.  enable = 0 turns it off. */
+int sg_emulator_set(sg_model *m, const void *const *W, const float *const *b, int32_t max_herd,
+                    double phi_lo, double phi_hi, int enable);
+
 /* Device-side primitives, exported for parity checks of the random stream
  * and arithmetic (each fills a caller-owned device buffer on `stream` and
  * waits for it):

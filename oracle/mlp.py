@@ -1,0 +1,66 @@
+"""FP64 reference of the emulator's network (test infrastructure only).
+
+Plain numpy: the 16-256-256-256-392 multilayer perceptron with GELU (erf
+form), the mean over rows of the summed cross-entropies of its three
+129-way heads, and the gradients of that loss by the chain rule.  The tests
+pin these gradients to central finite differences and compare the CUDA
+kernels' gradients with them.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+HEADS, BINS = 3, 129
+
+_erf = np.vectorize(math.erf)
+
+
+def gelu(x):
+    return 0.5 * x * (1.0 + _erf(x / math.sqrt(2.0)))
+
+
+def gelu_grad(x):
+    cdf = 0.5 * (1.0 + _erf(x / math.sqrt(2.0)))
+    pdf = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+    return cdf + x * pdf
+
+
+def forward(Ws, bs, X):
+    """Ws[l]: (out, in) weights, bs[l]: (out,) biases, X: (B, in).  Returns
+    logits and the per-layer (input, pre-activation) pairs."""
+    h = X
+    cache = []
+    for li, (Wl, bl) in enumerate(zip(Ws, bs)):
+        pre = h @ Wl.T + bl
+        cache.append((h, pre))
+        h = gelu(pre) if li < len(Ws) - 1 else pre
+    return h, cache
+
+
+def loss_and_grads(Ws, bs, X, targets):
+    """Mean over rows of the summed head cross-entropies, and dW, db."""
+    logits, cache = forward(Ws, bs, X)
+    B = X.shape[0]
+    d = np.zeros_like(logits)
+    loss = 0.0
+    for h in range(HEADS):
+        lg = logits[:, h * BINS:(h + 1) * BINS]
+        mx = lg.max(axis=1, keepdims=True)
+        lz = mx[:, 0] + np.log(np.exp(lg - mx).sum(axis=1))
+        t = targets[:, h]
+        loss += (lz - lg[np.arange(B), t]).sum()
+        p = np.exp(lg - lz[:, None])
+        p[np.arange(B), t] -= 1.0
+        d[:, h * BINS:(h + 1) * BINS] = p / B
+    dWs, dbs = [None] * len(Ws), [None] * len(Ws)
+    delta = d
+    for li in range(len(Ws) - 1, -1, -1):
+        hin, pre = cache[li]
+        dWs[li] = delta.T @ hin
+        dbs[li] = delta.sum(axis=0)
+        if li > 0:
+            _, pre_prev = cache[li - 1]
+            delta = (delta @ Ws[li]) * gelu_grad(pre_prev)
+    return loss / B, dWs, dbs

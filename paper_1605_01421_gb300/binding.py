@@ -120,7 +120,9 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_model_destroy", "sg_strerror", "sg_philox_batch", "sg_log_batch",
            "sg_u01_batch", "sg_set_kernel_timing", "sg_fp64_fma_probe",
            "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs",
-           "sg_gemm_bf16"]
+           "sg_gemm_bf16", "sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
+           "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
+           "sg_emu_sample", "sg_emulator_set"]
 
 _lock = threading.Lock()
 _lib = None
@@ -178,6 +180,21 @@ def lib(path: str | None = None):
         L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
                                    i32, vp]
         L.sg_gemm_bf16.restype = ctypes.c_int
+        f32, f64 = ctypes.c_float, ctypes.c_double
+        L.sg_mlp_ce_loss.argtypes = [vp, i32, vp, i32, vp, i32, vp, vp]
+        L.sg_gelu_backward.argtypes = [vp, vp, i64, vp, vp]
+        L.sg_transpose_bf16.argtypes = [vp, i32, i32, vp, vp]
+        L.sg_colsum_bf16.argtypes = [vp, i32, i32, vp, vp]
+        L.sg_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
+        L.sg_emu_features.argtypes = [vp, vp, i64, vp, i32, f64, f64, vp, vp, vp]
+        L.sg_emu_targets.argtypes = [vp, vp, i64, vp, vp]
+        L.sg_emu_sample.argtypes = [vp, i32, vp, vp, i64, i32, u64, i32, vp, vp]
+        L.sg_emulator_set.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, f64,
+                                      f64, ctypes.c_int]
+        for nm in ("sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
+                   "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
+                   "sg_emu_sample", "sg_emulator_set"):
+            getattr(L, nm).restype = ctypes.c_int
         _lib = L
         return L
 
@@ -310,6 +327,21 @@ class Model:
         if rc:
             raise SimInfError(rc)
         return npb.value, ha.value, ms.value
+
+    def set_emulator(self, emu, max_herd=2000, phi_lo=0.0, phi_hi=6.0, enable=True):
+        """Let sg_run use a trained emulator (emulator.Emulator) for the
+        in-range nodes; the emulator's tensors must outlive the runs."""
+        vp = ctypes.c_void_p
+        if enable:
+            W = (vp * 4)(*[ctypes.c_void_p(t.data_ptr()) for t in emu.W16])
+            b = (vp * 4)(*[ctypes.c_void_p(t.data_ptr()) for t in emu.b32])
+            self._emu_ref = emu
+        else:
+            W = b = None
+        rc = lib().sg_emulator_set(self._h, W, b, int(max_herd), float(phi_lo),
+                                   float(phi_hi), 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
 
     def set_graphs(self, enable=True):
         rc = lib().sg_set_graphs(self._h, 1 if enable else 0)

@@ -13,6 +13,7 @@
 // share a counter.
 #define SG_STREAM_SSA 0u
 #define SG_STREAM_EVENTS 1u
+#define SG_STREAM_EMU 2u
 
 // Model tables in the layout the kernels read (passed by value).
 struct SgTables {

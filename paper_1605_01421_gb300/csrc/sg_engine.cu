@@ -23,6 +23,7 @@
 
 #include "sg_common.h"
 #include "sg_device.cuh"
+#include "sg_mlp.h"
 #include "sg_plan.h"
 
 using namespace sg;
@@ -76,6 +77,8 @@ struct DayArgs {
   int32_t heavy_after;     // draws a thread takes before its warp takes over
   int32_t npb;             // nodes per block (<= kDayBlock); the other
                            // threads of the block only serve heavy nodes
+  const int32_t *emu;      // [R][Nn][4]: emulated increments of I_1..I_3 and
+                           // a flag (1 = use them instead of the SSA), or null
   uint32_t k0, k1;         // Philox key (seed)
   SgDevError *err;
   SgCounters *cnt;
@@ -481,7 +484,18 @@ k_days(const SgTables tb, const DayArgs a) {
     if (threadIdx.x == 0) s_nheavy = 0;
     __syncthreads();
     int my = -1;
-    if (live && code == 0) {
+    const bool emulated = live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
+    if (emulated) {
+      // the learned emulator's sampled one-day increments (SISe3 only):
+      // I_a += d_a, S_a -= d_a, each age class keeps its size
+#pragma unroll
+      for (int h = 0; h < C / 2; ++h) {
+        const int dlt = a.emu[gid * 4 + h];
+        u[2 * h] -= dlt;
+        u[2 * h + 1] += dlt;
+      }
+    }
+    if (live && code == 0 && !emulated) {
       double kf[NK], w[T];
       M::prepare(v, tb.gdata, kf);
 #pragma unroll
@@ -869,13 +883,13 @@ int upload(DevBuf<T> &b, const std::vector<T> &h) {
 // that was reallocated in between (by any call) forces a new capture.
 struct GraphKey {
   const void *u0, *v0, *U, *V;
-  const void *u, *v, *cur, *rec;
+  const void *u, *v, *cur, *rec, *emu;
   uint64_t seed;
   int32_t n_rep, n_tspan, t0, t_end, npb, heavy_after;
   uint64_t plan_version;
   bool operator==(const GraphKey &o) const {
     return u0 == o.u0 && v0 == o.v0 && U == o.U && V == o.V && u == o.u && v == o.v &&
-           cur == o.cur && rec == o.rec && seed == o.seed && n_rep == o.n_rep &&
+           cur == o.cur && rec == o.rec && emu == o.emu && seed == o.seed && n_rep == o.n_rep &&
            n_tspan == o.n_tspan && t0 == o.t0 && t_end == o.t_end && npb == o.npb &&
            heavy_after == o.heavy_after && plan_version == o.plan_version;
   }
@@ -922,6 +936,16 @@ struct sg_model {
   long long graph_launches = 0;
   int32_t graph_waves = 0;
   uint64_t plan_version = 0;
+  // learned one-day emulator (SISe3): caller-owned device weights, own buffers
+  bool emu_on = false;
+  const __nv_bfloat16 *emu_W[4] = {};
+  const float *emu_b[4] = {};
+  int32_t emu_max_herd = 2000;
+  double emu_phi_lo = 0.0, emu_phi_hi = 0.0;
+  uint64_t emu_version = 0;
+  DevBuf<__nv_bfloat16> emu_feat, emu_ha, emu_hb;
+  DevBuf<float> emu_logits;
+  DevBuf<int32_t> emu_flag, emu_delta;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -1022,6 +1046,8 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->e_prop.release(); m->e_index.release(); m->wave_ev.release(); m->wave_off.release();
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
+  m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
+  m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
@@ -1237,7 +1263,89 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
   }
   DayArgs da = da0;
   EvArgs ea = ea0;
-  if (Nn > 0 && days > 0) {
+  if (Nn > 0 && days > 0 && m->emu_on) {
+    // One day at a time: finish the previous day, emulator features and MLP
+    // for every node, sampling, then the day kernel (SSA only for the nodes
+    // outside the emulator's range) and the day's external transfers.
+    const long long units = (long long)Nn * n_rep;
+    EmuParams ep{};
+    for (int i = 0; i < 11; ++i) ep.gdata[i] = tb.gdata[i];
+    ep.max_herd = m->emu_max_herd;
+    ep.phi_lo = m->emu_phi_lo;
+    ep.phi_hi = m->emu_phi_hi;
+    const unsigned gu = (unsigned)std::max<long long>(1, std::min<long long>(16384, (units + 255) / 256));
+    const unsigned gw = (unsigned)std::max<long long>(1, std::min<long long>(1 << 20, (units * 32 + 255) / 256));
+    bool pending = false;
+    for (int32_t d = 0; d < days; ++d) {
+      const int32_t T = t0 + 1 + d;
+      if (pending) {
+        da.T_begin = T;
+        da.T_end = T;
+        da.finish_first = 1;
+        da.finish_last = 0;
+        da.emu = nullptr;
+        launch_days_kind(m, da, st);
+        ++launches;
+      }
+      k_emu_features<<<gu, 256, 0, st>>>(m->u.p, m->v.p, units, ep, m->emu_feat.p,
+                                         m->emu_flag.p);
+      const __nv_bfloat16 *in = m->emu_feat.p;
+      int kin = kEmuIn;
+      __nv_bfloat16 *outs[3] = {m->emu_ha.p, m->emu_hb.p, m->emu_ha.p};
+      for (int l = 0; l < 4; ++l) {
+        GemmArgs g{};
+        g.A = in;
+        g.lda = kin;
+        g.Bt = m->emu_W[l];
+        g.ldb = kin;
+        g.M = (int)units;
+        g.N = l < 3 ? kEmuHidden : kEmuOut;
+        g.K = kin;
+        g.bias = m->emu_b[l];
+        g.act = l < 3 ? 1 : 0;
+        g.C32 = l < 3 ? nullptr : m->emu_logits.p;
+        g.ldc32 = kEmuOut;
+        g.C16 = l < 3 ? outs[l] : nullptr;
+        g.ldc16 = kEmuHidden;
+        g.err = nullptr;
+        gemm_bf16(g, st);
+        ++launches;
+        if (l < 3) {
+          in = outs[l];
+          kin = kEmuHidden;
+        }
+      }
+      k_emu_sample<<<gw, 256, 0, st>>>(m->emu_logits.p, kEmuOut, m->u.p, m->emu_flag.p, units,
+                                       Nn, da.k0, da.k1, T, m->emu_delta.p);
+      launches += 2;
+      const bool e2_today = P.day_has_e2[d] != 0;
+      da.T_begin = T;
+      da.T_end = T + 1;
+      da.finish_first = 0;
+      da.finish_last = e2_today ? 0 : 1;
+      da.emu = m->emu_delta.p;
+      launch_days_kind(m, da, st);
+      ++launches;
+      if (e2_today) {
+        ea.day = T;
+        const long long b0 = (long long)d * slots, b1 = b0 + slots;
+        const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
+        launch_e2_kind(m, ea, wb, we, d, slots, n_rep, st);
+        ++launches;
+        waves += (int32_t)(we - wb);
+      }
+      pending = e2_today;
+    }
+    if (pending) {
+      da.T_begin = t_end + 1;
+      da.T_end = t_end + 1;
+      da.finish_first = 1;
+      da.finish_last = 0;
+      da.emu = nullptr;
+      launch_days_kind(m, da, st);
+      ++launches;
+    }
+  } else if (Nn > 0 && days > 0) {
     bool pending = false;  // the previous unit step still needs finishing
     int32_t d = 0;
     while (d < days) {
@@ -1312,6 +1420,15 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
       (rc = m->e1_cur.ensure((size_t)std::max(1, Nn * n_rep))) ||
       (rc = m->rec.ensure((size_t)days + 1)))
     return rc;
+  if (m->emu_on) {
+    const size_t units = (size_t)Nn * n_rep;
+    if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
+        (rc = m->emu_ha.ensure(units * kEmuHidden)) ||
+        (rc = m->emu_hb.ensure(units * kEmuHidden)) ||
+        (rc = m->emu_logits.ensure(units * kEmuOut)) || (rc = m->emu_flag.ensure(units)) ||
+        (rc = m->emu_delta.ensure(units * 4)) || (rc = gemm_prepare()))
+      return rc;
+  }
   // tspan slot of every unit time, uploaded when it changes
   std::vector<int32_t> rec(days + 1, -1);
   for (int i = 0; i < n_tspan; ++i) rec[tspan[i] - t0] = i;
@@ -1348,6 +1465,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.err = m->err.p;
   da.cnt = m->cnt.p;
   da.T_begin = da.T_end = da.finish_first = da.finish_last = 0;
+  da.emu = nullptr;
 
   EvArgs ea;
   ea.ev = evd;
@@ -1367,10 +1485,23 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   // while nothing it depends on changes (not on the legacy default stream,
   // which cannot be captured, and not while kernels are being timed).
   const bool use_graph = m->graphs && st != nullptr && !m->timing;
-  const GraphKey key{d_u0,      d_v0,     d_U,          d_V,       m->u.p,
-                     m->v.p,    m->e1_cur.p, m->rec.p,  seed,      n_rep,
-                     n_tspan,   t0,        t_end,        da.npb,    da.heavy_after,
-                     m->plan_version};
+  const GraphKey key{d_u0,
+                     d_v0,
+                     d_U,
+                     d_V,
+                     m->u.p,
+                     m->v.p,
+                     m->e1_cur.p,
+                     m->rec.p,
+                     m->emu_on ? (const void *)m->emu_logits.p : nullptr,
+                     seed,
+                     n_rep,
+                     n_tspan,
+                     t0,
+                     t_end,
+                     da.npb,
+                     da.heavy_after,
+                     m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)};
   if (use_graph) {
     if (!(m->graph_ok && m->graph_key == key)) {
       if (m->graph_exec) {
@@ -1438,6 +1569,13 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   if (e.code) {
     fill_error(err, e.code, e.rep, e.node, e.day, e.event);
     return e.code;
+  }
+  if (m->emu_on) {
+    rc = gemm_check(st);
+    if (rc) {
+      fill_error(err, rc, -1, -1, -1, -1);
+      return rc;
+    }
   }
   return SG_OK;
 }
@@ -1709,6 +1847,7 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.slots = 1;
       da.heavy_after = 2;
       da.npb = default_npb((long long)Nn * n_rep);
+      da.emu = nullptr;
       da.T_begin = t0 + 1;
       da.T_end = t_end + 1;
       da.finish_first = 0;
@@ -1817,5 +1956,28 @@ extern "C" int sg_set_graphs(sg_model *m, int enable) {
   if (!m) return SG_ERR_ARG;
   m->graphs = enable != 0;
   if (!m->graphs) m->graph_ok = false;
+  return SG_OK;
+}
+
+extern "C" int sg_emulator_set(sg_model *m, const void *const *W, const float *const *b,
+                               int32_t max_herd, double phi_lo, double phi_hi, int enable) {
+  if (!m) return SG_ERR_ARG;
+  if (!enable) {
+    m->emu_on = false;
+    m->graph_ok = false;
+    return SG_OK;
+  }
+  if (m->tb.kind != SG_SISE3 || !W || !b || max_herd < -1 || !(phi_lo <= phi_hi)) return SG_ERR_ARG;
+  for (int l = 0; l < 4; ++l) {
+    if (!W[l] || !b[l] || ((uintptr_t)W[l] & 15) != 0) return SG_ERR_ARG;
+    m->emu_W[l] = (const __nv_bfloat16 *)W[l];
+    m->emu_b[l] = b[l];
+  }
+  m->emu_max_herd = max_herd;
+  m->emu_phi_lo = phi_lo;
+  m->emu_phi_hi = phi_hi;
+  m->emu_on = true;
+  ++m->emu_version;
+  m->graph_ok = false;
   return SG_OK;
 }

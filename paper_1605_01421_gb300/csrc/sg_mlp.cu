@@ -206,6 +206,11 @@ int gemm_bf16(const GemmArgs &g0, cudaStream_t st) {
   return SG_OK;
 }
 
+int gemm_prepare() {
+  int *e = nullptr;
+  return gemm_err_buf(&e);
+}
+
 int gemm_check(cudaStream_t st) {
   int *e = nullptr;
   int rc = gemm_err_buf(&e);
@@ -247,4 +252,325 @@ extern "C" int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t 
   const int rc = sg::gemm_bf16(g, st);
   if (rc) return rc;
   return sg::gemm_check(st);
+}
+
+// ---------------------------------------------------------------------------
+// Element-wise kernels of the emulator: training loss, GELU backward,
+// transposes, bias gradients, Adam, input features, output sampling.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr int kHeads = 3;    // one head per age class
+constexpr int kBins = 129;   // increments -64 .. 64
+constexpr int kHalf = 64;
+
+__device__ __forceinline__ float gelu_grad(float x) {
+  const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+  const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
+  return cdf + x * pdf;
+}
+
+// Cross-entropy over the three 129-way heads, one warp per row: loss and
+// d loss / d logits (scaled by 1 / B, BF16; padding columns get 0).
+__global__ void k_ce_loss(const float *__restrict__ logits, int ldl,
+                          const int32_t *__restrict__ tgt, int B, __nv_bfloat16 *dlog, int ldd,
+                          int ncols_grad, double *loss_sum) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= B) return;
+  const float *row = logits + (long long)warp * ldl;
+  __nv_bfloat16 *grow = dlog + (long long)warp * ldd;
+  const float invB = 1.0f / (float)B;
+  float loss = 0.0f;
+  for (int h = 0; h < kHeads; ++h) {
+    const float *lg = row + h * kBins;
+    float mx = -INFINITY;
+    for (int c = lane; c < kBins; c += 32) mx = fmaxf(mx, lg[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float se = 0.0f;
+    for (int c = lane; c < kBins; c += 32) se += expf(lg[c] - mx);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) se += __shfl_xor_sync(0xffffffffu, se, o);
+    const float lz = mx + logf(se);
+    const int t = tgt[(long long)warp * kHeads + h];
+    if (lane == 0) loss += lz - lg[t];
+    for (int c = lane; c < kBins; c += 32) {
+      const float p = expf(lg[c] - lz) - (c == t ? 1.0f : 0.0f);
+      grow[h * kBins + c] = __float2bfloat16_rn(p * invB);
+    }
+  }
+  for (int c = kHeads * kBins + lane; c < ncols_grad; c += 32) grow[c] = __float2bfloat16_rn(0.0f);
+  if (lane == 0) atomicAdd(loss_sum, (double)loss);
+}
+
+__global__ void k_gelu_bwd(const float *__restrict__ dpost, const float *__restrict__ pre,
+                           long long n, __nv_bfloat16 *dpre) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dpre[i] = __float2bfloat16_rn(dpost[i] * gelu_grad(pre[i]));
+}
+
+// dst[c][r] = src[r][c] through 32 x 32 shared-memory tiles.
+__global__ void k_transpose(const __nv_bfloat16 *__restrict__ src, int rows, int cols,
+                            __nv_bfloat16 *dst) {
+  __shared__ __nv_bfloat16 tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = src[(long long)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[(long long)c * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+__global__ void k_colsum(const __nv_bfloat16 *__restrict__ src, int rows, int cols, float *out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  float s = 0.0f;
+  for (int r = 0; r < rows; ++r) s += __bfloat162float(src[(long long)r * cols + c]);
+  out[c] = s;
+}
+
+__global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v, long long n,
+                       float lr, float b1, float b2, float eps, float c1, float c2,
+                       __nv_bfloat16 *p16) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    if (p16) p16[i] = __float2bfloat16_rn(pi);
+  }
+}
+
+}  // namespace
+
+namespace sg {
+
+// Input features of one SISe3 node for the emulator, and whether the node is
+// in the emulator's range (herd <= max_herd and phi_lo <= phi <= phi_hi).
+__global__ void k_emu_features(const int32_t *__restrict__ u, const double *__restrict__ v,
+                               long long units, EmuParams ep, __nv_bfloat16 *feat,
+                               int32_t *flag) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < units;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int32_t *un = u + i * 6;
+    int herd = 0;
+#pragma unroll
+    for (int p = 0; p < 6; ++p) herd += un[p];
+    const double phi = v[i];
+    const bool in = herd <= ep.max_herd && phi >= ep.phi_lo && phi <= ep.phi_hi;
+    flag[i] = in ? 1 : 0;
+    float f[16];
+#pragma unroll
+    for (int p = 0; p < 6; ++p) f[p] = log1pf((float)max(un[p], 0));
+    f[6] = (float)phi;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      f[7 + a] = 50.0f * (float)ep.gdata[a];
+      f[10 + a] = 10.0f * (float)ep.gdata[3 + a];
+    }
+    f[13] = f[14] = f[15] = 0.0f;
+    __nv_bfloat16 *row = feat + i * 16;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) row[k] = __float2bfloat16_rn(f[k]);
+  }
+}
+
+// Sample each in-range node's increments from the emulator's three heads:
+// softmax over the 129 bins, inverse CDF at a uniform from the emulator's
+// Philox stream (seed, replicate, node, day), and clamp so that neither S_a
+// nor I_a becomes negative (each age class keeps its size within the day).
+// One warp per node; lane l holds bins 5 l .. 5 l + 4.
+__global__ void k_emu_sample(const float *__restrict__ logits, int ldl,
+                             const int32_t *__restrict__ u, const int32_t *__restrict__ flag,
+                             long long units, int n_nodes, uint32_t k0, uint32_t k1, int T,
+                             int32_t *delta) {
+  const long long w = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= units) return;
+  int32_t *out = delta + w * 4;
+  if (!flag[w]) {
+    if (lane == 0) out[3] = 0;
+    return;
+  }
+  const int rep = (int)(w / n_nodes), node = (int)(w - (long long)rep * n_nodes);
+  const U4 x = philox10(U4{0u, (uint32_t)node, (uint32_t)T, (SG_STREAM_EMU << 24) | (uint32_t)rep},
+                        k0, k1);
+  const uint32_t words[3] = {x.x, x.y, x.z};
+  const float *row = logits + w * ldl;
+  for (int h = 0; h < kHeads; ++h) {
+    const float *lg = row + h * kBins;
+    float vals[5];
+    float mx = -INFINITY;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      const int c = lane * 5 + j;
+      vals[j] = c < kBins ? lg[c] : -INFINITY;
+      mx = fmaxf(mx, vals[j]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    float part = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      vals[j] = lane * 5 + j < kBins ? expf(vals[j] - mx) : 0.0f;
+      part += vals[j];
+    }
+    // inclusive scan of the lane sums
+    float incl = part;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const float t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const float total = __shfl_sync(0xffffffffu, incl, 31);
+    const float target = ((float)(words[h] >> 8) + 0.5f) * (1.0f / 16777216.0f) * total;
+    // the lane whose range holds the target, then the bin inside it
+    const unsigned ge = __ballot_sync(0xffffffffu, incl >= target);
+    const int owner = ge ? __ffs(ge) - 1 : 31;
+    int bin = kBins - 1;
+    if (lane == owner) {
+      float acc = incl - part;
+      bin = min(lane * 5 + 4, kBins - 1);
+#pragma unroll
+      for (int j = 0; j < 5; ++j) {
+        acc += vals[j];
+        if (acc >= target && lane * 5 + j < kBins) {
+          bin = lane * 5 + j;
+          break;
+        }
+      }
+    }
+    bin = __shfl_sync(0xffffffffu, bin, owner);
+    if (lane == 0) {
+      const int S = u[w * 6 + 2 * h], I = u[w * 6 + 2 * h + 1];
+      int d = bin - kHalf;
+      d = max(d, -I);
+      d = min(d, S);
+      out[h] = d;
+    }
+  }
+  if (lane == 0) out[3] = 1;
+}
+
+// Training targets: the one-day increment of I_a, as a bin index in 0..128
+// (clamped to the edge bins).
+__global__ void k_emu_targets(const int32_t *__restrict__ u0, const int32_t *__restrict__ u1,
+                              long long units, int32_t *tgt) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < units;
+       i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int d = u1[i * 6 + 2 * a + 1] - u0[i * 6 + 2 * a + 1];
+      tgt[i * 3 + a] = min(max(d + kHalf, 0), kBins - 1);
+    }
+  }
+}
+
+}  // namespace sg
+
+static unsigned grid_n(long long n, int block) {
+  return (unsigned)std::max<long long>(1, std::min<long long>(16384, (n + block - 1) / block));
+}
+
+static int finish(cudaStream_t st) {
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  return SG_OK;
+}
+
+extern "C" int sg_mlp_ce_loss(const float *logits, int32_t ldl, const int32_t *targets,
+                              int32_t B, void *dlogits, int32_t ldd, double *loss_sum,
+                              void *stream) {
+  if (B < 0 || ldl < 387 || ldd < 387 || !logits || !targets || !dlogits || !loss_sum)
+    return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (B) k_ce_loss<<<grid_n((long long)B * 32, 256), 256, 0, st>>>(
+      logits, ldl, targets, B, (__nv_bfloat16 *)dlogits, ldd, ldd, loss_sum);
+  return finish(st);
+}
+
+extern "C" int sg_gelu_backward(const float *dpost, const float *pre, int64_t n, void *dpre,
+                                void *stream) {
+  if (n < 0 || (n && (!dpost || !pre || !dpre))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n) k_gelu_bwd<<<grid_n(n, 256), 256, 0, st>>>(dpost, pre, n, (__nv_bfloat16 *)dpre);
+  return finish(st);
+}
+
+extern "C" int sg_transpose_bf16(const void *src, int32_t rows, int32_t cols, void *dst,
+                                 void *stream) {
+  if (rows < 0 || cols < 0 || (rows && cols && (!src || !dst))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rows && cols)
+    k_transpose<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, st>>>(
+        (const __nv_bfloat16 *)src, rows, cols, (__nv_bfloat16 *)dst);
+  return finish(st);
+}
+
+extern "C" int sg_colsum_bf16(const void *src, int32_t rows, int32_t cols, float *out,
+                              void *stream) {
+  if (rows < 0 || cols < 0 || (cols && (!src || !out))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cols) k_colsum<<<(cols + 127) / 128, 128, 0, st>>>((const __nv_bfloat16 *)src, rows, cols, out);
+  return finish(st);
+}
+
+extern "C" int sg_adam_step(float *params, const float *grads, float *m, float *v, int64_t n,
+                            float lr, float beta1, float beta2, float eps, int32_t step,
+                            void *params_bf16, void *stream) {
+  if (n < 0 || step < 1 || (n && (!params || !grads || !m || !v))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+  if (n)
+    k_adam<<<grid_n(n, 256), 256, 0, st>>>(params, grads, m, v, n, lr, beta1, beta2, eps, c1, c2,
+                                           (__nv_bfloat16 *)params_bf16);
+  return finish(st);
+}
+
+extern "C" int sg_emu_features(const int32_t *u, const double *v, int64_t units,
+                               const double *gdata, int32_t max_herd, double phi_lo,
+                               double phi_hi, void *feat, int32_t *flag, void *stream) {
+  if (units < 0 || !gdata || (units && (!u || !v || !feat || !flag))) return SG_ERR_ARG;
+  EmuParams ep{};
+  for (int i = 0; i < 11; ++i) ep.gdata[i] = gdata[i];
+  ep.max_herd = max_herd;
+  ep.phi_lo = phi_lo;
+  ep.phi_hi = phi_hi;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (units)
+    k_emu_features<<<grid_n(units, 256), 256, 0, st>>>(u, v, units, ep, (__nv_bfloat16 *)feat,
+                                                       flag);
+  return finish(st);
+}
+
+extern "C" int sg_emu_targets(const int32_t *u_before, const int32_t *u_after, int64_t units,
+                              int32_t *targets, void *stream) {
+  if (units < 0 || (units && (!u_before || !u_after || !targets))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (units) k_emu_targets<<<grid_n(units, 256), 256, 0, st>>>(u_before, u_after, units, targets);
+  return finish(st);
+}
+
+extern "C" int sg_emu_sample(const float *logits, int32_t ldl, const int32_t *u,
+                             const int32_t *flag, int64_t units, int32_t n_nodes, uint64_t seed,
+                             int32_t day, int32_t *delta, void *stream) {
+  if (units < 0 || n_nodes < 1 || ldl < 387 || (units && (!logits || !u || !flag || !delta)))
+    return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (units)
+    k_emu_sample<<<grid_n(units * 32, 256), 256, 0, st>>>(
+        logits, ldl, u, flag, units, n_nodes, (uint32_t)seed, (uint32_t)(seed >> 32), day, delta);
+  return finish(st);
 }

@@ -29,5 +29,21 @@ struct GemmArgs {
 
 int gemm_bf16(const GemmArgs &g, cudaStream_t st);
 int gemm_check(cudaStream_t st);
+int gemm_prepare();  // allocates the error word (call before stream capture)
+
+constexpr int kEmuIn = 16, kEmuHidden = 256, kEmuOut = 392;  // 3 x 129 used
+
+// What the emulator's feature kernel needs of an SISe3 model.
+struct EmuParams {
+  double gdata[11];
+  int32_t max_herd;
+  double phi_lo, phi_hi;
+};
+
+__global__ void k_emu_features(const int32_t *u, const double *v, long long units, EmuParams ep,
+                               __nv_bfloat16 *feat, int32_t *flag);
+__global__ void k_emu_sample(const float *logits, int ldl, const int32_t *u, const int32_t *flag,
+                             long long units, int n_nodes, uint32_t k0, uint32_t k1, int T,
+                             int32_t *delta);
 
 }  // namespace sg

@@ -1,0 +1,142 @@
+"""The learned one-day emulator: gradients of the tensor-core training path
+against the FP64 oracle network, the optimiser, the sampler, training on
+SSA-generated data, and the engine's use of the emulator with SSA fallback."""
+import numpy as np
+import pytest
+
+from paper_1605_01421_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_01421_gb300 import binding, emulator
+    binding.build()
+    return torch, binding, emulator
+
+
+def test_gradients_match_fp64_oracle(env):
+    torch, binding, emulator = env
+    from oracle import mlp
+    emu = emulator.Emulator(seed=1)
+    rng = np.random.default_rng(2)
+    B = 512
+    X = torch.as_tensor(rng.normal(0, 1, (B, 16)), dtype=torch.float32).to(torch.bfloat16).cuda()
+    t = torch.as_tensor(rng.integers(40, 90, (B, 3)), dtype=torch.int32).cuda()
+    loss, dW, db = emu.gradients(X, t)
+    Ws = [w.double().cpu().numpy() for w in emu.W16]
+    bs = [b.double().cpu().numpy() for b in emu.b32]
+    ref_loss, rdW, rdb = mlp.loss_and_grads(Ws, bs, X.double().cpu().numpy(),
+                                            t.cpu().numpy())
+    assert abs(loss - ref_loss) < 2e-2 * abs(ref_loss)
+    for li in range(4):
+        g, r = dW[li].double().cpu().numpy(), rdW[li]
+        assert np.linalg.norm(g - r) <= 5e-2 * np.linalg.norm(r) + 1e-6, li
+        g, r = db[li].double().cpu().numpy(), rdb[li]
+        assert np.linalg.norm(g - r) <= 5e-2 * np.linalg.norm(r) + 1e-6, li
+
+
+def test_adam_step_matches_definition(env):
+    torch, binding, emulator = env
+    import ctypes
+    L = binding.lib()
+    n = 1000
+    g = torch.Generator().manual_seed(0)
+    p = torch.randn(n, generator=g).cuda()
+    gr = torch.randn(n, generator=g).cuda()
+    m = torch.randn(n, generator=g).cuda() * 0.1
+    v = torch.rand(n, generator=g).cuda() * 0.1
+    p0, m0, v0 = p.clone(), m.clone(), v.clone()
+    p16 = torch.empty(n, dtype=torch.bfloat16, device="cuda")
+    rc = L.sg_adam_step(ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(gr.data_ptr()),
+                        ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), n, 1e-2,
+                        0.9, 0.999, 1e-8, 3, ctypes.c_void_p(p16.data_ptr()),
+                        binding._stream_handle(None))
+    assert rc == 0
+    m1 = 0.9 * m0 + 0.1 * gr
+    v1 = 0.999 * v0 + 0.001 * gr * gr
+    p1 = p0 - 1e-2 * (m1 / (1 - 0.9 ** 3)) / (torch.sqrt(v1 / (1 - 0.999 ** 3)) + 1e-8)
+    assert torch.allclose(p, p1, rtol=1e-5, atol=1e-6)
+    assert torch.allclose(p16.float(), p1, rtol=1e-2, atol=1e-2)
+
+
+def test_sampler_law_and_clamping(env):
+    torch, binding, emulator = env
+    import ctypes
+    stats = pytest.importorskip("scipy.stats")
+    L = binding.lib()
+    units = 20000
+    rng = np.random.default_rng(3)
+    row = rng.normal(0, 1.5, 392).astype(np.float32)
+    logits = torch.as_tensor(np.tile(row, (units, 1))).cuda()
+    u = np.tile(np.array([[100, 100, 3, 2, 100, 100]], np.int32), (units, 1))
+    ud = torch.as_tensor(u).cuda()
+    flag = torch.ones(units, dtype=torch.int32, device="cuda")
+    flag[::7] = 0
+    delta = torch.full((units, 4), -99, dtype=torch.int32, device="cuda")
+    rc = L.sg_emu_sample(ctypes.c_void_p(logits.data_ptr()), 392, ctypes.c_void_p(ud.data_ptr()),
+                         ctypes.c_void_p(flag.data_ptr()), units, units, 11, 5,
+                         ctypes.c_void_p(delta.data_ptr()), binding._stream_handle(None))
+    assert rc == 0
+    dl = delta.cpu().numpy()
+    used = dl[:, 3] == 1
+    assert np.array_equal(used, flag.cpu().numpy() == 1)
+    # head 0: increments within [-100, 100] are not clamped: chi-square
+    # against the softmax law of the row
+    r64 = row[:129].astype(np.float64)
+    p = np.exp(r64 - r64.max())
+    p /= p.sum()
+    obs = np.bincount(dl[used, 0] + 64, minlength=129).astype(float)
+    keep = p * used.sum() >= 5
+    exp = p * used.sum()
+    obs_k = np.r_[obs[keep], obs[~keep].sum()]
+    exp_k = np.r_[exp[keep], exp[~keep].sum()]
+    exp_k *= obs_k.sum() / exp_k.sum()
+    assert stats.chisquare(obs_k, exp_k).pvalue > 1e-3
+    # head 1: S = 3, I = 2 bounds the increment to -2 .. 3
+    assert dl[used, 1].min() >= -2 and dl[used, 1].max() <= 3
+
+
+def test_engine_without_emulated_nodes_equals_ssa(env, orc):
+    # with no node in range every node falls back to the SSA: bit-exact
+    torch, binding, emulator = env
+    w = W.config_sise3(n_nodes=600, days=40, gen_seed=14)
+    emu = emulator.Emulator(seed=0)
+    code, U0, V0, R0, err = orc.run(w)
+    m = binding.Model(w)
+    m.set_emulator(emu, max_herd=-1)
+    u0, v0 = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (w.u0, w.v0))
+    M = len(w.tspan)
+    U = torch.empty((1, M, w.n_nodes, 6), dtype=torch.int32, device="cuda")
+    V = torch.empty((1, M, w.n_nodes, 1), dtype=torch.float64, device="cuda")
+    rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V)
+    assert np.array_equal(U.cpu().numpy(), U0)
+    assert np.array_equal(V.cpu().numpy().view(np.uint64), V0.view(np.uint64))
+
+
+def test_training_and_emulated_run(env):
+    torch, binding, emulator = env
+    feat, tgt = emulator.make_dataset(200_000, 4, seed=1)
+    emu = emulator.Emulator(seed=0)
+    hist = emu.train(feat, tgt, steps=600, batch=4096, lr=2e-3)
+    assert np.mean(hist[-50:]) < 0.7 * np.mean(hist[:10])
+    res = emulator.compare_with_ssa(emu, n_probes=200, n_rep=500, seed=9)
+    assert res["w1_mean"] < 1.5, res
+    # the engine with the emulator: populations per age class stay exact
+    w = W.config_sise3(n_nodes=3000, days=60, gen_seed=15, events_per_node_day=0)
+    m = binding.Model(w)
+    m.set_emulator(emu, max_herd=2000)
+    u0, v0 = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (w.u0, w.v0))
+    M = len(w.tspan)
+    U = torch.empty((1, M, w.n_nodes, 6), dtype=torch.int32, device="cuda")
+    V = torch.empty((1, M, w.n_nodes, 1), dtype=torch.float64, device="cuda")
+    rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V)
+    Uc = U.cpu().numpy()[0]
+    assert Uc.min() >= 0
+    for a in range(3):
+        tot = Uc[:, :, 2 * a] + Uc[:, :, 2 * a + 1]
+        assert np.all(tot == tot[0:1])
