@@ -354,6 +354,113 @@ def bench_gpu(args):
         dist.destroy_process_group()
 
 
+def bench_emulator(args):
+    """The learned one-day emulator on an SISe3 workload: train it on one-day
+    SSA outcomes with the library's own kernels, measure its error against
+    1,000-replicate SSA ensembles (W1, KS), and compare node-days/s of the
+    run with the emulator (SSA fallback for herds > 2,000) to the plain SSA
+    on the same workload.  Prints one JSON line."""
+    import torch
+    from paper_1605_01421_gb300 import binding, emulator
+    binding.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    t0 = time.perf_counter()
+    feat, tgt = emulator.make_dataset(1_000_000, args.emu_batches, seed=1)
+    t_data = time.perf_counter() - t0
+    emu = emulator.Emulator(seed=0)
+    t0 = time.perf_counter()
+    hist = emu.train(feat, tgt, steps=args.emu_steps, batch=8192, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    del feat, tgt
+    err_bf16 = emulator.compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5)
+    # precision study: weights rounded to FP8 E4M3 (activations stay BF16)
+    saved = [w.clone() for w in emu.W16]
+    for li in range(4):
+        emu.W16[li].copy_(emu.W16[li].float().to(torch.float8_e4m3fn).to(torch.bfloat16))
+    err_fp8w = emulator.compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5)
+    for li in range(4):
+        emu.W16[li].copy_(saved[li])
+
+    from paper_1605_01421_gb300 import workloads as Wk
+    if args.emu_workload == "endemic":
+        w = Wk.config_endemic(days=args.emu_days)
+    else:
+        w = Wk.config_sise3(n_nodes=args.emu_nodes, days=args.emu_days)
+    M = len(w.tspan)
+    u0 = torch.as_tensor(np.array(w.u0, dtype=np.int32, order="C"), device="cuda")
+    v0 = torch.as_tensor(np.array(w.v0, dtype=np.float64, order="C"), device="cuda")
+    U = torch.empty((1, M, w.n_nodes, 6), dtype=torch.int32, device="cuda")
+    V = torch.empty((1, M, w.n_nodes, 1), dtype=torch.float64, device="cuda")
+    node_days = w.n_nodes * w.n_days
+
+    def timed(m, steps):
+        for _ in range(2):
+            m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(steps):
+            rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / steps, st
+
+    plain = binding.Model(w)
+    ms_plain, st_plain = timed(plain, args.steps)
+    m = binding.Model(w)
+    m.set_emulator(emu, max_herd=2000)
+    ms_emu, st_emu = timed(m, args.steps)
+    in_range = float((w.u0[0].sum(axis=1) <= 2000).mean())
+
+    # tensor-core roofline: the emulator's GEMM launches timed with CUDA
+    # events around each launch in one more run (kernel timing on)
+    m.set_kernel_timing(True)
+    rc, st_t, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=stream)
+    m.set_kernel_timing(False)
+    rows = w.n_nodes
+    # per day: features + 4 GEMMs + sampling are timed as emulator kernels;
+    # the FLOPs are the GEMMs'
+    flops_per_day = 2.0 * rows * (16 * 256 + 256 * 256 * 2 + 256 * 392)
+    gemm_ms = st_t["ms_mlp"] / max(1, w.n_days)
+    flops = flops_per_day
+    peak = _measured_bf16_tflops()
+    line = {"metric": "node-days/s with the learned emulator (SSA fallback for herds > 2000)",
+            "value": node_days / (ms_emu * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": 2, "ms_per_step": ms_emu,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 MLP (fp32 accumulation) + f64/int32 SSA fallback",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
+                       "events": w.n_events, "in_range_fraction": in_range,
+                       "mlp": "16-256-256-256-392 GELU, 3 heads x 129 bins"},
+            "plain_ssa": {"value": node_days / (ms_plain * 1e-3), "ms_per_step": ms_plain,
+                          "reactions": st_plain["reactions"]},
+            "speedup_vs_plain_gpu_ssa": ms_plain / ms_emu,
+            "training": {"node_days": int(args.emu_batches * 1_000_000), "steps": args.emu_steps,
+                         "batch": 8192, "seconds": t_train, "data_seconds": t_data,
+                         "loss_first": float(np.mean(hist[:20])),
+                         "loss_last": float(np.mean(hist[-50:]))},
+            "error_vs_ssa_bf16": err_bf16, "error_vs_ssa_fp8_weights": err_fp8w,
+            "roofline": {"bound": "tensor", "achieved": flops / (gemm_ms * 1e-3) / 1e12,
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (gemm_ms * 1e-3) / 1e12 / peak, "traffic": None,
+                         "kernel": f"emulator day: features, k_gemm_tc x 4 ({rows} rows), sampling",
+                         "avg_launch_ms": gemm_ms,
+                         "mlp_share_of_run": st_t["ms_mlp"] / max(1e-9, st_t["ms_mlp"]
+                                                                   + st_t["ms_ssa"] + st_t["ms_e2"])}}
+    print(json.dumps(line))
+
+
+def _measured_bf16_tflops():
+    try:
+        with open(os.path.join(_ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(_ROOT, "MEASURED_PEAKS.json")) as f:
@@ -368,12 +475,20 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sise", choices=["sise", "sir", "sise3", "batched"])
+    ap.add_argument("--workload", default="sise",
+                    choices=["sise", "sir", "sise3", "batched", "emulator"])
+    ap.add_argument("--emu-batches", type=int, default=50)
+    ap.add_argument("--emu-steps", type=int, default=4000)
+    ap.add_argument("--emu-nodes", type=int, default=37000)
+    ap.add_argument("--emu-days", type=int, default=3650)
+    ap.add_argument("--emu-workload", default="sise3", choices=["sise3", "endemic"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "emulator":
+        bench_emulator(args)
     else:
         bench_gpu(args)
 

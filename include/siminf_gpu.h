@@ -129,6 +129,8 @@ typedef struct {
   double ms_e1;           /* exit / enter / internal-transfer kernels       */
   double ms_e2;           /* external-transfer wave kernels                 */
   int64_t launches_ssa, launches_e1, launches_e2;
+  double ms_mlp;          /* emulator kernels (features, GEMMs, sampling)    */
+  int64_t launches_mlp;
 } sg_stats;
 
 /* Create a model from its tables (Sec. 3.2).  Validates the sizes against

@@ -110,7 +110,8 @@ class Stats(ctypes.Structure):
                 ("e2_waves", ctypes.c_int32), ("days", ctypes.c_int32),
                 ("ms_ssa", ctypes.c_double), ("ms_e1", ctypes.c_double),
                 ("ms_e2", ctypes.c_double), ("launches_ssa", ctypes.c_int64),
-                ("launches_e1", ctypes.c_int64), ("launches_e2", ctypes.c_int64)]
+                ("launches_e1", ctypes.c_int64), ("launches_e2", ctypes.c_int64),
+                ("ms_mlp", ctypes.c_double), ("launches_mlp", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

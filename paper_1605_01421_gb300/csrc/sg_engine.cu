@@ -921,7 +921,7 @@ struct sg_model {
   // per-kernel timing (sg_set_kernel_timing)
   bool timing = false;
   std::vector<cudaEvent_t> evpool;
-  std::vector<int> ev_kind;  // per launch: 0 SSA, 1 E1, 2 E2
+  std::vector<int> ev_kind;  // per launch: 0 SSA, 1 E1, 2 E2, 3 emulator GEMM
   size_t ev_used = 0;
   // buffers of sg_run_host
   DevBuf<int32_t> hu0, hU;
@@ -1287,8 +1287,11 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
         launch_days_kind(m, da, st);
         ++launches;
       }
-      k_emu_features<<<gu, 256, 0, st>>>(m->u.p, m->v.p, units, ep, m->emu_feat.p,
-                                         m->emu_flag.p);
+      {
+        LaunchTimer lt(m, st, 3);
+        k_emu_features<<<gu, 256, 0, st>>>(m->u.p, m->v.p, units, ep, m->emu_feat.p,
+                                           m->emu_flag.p);
+      }
       const __nv_bfloat16 *in = m->emu_feat.p;
       int kin = kEmuIn;
       __nv_bfloat16 *outs[3] = {m->emu_ha.p, m->emu_hb.p, m->emu_ha.p};
@@ -1308,15 +1311,21 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
         g.C16 = l < 3 ? outs[l] : nullptr;
         g.ldc16 = kEmuHidden;
         g.err = nullptr;
-        gemm_bf16(g, st);
+        {
+          LaunchTimer lt(m, st, 3);
+          gemm_bf16(g, st);
+        }
         ++launches;
         if (l < 3) {
           in = outs[l];
           kin = kEmuHidden;
         }
       }
-      k_emu_sample<<<gw, 256, 0, st>>>(m->emu_logits.p, kEmuOut, m->u.p, m->emu_flag.p, units,
-                                       Nn, da.k0, da.k1, T, m->emu_delta.p);
+      {
+        LaunchTimer lt(m, st, 3);
+        k_emu_sample<<<gw, 256, 0, st>>>(m->emu_logits.p, kEmuOut, m->u.p, m->emu_flag.p,
+                                         units, Nn, da.k0, da.k1, T, m->emu_delta.p);
+      }
       launches += 2;
       const bool e2_today = P.day_has_e2[d] != 0;
       da.T_begin = T;
@@ -1324,12 +1333,16 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
       da.finish_first = 0;
       da.finish_last = e2_today ? 0 : 1;
       da.emu = m->emu_delta.p;
-      launch_days_kind(m, da, st);
+      {
+        LaunchTimer lt(m, st, 0);
+        launch_days_kind(m, da, st);
+      }
       ++launches;
       if (e2_today) {
         ea.day = T;
         const long long b0 = (long long)d * slots, b1 = b0 + slots;
         const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
+        LaunchTimer lt(m, st, 2);
         launch_e2_kind(m, ea, wb, we, d, slots, n_rep, st);
         ++launches;
         waves += (int32_t)(we - wb);
@@ -1553,8 +1566,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
       float ms = 0.f;
       cudaEventElapsedTime(&ms, m->evpool[2 * i], m->evpool[2 * i + 1]);
       const int k = m->ev_kind[i];
-      (k == 0 ? stats->ms_ssa : k == 1 ? stats->ms_e1 : stats->ms_e2) += ms;
-      ++(k == 0 ? stats->launches_ssa : k == 1 ? stats->launches_e1 : stats->launches_e2);
+      (k == 0 ? stats->ms_ssa : k == 1 ? stats->ms_e1 : k == 2 ? stats->ms_e2 : stats->ms_mlp) += ms;
+      ++(k == 0 ? stats->launches_ssa
+                : k == 1 ? stats->launches_e1 : k == 2 ? stats->launches_e2 : stats->launches_mlp);
     }
     cudaGetLastError();
     stats->draws = (int64_t)m->h_cnt->draws;

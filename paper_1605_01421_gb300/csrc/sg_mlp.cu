@@ -29,6 +29,13 @@ __device__ __forceinline__ uint32_t stage_off(int row, int kgroup) {
   return (uint32_t)(((row >> 3) * 8 + kgroup) * 128 + (row & 7) * 16);
 }
 
+// 16-byte asynchronous global-to-shared copy; src_bytes = 0 zero-fills.
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gsrc, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(gsrc),
+               "r"(src_bytes)
+               : "memory");
+}
+
 __device__ __forceinline__ float gelu(float x) {
   return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
 }
@@ -68,35 +75,34 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
   uint32_t uses[2] = {0, 0};
   bool ok = true;
 
-  for (int s = 0; s < stages && ok; ++s) {
-    const int b = s & 1;
-    if (s >= 2) {  // buffer b is free once the MMAs of stage s - 2 are done
-      if (!tc::mbar_wait(&bar[b], (uses[b] - 1) & 1, kWaitLimit)) s_fail = 1;
-    }
-    __syncthreads();
-    if (s_fail) {
-      ok = false;
-      break;
-    }
-    const int k0 = s * kBK;
-    // A stage: 128 rows x 64
+  // Stage loader: every thread issues its 16-byte asynchronous copies
+  // (cp.async) for stage s into buffer s & 1, rows past M / N and columns
+  // past K are zero-filled.
+  auto load_stage = [&](int s) {
+    const int b = s & 1, k0 = s * kBK;
+    const uint32_t a0 = tc::smem_u32(sA[b]), b0 = tc::smem_u32(sB[b]);
     for (int idx = tid; idx < kBM * 8; idx += 128) {
       const int r = idx >> 3, kg = idx & 7;
       const int m = m0 + r, k = k0 + kg * 8;
-      int4 val = make_int4(0, 0, 0, 0);
-      if (m < g.M && k < g.K)
-        val = *reinterpret_cast<const int4 *>(g.A + (long long)m * g.lda + k);
-      *reinterpret_cast<int4 *>(sA[b] + stage_off(r, kg)) = val;
+      const bool in = m < g.M && k < g.K;
+      const __nv_bfloat16 *src = in ? g.A + (long long)m * g.lda + k : g.A;
+      cp_async16(a0 + stage_off(r, kg), src, in ? 16 : 0);
     }
-    // B stage: BN rows x 64
     for (int idx = tid; idx < BN * 8; idx += 128) {
       const int r = idx >> 3, kg = idx & 7;
       const int n = n0 + r, k = k0 + kg * 8;
-      int4 val = make_int4(0, 0, 0, 0);
-      if (n < g.N && k < g.K)
-        val = *reinterpret_cast<const int4 *>(g.Bt + (long long)n * g.ldb + k);
-      *reinterpret_cast<int4 *>(sB[b] + stage_off(r, kg)) = val;
+      const bool in = n < g.N && k < g.K;
+      const __nv_bfloat16 *src = in ? g.Bt + (long long)n * g.ldb + k : g.Bt;
+      cp_async16(b0 + stage_off(r, kg), src, in ? 16 : 0);
     }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  if (stages > 0) load_stage(0);
+  for (int s = 0; s < stages && ok; ++s) {
+    const int b = s & 1;
+    // stage s has landed in shared memory
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     tc::fence_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -112,6 +118,18 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
       tc::mma_commit(&bar[b]);
     }
     ++uses[b];
+    if (s + 1 < stages) {
+      // the other buffer is free once the MMAs of stage s - 1 are done; its
+      // loads then overlap the MMAs of stage s
+      const int nb = (s + 1) & 1;
+      if (uses[nb] > 0 && !tc::mbar_wait(&bar[nb], (uses[nb] - 1) & 1, kWaitLimit)) s_fail = 1;
+      __syncthreads();
+      if (s_fail) {
+        ok = false;
+        break;
+      }
+      load_stage(s + 1);
+    }
   }
   // all MMAs done: the last stage's commit completes after every earlier one
   if (ok && stages > 0) {
@@ -124,20 +142,63 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
     for (int b = 0; b < 2; ++b)
       if (uses[b]) tc::mbar_wait(&bar[b], (uses[b] - 1) & 1, kWaitLimit);
   } else {
+    // Epilogue.  Thread (warp w, lane l) owns tile row 32 w + l, i.e. TMEM
+    // lane 32 w + l.  FP32 results go out as 16-byte vectors; BF16 results
+    // are staged in shared memory (the stage buffers are free now) and then
+    // written row by row, each warp storing whole contiguous rows.
     tc::tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
+    constexpr int kPitch = BN * 2 + 16;  // bytes per staged row (bank offset)
+    unsigned char *stage = smem;
+    const int lr = warp * 32 + lane;
+    const int row = m0 + lr;
+    const bool vec32 = g.C32 && (g.ldc32 % 4) == 0 && (((uintptr_t)g.C32) & 15) == 0;
     for (int c = 0; c < BN; c += 16) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
-      if (row < g.M) {
+      const int nb = n0 + c;
+      if (g.bias) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int n = n0 + c + i;
-          if (n >= g.N) break;
-          float x = v[i] + (g.bias ? g.bias[n] : 0.0f);
-          if (g.C32) g.C32[(long long)row * g.ldc32 + n] = x;
-          if (g.act == 1) x = gelu(x);
-          if (g.C16) g.C16[(long long)row * g.ldc16 + n] = __float2bfloat16_rn(x);
+        for (int i = 0; i < 16; ++i) v[i] += (nb + i < g.N) ? __ldg(g.bias + nb + i) : 0.0f;
+      }
+      if (g.C32 && row < g.M) {
+        float *dst = g.C32 + (long long)row * g.ldc32 + nb;
+        if (vec32 && nb + 16 <= g.N) {
+#pragma unroll
+          for (int i = 0; i < 16; i += 4)
+            *reinterpret_cast<float4 *>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+          for (int i = 0; i < 16 && nb + i < g.N; ++i) dst[i] = v[i];
+        }
+      }
+      if (g.C16) {
+        uint32_t packed[8];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+          const float x0 = g.act == 1 ? gelu(v[i]) : v[i];
+          const float x1 = g.act == 1 ? gelu(v[i + 1]) : v[i + 1];
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+          packed[i / 2] = *reinterpret_cast<const uint32_t *>(&h2);
+        }
+        uint4 *sp = reinterpret_cast<uint4 *>(stage + lr * kPitch + c * 2);
+        sp[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        sp[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+    }
+    if (g.C16) {
+      __syncthreads();
+      constexpr int kVecPerRow = BN * 2 / 16;
+      const bool vec16 = (g.ldc16 % 8) == 0 && (((uintptr_t)g.C16) & 15) == 0;
+      for (int idx = tid; idx < kBM * kVecPerRow; idx += 128) {
+        const int r = idx / kVecPerRow, j = idx - r * kVecPerRow;
+        const int grow = m0 + r, col = n0 + j * 8;
+        if (grow >= g.M || col >= g.N) continue;
+        const uint4 val = *reinterpret_cast<const uint4 *>(stage + r * kPitch + j * 16);
+        __nv_bfloat16 *dst = g.C16 + (long long)grow * g.ldc16 + col;
+        if (vec16 && col + 8 <= g.N) {
+          *reinterpret_cast<uint4 *>(dst) = val;
+        } else {
+          const __nv_bfloat16 *hv = reinterpret_cast<const __nv_bfloat16 *>(&val);
+          for (int i = 0; i < 8 && col + i < g.N; ++i) dst[i] = hv[i];
         }
       }
     }

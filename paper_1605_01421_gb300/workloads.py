@@ -529,3 +529,21 @@ def config_batched(n_rep=256, n_nodes=5000, days=365, gen_seed=1004, seed=42,
                          f"own events per replicate")
     w.meta = {"gen_seed": gen_seed}
     return w
+
+
+def config_endemic(n_nodes=100_000, days=365, gen_seed=1005, seed=42):
+    """SISe3 without events on large endemic herds: herd sizes log-uniform
+    in [200, 2000], 40% of each age class infected, phi at its equilibrium
+    10 I / N; default rates and seasonal decay.  Every node fires tens to
+    hundreds of transitions a day (the SSA's throughput regime)."""
+    rng = np.random.default_rng(gen_seed)
+    herd = np.rint(np.exp(rng.uniform(np.log(200), np.log(2000), n_nodes))).astype(np.int64)
+    ages = split_ages(herd)
+    I = np.rint(0.4 * ages).astype(np.int64)
+    S = ages - I
+    u0 = np.stack([S[:, 0], I[:, 0], S[:, 1], I[:, 1], S[:, 2], I[:, 2]], 1).astype(np.int32)
+    phi = 10.0 * I.sum(1) / herd
+    w = plain_model(SISE3, u0, np.arange(0, days + 1), sise3_gdata(), seed=seed,
+                    v0=phi[:, None], name=f"SISe3 endemic {n_nodes} nodes x {days} days")
+    w.meta = {"gen_seed": gen_seed}
+    return w
