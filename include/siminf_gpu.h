@@ -264,7 +264,7 @@ int sg_run_noalloc(const sg_desc *desc, const double *d_ldata, const int32_t *ts
  *   C = act(A . Bt^T + bias)
  * A: M x K BF16 row-major (leading dimension lda), Bt: N x K BF16 row-major
  * (ldb), i.e. the weight in "out x in" layout; bias: N floats or NULL;
- * act: 0 identity, 1 GELU (erf form).  C32 (FP32, before the activation,
+ * act: 0 identity, 1 GELU (tanh form, hardware tanh).  C32 (FP32, before the activation,
  * ldc32) and / or C16 (BF16, after it, ldc16) are written; either may be
  * NULL but not both.  K, lda and ldb must be multiples of 8 and A / Bt
  * 16-byte aligned (SG_ERR_ARG otherwise).  All pointers are device pointers;
@@ -292,7 +292,7 @@ int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t ldb, int32_
  * d loss / d logits / B as BF16 (leading dimension ldd; columns 387.. are 0). */
 int sg_mlp_ce_loss(const float *logits, int32_t ldl, const int32_t *targets, int32_t B,
                    void *dlogits, int32_t ldd, double *loss_sum, void *stream);
-/* dpre[i] = dpost[i] * GELU'(pre[i]) (BF16 out), n elements. */
+/* dpre[i] = dpost[i] * GELU'(pre[i]) (tanh form; BF16 out), n elements. */
 int sg_gelu_backward(const float *dpost, const float *pre, int64_t n, void *dpre, void *stream);
 /* dst (cols x rows) = src (rows x cols) transposed, BF16. */
 int sg_transpose_bf16(const void *src, int32_t rows, int32_t cols, void *dst, void *stream);

@@ -1,7 +1,7 @@
 """FP64 reference of the emulator's network (test infrastructure only).
 
-Plain numpy: the 16-256-256-256-392 multilayer perceptron with GELU (erf
-form), the mean over rows of the summed cross-entropies of its three
+Plain numpy: the 16-256-256-256-392 multilayer perceptron with GELU (tanh
+form: 0.5 x (1 + tanh(sqrt(2 / pi) (x + 0.044715 x^3)))), the mean over rows of the summed cross-entropies of its three
 129-way heads, and the gradients of that loss by the chain rule.  The tests
 pin these gradients to central finite differences and compare the CUDA
 kernels' gradients with them.
@@ -14,17 +14,17 @@ import numpy as np
 
 HEADS, BINS = 3, 129
 
-_erf = np.vectorize(math.erf)
+_C = math.sqrt(2.0 / math.pi)
+_A = 0.044715
 
 
 def gelu(x):
-    return 0.5 * x * (1.0 + _erf(x / math.sqrt(2.0)))
+    return 0.5 * x * (1.0 + np.tanh(_C * (x + _A * x ** 3)))
 
 
 def gelu_grad(x):
-    cdf = 0.5 * (1.0 + _erf(x / math.sqrt(2.0)))
-    pdf = np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
-    return cdf + x * pdf
+    t = np.tanh(_C * (x + _A * x ** 3))
+    return 0.5 * (1.0 + t) + 0.5 * x * (1.0 - t * t) * _C * (1.0 + 3.0 * _A * x * x)
 
 
 def forward(Ws, bs, X):

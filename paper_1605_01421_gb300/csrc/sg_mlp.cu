@@ -36,18 +36,29 @@ __device__ __forceinline__ void cp_async16(uint32_t saddr, const void *gsrc, int
                : "memory");
 }
 
+// GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2 / pi) (x + 0.044715 x^3))),
+// with the hardware tanh approximation (relative error ~2^-11, below the
+// BF16 rounding of the activations).
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float gelu(float x) {
-  return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f));
+  const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
+  return 0.5f * x * (1.0f + tanh_fast(u));
 }
 
 // C = act(A . Bt^T + bias) for one 128 x BN tile.  A: M x K, Bt: N x K, both
 // row-major BF16 with K contiguous (K % 8 == 0, rows 16-byte aligned).
-// 128 threads: all load the double-buffered K stages into shared memory,
-// thread 0 issues the MMAs (4 per stage, K = 16 each) and commits them to the
-// stage's mbarrier; the 4 warps then read the FP32 accumulator rows of their
-// TMEM lanes for the epilogue.
+// 256 threads: all load the double-buffered K stages into shared memory
+// (cp.async, overlapping the previous stage's MMAs), thread 0 issues the MMAs
+// (4 per stage, K = 16 each) and commits them to the stage's mbarrier; in the
+// epilogue warp w reads TMEM lane quarter w % 4 (32 tile rows), columns of
+// half w / 4 of the tile.
+constexpr int kGemmThreads = 256;
 template <int BN>
-__global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
+__global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr uint32_t kAStage = kBM * kBK * 2;  // 16 KB
   constexpr uint32_t kBStage = BN * kBK * 2;
@@ -81,14 +92,14 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
   auto load_stage = [&](int s) {
     const int b = s & 1, k0 = s * kBK;
     const uint32_t a0 = tc::smem_u32(sA[b]), b0 = tc::smem_u32(sB[b]);
-    for (int idx = tid; idx < kBM * 8; idx += 128) {
+    for (int idx = tid; idx < kBM * 8; idx += kGemmThreads) {
       const int r = idx >> 3, kg = idx & 7;
       const int m = m0 + r, k = k0 + kg * 8;
       const bool in = m < g.M && k < g.K;
       const __nv_bfloat16 *src = in ? g.A + (long long)m * g.lda + k : g.A;
       cp_async16(a0 + stage_off(r, kg), src, in ? 16 : 0);
     }
-    for (int idx = tid; idx < BN * 8; idx += 128) {
+    for (int idx = tid; idx < BN * 8; idx += kGemmThreads) {
       const int r = idx >> 3, kg = idx & 7;
       const int n = n0 + r, k = k0 + kg * 8;
       const bool in = n < g.N && k < g.K;
@@ -142,23 +153,35 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
     for (int b = 0; b < 2; ++b)
       if (uses[b]) tc::mbar_wait(&bar[b], (uses[b] - 1) & 1, kWaitLimit);
   } else {
-    // Epilogue.  Thread (warp w, lane l) owns tile row 32 w + l, i.e. TMEM
-    // lane 32 w + l.  FP32 results go out as 16-byte vectors; BF16 results
-    // are staged in shared memory (the stage buffers are free now) and then
-    // written row by row, each warp storing whole contiguous rows.
+    // Epilogue.  Warp w reads TMEM lanes 32 (w % 4) .. + 31 (tile rows) and
+    // the columns of half w / 4.  FP32 results go out as 16-byte vectors;
+    // BF16 results are staged in shared memory (the stage buffers are free
+    // now) and then written row by row, each warp storing whole rows.
     tc::tc_fence_after();
     constexpr int kPitch = BN * 2 + 16;  // bytes per staged row (bank offset)
     unsigned char *stage = smem;
-    const int lr = warp * 32 + lane;
+    const int q = warp & 3, half = warp >> 2;
+    const int lr = q * 32 + lane;
     const int row = m0 + lr;
     const bool vec32 = g.C32 && (g.ldc32 % 4) == 0 && (((uintptr_t)g.C32) & 15) == 0;
-    for (int c = 0; c < BN; c += 16) {
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
       float v[16];
-      tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
       const int nb = n0 + c;
       if (g.bias) {
+        if (nb + 16 <= g.N && (((uintptr_t)(g.bias + nb)) & 15) == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] += (nb + i < g.N) ? __ldg(g.bias + nb + i) : 0.0f;
+          for (int i = 0; i < 16; i += 4) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + nb + i));
+            v[i] += b4.x;
+            v[i + 1] += b4.y;
+            v[i + 2] += b4.z;
+            v[i + 3] += b4.w;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += (nb + i < g.N) ? __ldg(g.bias + nb + i) : 0.0f;
+        }
       }
       if (g.C32 && row < g.M) {
         float *dst = g.C32 + (long long)row * g.ldc32 + nb;
@@ -188,7 +211,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(const GemmArgs g) {
       __syncthreads();
       constexpr int kVecPerRow = BN * 2 / 16;
       const bool vec16 = (g.ldc16 % 8) == 0 && (((uintptr_t)g.C16) & 15) == 0;
-      for (int idx = tid; idx < kBM * kVecPerRow; idx += 128) {
+      for (int idx = tid; idx < kBM * kVecPerRow; idx += kGemmThreads) {
         const int r = idx / kVecPerRow, j = idx - r * kVecPerRow;
         const int grow = m0 + r, col = n0 + j * 8;
         if (grow >= g.M || col >= g.N) continue;
@@ -240,7 +263,7 @@ void launch_gemm(const GemmArgs &g, cudaStream_t st) {
     attr_set |= 1ull << dev;
   }
   const dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + BN - 1) / BN));
-  k_gemm_tc<BN><<<grid, 128, smem, st>>>(g);
+  k_gemm_tc<BN><<<grid, kGemmThreads, smem, st>>>(g);
 }
 
 }  // namespace
@@ -326,10 +349,11 @@ constexpr int kHeads = 3;    // one head per age class
 constexpr int kBins = 129;   // increments -64 .. 64
 constexpr int kHalf = 64;
 
+// d/dx of the tanh-form GELU: 0.5 (1 + t) + 0.5 x (1 - t^2) c (1 + 3 a x^2)
 __device__ __forceinline__ float gelu_grad(float x) {
-  const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
-  const float pdf = 0.39894228040143268f * expf(-0.5f * x * x);
-  return cdf + x * pdf;
+  const float c = 0.7978845608028654f, a = 0.044715f;
+  const float t = tanh_fast(c * (x + a * x * x * x));
+  return 0.5f * (1.0f + t) + 0.5f * x * (1.0f - t * t) * c * (1.0f + 3.0f * a * x * x);
 }
 
 // Cross-entropy over the three 129-way heads, one warp per row: loss and

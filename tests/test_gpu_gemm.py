@@ -42,5 +42,5 @@ def test_gemm_bias_gelu_epilogue(env):
     C32, C16 = binding.gemm_bf16(A, Bt, bias=bias, act=1, out32=True, out16=True)
     pre = A.double().cpu() @ Bt.double().cpu().T + bias.double().cpu()
     assert torch.allclose(C32.double().cpu(), pre, rtol=1e-5, atol=1e-4)
-    post = torch.nn.functional.gelu(pre)
+    post = torch.nn.functional.gelu(pre, approximate="tanh")
     assert torch.allclose(C16.double().cpu(), post, rtol=1e-2, atol=1e-2)

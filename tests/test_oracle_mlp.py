@@ -38,6 +38,17 @@ def test_gradients_match_finite_differences():
         assert abs(num - db[li][k]) < 1e-6 * max(1.0, abs(num))
 
 
+def test_gelu_matches_its_definition_and_derivative():
+    x = np.linspace(-6, 6, 2001)
+    # the tanh form approximates x Phi(x) to within 1e-3
+    from math import erf, sqrt
+    exact = np.array([0.5 * v * (1 + erf(v / sqrt(2))) for v in x])
+    assert np.abs(mlp.gelu(x) - exact).max() < 1e-3
+    h = 1e-6
+    num = (mlp.gelu(x + h) - mlp.gelu(x - h)) / (2 * h)
+    assert np.abs(num - mlp.gelu_grad(x)).max() < 1e-7
+
+
 def test_loss_of_uniform_logits():
     # zero weights and biases: every head is uniform over 129 bins
     dims = [(4, 3), (mlp.HEADS * mlp.BINS, 4)]
