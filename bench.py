@@ -50,6 +50,8 @@ def _workload(name):
         return W.config_sise3()
     if name == "batched":
         return W.config_batched()
+    if name == "sise_sp":
+        return W.config_sise_sp()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -476,7 +478,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sise",
-                    choices=["sise", "sir", "sise3", "batched", "emulator"])
+                    choices=["sise", "sir", "sise3", "batched", "emulator", "sise_sp"])
     ap.add_argument("--emu-batches", type=int, default=50)
     ap.add_argument("--emu-steps", type=int, default=4000)
     ap.add_argument("--emu-nodes", type=int, default=37000)

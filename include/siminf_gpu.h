@@ -52,8 +52,21 @@ extern "C" {
  *            end_t4] per node; v = [phi].
  *   SG_SISE3 SISe per age class, compartments [S1,I1,S2,I2,S3,I3]; gdata =
  *            [upsilon_1..3, gamma_1..3, alpha, beta_t1..beta_t4]; ldata and
- *            v as SG_SISE.                                                  */
-typedef enum { SG_SIR = 0, SG_SIS = 1, SG_SISE = 2, SG_SISE3 = 3 } sg_model_kind;
+ *            v as SG_SISE.
+ *   SG_SISE_SP SISe with the spatial coupling term of the environmental
+ *            pressure ODE of Sec. 4.2: phi_i' = alpha I_i / N_i + sum_k
+ *            (phi_k N_k - phi_i N_i) / N_i * D / d_ik - beta(t) phi_i over the
+ *            node's neighbours k (sg_set_neighbors), all nodes updated from the
+ *            same old values (one Euler step of length 1); both terms are 0 in
+ *            an empty node.  gdata = [upsilon, gamma, alpha, beta_t1..beta_t4,
+ *            D]; ldata and v as SG_SISE.                                     */
+typedef enum {
+  SG_SIR = 0,
+  SG_SIS = 1,
+  SG_SISE = 2,
+  SG_SISE3 = 3,
+  SG_SISE_SP = 4
+} sg_model_kind;
 
 /* Event types, coded as in the event table of Sec. 3.3. */
 typedef enum {
@@ -137,6 +150,13 @@ typedef struct {
  * the kind, copies every table to the device and returns the handle in
  * *out.  Errors: SG_ERR_ARG, SG_ERR_NOMEM, SG_ERR_CUDA. */
 int sg_model_create(const sg_desc *desc, sg_model **out);
+
+/* SG_SISE_SP neighbour lists (the distance matrix of Sec. 4.2 within a
+ * cutoff), compressed rows: node i's neighbours are idx[ptr[i] .. ptr[i+1])
+ * with distances dist[..] (> 0, finite), summed in that order.  ptr has
+ * n_nodes + 1 entries, ptr[0] = 0.  Host arrays, copied.  Without a call the
+ * nodes have no neighbours.  Errors: SG_ERR_ARG, SG_ERR_NOMEM. */
+int sg_set_neighbors(sg_model *m, const int64_t *ptr, const int32_t *idx, const double *dist);
 
 /* Replace the model's scheduled events (event table of Sec. 3.3): n_events
  * entries of type event[e] at integer time[e] on node[e] (and dest[e] for

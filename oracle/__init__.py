@@ -64,7 +64,8 @@ class _Model(ctypes.Structure):
         ("n_shift", ctypes.c_int), ("N", ctypes.c_void_p),
         ("n_v", ctypes.c_int), ("n_ldata", ctypes.c_int),
         ("ldata", ctypes.c_void_p), ("n_gdata", ctypes.c_int),
-        ("gdata", ctypes.c_void_p),
+        ("gdata", ctypes.c_void_p), ("nb_ptr", ctypes.c_void_p),
+        ("nb_idx", ctypes.c_void_p), ("nb_dist", ctypes.c_void_p),
     ]
 
 
@@ -197,11 +198,21 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None):
     gdata = _f64(w.gdata)
     n_comp, n_trans = w.S.shape
     n_nodes = u0.shape[1]
+    nb = getattr(w, "neighbors", None)
+    if nb is not None:
+        nb_ptr = np.ascontiguousarray(nb[0], dtype=np.int64)
+        nb_idx = _i32(nb[1])
+        nb_dist = _f64(nb[2])
+    else:
+        nb_ptr = nb_idx = nb_dist = None
     m = _Model(int(w.kind), int(n_nodes), int(n_comp), int(n_trans),
                _ptr(S), _ptr(G), int(w.E.shape[1]), _ptr(E),
                int(w.N.shape[1]), _ptr(N), int(w.n_v),
                int(np.asarray(w.ldata).shape[0]), _ptr(ldata) if ldata.size else None,
-               int(gdata.size), _ptr(gdata))
+               int(gdata.size), _ptr(gdata),
+               _ptr(nb_ptr) if nb_ptr is not None else None,
+               _ptr(nb_idx) if nb_idx is not None and nb_idx.size else None,
+               _ptr(nb_dist) if nb_dist is not None and nb_dist.size else None)
     ev = w.events
     keep = []
     if ev is not None and len(ev["event"]) > 0:

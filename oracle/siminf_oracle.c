@@ -27,6 +27,9 @@
  *     Appendix C (operation order kept); SIS Eq. (SIRstoich) of Sec. 2.1;
  *     SISe Eq. (vtectrans) and the environmental pressure ODE of Sec. 4.2
  *     without the spatial coupling term; SISe3 = SISe per age class;
+ *     SISe_sp = SISe with the coupling term of that ODE (Eq.
+ *     envInfPressure-local-spread), all nodes updated from the same old
+ *     values;
  *   - scheduled events: Sec. 3.3 (enter, internal transfer, external
  *     transfer, exit; select matrix E, shift matrix N; same-time order exit,
  *     enter, internal transfer, external transfer) and Appendix B;
@@ -252,6 +255,7 @@ static double model_rate(int kind, int j, const int *u, const double *v,
         if (j == 0) return gdata[0] * (double)u[0] * (double)u[1];
         return gdata[1] * (double)u[1];
     case ORACLE_SISE:
+    case ORACLE_SISE_SP:
         /* Sec. 4.2: S -> I at upsilon * phi * S, I -> S at gamma * I. */
         if (j == 0) return gdata[0] * v[0] * (double)u[0];
         return gdata[1] * (double)u[1];
@@ -302,6 +306,39 @@ static int model_pts(int kind, double *v_new, const int *u, const double *v,
     v_new[0] = phi + (shed - beta * phi);
     if (!isfinite(v_new[0])) return ORACLE_ERR_PTS;
     return v_new[0] != phi ? 1 : 0;
+}
+
+/* SISe_sp post time step of node i (Sec. 4.2, environmental pressure with
+ * spatial coupling), one Euler step of length 1 from the values of every
+ * node before the update:
+ *   phi_i' = phi_i + ((alpha I_i / N_i
+ *                      + sum_k ((phi_k N_k - phi_i N_i) / N_i) (D / d_ik))
+ *                     - beta(t) phi_i),
+ * N = S + I, the sum in neighbour-list order.  Reading: both the shedding
+ * and the coupling terms are 0 in an empty node. */
+static int sise_sp_pts(const oracle_model *m, int node, const int *u_all,
+                       const double *v_all, int t, double *phi_new)
+{
+    const int *u = u_all + (size_t)node * 2;
+    const double *g = m->gdata;
+    double N_i = (double)u[0] + (double)u[1];
+    double phi = v_all[node];
+    double shed = 0.0, coupling = 0.0, beta;
+    int64_t k;
+    if (N_i > 0.0) {
+        shed = (g[2] * (double)u[1]) / N_i;
+        if (m->nb_ptr) {
+            for (k = m->nb_ptr[node]; k < m->nb_ptr[node + 1]; k++) {
+                int j = m->nb_idx[k];
+                double N_k = (double)u_all[(size_t)j * 2] + (double)u_all[(size_t)j * 2 + 1];
+                double term = ((v_all[j] * N_k - phi * N_i) / N_i) * (g[7] / m->nb_dist[k]);
+                coupling = coupling + term;
+            }
+        }
+    }
+    beta = seasonal_beta(t, m->ldata + (size_t)node * m->n_ldata, g + 3);
+    *phi_new = phi + ((shed + coupling) - beta * phi);
+    return isfinite(*phi_new) ? 0 : ORACLE_ERR_PTS;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -431,12 +468,12 @@ static int validate(const oracle_model *m, const oracle_events *ev,
 {
     int64_t e;
     int i, p;
-    static const int ncomp[4] = {3, 2, 2, 6};
-    static const int ntrans[4] = {2, 2, 2, 6};
-    static const int nv[4] = {0, 0, 1, 1};
-    static const int ngd[4] = {2, 2, 7, 11};
-    static const int nld[4] = {0, 0, 4, 4};
-    if (m->kind < 0 || m->kind > 3 || m->n_nodes < 0 || n_rep < 1
+    static const int ncomp[5] = {3, 2, 2, 6, 2};
+    static const int ntrans[5] = {2, 2, 2, 6, 2};
+    static const int nv[5] = {0, 0, 1, 1, 1};
+    static const int ngd[5] = {2, 2, 7, 11, 8};
+    static const int nld[5] = {0, 0, 4, 4, 4};
+    if (m->kind < 0 || m->kind > 4 || m->n_nodes < 0 || n_rep < 1
         || n_tspan < 1 || m->n_comp != ncomp[m->kind]
         || m->n_trans != ntrans[m->kind] || m->n_v != nv[m->kind]
         || m->n_gdata < ngd[m->kind] || m->n_ldata < nld[m->kind]
@@ -448,6 +485,26 @@ static int validate(const oracle_model *m, const oracle_events *ev,
         if (tspan[i] <= tspan[i - 1]) {
             set_error(err, ORACLE_ERR_ARG, -1, -1, -1, -1);
             return ORACLE_ERR_ARG;
+        }
+    }
+    if (m->nb_ptr) {
+        int64_t k;
+        if (m->nb_ptr[0] != 0) {
+            set_error(err, ORACLE_ERR_ARG, -1, -1, -1, -1);
+            return ORACLE_ERR_ARG;
+        }
+        for (i = 0; i < m->n_nodes; i++) {
+            if (m->nb_ptr[i + 1] < m->nb_ptr[i]) {
+                set_error(err, ORACLE_ERR_ARG, -1, i, -1, -1);
+                return ORACLE_ERR_ARG;
+            }
+            for (k = m->nb_ptr[i]; k < m->nb_ptr[i + 1]; k++) {
+                if (m->nb_idx[k] < 0 || m->nb_idx[k] >= m->n_nodes
+                    || !(m->nb_dist[k] > 0.0) || isinf(m->nb_dist[k])) {
+                    set_error(err, ORACLE_ERR_ARG, -1, i, -1, -1);
+                    return ORACLE_ERR_ARG;
+                }
+            }
         }
     }
     if (!ev) return 0;
@@ -572,7 +629,7 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     int64_t n_sorted = 0, e;
     int rep, rc;
     int *u = NULL;
-    double *v = NULL, *v_new = NULL;
+    double *v = NULL, *v_new = NULL, *vtmp = NULL;
 
     if (err) memset(err, 0, sizeof *err);
     rc = validate(m, ev, tspan, n_tspan, n_rep, err);
@@ -597,8 +654,9 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     u = (int *)malloc((ustride ? ustride : 1) * sizeof *u);
     v = (double *)malloc((vstride ? vstride : 1) * sizeof *v);
     v_new = (double *)malloc((Nv ? Nv : 1) * sizeof *v_new);
-    if (!u || !v || !v_new) {
-        free(order); free(u); free(v); free(v_new);
+    vtmp = (double *)malloc((Nn ? Nn : 1) * sizeof *vtmp);
+    if (!u || !v || !v_new || !vtmp) {
+        free(order); free(u); free(v); free(v_new); free(vtmp);
         return ORACLE_ERR_NOMEM;
     }
 
@@ -660,7 +718,18 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
             }
 
             /* (3) post time step, Eq. numstep3, on the state after events */
-            for (node = 0; node < Nn && Nv > 0; node++) {
+            if (m->kind == ORACLE_SISE_SP) {
+                /* every node from the same old values: new values first */
+                for (node = 0; node < Nn; node++) {
+                    if (sise_sp_pts(m, node, u, v, T, &vtmp[node])) {
+                        set_error(err, ORACLE_ERR_PTS, rep, node, -1, T);
+                        rc = ORACLE_ERR_PTS;
+                        goto done;
+                    }
+                }
+                memcpy(v, vtmp, (size_t)Nn * sizeof *v);
+            }
+            for (node = 0; node < Nn && Nv > 0 && m->kind != ORACLE_SISE_SP; node++) {
                 int ret = model_pts(m->kind, v_new, u + (size_t)node * C,
                                     v + (size_t)node * Nv,
                                     m->ldata + (size_t)node * m->n_ldata,
@@ -690,5 +759,6 @@ done:
     free(u);
     free(v);
     free(v_new);
+    free(vtmp);
     return rc;
 }

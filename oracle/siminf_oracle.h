@@ -22,7 +22,13 @@
 #define ORACLE_MAX_COMP 16
 #define ORACLE_MAX_TRANS 16
 
-enum { ORACLE_SIR = 0, ORACLE_SIS = 1, ORACLE_SISE = 2, ORACLE_SISE3 = 3 };
+enum {
+    ORACLE_SIR = 0,
+    ORACLE_SIS = 1,
+    ORACLE_SISE = 2,
+    ORACLE_SISE3 = 3,
+    ORACLE_SISE_SP = 4
+};
 enum {
     ORACLE_EV_EXIT = 0,
     ORACLE_EV_ENTER = 1,
@@ -58,6 +64,11 @@ typedef struct {
     const double *ldata;
     int n_gdata;
     const double *gdata;
+    /* SISe_sp neighbours of node i: nb_idx[nb_ptr[i] .. nb_ptr[i+1]) with
+     * distances nb_dist (NULL pointers: no neighbours) */
+    const int64_t *nb_ptr;
+    const int *nb_idx;
+    const double *nb_dist;
 } oracle_model;
 
 typedef struct {

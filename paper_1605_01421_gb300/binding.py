@@ -123,7 +123,7 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs",
            "sg_gemm_bf16", "sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
-           "sg_emu_sample", "sg_emulator_set"]
+           "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors"]
 
 _lock = threading.Lock()
 _lib = None
@@ -192,6 +192,8 @@ def lib(path: str | None = None):
         L.sg_emu_sample.argtypes = [vp, i32, vp, vp, i64, i32, u64, i32, vp, vp]
         L.sg_emulator_set.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, f64,
                                       f64, ctypes.c_int]
+        L.sg_set_neighbors.argtypes = [vp, vp, vp, vp]
+        L.sg_set_neighbors.restype = ctypes.c_int
         for nm in ("sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
                    "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
                    "sg_emu_sample", "sg_emulator_set"):
@@ -261,6 +263,16 @@ class Model:
         self._h = h
         if getattr(w, "events", None) is not None:
             self.set_events(w.events)
+        if getattr(w, "neighbors", None) is not None:
+            self.set_neighbors(*w.neighbors)
+
+    def set_neighbors(self, ptr, idx, dist):
+        ptr = np.ascontiguousarray(ptr, dtype=np.int64)
+        idx = _i32(idx)
+        dist = np.ascontiguousarray(dist, dtype=np.float64)
+        rc = lib().sg_set_neighbors(self._h, _p(ptr), _p(idx), _p(dist))
+        if rc:
+            raise SimInfError(rc)
 
     def set_events(self, ev):
         L = lib()

@@ -236,6 +236,9 @@ template <> struct ModelTraits<SG_SISE> {
   }
 };
 
+// SISe_sp: the rates of SISe (the coupling acts on phi only).
+template <> struct ModelTraits<SG_SISE_SP> : ModelTraits<SG_SISE> {};
+
 // SISe3: transition 2a is S_a -> I_a at upsilon_a phi S_a, 2a + 1 is
 // I_a -> S_a at gamma_a I_a.
 template <> struct ModelTraits<SG_SISE3> {

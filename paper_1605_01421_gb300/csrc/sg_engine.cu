@@ -768,6 +768,68 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   if (applied) atomicAdd(&a.cnt->events, applied);
 }
 
+// SISe_sp post time step of every node for unit time T from the same old
+// values (Sec. 4.2 with the coupling term), one thread per (replicate, node):
+//   phi' = phi + ((alpha I / N + sum_k ((phi_k N_k - phi N) / N) (D / d_k))
+//                 - beta(T) phi),
+// neighbours in list order, both terms 0 in an empty node; then recording.
+struct PtsSpArgs {
+  const int *u;
+  const double *v_old;
+  double *v_new;
+  const double *ldata;
+  const int64_t *nb_ptr;
+  const int32_t *nb_idx;
+  const double *nb_dist;
+  int32_t *U;
+  double *V;
+  const int32_t *rec;
+  int32_t t0, M, n_rep, T;
+  SgDevError *err;
+};
+
+__global__ void __launch_bounds__(128) k_pts_sp(const SgTables tb, const PtsSpArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const int Nn = tb.n_nodes;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= (long long)Nn * a.n_rep) return;
+  const int rep = (int)(gid / Nn), node = (int)(gid - (long long)rep * Nn);
+  const int *ur = a.u + (long long)rep * Nn * 2;
+  const double *vr = a.v_old + (long long)rep * Nn;
+  const double *g = tb.gdata;
+  const int S = ur[node * 2], I = ur[node * 2 + 1];
+  const double Ni = i2d(S) + i2d(I);
+  const double phi = vr[node];
+  double shed = 0.0, coupling = 0.0;
+  if (gt0(Ni)) {
+    shed = (g[2] * i2d(I)) / Ni;
+    if (a.nb_ptr) {
+      const double DN = g[7];
+      for (long long k = a.nb_ptr[node]; k < a.nb_ptr[node + 1]; ++k) {
+        const int j = a.nb_idx[k];
+        const double Nk = i2d(ur[j * 2]) + i2d(ur[j * 2 + 1]);
+        const double term = ((vr[j] * Nk - phi * Ni) / Ni) * (DN / a.nb_dist[k]);
+        coupling = coupling + term;
+      }
+    }
+  }
+  int ends[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ends[i] = season_end_int(a.ldata[(long long)node * tb.n_ldata + i]);
+  const double beta = season_decay(a.T, ends, g + 3);
+  const double nv = phi + ((shed + coupling) - beta * phi);
+  a.v_new[gid] = nv;
+  if (!isfinite(nv)) report(a.err, SG_ERR_PTS, rep, node, a.T, -1);
+  const int m = a.rec[a.T - a.t0];
+  if (m >= 0) {
+    const long long base = ((long long)rep * a.M + m) * Nn + node;
+    a.U[base * 2] = S;
+    a.U[base * 2 + 1] = I;
+    a.V[base] = nv;
+  }
+}
+
 // U[r][0] = u0[r], V[r][0] = v0[r], working state = initial state.
 __global__ void k_init(const int32_t *__restrict__ u0, const double *__restrict__ v0, int *u,
                        double *v, int32_t *U, double *V, long long per_rep_u,
@@ -946,6 +1008,12 @@ struct sg_model {
   DevBuf<__nv_bfloat16> emu_feat, emu_ha, emu_hb;
   DevBuf<float> emu_logits;
   DevBuf<int32_t> emu_flag, emu_delta;
+  // SISe_sp neighbour lists and the second phi buffer of the coupled step
+  DevBuf<int64_t> nb_ptr;
+  DevBuf<int32_t> nb_idx;
+  DevBuf<double> nb_dist, v2;
+  bool has_nb = false;
+  uint64_t nb_version = 0;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -965,17 +1033,17 @@ extern "C" const char *sg_strerror(int code) {
   }
 }
 
-static const int kKindComp[4] = {3, 2, 2, 6};
-static const int kKindTrans[4] = {2, 2, 2, 6};
-static const int kKindNv[4] = {0, 0, 1, 1};
-static const int kKindGdata[4] = {2, 2, 7, 11};
-static const int kKindLdata[4] = {0, 0, 4, 4};
+static const int kKindComp[5] = {3, 2, 2, 6, 2};
+static const int kKindTrans[5] = {2, 2, 2, 6, 2};
+static const int kKindNv[5] = {0, 0, 1, 1, 1};
+static const int kKindGdata[5] = {2, 2, 7, 11, 8};
+static const int kKindLdata[5] = {0, 0, 4, 4, 4};
 
 extern "C" int sg_model_create(const sg_desc *d, sg_model **out) {
   if (!d || !out) return SG_ERR_ARG;
   *out = nullptr;
   const int k = d->kind;
-  if (k < SG_SIR || k > SG_SISE3) return SG_ERR_ARG;
+  if (k < SG_SIR || k > SG_SISE_SP) return SG_ERR_ARG;
   if (d->n_nodes < 0 || d->n_comp != kKindComp[k] || d->n_trans != kKindTrans[k] ||
       d->n_v != kKindNv[k] || d->n_gdata < kKindGdata[k] || d->n_gdata > SG_MAX_GDATA ||
       d->n_ldata < kKindLdata[k] || d->n_select < 0 || d->n_select > SG_MAX_SELECT ||
@@ -1048,6 +1116,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
   m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
+  m->nb_ptr.release(); m->nb_idx.release(); m->nb_dist.release(); m->v2.release();
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
@@ -1166,6 +1235,7 @@ static void launch_days_kind(sg_model *m, const DayArgs &a, cudaStream_t st) {
     case SG_SIR: launch_days<SG_SIR>(m, a, st); break;
     case SG_SIS: launch_days<SG_SIS>(m, a, st); break;
     case SG_SISE: launch_days<SG_SISE>(m, a, st); break;
+    case SG_SISE_SP: launch_days<SG_SISE_SP>(m, a, st); break;
     default: launch_days<SG_SISE3>(m, a, st); break;
   }
 }
@@ -1224,6 +1294,7 @@ static void launch_e2_kind(sg_model *m, const EvArgs &ea, long long wb, long lon
     case SG_SIR: launch_e2<SG_SIR>(m, ea, wb, we, day, slots, n_rep, st); break;
     case SG_SIS: launch_e2<SG_SIS>(m, ea, wb, we, day, slots, n_rep, st); break;
     case SG_SISE: launch_e2<SG_SISE>(m, ea, wb, we, day, slots, n_rep, st); break;
+    case SG_SISE_SP: launch_e2<SG_SISE_SP>(m, ea, wb, we, day, slots, n_rep, st); break;
     default: launch_e2<SG_SISE3>(m, ea, wb, we, day, slots, n_rep, st); break;
   }
 }
@@ -1263,7 +1334,57 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
   }
   DayArgs da = da0;
   EvArgs ea = ea0;
-  if (Nn > 0 && days > 0 && m->emu_on) {
+  if (Nn > 0 && days > 0 && tb.kind == SG_SISE_SP) {
+    // Coupled post time step: it reads other nodes' phi and sizes, so every
+    // day ends with its own kernel after the day's events (phi in two
+    // buffers, old and new).
+    double *vc = m->v.p, *vn = m->v2.p;
+    PtsSpArgs pa;
+    pa.u = m->u.p;
+    pa.ldata = m->ldata.p;
+    pa.nb_ptr = m->has_nb ? m->nb_ptr.p : nullptr;
+    pa.nb_idx = m->nb_idx.p;
+    pa.nb_dist = m->nb_dist.p;
+    pa.U = d_U;
+    pa.V = d_V;
+    pa.rec = m->rec.p;
+    pa.t0 = t0;
+    pa.M = n_tspan;
+    pa.n_rep = n_rep;
+    pa.err = m->err.p;
+    const long long units = (long long)Nn * n_rep;
+    for (int32_t d = 0; d < days; ++d) {
+      const int32_t T = t0 + 1 + d;
+      da.v = vc;
+      da.T_begin = T;
+      da.T_end = T + 1;
+      da.finish_first = 0;
+      da.finish_last = 0;
+      {
+        LaunchTimer lt(m, st, 0);
+        launch_days_kind(m, da, st);
+      }
+      ++launches;
+      if (P.day_has_e2[d]) {
+        ea.day = T;
+        const long long b0 = (long long)d * slots, b1 = b0 + slots;
+        const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
+        LaunchTimer lt(m, st, 2);
+        launch_e2_kind(m, ea, wb, we, d, slots, n_rep, st);
+        ++launches;
+        waves += (int32_t)(we - wb);
+      }
+      pa.v_old = vc;
+      pa.v_new = vn;
+      pa.T = T;
+      {
+        LaunchTimer lt(m, st, 0);
+        launch_pdl(k_pts_sp, (unsigned)((units + 127) / 128), 128, 0, st, tb, pa);
+      }
+      ++launches;
+      std::swap(vc, vn);
+    }
+  } else if (Nn > 0 && days > 0 && m->emu_on) {
     // One day at a time: finish the previous day, emulator features and MLP
     // for every node, sampling, then the day kernel (SSA only for the nodes
     // outside the emulator's range) and the day's external transfers.
@@ -1433,6 +1554,8 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
       (rc = m->e1_cur.ensure((size_t)std::max(1, Nn * n_rep))) ||
       (rc = m->rec.ensure((size_t)days + 1)))
     return rc;
+  if (tb.kind == SG_SISE_SP && (rc = m->v2.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))))
+    return rc;
   if (m->emu_on) {
     const size_t units = (size_t)Nn * n_rep;
     if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
@@ -1514,7 +1637,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                      t_end,
                      da.npb,
                      da.heavy_after,
-                     m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)};
+                     (m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)) *
+                             1000033ull +
+                         m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p};
   if (use_graph) {
     if (!(m->graph_ok && m->graph_key == key)) {
       if (m->graph_exec) {
@@ -1767,7 +1892,7 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
   if (stats) std::memset(stats, 0, sizeof *stats);
   if (!d || !tspan || n_tspan < 1 || n_rep < 1 || n_rep >= (1 << 24)) return SG_ERR_ARG;
   const int k = d->kind;
-  if (k < SG_SIR || k > SG_SISE3) return SG_ERR_ARG;
+  if (k < SG_SIR || k > SG_SISE3) return SG_ERR_ARG;  // coupled kinds need neighbour lists
   if (d->n_nodes < 0 || d->n_comp != kKindComp[k] || d->n_trans != kKindTrans[k] ||
       d->n_v != kKindNv[k] || d->n_gdata < kKindGdata[k] || d->n_gdata > SG_MAX_GDATA ||
       d->n_ldata < kKindLdata[k] || !d->S || !d->G || (d->n_gdata > 0 && !d->gdata) ||
@@ -1992,6 +2117,34 @@ extern "C" int sg_emulator_set(sg_model *m, const void *const *W, const float *c
   m->emu_phi_hi = phi_hi;
   m->emu_on = true;
   ++m->emu_version;
+  m->graph_ok = false;
+  return SG_OK;
+}
+
+extern "C" int sg_set_neighbors(sg_model *m, const int64_t *ptr, const int32_t *idx,
+                                const double *dist) {
+  if (!m || !ptr) return SG_ERR_ARG;
+  const int Nn = m->tb.n_nodes;
+  if (ptr[0] != 0) return SG_ERR_ARG;
+  for (int i = 0; i < Nn; ++i)
+    if (ptr[i + 1] < ptr[i]) return SG_ERR_ARG;
+  const int64_t nnz = ptr[Nn];
+  if (nnz > 0 && (!idx || !dist)) return SG_ERR_ARG;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (idx[k] < 0 || idx[k] >= Nn || !(dist[k] > 0.0) || std::isinf(dist[k])) return SG_ERR_ARG;
+  int rc;
+  try {
+    std::vector<int64_t> p(ptr, ptr + Nn + 1);
+    std::vector<int32_t> ix(idx ? idx : nullptr, idx ? idx + nnz : nullptr);
+    std::vector<double> ds(dist ? dist : nullptr, dist ? dist + nnz : nullptr);
+    if ((rc = upload(m->nb_ptr, p)) || (rc = upload(m->nb_idx, ix)) ||
+        (rc = upload(m->nb_dist, ds)))
+      return rc;
+  } catch (const std::bad_alloc &) {
+    return SG_ERR_NOMEM;
+  }
+  m->has_nb = true;
+  ++m->nb_version;
   m->graph_ok = false;
   return SG_OK;
 }

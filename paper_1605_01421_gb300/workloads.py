@@ -24,9 +24,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SIR, SIS, SISE, SISE3 = 0, 1, 2, 3
+SIR, SIS, SISE, SISE3, SISE_SP = 0, 1, 2, 3, 4
 EXIT, ENTER, INTERNAL, EXTERNAL = 0, 1, 2, 3
-KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3"}
+KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3", SISE_SP: "SISe_sp"}
 
 
 @dataclass
@@ -47,6 +47,8 @@ class Workload:
     seed: int
     n_rep: int = 1
     meta: dict = field(default_factory=dict)
+    # SISe_sp: neighbour lists (ptr (n_nodes + 1,), idx, distance) or None
+    neighbors: tuple | None = None
 
     @property
     def n_nodes(self) -> int:
@@ -153,6 +155,13 @@ def sise_gdata(upsilon=0.0173, gamma=0.1, alpha=1.0, betas=(0.1,) * 4):
     return np.array([upsilon, gamma, alpha, *betas], dtype=np.float64)
 
 
+def sise_sp_gdata(upsilon=0.012, gamma=0.1, alpha=1.0, betas=(0.10, 0.12, 0.12, 0.10),
+                  coupling=0.2):
+    """SISe_sp global data of Sec. 4.2: [upsilon, gamma, alpha, beta_t1..t4,
+    coupling D] (the paper's example values by default)."""
+    return np.array([upsilon, gamma, alpha, *betas, coupling], dtype=np.float64)
+
+
 def sise3_gdata(upsilons=(0.0173,) * 3, gammas=(0.1,) * 3, alpha=1.0,
                 betas=(0.10, 0.12, 0.12, 0.10)):
     return np.array([*upsilons, *gammas, alpha, *betas], dtype=np.float64)
@@ -168,13 +177,13 @@ def plain_model(kind, u0, tspan, gdata, seed=42, n_rep=1, events=None,
     """A workload on explicit initial state ``u0`` (n_nodes, n_comp) or
     (n_rep, n_nodes, n_comp)."""
     tables = {SIR: sir_tables, SIS: sis_tables, SISE: sise_tables,
-              SISE3: sise3_tables}[kind]()
+              SISE3: sise3_tables, SISE_SP: sise_tables}[kind]()
     S, G, E, N = tables
     u0 = np.asarray(u0, dtype=np.int32)
     if u0.ndim == 2:
         u0 = _tile_rep(u0, n_rep)
     n_nodes = u0.shape[1]
-    n_v = 1 if kind in (SISE, SISE3) else 0
+    n_v = 1 if kind in (SISE, SISE3, SISE_SP) else 0
     if ldata is None:
         ldata = (seasons_ldata(n_nodes) if n_v
                  else np.zeros((0, n_nodes), dtype=np.float64))
@@ -546,4 +555,55 @@ def config_endemic(n_nodes=100_000, days=365, gen_seed=1005, seed=42):
     w = plain_model(SISE3, u0, np.arange(0, days + 1), sise3_gdata(), seed=seed,
                     v0=phi[:, None], name=f"SISe3 endemic {n_nodes} nodes x {days} days")
     w.meta = {"gen_seed": gen_seed}
+    return w
+
+
+def distance_neighbors(x, y, cutoff):
+    """Neighbour lists of points within `cutoff` of each other (self
+    excluded): CSR (ptr, idx, distance), neighbours in increasing index."""
+    n = len(x)
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    idx, dist = [], []
+    order = np.argsort(x, kind="stable")
+    xs = x[order]
+    for i in range(n):
+        lo = np.searchsorted(xs, x[i] - cutoff, side="left")
+        hi = np.searchsorted(xs, x[i] + cutoff, side="right")
+        cand = order[lo:hi]
+        cand = cand[cand != i]
+        d = np.hypot(x[cand] - x[i], y[cand] - y[i])
+        keep = d <= cutoff
+        c, dd = cand[keep], d[keep]
+        o = np.argsort(c)
+        idx.append(c[o])
+        dist.append(dd[o])
+        ptr[i + 1] = ptr[i] + len(c)
+    return (ptr, np.concatenate(idx).astype(np.int32) if idx else np.zeros(0, np.int32),
+            np.concatenate(dist) if dist else np.zeros(0))
+
+
+def config_sise_sp(n_nodes=1600, days=365, gen_seed=1006, seed=42, side_m=50000.0,
+                   cutoff_m=2500.0, events=True):
+    """SISe_sp (Sec. 4.2): SISe with spatial coupling of phi between farms
+    within `cutoff_m` metres, farms placed uniformly in a 50 km x 50 km
+    square (the paper's "50 square kilometer region", read as 50 km a side:
+    about a dozen neighbours within 2,500 m), the paper's example parameters (upsilon 0.012, gamma
+    0.1, alpha 1, decay 0.10 / 0.12 / 0.12 / 0.10, season ends 91 / 182 / 273
+    / 365, coupling 0.2), 10% of farms with 5% infected, and the SISe
+    benchmark's synthetic event stream."""
+    base = config_sise(n_nodes=n_nodes, days=days, gen_seed=gen_seed)
+    rng = np.random.default_rng(gen_seed + 1)
+    x = rng.uniform(0, side_m, n_nodes)
+    y = rng.uniform(0, side_m, n_nodes)
+    nb = distance_neighbors(x, y, cutoff_m)
+    herd = base.u0[0].sum(axis=1).astype(np.int64)
+    I = np.zeros(n_nodes, dtype=np.int64)
+    inf = rng.choice(n_nodes, size=n_nodes // 10, replace=False)
+    I[inf] = (herd[inf] * 0.05).astype(np.int64)
+    u0 = np.stack([herd - I, I], axis=1).astype(np.int32)
+    w = plain_model(SISE_SP, u0, np.arange(0, days + 1), sise_sp_gdata(), seed=seed,
+                    events=base.events if events else None,
+                    name=f"SISe_sp {n_nodes} nodes x {days} days")
+    w.neighbors = nb
+    w.meta = {"gen_seed": gen_seed, "cutoff_m": cutoff_m, "side_m": side_m}
     return w

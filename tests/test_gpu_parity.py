@@ -314,3 +314,19 @@ def test_graph_recaptured_after_buffers_change(orc, gpu):
     s.synchronize()
     assert np.array_equal(U.cpu().numpy(), U0)
     assert np.array_equal(U3.cpu().numpy()[:1], U0)
+
+
+def test_sise_sp_coupled_post_step(orc, gpu):
+    # SISe_sp (spatial coupling of phi between farms within 2,500 m) with the
+    # SISe event stream, 1,600 farms x 365 days
+    w = W.config_sise_sp()
+    assert len(w.neighbors[1]) > 1600
+    _compare(orc, gpu, w)
+
+
+def test_sise_sp_replicates_and_sparse_tspan(orc, gpu):
+    w = W.config_sise_sp(n_nodes=500, days=90, gen_seed=44)
+    w = W.Workload(**{**w.__dict__, "tspan": np.array([0, 1, 7, 30, 31, 90], np.int32),
+                      "n_rep": 3, "u0": np.repeat(w.u0, 3, axis=0),
+                      "v0": np.repeat(w.v0, 3, axis=0)})
+    _compare(orc, gpu, w)

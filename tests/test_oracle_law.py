@@ -263,3 +263,59 @@ def test_node_without_infection_is_frozen(orc):
     assert code == 0
     assert np.all(U[0, :, 0] == [10, 0, 0])
     assert np.all(U[0].sum(axis=2) == 10)
+
+
+def test_sise_sp_two_farms_follow_the_linear_recursion(orc):
+    # no transitions: the coupled Euler step is a linear recursion
+    # phi' = A phi + b, A = [[1 - c - beta, c N2 / N1], [c N1 / N2, 1 - c - beta]],
+    # c = D / d, b = alpha I / N
+    alpha, beta, D, d = 0.7, 0.1, 0.2, 1500.0
+    u0 = np.array([[30, 10], [5, 15]])
+    g = W.sise_sp_gdata(upsilon=0.0, gamma=0.0, alpha=alpha, betas=(beta,) * 4,
+                        coupling=D)
+    w = W.plain_model(W.SISE_SP, u0, np.arange(0, 41), g, v0=np.array([[0.3], [1.1]]))
+    w.neighbors = (np.array([0, 1, 2]), np.array([1, 0], np.int32), np.array([d, d]))
+    code, U, V, R, err = orc.run(w)
+    assert code == 0
+    N = u0.sum(1).astype(float)
+    c = D / d
+    A = np.array([[1 - c - beta, c * N[1] / N[0]], [c * N[0] / N[1], 1 - c - beta]])
+    b = alpha * u0[:, 1] / N
+    phi = np.array([0.3, 1.1])
+    for t in range(1, 41):
+        phi = A @ phi + b
+        assert np.allclose(V[0, t, :, 0], phi, rtol=1e-12, atol=0)
+
+
+def test_sise_sp_coupling_conserves_total_pressure(orc):
+    # alpha = 0 and no decay: the coupling only moves N_i phi_i between
+    # farms with symmetric distances, so sum_i N_i phi_i stays constant
+    rng = np.random.default_rng(3)
+    n = 60
+    x, y = rng.uniform(0, 5000, n), rng.uniform(0, 5000, n)
+    u0 = np.stack([rng.integers(5, 50, n), rng.integers(0, 10, n)], 1)
+    g = W.sise_sp_gdata(upsilon=0.0, gamma=0.0, alpha=0.0, betas=(0.0,) * 4,
+                        coupling=0.05)
+    w = W.plain_model(W.SISE_SP, u0, np.arange(0, 50), g,
+                      v0=rng.uniform(0, 2, (n, 1)))
+    w.neighbors = W.distance_neighbors(x, y, 1500.0)
+    assert len(w.neighbors[1]) > n
+    code, U, V, R, err = orc.run(w)
+    assert code == 0
+    tot = (V[0, :, :, 0] * u0.sum(1)).sum(axis=1)
+    assert np.allclose(tot, tot[0], rtol=1e-11)
+    assert not np.allclose(V[0, -1, :, 0], V[0, 0, :, 0])
+
+
+def test_sise_sp_without_coupling_is_sise(orc):
+    w = W.config_sise(n_nodes=300, days=60, gen_seed=5)
+    g = w.gdata
+    w_sp = W.plain_model(W.SISE_SP, w.u0, w.tspan, np.r_[g, 0.0], events=w.events,
+                         seed=w.seed)
+    rng = np.random.default_rng(1)
+    w_sp.neighbors = W.distance_neighbors(rng.uniform(0, 1e4, 300), rng.uniform(0, 1e4, 300),
+                                          2000.0)
+    c1, U1, V1, R1, e1 = orc.run(w)
+    c2, U2, V2, R2, e2 = orc.run(w_sp)
+    assert c1 == 0 and c2 == 0
+    assert np.array_equal(U1, U2) and np.array_equal(V1, V2)
