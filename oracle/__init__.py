@@ -66,6 +66,7 @@ class _Model(ctypes.Structure):
         ("ldata", ctypes.c_void_p), ("n_gdata", ctypes.c_int),
         ("gdata", ctypes.c_void_p), ("nb_ptr", ctypes.c_void_p),
         ("nb_idx", ctypes.c_void_p), ("nb_dist", ctypes.c_void_p),
+        ("solver", ctypes.c_int),
     ]
 
 
@@ -180,9 +181,12 @@ def apply_event(E, N, etype, u_node, u_dest=None, n=0, proportion=0.0,
     return rc, un, ud
 
 
-def run(w, seed=None, n_rep=None, u0=None, v0=None):
+def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
     """Run the oracle on a workload description (see
     ``paper_1605_01421_gb300.workloads.Workload``).
+
+    ``solver`` (default ``w.solver``): 0 the direct-method split step
+    ('ssm'), 1 the all events method ('aem').
 
     Returns ``(code, U, V, reactions, err)`` with U [R][M][Nn][C] int32,
     V [R][M][Nn][Nv] float64, reactions [R] int64 and err a dict.
@@ -212,7 +216,8 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None):
                int(gdata.size), _ptr(gdata),
                _ptr(nb_ptr) if nb_ptr is not None else None,
                _ptr(nb_idx) if nb_idx is not None and nb_idx.size else None,
-               _ptr(nb_dist) if nb_dist is not None and nb_dist.size else None)
+               _ptr(nb_dist) if nb_dist is not None and nb_dist.size else None,
+               int(getattr(w, "solver", 0) if solver is None else solver))
     ev = w.events
     keep = []
     if ev is not None and len(ev["event"]) > 0:

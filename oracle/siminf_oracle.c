@@ -20,6 +20,9 @@
  *     pseudo-code of Appendix A: per node, direct SSA up to the next unit of
  *     time, then the node's E1 events, then all E2 events, then the post time
  *     step function, then recording at tspan points (Sec. 3.4.2);
+ *   - the 'aem' solver of Sec. 3.4.2 (channels with private random streams),
+ *     read as the next reaction method of Gibson and Bruck with one Philox
+ *     stream per (node, transition) channel (see aem_node_day);
  *   - direct SSA step: Appendix A (rate sum, exponential waiting time with
  *     log of an open-interval uniform, inversion on lambda * r2, update by
  *     column n of S, recomputation of the rates that column n of G marks);
@@ -106,6 +109,7 @@ double oracle_u01(uint32_t a, uint32_t b)
 /*   x = 2^k * m, m in (sqrt(2)/2, sqrt(2)];  f = m - 1;  s = f / (2 + f);  */
 /*   log(1 + f) = 2 atanh(s) = 2 s + s R(s^2),                              */
 /*   R(z) = sum_{j=1..10} 2 z^j / (2 j + 1)   (Taylor series of atanh),     */
+/*   evaluated in Estrin's scheme (depth 8 instead of Horner's 20),         */
 /* rearranged with 2 s = f - hfsq + s hfsq, hfsq = f^2 / 2, into            */
 /*   log(1 + f) = f - (hfsq - s (hfsq + R)),                                */
 /* and log x = k ln2_hi + (f - (hfsq - (s (hfsq + R) + k ln2_lo))) with a   */
@@ -144,9 +148,20 @@ double oracle_log(double x)
     hfsq = (0.5 * f) * f;
     s = f / (2.0 + f);
     z = s * s;
-    R = z * (2.0 / 3.0 + z * (2.0 / 5.0 + z * (2.0 / 7.0 + z * (2.0 / 9.0
-        + z * (2.0 / 11.0 + z * (2.0 / 13.0 + z * (2.0 / 15.0
-        + z * (2.0 / 17.0 + z * (2.0 / 19.0 + z * (2.0 / 21.0))))))))));
+    /* R(z) = z P(z), P(z) = sum_{j=1..10} c_j z^(j-1), c_j = 2 / (2 j + 1),
+     * in Estrin's scheme: pairs c_j + c_(j+1) z, combined with z^2, z^4, z^8 */
+    {
+        double z2 = z * z, z4 = z2 * z2, z8 = z4 * z4;
+        double p01 = 2.0 / 3.0 + (2.0 / 5.0) * z;
+        double p23 = 2.0 / 7.0 + (2.0 / 9.0) * z;
+        double p45 = 2.0 / 11.0 + (2.0 / 13.0) * z;
+        double p67 = 2.0 / 15.0 + (2.0 / 17.0) * z;
+        double p89 = 2.0 / 19.0 + (2.0 / 21.0) * z;
+        double q03 = p01 + z2 * p23;
+        double q47 = p45 + z2 * p67;
+        double P = (q03 + z4 * q47) + z8 * p89;
+        R = z * P;
+    }
     dk = (double)k;
     return dk * ln2_hi + (f - (hfsq - (s * (hfsq + R) + dk * ln2_lo)));
 }
@@ -617,6 +632,127 @@ static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
     return 0;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The 'aem' solver (Sec. 3.4.2): transitions carried out in channels with   */
+/* private random streams.  Reading: channel (node i, transition j) owns the */
+/* Philox stream with counter (c_ij, i, j, (3 << 24) | replicate), c_ij the */
+/* number of draws the channel has taken so far, and the channels are advanced by the next reaction method of   */
+/* Gibson and Bruck (J. Phys. Chem. A 104, 2000): every channel holds an     */
+/* absolute firing time tau_ij; the earliest one fires; the fired channel    */
+/* draws a fresh exponential, and a channel whose rate changed from a_old > 0 */
+/* to a_new > 0 rescales its residual waiting time by a_old / a_new, which   */
+/* keeps it exponential with the new rate.  A channel whose rate drops to 0  */
+/* sleeps (tau = +inf); one that wakes draws a fresh exponential (memoryless  */
+/* property).  Residual times carry over from day to day: at the start of    */
+/* every day the rates of all channels are recomputed (events and the post   */
+/* time step may have changed u and v) and the same update rule is applied. */
+/* ------------------------------------------------------------------------ */
+
+/* Exponential(1) draw number *cnt of channel (node, j): -log u, u from the
+ * first two words of Philox call (*cnt, node, j, (3 << 24) | rep). */
+static int aem_draw(uint64_t seed, int node, int j, int rep, uint32_t *cnt,
+                    double *E)
+{
+    uint32_t ctr[4], key[2], x[4];
+    if (*cnt == UINT32_MAX) return ORACLE_ERR_STEP_LIMIT;
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    ctr[0] = *cnt;
+    ctr[1] = (uint32_t)node;
+    ctr[2] = (uint32_t)j;
+    ctr[3] = ((uint32_t)ORACLE_STREAM_AEM << 24) | (uint32_t)rep;
+    oracle_philox4x32_10(ctr, key, x);
+    *cnt += 1;
+    *E = -oracle_log(oracle_u01(x[0], x[1]));
+    return 0;
+}
+
+/* The update rule of channel j at time t when its rate becomes a_new. */
+static int aem_update(uint64_t seed, int node, int j, int rep, double t,
+                      double a_new, double *a, double *tau, uint32_t *cnt)
+{
+    double E;
+    int rc;
+    if (a_new == a[j]) return 0;  /* unchanged rate: nothing to do */
+    if (a[j] > 0.0 && a_new > 0.0) {
+        tau[j] = t + (a[j] / a_new) * (tau[j] - t);
+    } else if (a_new > 0.0) {
+        rc = aem_draw(seed, node, j, rep, &cnt[j], &E);
+        if (rc) return rc;
+        tau[j] = t + E / a_new;
+    } else {
+        tau[j] = INFINITY;
+    }
+    a[j] = a_new;
+    return 0;
+}
+
+/* One node from t0 = T - 1 to T under the all events method.  a, tau, cnt
+ * are the node's n_trans channel states (a = 0, tau = +inf, cnt = 0 before
+ * the first day). */
+static int aem_node_day(const oracle_model *m, int node, int rep, int T,
+                        double t0, int *u, const double *v, double *a,
+                        double *tau, uint32_t *cnt, uint64_t seed,
+                        int64_t *reactions)
+{
+    const double *ld = m->ldata + (size_t)node * (size_t)m->n_ldata;
+    double t = t0;
+    uint32_t fired = 0;
+    int j, k, rc;
+
+    for (j = 0; j < m->n_trans; j++) {
+        double w = model_rate(m->kind, j, u, v, ld, m->gdata);
+        if (!(w >= 0.0) || isinf(w)) return ORACLE_ERR_RATE;
+        rc = aem_update(seed, node, j, rep, t, w, a, tau, cnt);
+        if (rc) return rc;
+    }
+    for (;;) {
+        /* the earliest channel; ties go to the lowest index */
+        int mu = -1;
+        double best = INFINITY, E;
+        for (j = 0; j < m->n_trans; j++) {
+            if (tau[j] < best) {
+                best = tau[j];
+                mu = j;
+            }
+        }
+        if (mu < 0 || best >= (double)T) break;
+        /* Guard (not in the paper), as for the direct method. */
+        if (fired >= ORACLE_MAX_DRAWS_PER_NODE_DAY) return ORACLE_ERR_STEP_LIMIT;
+        fired++;
+        t = best;
+        for (k = 0; k < m->n_comp; k++)
+            u[k] += m->S[(size_t)mu * (size_t)m->n_comp + (size_t)k];
+        *reactions += 1;
+        /* the rates column mu of G marks; the fired channel itself always
+         * draws a fresh waiting time */
+        for (k = 0; k < m->n_trans; k++) {
+            double w;
+            if (k != mu && m->G[(size_t)mu * (size_t)m->n_trans + (size_t)k] == 0)
+                continue;
+            w = a[k];
+            if (m->G[(size_t)mu * (size_t)m->n_trans + (size_t)k] != 0) {
+                w = model_rate(m->kind, k, u, v, ld, m->gdata);
+                if (!(w >= 0.0) || isinf(w)) return ORACLE_ERR_RATE;
+            }
+            if (k == mu) {
+                a[k] = w;
+                if (w > 0.0) {
+                    rc = aem_draw(seed, node, k, rep, &cnt[k], &E);
+                    if (rc) return rc;
+                    tau[k] = t + E / w;
+                } else {
+                    tau[k] = INFINITY;
+                }
+            } else {
+                rc = aem_update(seed, node, k, rep, t, w, a, tau, cnt);
+                if (rc) return rc;
+            }
+        }
+    }
+    return 0;
+}
+
 int oracle_run(const oracle_model *m, const oracle_events *ev,
                const int *tspan, int n_tspan, uint64_t seed, int n_rep,
                const int *u0, const double *v0, int *U, double *V,
@@ -630,6 +766,9 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     int rep, rc;
     int *u = NULL;
     double *v = NULL, *v_new = NULL, *vtmp = NULL;
+    double *aem_a = NULL, *aem_tau = NULL;
+    uint32_t *aem_cnt = NULL;
+    const size_t nch = (size_t)Nn * (size_t)m->n_trans;
 
     if (err) memset(err, 0, sizeof *err);
     rc = validate(m, ev, tspan, n_tspan, n_rep, err);
@@ -655,8 +794,15 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     v = (double *)malloc((vstride ? vstride : 1) * sizeof *v);
     v_new = (double *)malloc((Nv ? Nv : 1) * sizeof *v_new);
     vtmp = (double *)malloc((Nn ? Nn : 1) * sizeof *vtmp);
-    if (!u || !v || !v_new || !vtmp) {
+    if (m->solver == ORACLE_SOLVER_AEM) {
+        aem_a = (double *)malloc((nch ? nch : 1) * sizeof *aem_a);
+        aem_tau = (double *)malloc((nch ? nch : 1) * sizeof *aem_tau);
+        aem_cnt = (uint32_t *)malloc((nch ? nch : 1) * sizeof *aem_cnt);
+    }
+    if (!u || !v || !v_new || !vtmp ||
+        (m->solver == ORACLE_SOLVER_AEM && (!aem_a || !aem_tau || !aem_cnt))) {
         free(order); free(u); free(v); free(v_new); free(vtmp);
+        free(aem_a); free(aem_tau); free(aem_cnt);
         return ORACLE_ERR_NOMEM;
     }
 
@@ -666,6 +812,14 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
         memcpy(u, u0 + (size_t)rep * ustride, ustride * sizeof *u);
         if (vstride) memcpy(v, v0 + (size_t)rep * vstride, vstride * sizeof *v);
         if (reactions) reactions[rep] = 0;
+        if (aem_a) {
+            size_t q;
+            for (q = 0; q < nch; q++) {
+                aem_a[q] = 0.0;
+                aem_tau[q] = INFINITY;
+                aem_cnt[q] = 0;
+            }
+        }
         /* U[, 1] = u0 and V[, 1] = v0: the state at tspan[0]. */
         memcpy(U + (size_t)rep * (size_t)n_tspan * ustride, u,
                ustride * sizeof *u);
@@ -680,8 +834,15 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
 
             /* (1) local stochastic step, Eq. numstep1, node by node */
             for (node = 0; node < Nn; node++) {
-                rc = ssa_node_day(m, node, rep, T, t0, u + (size_t)node * C,
-                                  v + (size_t)node * Nv, seed, &nr);
+                if (aem_a) {
+                    const size_t o = (size_t)node * (size_t)m->n_trans;
+                    rc = aem_node_day(m, node, rep, T, t0, u + (size_t)node * C,
+                                      v + (size_t)node * Nv, aem_a + o,
+                                      aem_tau + o, aem_cnt + o, seed, &nr);
+                } else {
+                    rc = ssa_node_day(m, node, rep, T, t0, u + (size_t)node * C,
+                                      v + (size_t)node * Nv, seed, &nr);
+                }
                 if (rc) {
                     set_error(err, rc, rep, node, -1, T);
                     goto done;
@@ -755,6 +916,9 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     }
     rc = 0;
 done:
+    free(aem_a);
+    free(aem_tau);
+    free(aem_cnt);
     free(order);
     free(u);
     free(v);

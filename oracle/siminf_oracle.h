@@ -35,7 +35,8 @@ enum {
     ORACLE_EV_INTERNAL = 2,
     ORACLE_EV_EXTERNAL = 3
 };
-enum { ORACLE_STREAM_SSA = 0, ORACLE_STREAM_EVENTS = 1 };
+enum { ORACLE_STREAM_SSA = 0, ORACLE_STREAM_EVENTS = 1, ORACLE_STREAM_AEM = 3 };
+enum { ORACLE_SOLVER_SSM = 0, ORACLE_SOLVER_AEM = 1 };
 enum {
     ORACLE_OK = 0,
     ORACLE_ERR_ARG = -1,
@@ -47,7 +48,8 @@ enum {
     ORACLE_ERR_STEP_LIMIT = -9
 };
 
-/* A node-day stops with ORACLE_ERR_STEP_LIMIT before its 2^24 + 1-th draw. */
+/* A node-day stops with ORACLE_ERR_STEP_LIMIT before its 2^24 + 1-th draw
+ * (direct method) or firing ('aem'). */
 #define ORACLE_MAX_DRAWS_PER_NODE_DAY (1u << 24)
 
 typedef struct {
@@ -69,6 +71,8 @@ typedef struct {
     const int64_t *nb_ptr;
     const int *nb_idx;
     const double *nb_dist;
+    /* ORACLE_SOLVER_SSM (direct SSA per day) or ORACLE_SOLVER_AEM */
+    int solver;
 } oracle_model;
 
 typedef struct {

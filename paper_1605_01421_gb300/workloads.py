@@ -25,6 +25,8 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SIR, SIS, SISE, SISE3, SISE_SP = 0, 1, 2, 3, 4
+# solvers (Sec. 3.4.2): split-step direct SSA, all events method
+SSM, AEM = 0, 1
 EXIT, ENTER, INTERNAL, EXTERNAL = 0, 1, 2, 3
 KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3", SISE_SP: "SISe_sp"}
 
@@ -49,6 +51,8 @@ class Workload:
     meta: dict = field(default_factory=dict)
     # SISe_sp: neighbour lists (ptr (n_nodes + 1,), idx, distance) or None
     neighbors: tuple | None = None
+    # solver: SSM (direct SSA per day) or AEM (all events method)
+    solver: int = 0
 
     @property
     def n_nodes(self) -> int:

@@ -6,6 +6,7 @@
   SIR, SIS, SISe with frozen phi and SISe3 per age class with distinct
   parameters, so that a wrong index, sign or transposed rate fails.
 - Pure death: I(t) ~ Binomial(I0, exp(-gamma t)).
+- All of the above for both solvers ('ssm' and 'aem').
 - Mean-field limit: the ensemble mean of large nodes follows Eq. (ODE).
 - Conservation of every node's population under the SSA.
 - The post time step: phi follows the closed form of the Euler recursion.
@@ -64,6 +65,10 @@ def _cme(states, rates_and_targets, p0_index, times):
     return {t: p0 @ expm(Q * t) for t in times}, index
 
 
+# every law holds for both solvers of Sec. 3.4.2: the direct method and the
+# all events method (next reaction method over private channel streams)
+SOLVERS = pytest.mark.parametrize("solver", [W.SSM, W.AEM], ids=["ssm", "aem"])
+
 NODES = 100_000
 DAYS = (1, 2, 5, 10)
 
@@ -77,7 +82,8 @@ def _empirical(U, comps, index, day):
     return counts
 
 
-def test_sir_matches_cme(orc):
+@SOLVERS
+def test_sir_matches_cme(orc, solver):
     beta, gamma, N = 1.2, 0.4, 5
     states = [(s, i) for s in range(N + 1) for i in range(N + 1 - s)]
 
@@ -88,6 +94,7 @@ def test_sir_matches_cme(orc):
     p, index = _cme(states, moves, states.index((4, 1)), DAYS)
     w = W.plain_model(W.SIR, np.tile([[4, 1, 0]], (NODES, 1)),
                       np.arange(0, 11), [beta, gamma], seed=2024)
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
     for d in DAYS:
@@ -96,7 +103,8 @@ def test_sir_matches_cme(orc):
         assert _chi2_pvalue(obs, p[d] * NODES) > 1e-3, d
 
 
-def test_sis_matches_cme(orc):
+@SOLVERS
+def test_sis_matches_cme(orc, solver):
     # Sec. 2.1: R(x) = [beta x1 x2, gamma x2] without division by N
     beta, gamma, N = 0.3, 1.0, 5
     states = [(N - i, i) for i in range(N + 1)]
@@ -108,6 +116,7 @@ def test_sis_matches_cme(orc):
     p, index = _cme(states, moves, states.index((3, 2)), DAYS)
     w = W.plain_model(W.SIS, np.tile([[3, 2]], (NODES, 1)), np.arange(0, 11),
                       [beta, gamma], seed=77)
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
     for d in DAYS:
@@ -115,7 +124,8 @@ def test_sis_matches_cme(orc):
         assert _chi2_pvalue(obs, p[d] * NODES) > 1e-3, d
 
 
-def test_sise_frozen_phi_matches_cme(orc):
+@SOLVERS
+def test_sise_frozen_phi_matches_cme(orc, solver):
     # alpha = 0 and zero decay keep phi at v0, so the node is a linear
     # birth-death chain with S -> I at upsilon phi S and I -> S at gamma I
     upsilon, gamma, phi, N = 0.3, 0.7, 2.0, 5
@@ -129,6 +139,7 @@ def test_sise_frozen_phi_matches_cme(orc):
     g = W.sise_gdata(upsilon=upsilon, gamma=gamma, alpha=0.0, betas=(0.0,) * 4)
     w = W.plain_model(W.SISE, np.tile([[5, 0]], (NODES, 1)), np.arange(0, 11),
                       g, seed=5, v0=np.full((NODES, 1), phi))
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
     assert np.all(V == phi)
@@ -137,13 +148,15 @@ def test_sise_frozen_phi_matches_cme(orc):
         assert _chi2_pvalue(obs, p[d] * NODES) > 1e-3, d
 
 
-def test_sise3_each_age_class_matches_cme(orc):
+@SOLVERS
+def test_sise3_each_age_class_matches_cme(orc, solver):
     ups, gams, phi = (0.1, 0.35, 0.8), (0.9, 0.5, 0.2), 1.5
     n_nodes = 50_000
     u0 = np.tile([[4, 0, 3, 1, 2, 2]], (n_nodes, 1))
     g = W.sise3_gdata(upsilons=ups, gammas=gams, alpha=0.0, betas=(0.0,) * 4)
     w = W.plain_model(W.SISE3, u0, np.arange(0, 6), g, seed=9,
                       v0=np.full((n_nodes, 1), phi))
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
     for a in range(3):
@@ -163,10 +176,12 @@ def test_sise3_each_age_class_matches_cme(orc):
             assert _chi2_pvalue(obs, p[d] * n_nodes) > 1e-3, (a, d)
 
 
-def test_pure_death_is_binomial(orc):
+@SOLVERS
+def test_pure_death_is_binomial(orc, solver):
     gamma, I0 = 0.25, 12
     w = W.plain_model(W.SIR, np.tile([[0, I0, 0]], (40_000, 1)),
                       np.arange(0, 9), [0.0, gamma], seed=31)
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
     for d in (1, 3, 8):
@@ -178,11 +193,13 @@ def test_pure_death_is_binomial(orc):
     assert R[0] == I0 * 40_000 - U[0, -1][:, 1].sum()
 
 
-def test_mean_field_limit(orc):
+@SOLVERS
+def test_mean_field_limit(orc, solver):
     beta, gamma, N, I0 = 0.5, 0.2, 20_000, 400
     nodes = 60
     w = W.plain_model(W.SIR, np.tile([[N - I0, I0, 0]], (nodes, 1)),
                       np.arange(0, 31), [beta, gamma], seed=8)
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0
 
@@ -198,8 +215,10 @@ def test_mean_field_limit(orc):
         assert abs(mean[1] - sol.y[1, d]) / N < 0.01
 
 
-def test_ssa_conserves_population(orc):
+@SOLVERS
+def test_ssa_conserves_population(orc, solver):
     w = W.config_sise3(n_nodes=300, days=60, gen_seed=4, events_per_node_day=0)
+    w.solver = solver
     code, U, V, R, err = orc.run(w)
     assert code == 0 and R[0] > 0
     for a in range(3):
