@@ -28,6 +28,8 @@ sys.path.insert(0, _ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "node-days/s (direct-method SSA + scheduled events + post time step + recording)"
+METRIC_AEM = ("node-days/s (all events method: per-channel streams, next reaction method"
+              " + scheduled events + post time step + recording)")
 UNIT = "node-days/s"
 L2_BYTES = 129 * 2 ** 20
 # FP64 ops (adds, multiplies, divides, conversions each counted once) of one
@@ -38,9 +40,27 @@ FP64_PER_DRAW = 44
 FP64_PER_REACTION = 9
 FP64_PER_NODE_DAY = 14  # day-start rates (6) + post time step (8)
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal table figure)
+# The same counts for the all events method: a channel draw is a uniform (6),
+# logarithm (34), divide by the rate (1) and add to the time (1); a firing
+# compares the firing times (2), recomputes two rates (6) and rescales the
+# other dependent channel (4); a node-day adds the day-start rescale checks.
+FP64_PER_DRAW_AEM = 42
+FP64_PER_REACTION_AEM = 12
+FP64_PER_NODE_DAY_AEM = 16
 
 
-def _workload(name):
+def _workload(name, solver="ssm"):
+    w = _base_workload(name)
+    from paper_1605_01421_gb300 import workloads as W
+    w.solver = W.AEM if solver == "aem" else W.SSM
+    return w
+
+
+def _metric(w):
+    return METRIC_AEM if getattr(w, "solver", 0) == 1 else METRIC
+
+
+def _base_workload(name):
     from paper_1605_01421_gb300 import workloads as W
     if name == "sise":
         return W.config_sise()
@@ -171,7 +191,7 @@ def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w_full = _workload(args.workload)
+    w_full = _workload(args.workload, args.solver)
     w, desc = _oracle_sample(w_full, max_node_days=3e6)
     node_days = w.n_nodes * w.n_days * w.n_rep
     import oracle
@@ -187,7 +207,7 @@ def bench_reference(args):
         reactions += int(R.sum())
     total = sum(times)
     value = node_days * args.steps / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+    line = {"impl": "reference", "metric": _metric(w_full), "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
@@ -216,7 +236,8 @@ def bench_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     binding.build()
-    w = _workload(args.workload)
+    w = _workload(args.workload, args.solver)
+    aem = w.solver == 1
     n_rep = w.n_rep
     M = len(w.tspan)
     dev = torch.device("cuda", local)
@@ -285,13 +306,18 @@ def bench_gpu(args):
     shares = {k: kt[f"ms_{k}"] for k in ("ssa", "e1", "e2")}
     dominant = max(shares, key=shares.get)
     fp64_measured = binding.fp64_fma_probe()
-    ssa_flops = (FP64_PER_DRAW * kt["draws"] + FP64_PER_REACTION * kt["reactions"]
-                 + FP64_PER_NODE_DAY * kt["node_days"])
+    if aem:
+        ssa_flops = (FP64_PER_DRAW_AEM * kt["draws"] + FP64_PER_REACTION_AEM * kt["reactions"]
+                     + FP64_PER_NODE_DAY_AEM * kt["node_days"])
+    else:
+        ssa_flops = (FP64_PER_DRAW * kt["draws"] + FP64_PER_REACTION * kt["reactions"]
+                     + FP64_PER_NODE_DAY * kt["node_days"])
     if dominant == "ssa":
         achieved = ssa_flops / (kt["ms_ssa"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": "k_days (SSA + post time step + recording)",
+                "kernel": ("k_days<aem> (channels + post time step + recording)" if aem
+                           else "k_days (SSA + post time step + recording)"),
                 "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s)",
                 "fp64_fma_measured_tflops": fp64_measured,
                 "frac_of_measured_fp64": achieved / fp64_measured,
@@ -337,7 +363,7 @@ def bench_gpu(args):
             dist.destroy_process_group()
         return
     cpu = time_oracle(w, budget_s=args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+    line = {"metric": _metric(w), "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
@@ -345,6 +371,7 @@ def bench_gpu(args):
             "reactions_per_s": reactions * world / (total_ms * 1e-3),
             "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
                        "replicates": n_rep, "events": w.n_events, "seed": w.seed,
+                       "solver": "aem" if aem else "ssm",
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas{world}"},
             "gpu_launches": launches,
@@ -486,6 +513,8 @@ def main():
     ap.add_argument("--emu-workload", default="sise3", choices=["sise3", "endemic"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--solver", default="ssm", choices=["ssm", "aem"],
+                    help="ssm: split-step direct SSA; aem: all events method (Sec. 3.4.2)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)

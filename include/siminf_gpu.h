@@ -68,6 +68,24 @@ typedef enum {
   SG_SISE_SP = 4
 } sg_model_kind;
 
+/* Solvers of Sec. 3.4.2.  Both process the scheduled events and the post
+ * time step once per unit of time; they differ in how transitions fire
+ * between those points.
+ *   SG_SOLVER_SSM  split-step method: per node and day, direct SSA
+ *                  (Appendix A) with one random stream for all transitions,
+ *                  Philox counter (draw, node, day, (0 << 24) | replicate).
+ *   SG_SOLVER_AEM  all events method: every (node, transition) is a channel
+ *                  with its own random stream, Philox counter (draws taken by
+ *                  the channel, node, transition, (3 << 24) | replicate),
+ *                  advanced by the next reaction method of Gibson and Bruck
+ *                  (absolute firing times; the earliest fires and redraws;
+ *                  a channel whose rate changes from a > 0 to a' > 0 rescales
+ *                  its residual time by a / a'; rate 0 sleeps, waking
+ *                  redraws).  Firing times carry over between days, and every
+ *                  rate is recomputed at each day start.  The draw is
+ *                  E = -log u with u from the first two words of the call. */
+typedef enum { SG_SOLVER_SSM = 0, SG_SOLVER_AEM = 1 } sg_solver;
+
 /* Event types, coded as in the event table of Sec. 3.3. */
 typedef enum {
   SG_EXIT = 0,
@@ -236,6 +254,63 @@ int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t see
  * directly.  enable = 0 turns capture off. */
 int sg_set_graphs(sg_model *m, int enable);
 
+/* Output selection of later sg_run calls.
+ *
+ * Sec. 3.2 (the model's result slots U, V, U_sparse, V_sparse): besides the
+ * dense trajectories, the solver can write the state only where a sparse
+ * pattern with the layout of U (rows node * n_comp + compartment) or of V
+ * (rows node * n_v + index), one column per tspan point, has entries; this
+ * saves memory when only a few points of many nodes and days matter.  The
+ * prevalence summary (Sec. 4.2, prevalence with a formula cases ~ at risk)
+ * is accumulated on the device at every tspan point.
+ *
+ *   dense        1: sg_run writes d_U and d_V as before; 0: they are not
+ *                written and may be NULL (sg_run_host: U and V may be NULL).
+ *   n_tspan      columns of the patterns and points of the prevalence
+ *                counters; every later sg_run must use this many tspan
+ *                points (SG_ERR_ARG otherwise) while a pattern or the
+ *                prevalence is set.
+ *   u_nnz, u_colptr, u_row   U_sparse pattern in compressed-column form:
+ *                the entries of column m are u_colptr[m] .. u_colptr[m+1]-1
+ *                (u_colptr[0] = 0, u_colptr[n_tspan] = u_nnz), u_row their
+ *                rows, strictly increasing within a column.  Host memory,
+ *                copied by this call.  u_nnz = 0: no U_sparse.
+ *   d_u_val      device, int32 [n_rep][u_nnz]: U at the pattern's entries.
+ *   v_nnz, v_colptr, v_row, d_v_val   the same for V_sparse (double).
+ *   prev_cases, prev_at_risk   bit p set: compartment p is a case / at risk
+ *                (both 0: no prevalence, else both nonzero).
+ *   d_prev       device, int64 [n_rep][n_tspan][4]: per replicate and point
+ *                the sum over nodes of the cases, the sum of those at risk,
+ *                the number of nodes with a case and the number of nodes
+ *                with anyone at risk.  "pop" prevalence = [0] / [1], "nop"
+ *                (proportion of nodes with a case) = [2] / [3].
+ * The d_ buffers are caller-owned and must stay valid for every later run.
+ * o = NULL restores the default (dense only).  Returns SG_ERR_ARG for an
+ * invalid pattern or mask (the selection is then reset to the default). */
+typedef struct {
+  int32_t dense;
+  int32_t n_tspan;
+  int64_t u_nnz;
+  const int64_t *u_colptr;
+  const int32_t *u_row;
+  int32_t *d_u_val;
+  int64_t v_nnz;
+  const int64_t *v_colptr;
+  const int32_t *v_row;
+  double *d_v_val;
+  uint32_t prev_cases, prev_at_risk;
+  int64_t *d_prev;
+} sg_output;
+
+int sg_set_output(sg_model *m, const sg_output *o);
+
+/* Select the solver of later sg_run calls (SG_SOLVER_SSM by default).
+ * SG_SOLVER_AEM keeps 20 bytes of channel state per (replicate, node,
+ * transition) on the device, allocated by sg_run.  It cannot be combined
+ * with a learned emulator (sg_run returns SG_ERR_ARG).  Returns SG_ERR_ARG
+ * for an unknown solver. */
+int sg_set_solver(sg_model *m, int32_t solver);
+
 /* Release the model and all its device memory. */
 void sg_model_destroy(sg_model *m);
 
@@ -257,7 +332,8 @@ const char *sg_strerror(int code);
  * lives in one fixed array of SG_NOALLOC_SCRATCH_BYTES bytes inside this
  * library, which every GPU that loads the library keeps until the process
  * exits.  It runs the model without scheduled events (the event schedule
- * needs memory proportional to the event table).
+ * needs memory proportional to the event table), with the direct-method
+ * solver SG_SOLVER_SSM.
  *
  * Limits and behaviour:
  *   - needed scratch = 1024 + 4 (days + 1) + 4 n_tspan + 4 n_rep n_nodes

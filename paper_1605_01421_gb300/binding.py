@@ -123,7 +123,8 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_run_noalloc", "sg_set_tuning", "sg_autotune", "sg_set_graphs",
            "sg_gemm_bf16", "sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
-           "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors"]
+           "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
+           "sg_set_output"]
 
 _lock = threading.Lock()
 _lib = None
@@ -178,6 +179,10 @@ def lib(path: str | None = None):
         L.sg_autotune.restype = ctypes.c_int
         L.sg_set_graphs.argtypes = [vp, ctypes.c_int]
         L.sg_set_graphs.restype = ctypes.c_int
+        L.sg_set_solver.argtypes = [vp, i32]
+        L.sg_set_solver.restype = ctypes.c_int
+        L.sg_set_output.argtypes = [vp, vp]
+        L.sg_set_output.restype = ctypes.c_int
         L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
                                    i32, vp]
         L.sg_gemm_bf16.restype = ctypes.c_int
@@ -237,6 +242,16 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+class _Output(ctypes.Structure):
+    _fields_ = [("dense", ctypes.c_int32), ("n_tspan", ctypes.c_int32),
+                ("u_nnz", ctypes.c_int64), ("u_colptr", ctypes.c_void_p),
+                ("u_row", ctypes.c_void_p), ("d_u_val", ctypes.c_void_p),
+                ("v_nnz", ctypes.c_int64), ("v_colptr", ctypes.c_void_p),
+                ("v_row", ctypes.c_void_p), ("d_v_val", ctypes.c_void_p),
+                ("prev_cases", ctypes.c_uint32), ("prev_at_risk", ctypes.c_uint32),
+                ("d_prev", ctypes.c_void_p)]
+
+
 class Model:
     """A model handle (sg_model): tables of Sec. 3.2 plus scheduled events.
 
@@ -261,10 +276,64 @@ class Model:
         if rc:
             raise SimInfError(rc)
         self._h = h
+        self.dense = True
         if getattr(w, "events", None) is not None:
             self.set_events(w.events)
         if getattr(w, "neighbors", None) is not None:
             self.set_neighbors(*w.neighbors)
+        if getattr(w, "solver", 0):
+            self.set_solver(w.solver)
+
+    def set_output(self, dense=True, n_tspan=0, u_pattern=None, u_values=None,
+                   v_pattern=None, v_values=None, prevalence=None, prev_out=None):
+        """Output selection (sg_set_output): dense U / V on or off, U_sparse
+        and V_sparse patterns (colptr, row) with the layouts of U and V and
+        their value tensors (CUDA int32 (R, nnz), float64 (R, nnz)), and the
+        prevalence counters for ``prevalence = (cases, at_risk)``
+        (compartment index lists) into ``prev_out`` (CUDA int64 (R, M, 4)).
+        The tensors must stay alive for the runs that follow."""
+        import torch
+        keep = []
+
+        def pat(p):
+            if p is None:
+                return 0, None, None
+            cp = np.ascontiguousarray(p[0], dtype=np.int64)
+            rw = _i32(p[1])
+            keep.extend([cp, rw])
+            return int(rw.size), _p(cp), (_p(rw) if rw.size else None)
+
+        un, ucp, urw = pat(u_pattern)
+        vn, vcp, vrw = pat(v_pattern)
+        for t, n, nm in ((u_values, un, "u_values"), (v_values, vn, "v_values")):
+            if n and (t is None or t.dim() != 2 or t.shape[1] != n):
+                raise ValueError(f"{nm} must be a (n_rep, {n}) CUDA tensor")
+        if prevalence is not None and (prev_out is None or prev_out.dim() != 3
+                                       or tuple(prev_out.shape[1:]) != (int(n_tspan), 4)):
+            raise ValueError(f"prev_out must be a (n_rep, {int(n_tspan)}, 4) CUDA tensor")
+        cm = rm = 0
+        if prevalence is not None:
+            for c in prevalence[0]:
+                cm |= 1 << int(c)
+            for c in prevalence[1]:
+                rm |= 1 << int(c)
+        o = _Output(1 if dense else 0, int(n_tspan), un, ucp, urw,
+                    _dev_ptr(u_values, torch.int32, None, "u_values") if un else None,
+                    vn, vcp, vrw,
+                    _dev_ptr(v_values, torch.float64, None, "v_values") if vn else None,
+                    cm, rm,
+                    _dev_ptr(prev_out, torch.int64, None, "prev_out") if prevalence else None)
+        rc = lib().sg_set_output(self._h, ctypes.byref(o))
+        if rc:
+            raise SimInfError(rc)
+        self._out_refs = (u_values, v_values, prev_out)
+        self.dense = bool(dense)
+
+    def set_solver(self, solver):
+        """0: split-step direct SSA ('ssm'), 1: all events method ('aem')."""
+        rc = lib().sg_set_solver(self._h, int(solver))
+        if rc:
+            raise SimInfError(rc)
 
     def set_neighbors(self, ptr, idx, dist):
         ptr = np.ascontiguousarray(ptr, dtype=np.int64)
@@ -297,8 +366,8 @@ class Model:
         rc = L.sg_run(self._h, _p(ts), M, int(seed), R,
                       _dev_ptr(u0, torch.int32, (R, Nn, C), "u0"),
                       _dev_ptr(v0, torch.float64, (R, Nn, Nv), "v0"),
-                      _dev_ptr(U, torch.int32, (R, M, Nn, C), "U"),
-                      _dev_ptr(V, torch.float64, (R, M, Nn, Nv), "V"),
+                      _dev_ptr(U, torch.int32, (R, M, Nn, C), "U") if self.dense else None,
+                      _dev_ptr(V, torch.float64, (R, M, Nn, Nv), "V") if self.dense else None,
                       _stream_handle(stream), ctypes.byref(st), ctypes.byref(er))
         if rc and check:
             raise SimInfError(rc, er.as_dict())
@@ -310,14 +379,19 @@ class Model:
         ts = _i32(tspan)
         st, er = Stats(), Error()
         R, Nn, C, Nv, M = int(n_rep), self.n_nodes, self.n_comp, self.n_v, int(ts.size)
-        for a, dt, shp, nm in ((u0, np.int32, (R, Nn, C), "u0"), (v0, np.float64, (R, Nn, Nv), "v0"),
-                               (U, np.int32, (R, M, Nn, C), "U"), (V, np.float64, (R, M, Nn, Nv), "V")):
+        checks = [(u0, np.int32, (R, Nn, C), "u0"), (v0, np.float64, (R, Nn, Nv), "v0")]
+        if self.dense:
+            checks += [(U, np.int32, (R, M, Nn, C), "U"), (V, np.float64, (R, M, Nn, Nv), "V")]
+        else:
+            U = V = None
+        for a, dt, shp, nm in checks:
             if (a.dtype != dt or a.shape != shp or not a.flags.c_contiguous
                     or (nm in ("U", "V") and not a.flags.writeable)):
                 raise ValueError(f"{nm} must be a C-contiguous {np.dtype(dt).name} array "
                                  f"of shape {shp}")
         rc = L.sg_run_host(self._h, _p(ts), M, int(seed), R,
-                           _p(u0), _p(v0), _p(U), _p(V), _stream_handle(stream),
+                           _p(u0), _p(v0), _p(U) if U is not None else None,
+                           _p(V) if V is not None else None, _stream_handle(stream),
                            ctypes.byref(st), ctypes.byref(er))
         if rc and check:
             raise SimInfError(rc, er.as_dict())

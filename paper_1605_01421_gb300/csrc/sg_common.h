@@ -14,6 +14,7 @@
 #define SG_STREAM_SSA 0u
 #define SG_STREAM_EVENTS 1u
 #define SG_STREAM_EMU 2u
+#define SG_STREAM_AEM 3u
 
 // Model tables in the layout the kernels read (passed by value).
 struct SgTables {

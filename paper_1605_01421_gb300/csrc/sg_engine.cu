@@ -61,6 +61,108 @@ struct EvDev {
   const int64_t *e1_node_off;  // [slots * Nn + 1]; nullptr when there are none
 };
 
+// Output selection (Sec. 3.2 result slots U_sparse and V_sparse, and the
+// prevalence summary): compressed-column patterns with the layouts of U
+// (rows node * C + compartment) and V (rows node * NV + index), one column
+// per tspan point; values [R][nnz]; prevalence counters [R][M][4] (sum of
+// cases, sum at risk, nodes with a case, nodes with anyone at risk).
+struct OutDev {
+  const int64_t *u_colptr = nullptr;
+  const int32_t *u_row = nullptr;
+  int32_t *u_val = nullptr;
+  long long u_nnz = 0;
+  const int64_t *v_colptr = nullptr;
+  const int32_t *v_row = nullptr;
+  double *v_val = nullptr;
+  long long v_nnz = 0;
+  uint32_t cases = 0, at_risk = 0;
+  unsigned long long *prev = nullptr;
+};
+
+// First index in row[lo, hi) whose value is >= x.
+__device__ __forceinline__ long long lower_bound_i32(const int32_t *row, long long lo,
+                                                     long long hi, int32_t x) {
+  while (lo < hi) {
+    const long long mid = lo + ((hi - lo) >> 1);
+    if (row[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The U_sparse / V_sparse entries of one node at tspan slot m.
+template <int C, int NV>
+__device__ __forceinline__ void record_sparse(const OutDev &o, int m, int rep, int node,
+                                              const int *u, const double *v) {
+  if (o.u_nnz > 0) {
+    const long long hi = o.u_colptr[m + 1];
+    long long e = lower_bound_i32(o.u_row, o.u_colptr[m], hi, node * C);
+    for (; e < hi && o.u_row[e] < node * C + C; ++e) {
+      const int p = o.u_row[e] - node * C;
+      int x = 0;
+#pragma unroll
+      for (int q = 0; q < C; ++q)
+        if (q == p) x = u[q];
+      o.u_val[(long long)rep * o.u_nnz + e] = x;
+    }
+  }
+  if (NV > 0 && o.v_nnz > 0) {
+    const long long hi = o.v_colptr[m + 1];
+    long long e = lower_bound_i32(o.v_row, o.v_colptr[m], hi, node * NV);
+    for (; e < hi && o.v_row[e] < node * NV + NV; ++e) {
+      const int p = o.v_row[e] - node * NV;
+      double x = 0.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        if (q == p) x = v[q];
+      o.v_val[(long long)rep * o.v_nnz + e] = x;
+    }
+  }
+}
+
+// Adds recorded nodes to the prevalence counters of (replicate, slot m).
+// Called by all 32 lanes of the warp together; `key` = rep * M + m for a
+// thread that holds a unit (-1 otherwise; such lanes sit at the end of the
+// warp, so equal keys are contiguous), `on` = its state is recorded.  A
+// segmented inclusive scan over the warp, then one atomic per segment.
+template <int C>
+__device__ __forceinline__ void prevalence_add(const OutDev &o, long long key, bool on,
+                                               const int *u) {
+  long long cs = 0, rk = 0;
+  int nc = 0, nr = 0;
+  if (on) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) {
+      if ((o.cases >> p) & 1u) cs += u[p];
+      if ((o.at_risk >> p) & 1u) rk += u[p];
+    }
+    nc = cs > 0;
+    nr = rk > 0;
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long k2 = __shfl_up_sync(full, key, d);
+    const long long c2 = __shfl_up_sync(full, cs, d), r2 = __shfl_up_sync(full, rk, d);
+    const int nc2 = __shfl_up_sync(full, nc, d), nr2 = __shfl_up_sync(full, nr, d);
+    if (lane >= d && k2 == key) {
+      cs += c2;
+      rk += r2;
+      nc += nc2;
+      nr += nr2;
+    }
+  }
+  const long long next = __shfl_down_sync(full, key, 1);
+  if (key >= 0 && (lane == 31 || next != key)) {
+    unsigned long long *q = o.prev + key * 4;
+    if (cs) atomicAdd(q, (unsigned long long)cs);
+    if (rk) atomicAdd(q + 1, (unsigned long long)rk);
+    if (nc) atomicAdd(q + 2, (unsigned long long)nc);
+    if (nr) atomicAdd(q + 3, (unsigned long long)nr);
+  }
+}
+
 struct DayArgs {
   int *u;              // [R][Nn][C] working counts
   double *v;           // [R][Nn][NV] working continuous state
@@ -82,6 +184,11 @@ struct DayArgs {
   uint32_t k0, k1;         // Philox key (seed)
   SgDevError *err;
   SgCounters *cnt;
+  // all events method: channel state [T][R * Nn] (rate, firing time, draws
+  // taken); null for the direct method
+  double *aem_a, *aem_tau;
+  uint32_t *aem_cnt;
+  OutDev out;            // sparse output and prevalence (U, V may be null)
 };
 
 // One transition (Appendix A, inversion and update): the smallest n with
@@ -338,6 +445,115 @@ __device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> 
   __syncwarp();
 }
 
+// ---------------------------------------------------------------------------
+// The all events method (solver 'aem' of Sec. 3.4.2): every transition of a
+// node is a channel with its own random stream, Philox counter (draws taken
+// by the channel, node, transition, (3 << 24) | replicate), and the channels
+// advance by the next reaction method of Gibson and Bruck: each holds an
+// absolute firing time, the earliest fires, the fired channel draws a fresh
+// Exp(1) waiting time scaled by its rate, a channel whose rate changes from
+// a > 0 to a' > 0 rescales its residual time by a / a', one whose rate drops
+// to 0 sleeps (time +inf), one that wakes draws afresh.  Firing times carry
+// over from day to day; at each day start every rate is recomputed and the
+// same rule applied.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int aem_draw(uint32_t &c, uint32_t node, uint32_t j, uint32_t tag,
+                                        uint32_t k0, uint32_t k1, double &E) {
+  if (c == 0xffffffffu) return SG_ERR_STEP_LIMIT;
+  const U4 x = philox10(U4{c, node, j, tag}, k0, k1);
+  ++c;
+  E = -log_pos(u01_open(x.x, x.y));
+  return 0;
+}
+
+// Channel j's new rate a_new at time t (the update rule above).
+__device__ __forceinline__ int aem_update(double t, double a_new, double &a, double &tau,
+                                          uint32_t &c, uint32_t node, uint32_t j, uint32_t tag,
+                                          uint32_t k0, uint32_t k1, unsigned long long &drawn) {
+  if (a_new == a) return 0;
+  if (gt0(a) && gt0(a_new)) {
+    tau = t + (a / a_new) * (tau - t);
+  } else if (gt0(a_new)) {
+    double E;
+    const int rc = aem_draw(c, node, j, tag, k0, k1, E);
+    if (rc) return rc;
+    ++drawn;
+    tau = t + E / a_new;
+  } else {
+    tau = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  }
+  a = a_new;
+  return 0;
+}
+
+// One node-day from Tn - 1 to Tn under the all events method, channel state
+// in registers.  Returns 0 or an error.
+template <int KIND>
+__device__ __forceinline__ int aem_node_day(int *u, const double *kf, double *a, double *tau,
+                                            uint32_t *c, double Tn, uint32_t node, uint32_t tag,
+                                            uint32_t k0, uint32_t k1, const SgTables &tb,
+                                            unsigned long long &fired,
+                                            unsigned long long &drawn) {
+  using M = ModelTraits<KIND>;
+  constexpr int T = M::T;
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  double t = Tn - 1.0;
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    const double w = M::rate_k(j, u, kf, tb.gdata);
+    if (bad_rate(w)) return SG_ERR_RATE;
+    const int rc = aem_update(t, w, a[j], tau[j], c[j], node, (uint32_t)j, tag, k0, k1, drawn);
+    if (rc) return rc;
+  }
+  uint32_t nfired = 0;
+  for (;;) {
+    // the earliest channel, ties to the lowest index
+    int mu = -1;
+    double best = inf;
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      if (tau[j] < best) {
+        best = tau[j];
+        mu = j;
+      }
+    }
+    if (mu < 0 || best >= Tn) return 0;
+    if (nfired >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+    ++nfired;
+    t = best;
+#pragma unroll
+    for (int p = 0; p < M::C; ++p) u[p] += tb.S[mu][p];
+    ++fired;
+    const uint32_t dep = tb.dep[mu];
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      const bool marked = (dep >> k) & 1u;
+      if (k != mu && !marked) continue;
+      double w = a[k];
+      if (marked) {
+        w = M::rate_k(k, u, kf, tb.gdata);
+        if (bad_rate(w)) return SG_ERR_RATE;
+      }
+      if (k == mu) {
+        a[k] = w;
+        if (gt0(w)) {
+          double E;
+          const int rc = aem_draw(c[k], node, (uint32_t)k, tag, k0, k1, E);
+          if (rc) return rc;
+          ++drawn;
+          tau[k] = t + E / w;
+        } else {
+          tau[k] = inf;
+        }
+      } else {
+        const int rc = aem_update(t, w, a[k], tau[k], c[k], node, (uint32_t)k, tag, k0, k1, drawn);
+        if (rc) return rc;
+      }
+    }
+  }
+}
+
 // One E1 event (exit, enter or internal transfer, Sec. 3.3) on a node whose
 // counts are in the calling thread's registers.  Returns 0 or an error.
 template <int C>
@@ -411,10 +627,15 @@ __device__ __forceinline__ int finish_step(int Tf, const int *u, double *v, cons
   const int m = a.rec[Tf - a.t0];
   if (m >= 0) {
     const long long base = ((long long)rep * a.M + m) * tb.n_nodes + node;
+    if (a.U) {
 #pragma unroll
-    for (int p = 0; p < M::C; ++p) a.U[base * M::C + p] = u[p];
+      for (int p = 0; p < M::C; ++p) a.U[base * M::C + p] = u[p];
+    }
+    if (a.V) {
 #pragma unroll
-    for (int q = 0; q < M::NV; ++q) a.V[base * M::NV + q] = v[q];
+      for (int q = 0; q < M::NV; ++q) a.V[base * M::NV + q] = v[q];
+    }
+    record_sparse<M::C, M::NV>(a.out, m, rep, node, u, v);
   }
   return code;
 }
@@ -423,12 +644,12 @@ __device__ __forceinline__ int finish_step(int Tf, const int *u, double *v, cons
 // T_begin .. T_end - 1 with no external transfers before T_end - 1.  Per day:
 // rates, SSA (thread, then warp for heavy nodes), the node's E1 events, and
 // (unless a kernel boundary follows) the post time step and recording.
-template <int KIND>
+template <int KIND, bool AEM>
 __global__ void __launch_bounds__(kDayBlock)
 k_days(const SgTables tb, const DayArgs a) {
   using M = ModelTraits<KIND>;
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
-  __shared__ HeavySlot<C, NK> s_heavy[kDayBlock];
+  __shared__ HeavySlot<C, NK> s_heavy[AEM ? 1 : kDayBlock];
   __shared__ int s_nheavy;
   pdl_trigger();
   const int Nn = tb.n_nodes;
@@ -447,6 +668,8 @@ k_days(const SgTables tb, const DayArgs a) {
   v[0] = 0.0;
   long long ecur = 0, ebase = 0, eend = 0;
   int next_day = 0x7fffffff;
+  double ch_a[AEM ? T : 1], ch_tau[AEM ? T : 1];  // all events method channels
+  uint32_t ch_c[AEM ? T : 1];
   // static inputs first (they overlap the previous kernel's tail)
   if (in_range) {
     rep = (int)(gid / Nn);
@@ -473,18 +696,34 @@ k_days(const SgTables tb, const DayArgs a) {
       ecur = ebase + a.e1_cur[gid];
       if (ecur < eend) next_day = a.ev.e1_day[ecur];
     }
+    if constexpr (AEM) {
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ch_a[j] = a.aem_a[j * total + gid];
+        ch_tau[j] = a.aem_tau[j * total + gid];
+        ch_c[j] = a.aem_cnt[j * total + gid];
+      }
+    }
     if (a.finish_first) {
       code = finish_step<KIND>(a.T_begin - 1, u, v, ld, tb, a, rep, node);
       if (code) bad_day = a.T_begin - 1;
     }
   }
+  if (a.finish_first && a.out.prev) {
+    const int m = a.rec[a.T_begin - 1 - a.t0];
+    if (m >= 0)
+      prevalence_add<C>(a.out, in_range ? (long long)rep * a.M + m : -1, live && code == 0, u);
+  }
   const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
   for (int Td = a.T_begin; Td < a.T_end; ++Td) {
     const double Tn = (double)Td;
-    if (threadIdx.x == 0) s_nheavy = 0;
-    __syncthreads();
+    if constexpr (!AEM) {
+      if (threadIdx.x == 0) s_nheavy = 0;
+      __syncthreads();
+    }
     int my = -1;
-    const bool emulated = live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
+    const bool emulated =
+        !AEM && live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
     if (emulated) {
       // the learned emulator's sampled one-day increments (SISe3 only):
       // I_a += d_a, S_a -= d_a, each age class keeps its size
@@ -495,7 +734,15 @@ k_days(const SgTables tb, const DayArgs a) {
         u[2 * h + 1] += dlt;
       }
     }
-    if (live && code == 0 && !emulated) {
+    if (AEM && live && code == 0) {
+      double kf[NK];
+      M::prepare(v, tb.gdata, kf);
+      code = aem_node_day<KIND>(u, kf, ch_a, ch_tau, ch_c, Tn, (uint32_t)node,
+                                (SG_STREAM_AEM << 24) | (uint32_t)rep, a.k0, a.k1, tb, fired,
+                                drawn);
+      if (code) bad_day = Td;
+    }
+    if (!AEM && live && code == 0 && !emulated) {
       double kf[NK], w[T];
       M::prepare(v, tb.gdata, kf);
 #pragma unroll
@@ -527,11 +774,13 @@ k_days(const SgTables tb, const DayArgs a) {
       }
       if (code) bad_day = Td;
     }
-    __syncthreads();
-    const int nh = s_nheavy;
-    for (int h = warp; h < nh; h += nwarps)
-      ssa_warp<KIND>(s_heavy[h], Tn, (uint32_t)Td, a.k0, a.k1, tb, fired, drawn);
-    __syncthreads();
+    if constexpr (!AEM) {
+      __syncthreads();
+      const int nh = s_nheavy;
+      for (int h = warp; h < nh; h += nwarps)
+        ssa_warp<KIND>(s_heavy[h], Tn, (uint32_t)Td, a.k0, a.k1, tb, fired, drawn);
+      __syncthreads();
+    }
     if (my >= 0) {
 #pragma unroll
       for (int p = 0; p < C; ++p) u[p] = s_heavy[my].u[p];
@@ -560,6 +809,12 @@ k_days(const SgTables tb, const DayArgs a) {
       code = finish_step<KIND>(Td, u, v, ld, tb, a, rep, node);
       if (code) bad_day = Td;
     }
+    if ((Td + 1 < a.T_end || a.finish_last) && a.out.prev) {
+      const int m = a.rec[Td - a.t0];
+      if (m >= 0)
+        prevalence_add<C>(a.out, in_range ? (long long)rep * a.M + m : -1, live && code == 0,
+                          u);
+    }
   }
   if (live) {
     if (code) report(a.err, code, rep, node, bad_day, bad_event);
@@ -568,6 +823,14 @@ k_days(const SgTables tb, const DayArgs a) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) a.v[gid * NV + q] = v[q];
     if (a.ev.e1_node_off) a.e1_cur[gid] = (int32_t)(ecur - ebase);
+    if constexpr (AEM) {
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        a.aem_a[j * total + gid] = ch_a[j];
+        a.aem_tau[j * total + gid] = ch_tau[j];
+        a.aem_cnt[j * total + gid] = ch_c[j];
+      }
+    }
   }
   // one atomic per warp for the counters
 #pragma unroll
@@ -577,7 +840,7 @@ k_days(const SgTables tb, const DayArgs a) {
     applied += __shfl_down_sync(0xffffffffu, applied, off);
   }
   if ((threadIdx.x & 31) == 0) {
-    if (drawn) {
+    if (drawn | fired) {
       atomicAdd(&a.cnt->reactions, fired);
       atomicAdd(&a.cnt->draws, drawn);
     }
@@ -786,14 +1049,14 @@ struct PtsSpArgs {
   const int32_t *rec;
   int32_t t0, M, n_rep, T;
   SgDevError *err;
+  OutDev out;
 };
 
-__global__ void __launch_bounds__(128) k_pts_sp(const SgTables tb, const PtsSpArgs a) {
-  pdl_trigger();
-  pdl_wait();
+// The coupled post time step of one (replicate, node) and its recording at
+// slot m; the node's counts are returned in uu.
+__device__ __forceinline__ void pts_sp_node(const SgTables &tb, const PtsSpArgs &a, long long gid,
+                                          int m, int *uu) {
   const int Nn = tb.n_nodes;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= (long long)Nn * a.n_rep) return;
   const int rep = (int)(gid / Nn), node = (int)(gid - (long long)rep * Nn);
   const int *ur = a.u + (long long)rep * Nn * 2;
   const double *vr = a.v_old + (long long)rep * Nn;
@@ -821,16 +1084,48 @@ __global__ void __launch_bounds__(128) k_pts_sp(const SgTables tb, const PtsSpAr
   const double nv = phi + ((shed + coupling) - beta * phi);
   a.v_new[gid] = nv;
   if (!isfinite(nv)) report(a.err, SG_ERR_PTS, rep, node, a.T, -1);
-  const int m = a.rec[a.T - a.t0];
+  uu[0] = S;
+  uu[1] = I;
   if (m >= 0) {
     const long long base = ((long long)rep * a.M + m) * Nn + node;
-    a.U[base * 2] = S;
-    a.U[base * 2 + 1] = I;
-    a.V[base] = nv;
+    if (a.U) {
+      a.U[base * 2] = S;
+      a.U[base * 2 + 1] = I;
+    }
+    if (a.V) a.V[base] = nv;
+    record_sparse<2, 1>(a.out, m, rep, node, uu, &nv);
   }
 }
 
-// U[r][0] = u0[r], V[r][0] = v0[r], working state = initial state.
+__global__ void __launch_bounds__(128) k_pts_sp(const SgTables tb, const PtsSpArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  const int Nn = tb.n_nodes;
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_range = gid < (long long)Nn * a.n_rep;
+  const int m = a.rec[a.T - a.t0];
+  int uu[2] = {0, 0};
+  if (in_range) pts_sp_node(tb, a, gid, m, uu);
+  if (m >= 0 && a.out.prev) {
+    const int rep = in_range ? (int)(gid / Nn) : 0;
+    prevalence_add<2>(a.out, in_range ? (long long)rep * a.M + m : -1, in_range, uu);
+  }
+}
+
+
+// Channels of the all events method before the first day: rate 0, asleep
+// (firing time +inf), no draws taken.
+__global__ void k_aem_init(double *a, double *tau, uint32_t *c, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    a[i] = 0.0;
+    tau[i] = __longlong_as_double(0x7ff0000000000000ll);
+    c[i] = 0u;
+  }
+}
+
+// U[r][0] = u0[r], V[r][0] = v0[r] (when recorded densely), working state =
+// initial state.
 __global__ void k_init(const int32_t *__restrict__ u0, const double *__restrict__ v0, int *u,
                        double *v, int32_t *U, double *V, long long per_rep_u,
                        long long per_rep_v, int M, int n_rep) {
@@ -841,15 +1136,40 @@ __global__ void k_init(const int32_t *__restrict__ u0, const double *__restrict_
       const long long r = i / per_rep_u, k = i - r * per_rep_u;
       const int32_t x = u0[i];
       u[i] = x;
-      U[r * M * per_rep_u + k] = x;
+      if (U) U[r * M * per_rep_u + k] = x;
     } else {
       const long long ii = i - nu;
       const long long r = ii / per_rep_v, k = ii - r * per_rep_v;
       const double x = v0[ii];
       v[ii] = x;
-      V[r * M * per_rep_v + k] = x;
+      if (V) V[r * M * per_rep_v + k] = x;
     }
   }
+}
+
+// U_sparse / V_sparse entries and prevalence counters of tspan slot 0 (the
+// initial state), one thread per (replicate, node).
+template <int C, int NV>
+__global__ void k_record0(const int32_t *__restrict__ u0, const double *__restrict__ v0, int Nn,
+                          int n_rep, int M, const OutDev o) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_range = gid < (long long)Nn * n_rep;
+  int u[C];
+  double v[NV > 0 ? NV : 1];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = 0;
+  v[0] = 0.0;
+  int rep = 0;
+  if (in_range) {
+    rep = (int)(gid / Nn);
+    const int node = (int)(gid - (long long)rep * Nn);
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = u0[gid * C + p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = v0[gid * NV + q];
+    record_sparse<C, NV>(o, 0, rep, node, u, v);
+  }
+  if (o.prev) prevalence_add<C>(o, in_range ? (long long)rep * M : -1, in_range, u);
 }
 
 __global__ void k_philox_batch(const uint32_t *ctr, uint32_t k0, uint32_t k1, uint32_t *out,
@@ -1014,6 +1334,17 @@ struct sg_model {
   DevBuf<double> nb_dist, v2;
   bool has_nb = false;
   uint64_t nb_version = 0;
+  // solver (SG_SOLVER_SSM or SG_SOLVER_AEM) and the channel state of 'aem'
+  int32_t solver = SG_SOLVER_SSM;
+  DevBuf<double> aem_a, aem_tau;
+  DevBuf<uint32_t> aem_cnt;
+  // output selection (sg_set_output)
+  bool out_dense = true;
+  int32_t out_cols = -1;  // tspan points the patterns were made for (-1: none)
+  OutDev out;
+  DevBuf<int64_t> out_u_colptr, out_v_colptr;
+  DevBuf<int32_t> out_u_row, out_v_row;
+  uint64_t out_version = 0;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -1117,6 +1448,9 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
   m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
   m->nb_ptr.release(); m->nb_idx.release(); m->nb_dist.release(); m->v2.release();
+  m->aem_a.release(); m->aem_tau.release(); m->aem_cnt.release();
+  m->out_u_colptr.release(); m->out_v_colptr.release();
+  m->out_u_row.release(); m->out_v_row.release();
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
@@ -1227,7 +1561,10 @@ template <int KIND>
 static void launch_days(sg_model *m, const DayArgs &a, cudaStream_t st) {
   const long long units = (long long)m->tb.n_nodes * a.n_rep;
   const unsigned grid = (unsigned)std::max<long long>(1, (units + a.npb - 1) / a.npb);
-  launch_pdl(k_days<KIND>, grid, kDayBlock, 0, st, m->tb, a);
+  if (a.aem_tau)
+    launch_pdl(k_days<KIND, true>, grid, kDayBlock, 0, st, m->tb, a);
+  else
+    launch_pdl(k_days<KIND, false>, grid, kDayBlock, 0, st, m->tb, a);
 }
 
 static void launch_days_kind(sg_model *m, const DayArgs &a, cudaStream_t st) {
@@ -1328,9 +1665,29 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
     const unsigned g = (unsigned)std::min<long long>(4096, (nthreads + 255) / 256);
     k_init<<<std::max(1u, g), 256, 0, st>>>(d_u0, NV ? d_v0 : nullptr, m->u.p,
-                                            NV ? m->v.p : nullptr, d_U, NV ? d_V : nullptr,
+                                            NV ? m->v.p : nullptr, da0.U, NV ? da0.V : nullptr,
                                             per_rep_u, per_rep_v, n_tspan, n_rep);
     ++launches;
+    if (da0.out.prev)
+      cudaMemsetAsync(da0.out.prev, 0, sizeof(unsigned long long) * 4 * (size_t)n_rep * n_tspan,
+                      st);
+    if (da0.out.prev || da0.out.u_nnz > 0 || da0.out.v_nnz > 0) {
+      const long long units = (long long)Nn * n_rep;
+      const unsigned g0 = (unsigned)((units + 255) / 256);
+      switch (tb.kind) {
+        case SG_SIR: k_record0<3, 0><<<g0, 256, 0, st>>>(d_u0, d_v0, Nn, n_rep, n_tspan, da0.out); break;
+        case SG_SIS: k_record0<2, 0><<<g0, 256, 0, st>>>(d_u0, d_v0, Nn, n_rep, n_tspan, da0.out); break;
+        case SG_SISE3: k_record0<6, 1><<<g0, 256, 0, st>>>(d_u0, d_v0, Nn, n_rep, n_tspan, da0.out); break;
+        default: k_record0<2, 1><<<g0, 256, 0, st>>>(d_u0, d_v0, Nn, n_rep, n_tspan, da0.out); break;
+      }
+      ++launches;
+    }
+    if (da0.aem_tau) {
+      const long long n = (long long)Nn * n_rep * tb.n_trans;
+      const unsigned ga = (unsigned)std::min<long long>(4096, (n + 255) / 256);
+      k_aem_init<<<std::max(1u, ga), 256, 0, st>>>(da0.aem_a, da0.aem_tau, da0.aem_cnt, n);
+      ++launches;
+    }
   }
   DayArgs da = da0;
   EvArgs ea = ea0;
@@ -1345,8 +1702,9 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     pa.nb_ptr = m->has_nb ? m->nb_ptr.p : nullptr;
     pa.nb_idx = m->nb_idx.p;
     pa.nb_dist = m->nb_dist.p;
-    pa.U = d_U;
-    pa.V = d_V;
+    pa.U = da0.U;
+    pa.V = da0.V;
+    pa.out = da0.out;
     pa.rec = m->rec.p;
     pa.t0 = t0;
     pa.M = n_tspan;
@@ -1535,7 +1893,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     if (tspan[i] <= tspan[i - 1]) return SG_ERR_ARG;
   const SgTables &tb = m->tb;
   const int C = tb.n_comp, NV = tb.n_v, Nn = tb.n_nodes;
-  if (Nn > 0 && (!d_u0 || !d_U || (NV > 0 && (!d_v0 || !d_V)))) return SG_ERR_ARG;
+  if (Nn > 0 && (!d_u0 || (NV > 0 && !d_v0))) return SG_ERR_ARG;
+  if (Nn > 0 && m->out_dense && (!d_U || (NV > 0 && !d_V))) return SG_ERR_ARG;
+  if (m->out_cols >= 0 && m->out_cols != n_tspan) return SG_ERR_ARG;
   if (m->ev.per_rep && m->ev.max_rep >= n_rep) {
     fill_error(err, SG_ERR_ARG, m->ev.max_rep, -1, -1, -1);
     return SG_ERR_ARG;
@@ -1556,6 +1916,14 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     return rc;
   if (tb.kind == SG_SISE_SP && (rc = m->v2.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))))
     return rc;
+  const bool aem = m->solver == SG_SOLVER_AEM;
+  if (aem && m->emu_on) return SG_ERR_ARG;  // the emulator replaces direct-method days only
+  if (aem) {
+    const size_t nch = (size_t)std::max<long long>(1, (long long)Nn * n_rep * tb.n_trans);
+    if ((rc = m->aem_a.ensure(nch)) || (rc = m->aem_tau.ensure(nch)) ||
+        (rc = m->aem_cnt.ensure(nch)))
+      return rc;
+  }
   if (m->emu_on) {
     const size_t units = (size_t)Nn * n_rep;
     if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
@@ -1602,6 +1970,14 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.cnt = m->cnt.p;
   da.T_begin = da.T_end = da.finish_first = da.finish_last = 0;
   da.emu = nullptr;
+  if (!m->out_dense) {
+    da.U = nullptr;
+    da.V = nullptr;
+  }
+  da.out = m->out;
+  da.aem_a = aem ? m->aem_a.p : nullptr;
+  da.aem_tau = aem ? m->aem_tau.p : nullptr;
+  da.aem_cnt = aem ? m->aem_cnt.p : nullptr;
 
   EvArgs ea;
   ea.ev = evd;
@@ -1639,7 +2015,12 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                      da.heavy_after,
                      (m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)) *
                              1000033ull +
-                         m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p};
+                         m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p +
+                         m->out_version * 0x100000001b3ull +
+                         (aem ? 0x9e3779b97f4a7c15ull ^ (uint64_t)(uintptr_t)m->aem_tau.p ^
+                                    ((uint64_t)(uintptr_t)m->aem_a.p << 1) ^
+                                    ((uint64_t)(uintptr_t)m->aem_cnt.p << 2)
+                              : 0)};
   if (use_graph) {
     if (!(m->graph_ok && m->graph_key == key)) {
       if (m->graph_exec) {
@@ -1727,10 +2108,12 @@ extern "C" int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
   const size_t nu = (size_t)n_rep * tb.n_nodes * tb.n_comp;
   const size_t nv = (size_t)n_rep * tb.n_nodes * tb.n_v;
   const size_t M = (size_t)n_tspan;
-  if (tb.n_nodes > 0 && (!u0 || !U || (tb.n_v > 0 && (!v0 || !V)))) return SG_ERR_ARG;
+  const bool dense = m->out_dense;
+  if (tb.n_nodes > 0 && (!u0 || (tb.n_v > 0 && !v0))) return SG_ERR_ARG;
+  if (tb.n_nodes > 0 && dense && (!U || (tb.n_v > 0 && !V))) return SG_ERR_ARG;
   int rc;
-  if ((rc = m->hu0.ensure(nu)) || (rc = m->hU.ensure(nu * M)) ||
-      (rc = m->hv0.ensure(std::max<size_t>(1, nv))) || (rc = m->hV.ensure(std::max<size_t>(1, nv * M))))
+  if ((rc = m->hu0.ensure(nu)) || (rc = m->hv0.ensure(std::max<size_t>(1, nv))) ||
+      (dense && ((rc = m->hU.ensure(nu * M)) || (rc = m->hV.ensure(std::max<size_t>(1, nv * M))))))
     return rc;
   cudaStream_t st = (cudaStream_t)stream;
   if ((nu && cudaMemcpyAsync(m->hu0.p, u0, nu * sizeof(int32_t), cudaMemcpyHostToDevice, st) !=
@@ -1740,13 +2123,15 @@ extern "C" int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
     cudaGetLastError();
     return SG_ERR_CUDA;
   }
-  rc = sg_run(m, tspan, n_tspan, seed, n_rep, m->hu0.p, nv ? m->hv0.p : nullptr, m->hU.p,
-              nv ? m->hV.p : nullptr, stream, stats, err);
+  rc = sg_run(m, tspan, n_tspan, seed, n_rep, m->hu0.p, nv ? m->hv0.p : nullptr,
+              dense ? m->hU.p : nullptr, dense && nv ? m->hV.p : nullptr, stream, stats, err);
   if (rc) return rc;
-  if ((nu && cudaMemcpyAsync(U, m->hU.p, nu * M * sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             st) != cudaSuccess) ||
-      (nv && cudaMemcpyAsync(V, m->hV.p, nv * M * sizeof(double), cudaMemcpyDeviceToHost, st) !=
-                 cudaSuccess) ||
+  if ((dense && nu &&
+       cudaMemcpyAsync(U, m->hU.p, nu * M * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess) ||
+      (dense && nv &&
+       cudaMemcpyAsync(V, m->hV.p, nv * M * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+           cudaSuccess) ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
     return SG_ERR_CUDA;
@@ -1995,13 +2380,15 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.k1 = (uint32_t)(seed >> 32);
       da.err = d_err;
       da.cnt = d_cnt;
+      da.aem_a = da.aem_tau = nullptr;
+      da.aem_cnt = nullptr;
       const long long units = (long long)Nn * n_rep;
       const unsigned grid = (unsigned)std::max<long long>(1, (units + da.npb - 1) / da.npb);
       switch (k) {
-        case SG_SIR: k_days<SG_SIR><<<grid, kDayBlock, 0, st>>>(tb, da); break;
-        case SG_SIS: k_days<SG_SIS><<<grid, kDayBlock, 0, st>>>(tb, da); break;
-        case SG_SISE: k_days<SG_SISE><<<grid, kDayBlock, 0, st>>>(tb, da); break;
-        default: k_days<SG_SISE3><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        case SG_SIR: k_days<SG_SIR, false><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        case SG_SIS: k_days<SG_SIS, false><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        case SG_SISE: k_days<SG_SISE, false><<<grid, kDayBlock, 0, st>>>(tb, da); break;
+        default: k_days<SG_SISE3, false><<<grid, kDayBlock, 0, st>>>(tb, da); break;
       }
       ++launches;
     }
@@ -2088,6 +2475,84 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
   if (npb_out) *npb_out = best_npb;
   if (heavy_after_out) *heavy_after_out = best_heavy;
   if (ms_out) *ms_out = best;
+  return SG_OK;
+}
+
+// Checks one compressed-column pattern (see sg_output) and uploads it.
+static int upload_pattern(int32_t cols, int64_t nnz, const int64_t *colptr, const int32_t *row,
+                          long long rows, DevBuf<int64_t> &dptr, DevBuf<int32_t> &drow) {
+  if (nnz < 0 || (nnz > 0 && (!colptr || !row))) return SG_ERR_ARG;
+  if (nnz == 0 && !colptr) return SG_OK;
+  if (colptr[0] != 0 || colptr[cols] != nnz) return SG_ERR_ARG;
+  for (int32_t c = 0; c < cols; ++c) {
+    if (colptr[c + 1] < colptr[c]) return SG_ERR_ARG;
+    for (int64_t e = colptr[c]; e < colptr[c + 1]; ++e) {
+      if (row[e] < 0 || row[e] >= rows) return SG_ERR_ARG;
+      if (e > colptr[c] && row[e] <= row[e - 1]) return SG_ERR_ARG;
+    }
+  }
+  std::vector<int64_t> p(colptr, colptr + cols + 1);
+  std::vector<int32_t> r(row, row + nnz);
+  int rc = upload(dptr, p);
+  if (!rc && nnz > 0) rc = upload(drow, r);
+  return rc;
+}
+
+extern "C" int sg_set_output(sg_model *m, const sg_output *o) {
+  if (!m) return SG_ERR_ARG;
+  m->graph_ok = false;
+  ++m->out_version;
+  m->out = OutDev{};
+  m->out_dense = true;
+  m->out_cols = -1;
+  if (!o) return SG_OK;
+  const SgTables &tb = m->tb;
+  const uint32_t all = tb.n_comp >= 32 ? 0xffffffffu : ((1u << tb.n_comp) - 1u);
+  const bool sparse = o->u_nnz > 0 || o->v_nnz > 0;
+  const bool prev = o->prev_cases != 0 || o->prev_at_risk != 0;
+  if ((o->dense != 0 && o->dense != 1) || (o->prev_cases & ~all) || (o->prev_at_risk & ~all) ||
+      (prev && (!o->prev_cases || !o->prev_at_risk || !o->d_prev)) ||
+      ((sparse || prev) && o->n_tspan < 1) || (o->u_nnz > 0 && !o->d_u_val) ||
+      (o->v_nnz > 0 && (!o->d_v_val || tb.n_v == 0)))
+    return SG_ERR_ARG;
+  int rc = SG_OK;
+  if (o->u_nnz > 0)
+    rc = upload_pattern(o->n_tspan, o->u_nnz, o->u_colptr, o->u_row,
+                        (long long)tb.n_nodes * tb.n_comp, m->out_u_colptr, m->out_u_row);
+  if (!rc && o->v_nnz > 0)
+    rc = upload_pattern(o->n_tspan, o->v_nnz, o->v_colptr, o->v_row,
+                        (long long)tb.n_nodes * tb.n_v, m->out_v_colptr, m->out_v_row);
+  if (rc) return rc;
+  OutDev d;
+  if (o->u_nnz > 0) {
+    d.u_colptr = m->out_u_colptr.p;
+    d.u_row = m->out_u_row.p;
+    d.u_val = o->d_u_val;
+    d.u_nnz = o->u_nnz;
+  }
+  if (o->v_nnz > 0) {
+    d.v_colptr = m->out_v_colptr.p;
+    d.v_row = m->out_v_row.p;
+    d.v_val = o->d_v_val;
+    d.v_nnz = o->v_nnz;
+  }
+  if (prev) {
+    d.cases = o->prev_cases;
+    d.at_risk = o->prev_at_risk;
+    d.prev = reinterpret_cast<unsigned long long *>(o->d_prev);
+  }
+  m->out = d;
+  m->out_dense = o->dense != 0;
+  m->out_cols = (sparse || prev) ? o->n_tspan : -1;
+  return SG_OK;
+}
+
+extern "C" int sg_set_solver(sg_model *m, int32_t solver) {
+  if (!m || (solver != SG_SOLVER_SSM && solver != SG_SOLVER_AEM)) return SG_ERR_ARG;
+  if (solver != m->solver) {
+    m->solver = solver;
+    m->graph_ok = false;
+  }
   return SG_OK;
 }
 
