@@ -67,6 +67,7 @@ class _Model(ctypes.Structure):
         ("gdata", ctypes.c_void_p), ("nb_ptr", ctypes.c_void_p),
         ("nb_idx", ctypes.c_void_p), ("nb_dist", ctypes.c_void_p),
         ("solver", ctypes.c_int),
+        ("rate_fn", ctypes.c_void_p),
     ]
 
 
@@ -181,6 +182,17 @@ def apply_event(E, N, etype, u_node, u_dest=None, n=0, proportion=0.0,
     return rc, un, ud
 
 
+def _generic(w):
+    """For a model given by transition strings (kind 5): the oracle's own
+    parse (S, G) and the address of its compiled propensity function."""
+    g = getattr(w, "generic", None)
+    if g is None:
+        return None
+    from . import mparse
+    c = mparse.compiled(g)
+    return c.parsed.S, c.parsed.G, c.address
+
+
 def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
     """Run the oracle on a workload description (see
     ``paper_1605_01421_gb300.workloads.Workload``).
@@ -196,11 +208,13 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
     n_rep = w.n_rep if n_rep is None else n_rep
     u0 = _i32(w.u0 if u0 is None else u0)
     v0 = _f64(w.v0 if v0 is None else v0)
-    S, G = _colmajor_i32(w.S), _colmajor_i32(w.G)
+    gen = _generic(w)
+    S0, G0 = (gen[0], gen[1]) if gen else (w.S, w.G)
+    S, G = _colmajor_i32(S0), _colmajor_i32(G0)
     E, N = _colmajor_i32(w.E), _colmajor_i32(w.N)
     ldata = _f64(np.asarray(w.ldata, dtype=np.float64).ravel(order="F"))
     gdata = _f64(w.gdata)
-    n_comp, n_trans = w.S.shape
+    n_comp, n_trans = S0.shape
     n_nodes = u0.shape[1]
     nb = getattr(w, "neighbors", None)
     if nb is not None:
@@ -217,7 +231,8 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
                _ptr(nb_ptr) if nb_ptr is not None else None,
                _ptr(nb_idx) if nb_idx is not None and nb_idx.size else None,
                _ptr(nb_dist) if nb_dist is not None and nb_dist.size else None,
-               int(getattr(w, "solver", 0) if solver is None else solver))
+               int(getattr(w, "solver", 0) if solver is None else solver),
+               gen[2] if gen else None)
     ev = w.events
     keep = []
     if ev is not None and len(ev["event"]) > 0:

@@ -248,11 +248,12 @@ static double seasonal_beta(int t, const double *ldata, const double *beta4)
 }
 
 /* rate j of the model for a node with counts u, continuous state v */
-static double model_rate(int kind, int j, const int *u, const double *v,
-                         const double *ldata, const double *gdata)
+static double model_rate(const oracle_model *m, int j, const int *u,
+                         const double *v, const double *ldata,
+                         const double *gdata)
 {
     (void)ldata;
-    switch (kind) {
+    switch (m->kind) {
     case ORACLE_SIR: {
         /* Appendix C: S_n, I_n as doubles, n = S_n + I_n + R, then
          * (beta * S_n * I_n) / n when n > 0; recovery gamma * I. */
@@ -282,6 +283,11 @@ static double model_rate(int kind, int j, const int *u, const double *v,
         if ((j & 1) == 0) return gdata[a] * v[0] * (double)u[2 * a];
         return gdata[3 + a] * (double)u[2 * a + 1];
     }
+    case ORACLE_GENERIC:
+        /* a model from transition strings (Sec. 3.5, mparse): the
+         * propensity functions are C code generated from the strings and
+         * compiled separately */
+        return m->rate_fn(j, u, gdata);
     default:
         return 0.0;
     }
@@ -488,11 +494,17 @@ static int validate(const oracle_model *m, const oracle_events *ev,
     static const int nv[5] = {0, 0, 1, 1, 1};
     static const int ngd[5] = {2, 2, 7, 11, 8};
     static const int nld[5] = {0, 0, 4, 4, 4};
-    if (m->kind < 0 || m->kind > 4 || m->n_nodes < 0 || n_rep < 1
-        || n_tspan < 1 || m->n_comp != ncomp[m->kind]
-        || m->n_trans != ntrans[m->kind] || m->n_v != nv[m->kind]
-        || m->n_gdata < ngd[m->kind] || m->n_ldata < nld[m->kind]
-        || m->n_comp > ORACLE_MAX_COMP) {
+    const int generic = m->kind == ORACLE_GENERIC;
+    if (m->kind < 0 || m->kind > ORACLE_GENERIC || m->n_nodes < 0 || n_rep < 1
+        || n_tspan < 1 || m->n_comp > ORACLE_MAX_COMP
+        || m->n_trans > ORACLE_MAX_TRANS
+        || (generic && (!m->rate_fn || m->n_v != 0 || m->n_comp < 1
+                        || m->n_trans < 1 || m->n_gdata < 0))
+        || (!generic && (m->n_comp != ncomp[m->kind]
+                         || m->n_trans != ntrans[m->kind]
+                         || m->n_v != nv[m->kind]
+                         || m->n_gdata < ngd[m->kind]
+                         || m->n_ldata < nld[m->kind]))) {
         set_error(err, ORACLE_ERR_ARG, -1, -1, -1, -1);
         return ORACLE_ERR_ARG;
     }
@@ -584,7 +596,7 @@ static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
     /* Reading: all rates are computed at the start of every day, so that
      * changes made by events and the post time step are always seen. */
     for (j = 0; j < m->n_trans; j++) {
-        w[j] = model_rate(m->kind, j, u, v, ld, m->gdata);
+        w[j] = model_rate(m, j, u, v, ld, m->gdata);
         if (!(w[j] >= 0.0) || isinf(w[j])) return ORACLE_ERR_RATE;
     }
 
@@ -624,7 +636,7 @@ static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
             u[k] += m->S[(size_t)n * (size_t)m->n_comp + (size_t)k];
         for (k = 0; k < m->n_trans; k++) {
             if (m->G[(size_t)n * (size_t)m->n_trans + (size_t)k] == 0) continue;
-            w[k] = model_rate(m->kind, k, u, v, ld, m->gdata);
+            w[k] = model_rate(m, k, u, v, ld, m->gdata);
             if (!(w[k] >= 0.0) || isinf(w[k])) return ORACLE_ERR_RATE;
         }
         *reactions += 1;
@@ -701,7 +713,7 @@ static int aem_node_day(const oracle_model *m, int node, int rep, int T,
     int j, k, rc;
 
     for (j = 0; j < m->n_trans; j++) {
-        double w = model_rate(m->kind, j, u, v, ld, m->gdata);
+        double w = model_rate(m, j, u, v, ld, m->gdata);
         if (!(w >= 0.0) || isinf(w)) return ORACLE_ERR_RATE;
         rc = aem_update(seed, node, j, rep, t, w, a, tau, cnt);
         if (rc) return rc;
@@ -732,7 +744,7 @@ static int aem_node_day(const oracle_model *m, int node, int rep, int T,
                 continue;
             w = a[k];
             if (m->G[(size_t)mu * (size_t)m->n_trans + (size_t)k] != 0) {
-                w = model_rate(m->kind, k, u, v, ld, m->gdata);
+                w = model_rate(m, k, u, v, ld, m->gdata);
                 if (!(w >= 0.0) || isinf(w)) return ORACLE_ERR_RATE;
             }
             if (k == mu) {

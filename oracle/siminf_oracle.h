@@ -27,7 +27,8 @@ enum {
     ORACLE_SIS = 1,
     ORACLE_SISE = 2,
     ORACLE_SISE3 = 3,
-    ORACLE_SISE_SP = 4
+    ORACLE_SISE_SP = 4,
+    ORACLE_GENERIC = 5
 };
 enum {
     ORACLE_EV_EXIT = 0,
@@ -73,6 +74,9 @@ typedef struct {
     const double *nb_dist;
     /* ORACLE_SOLVER_SSM (direct SSA per day) or ORACLE_SOLVER_AEM */
     int solver;
+    /* ORACLE_GENERIC: propensity of transition j for counts u and global
+     * data gdata (generated from transition strings, compiled separately) */
+    double (*rate_fn)(int j, const int *u, const double *gdata);
 } oracle_model;
 
 typedef struct {

@@ -24,11 +24,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-SIR, SIS, SISE, SISE3, SISE_SP = 0, 1, 2, 3, 4
+SIR, SIS, SISE, SISE3, SISE_SP, GENERIC = 0, 1, 2, 3, 4, 5
 # solvers (Sec. 3.4.2): split-step direct SSA, all events method
 SSM, AEM = 0, 1
 EXIT, ENTER, INTERNAL, EXTERNAL = 0, 1, 2, 3
-KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3", SISE_SP: "SISe_sp"}
+KIND_NAMES = {SIR: "SIR", SIS: "SIS", SISE: "SISe", SISE3: "SISe3", SISE_SP: "SISe_sp",
+              GENERIC: "mparse"}
 
 
 @dataclass
@@ -53,6 +54,10 @@ class Workload:
     neighbors: tuple | None = None
     # solver: SSM (direct SSA per day) or AEM (all events method)
     solver: int = 0
+    # GENERIC: the model as transition strings (Sec. 3.5): a dict with
+    # "transitions", "compartments", "gdata_names"; S and G are then None
+    # (each side derives them from the strings)
+    generic: dict | None = None
 
     @property
     def n_nodes(self) -> int:
@@ -60,6 +65,8 @@ class Workload:
 
     @property
     def n_comp(self) -> int:
+        if self.generic is not None:
+            return len(self.generic["compartments"])
         return int(self.S.shape[0])
 
     @property
@@ -204,6 +211,100 @@ def plain_model(kind, u0, tspan, gdata, seed=42, n_rep=1, events=None,
                     int(seed), int(n_rep))
 
 
+def parsed_model(transitions, compartments, gdata, u0, tspan, seed=42, n_rep=1,
+                 events=None, E=None, N=None, name="mparse model"):
+    """A model given as transition strings "LHS -> propensity -> RHS" (Sec.
+    3.5); gdata is an ordered mapping name -> value.  S and G are left to the
+    parsers of the two sides."""
+    comps = list(compartments)
+    C = len(comps)
+    u0 = np.asarray(u0, dtype=np.int32)
+    if u0.ndim == 2:
+        u0 = _tile_rep(u0, n_rep)
+    n_nodes = u0.shape[1]
+    E = np.zeros((C, 0), np.int32) if E is None else np.asarray(E, np.int32)
+    N = np.zeros((C, 0), np.int32) if N is None else np.asarray(N, np.int32)
+    return Workload(name, GENERIC, None, None, E, N,
+                    np.array(list(gdata.values()), dtype=np.float64),
+                    np.zeros((0, n_nodes), dtype=np.float64), 0, u0,
+                    np.zeros((u0.shape[0], n_nodes, 0), dtype=np.float64),
+                    np.asarray(tspan, dtype=np.int32),
+                    events if events is not None else empty_events(), int(seed),
+                    int(u0.shape[0]),
+                    generic={"transitions": list(transitions), "compartments": comps,
+                             "gdata_names": list(gdata.keys())})
+
+
+# The model-parser examples of Sec. 3.5 (transition strings as printed).
+MPARSE_SIR = ["S -> b*S*I/(S+I+R) -> I", "I -> g*I -> R"]
+MPARSE_SIR_ICUM = ["S -> b*S*I/(S+I+R) -> I + Icum", "I -> g*I -> R"]
+MPARSE_PREDATOR_PREY = ["@ -> bR*R -> R", "R -> (dR+(bR-dR)*R/K)*R -> @",
+                        "R -> alpha/(1+w*R)*R*F -> @", "@ -> bF*alpha/(1+w*R)*R*F -> F",
+                        "F -> dF*F -> @"]
+PREDATOR_PREY_GDATA = {"bR": 2.0, "bF": 2.0, "dR": 1.0, "K": 1000.0, "alpha": 0.007,
+                       "w": 0.0035, "dF": 2.0}
+
+
+def config_predator_prey(n_nodes=1000, days=99, seed=123, n_rep=1):
+    """The Rosenzweig-MacArthur predator-prey model of Sec. 3.5 from its
+    transition strings: R = 1000 prey and F = 100 predators in every node,
+    tspan 1..days+1, the paper's parameters."""
+    u0 = np.tile(np.array([[1000, 100]], dtype=np.int32), (n_nodes, 1))
+    return parsed_model(MPARSE_PREDATOR_PREY, ["R", "F"], PREDATOR_PREY_GDATA, u0,
+                        np.arange(1, days + 2), seed=seed, n_rep=n_rep,
+                        name=f"PredatorPrey {n_nodes} nodes x {days} days")
+
+
+def config_sir_icum(n_nodes=1000, days=149, seed=123):
+    """SIR with the incidence counter Icum (Sec. 3.5): S=99 I=1 Icum=0 R=0,
+    b = 0.16, g = 0.077, tspan 1..days+1."""
+    u0 = np.tile(np.array([[99, 1, 0, 0]], dtype=np.int32), (n_nodes, 1))
+    return parsed_model(MPARSE_SIR_ICUM, ["S", "I", "Icum", "R"], {"b": 0.16, "g": 0.077},
+                        u0, np.arange(1, days + 2), seed=seed,
+                        name=f"SIR+Icum {n_nodes} nodes x {days} days")
+
+
+def config_vaccination(n_nodes=1600, days=300, gen_seed=1005, seed=42, vaccinate=True,
+                       events_per_node_day=0.41, n_seeded=16):
+    """The vaccination example of Sec. 3.5 on a synthetic stand-in for its
+    1,600 cattle herds: compartments S, I, Icum, R, V, the printed E and N
+    (enter -> S; exit and external transfer sample S, I, R, V; vaccination
+    samples S, I, R and shifts them to V), synthetic births, deaths and
+    movements, one infected animal in each of `n_seeded` herds (the paper
+    introduces one and averages 1,000 runs), and vaccination of 80% of the
+    animals in herds 1-50 on day 21, 51-100 on day 22, ... (internal transfer,
+    select 3, shift 1 in the paper's 1-based numbering)."""
+    rng = np.random.default_rng(gen_seed)
+    herd = lognormal_herds(rng, n_nodes, 50, 1.0, 2, 5000)
+    S = herd.copy()
+    I = np.zeros(n_nodes, dtype=np.int64)
+    j = rng.choice(n_nodes, size=n_seeded, replace=False)
+    S[j] -= 1
+    I[j] = 1
+    u0 = np.stack([S, I, np.zeros_like(S), np.zeros_like(S), np.zeros_like(S)],
+                  axis=1).astype(np.int32)
+    E = np.array([[1, 1, 1], [0, 1, 1], [0, 0, 0], [0, 1, 1], [0, 1, 0]], dtype=np.int32)
+    N = np.array([[4], [3], [0], [1], [0]], dtype=np.int32)
+    net = powerlaw_network(rng, n_nodes)
+    totals = herd[:, None].copy()
+    # herds never empty: the printed propensity divides by S + I + R + V
+    ev = _cattle_events(rng, totals, days, 0, events_per_node_day,
+                        (1 / 3, 1 / 3, 0.0, 1 / 3), 1, net, enter_sel=0,
+                        exit_sel=[1], ages_shift=None, keep=1)
+    if vaccinate:
+        t = np.repeat(np.arange(21, 21 + (n_nodes + 49) // 50), 50)[:n_nodes]
+        rows = [(2, int(t[i]), i, 0, 0, 0.8, 2, 0) for i in range(n_nodes) if t[i] <= days]
+        vac = make_events(rows)
+        ev = {k: (np.concatenate([ev[k], vac[k]]) if k != "rep" else None) for k in ev}
+    trans = ["S -> b*S*I/(S+I+R+V) -> I + Icum", "I -> g*I -> R"]
+    w = parsed_model(trans, ["S", "I", "Icum", "R", "V"], {"b": 0.16, "g": 0.077}, u0,
+                     np.arange(0, days + 1), seed=seed, events=ev, E=E, N=N,
+                     name=f"SIR+Icum+V {n_nodes} nodes x {days} days"
+                          + (" with vaccination" if vaccinate else ""))
+    w.meta = {"gen_seed": gen_seed}
+    return w
+
+
 # --------------------------------------------------------------------------
 # Synthetic cattle-shaped populations and event streams.
 # --------------------------------------------------------------------------
@@ -253,8 +354,9 @@ def _geometric3(rng, size):
 
 
 def _cattle_events(rng, totals, n_days, t0, rate, mix, n_ages, net, enter_sel,
-                   exit_sel, ages_shift):
-    """Daily events with exact tracking of per-age totals.
+                   exit_sel, ages_shift, keep=0):
+    """Daily events with exact tracking of per-age totals.  Exits and
+    external transfers leave at least `keep` individuals in each group.
 
     totals: (n_nodes, n_ages) int64, modified in place.
     mix: fractions (exit, enter, internal, external).
@@ -284,7 +386,7 @@ def _cattle_events(rng, totals, n_days, t0, rate, mix, n_ages, net, enter_sel,
             cs = np.cumsum(w_s)
             base = np.r_[0, cs][np.flatnonzero(starts)][grp]
             cum = cs - base
-            avail = totals.reshape(-1)[k_s]
+            avail = np.maximum(totals.reshape(-1)[k_s] - keep, 0)
             capped = np.minimum(cum, avail)
             got = capped - np.r_[0, capped[:-1]]
             got[starts] = capped[starts]
@@ -320,7 +422,7 @@ def _cattle_events(rng, totals, n_days, t0, rate, mix, n_ages, net, enter_sel,
                                    want.tolist(), ages.tolist()):
                 nb = adj[ptr[s]:ptr[s + 1]]
                 dst = int(nb[int(pk * len(nb))])
-                avail = int(totals[s, a])
+                avail = int(totals[s, a]) - keep
                 w = min(w, avail)
                 if w <= 0:
                     continue
