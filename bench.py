@@ -72,6 +72,15 @@ def _base_workload(name):
         return W.config_batched()
     if name == "sise_sp":
         return W.config_sise_sp()
+    if name == "predator_prey":
+        # the paper's parsed-model example (Sec. 3.5), 1,000 nodes x 100 days;
+        # thousands of transitions per node-day, so the oracle's sample is
+        # sized by this relative cost per node-day
+        w = W.config_predator_prey()
+        w.meta = {"oracle_cost": 400}
+        return w
+    if name == "vaccination":
+        return W.config_vaccination()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -169,7 +178,7 @@ def time_oracle(w, budget_s=10.0, max_runs=50):
     ~budget_s (at least once); node-days/s and reactions/s."""
     import oracle
     oracle.build()
-    w, desc = _oracle_sample(w, max_node_days=1.5e6 * budget_s)
+    w, desc = _oracle_sample(w, max_node_days=1.5e6 * budget_s / w.meta.get("oracle_cost", 1))
     node_days = w.n_nodes * w.n_days * w.n_rep
     runs, t_total, reactions = 0, 0.0, 0
     while runs < max_runs and (runs == 0 or t_total < budget_s):
@@ -192,7 +201,7 @@ def bench_reference(args):
     if rank != 0:
         return
     w_full = _workload(args.workload, args.solver)
-    w, desc = _oracle_sample(w_full, max_node_days=3e6)
+    w, desc = _oracle_sample(w_full, max_node_days=3e6 / w_full.meta.get("oracle_cost", 1))
     node_days = w.n_nodes * w.n_days * w.n_rep
     import oracle
     oracle.build()
@@ -505,7 +514,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="sise",
-                    choices=["sise", "sir", "sise3", "batched", "emulator", "sise_sp"])
+                    choices=["sise", "sir", "sise3", "batched", "emulator", "sise_sp",
+                             "predator_prey", "vaccination"])
     ap.add_argument("--emu-batches", type=int, default=50)
     ap.add_argument("--emu-steps", type=int, default=4000)
     ap.add_argument("--emu-nodes", type=int, default=37000)

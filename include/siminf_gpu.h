@@ -65,7 +65,8 @@ typedef enum {
   SG_SIS = 1,
   SG_SISE = 2,
   SG_SISE3 = 3,
-  SG_SISE_SP = 4
+  SG_SISE_SP = 4,
+  SG_GENERIC = 5 /* from transition strings, sg_model_create_parsed */
 } sg_model_kind;
 
 /* Solvers of Sec. 3.4.2.  Both process the scheduled events and the post
@@ -107,8 +108,10 @@ enum {
   SG_ERR_NOMEM = -8,           /* host or device allocation failed         */
   SG_ERR_STEP_LIMIT = -9,      /* a node needed more than SG_MAX_DRAWS draws
                                   in one unit step (rates far too large)    */
-  SG_ERR_TOO_LARGE = -10       /* the problem does not fit the fixed scratch
+  SG_ERR_TOO_LARGE = -10,      /* the problem does not fit the fixed scratch
                                   of sg_run_noalloc                         */
+  SG_ERR_PARSE = -11,          /* a transition string does not parse       */
+  SG_ERR_JIT = -12             /* run-time compilation or loading failed   */
 };
 
 /* Draws one node may take in one unit step before the run stops with
@@ -168,6 +171,34 @@ typedef struct {
  * the kind, copies every table to the device and returns the handle in
  * *out.  Errors: SG_ERR_ARG, SG_ERR_NOMEM, SG_ERR_CUDA. */
 int sg_model_create(const sg_desc *desc, sg_model **out);
+
+/* Create a model from transition strings (Sec. 3.5, the model parser):
+ * transitions[j] = "LHS -> propensity -> RHS", LHS / RHS "@" (the empty
+ * set) or compartment names joined by "+" (optionally "k*name"); the
+ * propensity is an expression over compartment names (the node's counts),
+ * the names in gdata_names (values gdata), decimal numbers, + - * /, unary
+ * minus and parentheses; * and / bind tighter than + and -, all group left
+ * to right, and each operation is one IEEE double operation.  The parser
+ * builds S (S[p, j] = count of p on the RHS minus on the LHS) and G (G[k, j]
+ * = 1 when propensity k reads a compartment transition j changes); the
+ * propensities become CUDA code, compiled at run time with NVRTC for sm_103a
+ * together with the engine's day and event kernels, and loaded on the
+ * current device (the model must then run on that device).  E (n_comp x
+ * n_select) and N (n_comp x n_shift) are the event tables of Sec. 3.3,
+ * column-major.  The model has no continuous state and no local data.
+ * Host arrays are copied.  msg (msg_len bytes, may be NULL) receives the
+ * parse or compiler message.  Errors: SG_ERR_ARG, SG_ERR_PARSE, SG_ERR_JIT,
+ * SG_ERR_NOMEM, SG_ERR_CUDA. */
+int sg_model_create_parsed(const char *const *transitions, int32_t n_trans,
+                           const char *const *compartments, int32_t n_comp,
+                           const char *const *gdata_names, const double *gdata,
+                           int32_t n_gdata, int32_t n_nodes, const int32_t *E,
+                           int32_t n_select, const int32_t *N, int32_t n_shift,
+                           sg_model **out, char *msg, int32_t msg_len);
+
+/* The model's S (n_comp x n_trans) and G (n_trans x n_trans) as the engine
+ * uses them, column-major, into caller arrays (either may be NULL). */
+int sg_model_tables(const sg_model *m, int32_t *S, int32_t *G);
 
 /* SG_SISE_SP neighbour lists (the distance matrix of Sec. 4.2 within a
  * cutoff), compressed rows: node i's neighbours are idx[ptr[i] .. ptr[i+1])

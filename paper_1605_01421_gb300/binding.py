@@ -22,12 +22,32 @@ _INCLUDE = os.path.join(_ROOT, "include")
 _BUILD = os.path.join(_PKG, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsiminf_gpu.so")
 
-SOURCES = ["sg_engine.cu", "sg_plan.cpp", "sg_mlp.cu"]
-HEADERS = ["sg_common.h", "sg_device.cuh", "sg_plan.h", "sg_mlp.h", "sg_tc.cuh"]
+SOURCES = ["sg_engine.cu", "sg_plan.cpp", "sg_mlp.cu", "sg_mparse.cpp"]
+HEADERS = ["sg_common.h", "sg_device.cuh", "sg_kernels.cuh", "sg_plan.h", "sg_mlp.h", "sg_tc.cuh",
+           "sg_mparse.h"]
+# The headers the run-time compiler (NVRTC) sees for a model from transition
+# strings, embedded into the library; NVRTC has no C library, so the two
+# standard headers they include are replaced by minimal ones.
+JIT_HEADERS = [("siminf_gpu.h", "include"), ("sg_common.h", "csrc"), ("sg_device.cuh", "csrc"),
+               ("sg_kernels.cuh", "csrc")]
+_JIT_STDINT = """#pragma once
+typedef signed char int8_t;
+typedef unsigned char uint8_t;
+typedef short int16_t;
+typedef unsigned short uint16_t;
+typedef int int32_t;
+typedef unsigned int uint32_t;
+typedef long int64_t;
+typedef unsigned long uint64_t;
+typedef unsigned long uintptr_t;
+"""
+_JIT_STDDEF = """#pragma once
+typedef unsigned long size_t;
+"""
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", ARCH,
               "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
-              "-I" + _INCLUDE, "-I" + _CSRC]
+              "-I" + _INCLUDE, "-I" + _CSRC, "-I" + _BUILD]
 
 OK = 0
 ERR_NAMES = {0: "ok", -1: "invalid argument",
@@ -37,7 +57,9 @@ ERR_NAMES = {0: "ok", -1: "invalid argument",
              -5: "post time step error", -6: "device wait timed out",
              -7: "CUDA runtime error", -8: "out of memory",
              -9: "more than 2^24 draws in one node-day",
-             -10: "problem exceeds the fixed scratch of sg_run_noalloc"}
+             -10: "problem exceeds the fixed scratch of sg_run_noalloc",
+             -11: "transition string does not parse",
+             -12: "run-time compilation or loading failed"}
 
 
 class SimInfError(RuntimeError):
@@ -54,6 +76,29 @@ def _nvcc():
     return "nvcc"
 
 
+def _write_jit_sources():
+    """_build/sg_jit_sources.inc: names and texts of the headers NVRTC sees."""
+    names, texts = ["stdint.h", "stddef.h"], [_JIT_STDINT, _JIT_STDDEF]
+    for name, where in JIT_HEADERS:
+        d = _INCLUDE if where == "include" else _CSRC
+        with open(os.path.join(d, name)) as f:
+            names.append(name)
+            texts.append(f.read())
+    out = ["// generated by binding.build(): the kernel headers for NVRTC"]
+    out.append("static const char *const kJitNames[] = {"
+               + ", ".join('"%s"' % n for n in names) + "};")
+    for i, t in enumerate(texts):
+        assert ')SGSRC"' not in t
+        out.append('static const char kJitSrc%d[] = R"SGSRC(%s)SGSRC";' % (i, t))
+    out.append("static const char *const kJitSources[] = {"
+               + ", ".join("kJitSrc%d" % i for i in range(len(texts))) + "};")
+    path = os.path.join(_BUILD, "sg_jit_sources.inc")
+    text = "\n".join(out) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as f:
+            f.write(text)
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile the CUDA library for sm_103a into ``_build/libsiminf_gpu.so``."""
     os.makedirs(_BUILD, exist_ok=True)
@@ -64,6 +109,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB_PATH
     nvcc = _nvcc()
     objs = []
+    _write_jit_sources()
 
     def compile_one(src):
         obj = os.path.join(_BUILD, os.path.splitext(src)[0] + ".o")
@@ -76,7 +122,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-Xcompiler", "-fPIC"]
+    cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-Xcompiler", "-fPIC", "-ldl"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -124,7 +170,7 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_gemm_bf16", "sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
            "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
-           "sg_set_output"]
+           "sg_set_output", "sg_model_create_parsed", "sg_model_tables"]
 
 _lock = threading.Lock()
 _lib = None
@@ -183,6 +229,12 @@ def lib(path: str | None = None):
         L.sg_set_solver.restype = ctypes.c_int
         L.sg_set_output.argtypes = [vp, vp]
         L.sg_set_output.restype = ctypes.c_int
+        L.sg_model_create_parsed.argtypes = [vp, i32, vp, i32, vp, vp, i32, i32, vp, i32, vp,
+                                             i32, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.c_char_p, i32]
+        L.sg_model_create_parsed.restype = ctypes.c_int
+        L.sg_model_tables.argtypes = [vp, vp, vp]
+        L.sg_model_tables.restype = ctypes.c_int
         L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
                                    i32, vp]
         L.sg_gemm_bf16.restype = ctypes.c_int
@@ -260,22 +312,10 @@ class Model:
     """
 
     def __init__(self, w):
-        L = lib()
-        S, G = _colmajor(w.S), _colmajor(w.G)
-        E, N = _colmajor(w.E), _colmajor(w.N)
-        ldata = np.ascontiguousarray(np.asarray(w.ldata, np.float64).ravel(order="F"))
-        gdata = np.ascontiguousarray(w.gdata, dtype=np.float64)
-        n_nodes = int(np.asarray(w.u0).shape[-2])
-        self.n_nodes, self.n_comp, self.n_v = n_nodes, int(w.S.shape[0]), int(w.n_v)
-        d = _Desc(int(w.kind), n_nodes, int(w.S.shape[0]), int(w.S.shape[1]),
-                  _p(S), _p(G), int(w.E.shape[1]), _p(E), int(w.N.shape[1]), _p(N),
-                  int(w.n_v), int(np.asarray(w.ldata).shape[0]), _p(ldata),
-                  int(gdata.size), _p(gdata))
-        h = ctypes.c_void_p()
-        rc = L.sg_model_create(ctypes.byref(d), ctypes.byref(h))
-        if rc:
-            raise SimInfError(rc)
-        self._h = h
+        if getattr(w, "generic", None) is not None:
+            self._init_parsed(w)
+        else:
+            self._init_tables(w)
         self.dense = True
         if getattr(w, "events", None) is not None:
             self.set_events(w.events)
@@ -283,6 +323,63 @@ class Model:
             self.set_neighbors(*w.neighbors)
         if getattr(w, "solver", 0):
             self.set_solver(w.solver)
+
+    def _init_tables(self, w):
+        S, G = _colmajor(w.S), _colmajor(w.G)
+        E, N = _colmajor(w.E), _colmajor(w.N)
+        ldata = np.ascontiguousarray(np.asarray(w.ldata, np.float64).ravel(order="F"))
+        gdata = np.ascontiguousarray(w.gdata, dtype=np.float64)
+        n_nodes = int(np.asarray(w.u0).shape[-2])
+        self.n_nodes, self.n_comp, self.n_v = n_nodes, int(w.S.shape[0]), int(w.n_v)
+        self.n_trans = int(w.S.shape[1])
+        d = _Desc(int(w.kind), n_nodes, int(w.S.shape[0]), int(w.S.shape[1]),
+                  _p(S), _p(G), int(w.E.shape[1]), _p(E), int(w.N.shape[1]), _p(N),
+                  int(w.n_v), int(np.asarray(w.ldata).shape[0]), _p(ldata),
+                  int(gdata.size), _p(gdata))
+        h = ctypes.c_void_p()
+        rc = lib().sg_model_create(ctypes.byref(d), ctypes.byref(h))
+        if rc:
+            raise SimInfError(rc)
+        self._h = h
+
+    def _init_parsed(self, w):
+        """A model from transition strings (sg_model_create_parsed): the
+        library parses them and compiles the propensities with NVRTC."""
+        g = w.generic
+
+        def cstrs(items):
+            arr = (ctypes.c_char_p * max(1, len(items)))()
+            for i, x in enumerate(items):
+                arr[i] = x.encode()
+            return arr
+
+        tr, cp, gn = cstrs(g["transitions"]), cstrs(g["compartments"]), cstrs(g["gdata_names"])
+        gd = np.ascontiguousarray(w.gdata, dtype=np.float64)
+        E, N = _colmajor(w.E), _colmajor(w.N)
+        n_nodes = int(np.asarray(w.u0).shape[-2])
+        msg = ctypes.create_string_buffer(4096)
+        h = ctypes.c_void_p()
+        rc = lib().sg_model_create_parsed(
+            ctypes.cast(tr, ctypes.c_void_p), len(g["transitions"]),
+            ctypes.cast(cp, ctypes.c_void_p), len(g["compartments"]),
+            ctypes.cast(gn, ctypes.c_void_p), _p(gd), int(gd.size), n_nodes,
+            _p(E), int(w.E.shape[1]), _p(N), int(w.N.shape[1]), ctypes.byref(h), msg, 4096)
+        if rc:
+            raise SimInfError(rc, {"message": msg.value.decode(errors="replace")})
+        self._h = h
+        self.n_nodes, self.n_comp, self.n_v = n_nodes, len(g["compartments"]), 0
+        self.n_trans = len(g["transitions"])
+
+    def tables(self):
+        """(S, G) as the engine uses them: S (n_comp, n_trans), G (n_trans,
+        n_trans) with G[k, j] = 1 when rate k is recomputed after j."""
+        T = self.n_trans
+        S = np.zeros(self.n_comp * T, np.int32)
+        G = np.zeros(T * T, np.int32)
+        rc = lib().sg_model_tables(self._h, _p(S), _p(G))
+        if rc:
+            raise SimInfError(rc)
+        return S.reshape(T, self.n_comp).T.copy(), G.reshape(T, T).T.copy()
 
     def set_output(self, dense=True, n_tspan=0, u_pattern=None, u_values=None,
                    v_pattern=None, v_values=None, prevalence=None, prev_out=None):

@@ -1,0 +1,1041 @@
+// sg_kernels.cuh -- the day kernel, the external-transfer kernel and the
+// recording helpers of the SimInf GB300 engine, templated on the model kind.
+//
+// Compiled twice: by nvcc into the library for the built-in kinds, and by
+// NVRTC at run time for a model given as transition strings (the generated
+// ModelTraits<SG_GENERIC> is defined before this header is included).  So it
+// holds device code only and includes nothing but the engine's own headers.
+#pragma once
+
+#include "sg_common.h"
+#include "sg_device.cuh"
+
+namespace sg {
+
+constexpr int kDayBlock = 128;
+constexpr int kE2Block = 256;
+
+// Programmatic dependent launch: the day kernels and the E2 kernels are
+// launched so that the next kernel in the stream may start while the
+// previous one finishes.  Each kernel lets its successor launch at once,
+// reads only static inputs (model tables, event plan) before pdl_wait, and
+// waits for its predecessor (completion and memory) before it touches state.
+// Every such kernel executes pdl_wait on all paths, so its completion implies
+// its predecessor's.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Events of the plan, structure of arrays in planned order (E1 part first).
+struct EvDev {
+  const int8_t *type;
+  const uint8_t *select;
+  const int8_t *shift;       // -1 = no shift
+  const int32_t *node, *dest, *n;
+  const double *proportion;
+  const int64_t *index;      // position in the caller's list (random stream key)
+  const int32_t *e1_day;     // day index of each E1 event
+  const int64_t *e1_node_off;  // [slots * Nn + 1]; nullptr when there are none
+};
+
+// Output selection (Sec. 3.2 result slots U_sparse and V_sparse, and the
+// prevalence summary): compressed-column patterns with the layouts of U
+// (rows node * C + compartment) and V (rows node * NV + index), one column
+// per tspan point; values [R][nnz]; prevalence counters [R][M][4] (sum of
+// cases, sum at risk, nodes with a case, nodes with anyone at risk).
+struct OutDev {
+  const int64_t *u_colptr = nullptr;
+  const int32_t *u_row = nullptr;
+  int32_t *u_val = nullptr;
+  long long u_nnz = 0;
+  const int64_t *v_colptr = nullptr;
+  const int32_t *v_row = nullptr;
+  double *v_val = nullptr;
+  long long v_nnz = 0;
+  uint32_t cases = 0, at_risk = 0;
+  unsigned long long *prev = nullptr;
+};
+
+// First index in row[lo, hi) whose value is >= x.
+__device__ __forceinline__ long long lower_bound_i32(const int32_t *row, long long lo,
+                                                     long long hi, int32_t x) {
+  while (lo < hi) {
+    const long long mid = lo + ((hi - lo) >> 1);
+    if (row[mid] < x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// The U_sparse / V_sparse entries of one node at tspan slot m.
+template <int C, int NV>
+__device__ __forceinline__ void record_sparse(const OutDev &o, int m, int rep, int node,
+                                              const int *u, const double *v) {
+  if (o.u_nnz > 0) {
+    const long long hi = o.u_colptr[m + 1];
+    long long e = lower_bound_i32(o.u_row, o.u_colptr[m], hi, node * C);
+    for (; e < hi && o.u_row[e] < node * C + C; ++e) {
+      const int p = o.u_row[e] - node * C;
+      int x = 0;
+#pragma unroll
+      for (int q = 0; q < C; ++q)
+        if (q == p) x = u[q];
+      o.u_val[(long long)rep * o.u_nnz + e] = x;
+    }
+  }
+  if (NV > 0 && o.v_nnz > 0) {
+    const long long hi = o.v_colptr[m + 1];
+    long long e = lower_bound_i32(o.v_row, o.v_colptr[m], hi, node * NV);
+    for (; e < hi && o.v_row[e] < node * NV + NV; ++e) {
+      const int p = o.v_row[e] - node * NV;
+      double x = 0.0;
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        if (q == p) x = v[q];
+      o.v_val[(long long)rep * o.v_nnz + e] = x;
+    }
+  }
+}
+
+// Adds recorded nodes to the prevalence counters of (replicate, slot m).
+// Called by all 32 lanes of the warp together; `key` = rep * M + m for a
+// thread that holds a unit (-1 otherwise; such lanes sit at the end of the
+// warp, so equal keys are contiguous), `on` = its state is recorded.  A
+// segmented inclusive scan over the warp, then one atomic per segment.
+template <int C>
+__device__ __forceinline__ void prevalence_add(const OutDev &o, long long key, bool on,
+                                               const int *u) {
+  long long cs = 0, rk = 0;
+  int nc = 0, nr = 0;
+  if (on) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) {
+      if ((o.cases >> p) & 1u) cs += u[p];
+      if ((o.at_risk >> p) & 1u) rk += u[p];
+    }
+    nc = cs > 0;
+    nr = rk > 0;
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const long long k2 = __shfl_up_sync(full, key, d);
+    const long long c2 = __shfl_up_sync(full, cs, d), r2 = __shfl_up_sync(full, rk, d);
+    const int nc2 = __shfl_up_sync(full, nc, d), nr2 = __shfl_up_sync(full, nr, d);
+    if (lane >= d && k2 == key) {
+      cs += c2;
+      rk += r2;
+      nc += nc2;
+      nr += nr2;
+    }
+  }
+  const long long next = __shfl_down_sync(full, key, 1);
+  if (key >= 0 && (lane == 31 || next != key)) {
+    unsigned long long *q = o.prev + key * 4;
+    if (cs) atomicAdd(q, (unsigned long long)cs);
+    if (rk) atomicAdd(q + 1, (unsigned long long)rk);
+    if (nc) atomicAdd(q + 2, (unsigned long long)nc);
+    if (nr) atomicAdd(q + 3, (unsigned long long)nr);
+  }
+}
+
+struct DayArgs {
+  int *u;              // [R][Nn][C] working counts
+  double *v;           // [R][Nn][NV] working continuous state
+  const double *ldata; // [Nn][n_ldata]
+  int32_t *U;          // [R][M][Nn][C]
+  double *V;           // [R][M][Nn][NV]
+  const int32_t *rec;  // [days + 1]: tspan slot of T = t0 + i, or -1
+  int32_t *e1_cur;     // [R][Nn]: next E1 event, relative to the node's list
+  EvDev ev;
+  int32_t t0, M, n_rep, slots;
+  int32_t T_begin, T_end;  // SSA toward T = T_begin .. T_end - 1
+  int32_t finish_first;    // finish unit step T_begin - 1 before the SSA
+  int32_t finish_last;     // finish unit step T_end - 1 after the SSA
+  int32_t heavy_after;     // draws a thread takes before its warp takes over
+  int32_t npb;             // nodes per block (<= kDayBlock); the other
+                           // threads of the block only serve heavy nodes
+  const int32_t *emu;      // [R][Nn][4]: emulated increments of I_1..I_3 and
+                           // a flag (1 = use them instead of the SSA), or null
+  uint32_t k0, k1;         // Philox key (seed)
+  SgDevError *err;
+  SgCounters *cnt;
+  // all events method: channel state [T][R * Nn] (rate, firing time, draws
+  // taken); null for the direct method
+  double *aem_a, *aem_tau;
+  uint32_t *aem_cnt;
+  OutDev out;            // sparse output and prevalence (U, V may be null)
+};
+
+// One transition (Appendix A, inversion and update): the smallest n with
+// target <= running sum of the positive rates (last positive one if rounding
+// leaves none), u += S[, n], and the rates that column n of G marks are
+// recomputed.  Returns 0 or SG_ERR_RATE.
+template <int KIND>
+__device__ __forceinline__ int fire(int *u, double *w, double target, const double *kf,
+                                    const SgTables &tb) {
+  using M = ModelTraits<KIND>;
+  // running sum over the positive rates in index order; the first term is
+  // taken as is (0 + w == w exactly), the comparisons are exact integer
+  // comparisons of non-negative doubles
+  double cum = 0.0;
+  int n = -1, last = -1;
+#pragma unroll
+  for (int j = 0; j < M::T; ++j) {
+    if (n < 0 && gt0(w[j])) {
+      cum = last < 0 ? w[j] : cum + w[j];
+      last = j;
+      if (le_nonneg(target, cum)) n = j;
+    }
+  }
+  if (n < 0) n = last;
+#pragma unroll
+  for (int p = 0; p < M::C; ++p) u[p] += tb.S[n][p];
+  const uint32_t dep = tb.dep[n];
+  int code = 0;
+#pragma unroll
+  for (int k = 0; k < M::T; ++k) {
+    if ((dep >> k) & 1u) {
+      w[k] = M::rate_k(k, u, kf, tb.gdata);
+      if (bad_rate(w[k])) code = SG_ERR_RATE;
+    }
+  }
+  return code;
+}
+
+enum { SSA_DONE = 0, SSA_HEAVY = 1 };
+
+// Direct SSA of one node toward the unit time Tn in its own thread, for at
+// most `budget` draws (Appendix A, one iteration per draw).  Returns SSA_DONE,
+// SSA_HEAVY (budget spent, state and counter ready for the warp) or an error.
+template <int KIND>
+__device__ __forceinline__ int ssa_thread(int *u, double *w, const double *kf, double &t,
+                                          uint32_t &c, double Tn, uint32_t node, uint32_t Td,
+                                          uint32_t tag, uint32_t k0, uint32_t k1, int budget,
+                                          const SgTables &tb, unsigned long long &fired) {
+  using M = ModelTraits<KIND>;
+  const long long Tkey = order_key(Tn);
+  for (int b = 0;; ++b) {
+    // lambda = ((0 + w_1) + w_2) + ...; the leading 0 + w_1 changes no
+    // decision or value, so the sum starts at w_1
+    double lam = w[0];
+#pragma unroll
+    for (int j = 1; j < M::T; ++j) lam = lam + w[j];
+    if (!gt0(lam)) return SSA_DONE;  // nothing can fire: jump to Tn
+    if (c >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+    if (b == budget) return SSA_HEAVY;
+    const U4 x = philox10(U4{c, node, Td, tag}, k0, k1);
+    ++c;
+    const double r1 = u01_open(x.x, x.y);
+    const double r2 = u01_open(x.z, x.w);
+    const double tau = -log_pos(r1) / lam;
+    const double tt = t + tau;
+    if (order_key(tt) >= Tkey) return SSA_DONE;
+    t = tt;
+    const int rc = fire<KIND>(u, w, lam * r2, kf, tb);
+    ++fired;
+    if (rc) return rc;
+  }
+}
+
+// A node handed from its thread to a warp.
+template <int C, int NK>
+struct HeavySlot {
+  double t;
+  double kf[NK];
+  uint32_t c;
+  int32_t node, rep, code;
+  int32_t u[C];
+};
+
+// Direct SSA of one heavy node by a whole warp.  The draws depend only on
+// (seed, replicate, node, day, draw index), so lane l computes the Philox
+// words, uniforms and logarithm of draw c0 + l for 32 draws at once; the
+// sequential part (waiting time, boundary test, transition) then runs on all
+// lanes in step, reading draw j from lane j.  The transition for a draw is
+// evaluated alongside the waiting-time division and kept only if the draw
+// falls before Tn.  Same operations, in the same order, as ssa_thread.
+template <int KIND>
+__device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> &hs, double Tn,
+                         uint32_t Td, uint32_t k0, uint32_t k1, const SgTables &tb,
+                         unsigned long long &fired, unsigned long long &drawn) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NK = M::NK;
+  const int lane = threadIdx.x & 31;
+  int u[C];
+  double kf[NK], w[T];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = hs.u[p];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) kf[i] = hs.kf[i];
+  double t = hs.t;
+  uint32_t c = hs.c;
+  const uint32_t c_in = c, node = (uint32_t)hs.node;
+  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)hs.rep;
+  int code = 0;
+#pragma unroll
+  for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
+  uint32_t c0 = c;
+  double nE = 0.0, r2 = 0.0;
+  bool have = false;
+  unsigned long long f = 0;
+  const long long Tkey = order_key(Tn);
+  if (T == 2 && tb.dep[0] == 3u && tb.dep[1] == 3u) {
+    // Two transitions, every rate recomputed after every transition: the
+    // states reachable within the next J = 7 draws are u + (j - b) S0 + b S1,
+    // 0 <= b <= j < 7 (28 of them).  Lane l = j (j + 1) / 2 + b evaluates
+    // draw c + j at state (j, b): rates, lambda, waiting time, inversion.
+    // The walk then follows the fired transitions through the table, so each
+    // draw costs one addition (t + tau) and a branch.  Rates from scratch
+    // equal the incrementally kept ones (pure functions of the counts).
+    constexpr int J = 7;
+    int lj = 0, lb = 0;
+    {
+      int l = lane < J * (J + 1) / 2 ? lane : 0;
+      while (l > lj) { l -= lj + 1; ++lj; }
+      lb = l;
+    }
+    bool done = false;
+    while (!done && code == 0) {
+      if (!have || c + (uint32_t)J - c0 > 32u) {
+        c0 = c;
+        const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+        nE = -log_pos(u01_open(x.x, x.y));
+        r2 = u01_open(x.z, x.w);
+        have = true;
+      }
+      // this lane's state and draw
+      int us[C];
+#pragma unroll
+      for (int p = 0; p < C; ++p) us[p] = u[p] + (lj - lb) * tb.S[0][p] + lb * tb.S[1][p];
+      double ws[T];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ws[j] = M::rate_k(j, us, kf, tb.gdata);
+        bad = bad || bad_rate(ws[j]);
+      }
+      const int src = (int)(c - c0) + lj;  // lane holding draw c + lj
+      const double E = __shfl_sync(0xffffffffu, nE, src);
+      const double R2 = __shfl_sync(0xffffffffu, r2, src);
+      const double lam = ws[0] + ws[1];
+      const double tau = E / lam;
+      const double target = lam * R2;
+      const int fire0 = gt0(ws[0]) && le_nonneg(target, ws[0]);
+      // inversion: transition 0 if target <= w0 (w0 > 0), else 1 if w1 > 0,
+      // else the last positive one (w0)
+      const int nsel = fire0 ? 0 : (gt0(ws[1]) ? 1 : 0);
+      const unsigned pos_mask = __ballot_sync(0xffffffffu, gt0(lam));
+      const unsigned bad_mask = __ballot_sync(0xffffffffu, bad);
+      const unsigned n1_mask = __ballot_sync(0xffffffffu, nsel == 1);
+      int j = 0, b = 0;
+      for (; j < J; ++j) {
+        const int L = j * (j + 1) / 2 + b;
+        if (j > 0 && ((bad_mask >> L) & 1u)) {
+          code = SG_ERR_RATE;  // the transition into this state gave a bad rate
+          break;
+        }
+        if (!((pos_mask >> L) & 1u)) {
+          done = true;  // nothing can fire: jump to Tn
+          break;
+        }
+        if (c >= SG_MAX_DRAWS) {
+          code = SG_ERR_STEP_LIMIT;
+          break;
+        }
+        const double tauL = __shfl_sync(0xffffffffu, tau, L);
+        ++c;
+        const double tt = t + tauL;
+        if (order_key(tt) >= Tkey) {
+          done = true;
+          break;
+        }
+        t = tt;
+        b += (int)((n1_mask >> L) & 1u);
+        ++f;
+      }
+      // move to the state reached
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = u[p] + (j - b) * tb.S[0][p] + b * tb.S[1][p];
+      if (!done && code == 0) {
+        // j == J: a new window starts from the state after J transitions
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          w[k] = M::rate_k(k, u, kf, tb.gdata);
+          if (bad_rate(w[k])) code = SG_ERR_RATE;
+        }
+      }
+    }
+  } else {
+  for (;;) {
+    double lam = w[0];
+#pragma unroll
+    for (int j = 1; j < T; ++j) lam = lam + w[j];
+    if (!gt0(lam)) break;
+    if (c >= SG_MAX_DRAWS) {
+      code = SG_ERR_STEP_LIMIT;
+      break;
+    }
+    if (!have || c - c0 >= 32u) {
+      c0 = c;
+      const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+      nE = -log_pos(u01_open(x.x, x.y));
+      r2 = u01_open(x.z, x.w);
+      have = true;
+    }
+    const int jj = (int)(c - c0);
+    const double E = __shfl_sync(0xffffffffu, nE, jj);
+    const double R2 = __shfl_sync(0xffffffffu, r2, jj);
+    ++c;
+    const double tau = E / lam;
+    int u2[C];
+    double w2[T];
+#pragma unroll
+    for (int p = 0; p < C; ++p) u2[p] = u[p];
+#pragma unroll
+    for (int j = 0; j < T; ++j) w2[j] = w[j];
+    const int rc = fire<KIND>(u2, w2, lam * R2, kf, tb);
+    const double tt = t + tau;
+    if (order_key(tt) >= Tkey) break;
+    t = tt;
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = u2[p];
+#pragma unroll
+    for (int j = 0; j < T; ++j) w[j] = w2[j];
+    ++f;
+    if (rc) {
+      code = rc;
+      break;
+    }
+  }
+  }
+  __syncwarp();
+  if (lane == 0) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+    hs.c = c;
+    hs.code = code;
+    fired += f;
+    drawn += c - c_in;
+  }
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// The all events method (solver 'aem' of Sec. 3.4.2): every transition of a
+// node is a channel with its own random stream, Philox counter (draws taken
+// by the channel, node, transition, (3 << 24) | replicate), and the channels
+// advance by the next reaction method of Gibson and Bruck: each holds an
+// absolute firing time, the earliest fires, the fired channel draws a fresh
+// Exp(1) waiting time scaled by its rate, a channel whose rate changes from
+// a > 0 to a' > 0 rescales its residual time by a / a', one whose rate drops
+// to 0 sleeps (time +inf), one that wakes draws afresh.  Firing times carry
+// over from day to day; at each day start every rate is recomputed and the
+// same rule applied.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int aem_draw(uint32_t &c, uint32_t node, uint32_t j, uint32_t tag,
+                                        uint32_t k0, uint32_t k1, double &E) {
+  if (c == 0xffffffffu) return SG_ERR_STEP_LIMIT;
+  const U4 x = philox10(U4{c, node, j, tag}, k0, k1);
+  ++c;
+  E = -log_pos(u01_open(x.x, x.y));
+  return 0;
+}
+
+// Channel j's new rate a_new at time t (the update rule above).
+__device__ __forceinline__ int aem_update(double t, double a_new, double &a, double &tau,
+                                          uint32_t &c, uint32_t node, uint32_t j, uint32_t tag,
+                                          uint32_t k0, uint32_t k1, unsigned long long &drawn) {
+  if (a_new == a) return 0;
+  if (gt0(a) && gt0(a_new)) {
+    tau = t + (a / a_new) * (tau - t);
+  } else if (gt0(a_new)) {
+    double E;
+    const int rc = aem_draw(c, node, j, tag, k0, k1, E);
+    if (rc) return rc;
+    ++drawn;
+    tau = t + E / a_new;
+  } else {
+    tau = __longlong_as_double(0x7ff0000000000000ll);  // +inf
+  }
+  a = a_new;
+  return 0;
+}
+
+// One node-day from Tn - 1 to Tn under the all events method, channel state
+// in registers.  Returns 0 or an error.
+template <int KIND>
+__device__ __forceinline__ int aem_node_day(int *u, const double *kf, double *a, double *tau,
+                                            uint32_t *c, double Tn, uint32_t node, uint32_t tag,
+                                            uint32_t k0, uint32_t k1, const SgTables &tb,
+                                            unsigned long long &fired,
+                                            unsigned long long &drawn) {
+  using M = ModelTraits<KIND>;
+  constexpr int T = M::T;
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  double t = Tn - 1.0;
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    const double w = M::rate_k(j, u, kf, tb.gdata);
+    if (bad_rate(w)) return SG_ERR_RATE;
+    const int rc = aem_update(t, w, a[j], tau[j], c[j], node, (uint32_t)j, tag, k0, k1, drawn);
+    if (rc) return rc;
+  }
+  uint32_t nfired = 0;
+  for (;;) {
+    // the earliest channel, ties to the lowest index
+    int mu = -1;
+    double best = inf;
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      if (tau[j] < best) {
+        best = tau[j];
+        mu = j;
+      }
+    }
+    if (mu < 0 || best >= Tn) return 0;
+    if (nfired >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+    ++nfired;
+    t = best;
+#pragma unroll
+    for (int p = 0; p < M::C; ++p) u[p] += tb.S[mu][p];
+    ++fired;
+    const uint32_t dep = tb.dep[mu];
+#pragma unroll
+    for (int k = 0; k < T; ++k) {
+      const bool marked = (dep >> k) & 1u;
+      if (k != mu && !marked) continue;
+      double w = a[k];
+      if (marked) {
+        w = M::rate_k(k, u, kf, tb.gdata);
+        if (bad_rate(w)) return SG_ERR_RATE;
+      }
+      if (k == mu) {
+        a[k] = w;
+        if (gt0(w)) {
+          double E;
+          const int rc = aem_draw(c[k], node, (uint32_t)k, tag, k0, k1, E);
+          if (rc) return rc;
+          ++drawn;
+          tau[k] = t + E / w;
+        } else {
+          tau[k] = inf;
+        }
+      } else {
+        const int rc = aem_update(t, w, a[k], tau[k], c[k], node, (uint32_t)k, tag, k0, k1, drawn);
+        if (rc) return rc;
+      }
+    }
+  }
+}
+
+// One E1 event (exit, enter or internal transfer, Sec. 3.3) on a node whose
+// counts are in the calling thread's registers.  Returns 0 or an error.
+template <int C>
+__device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const EvDev &ev, long long j,
+                                        int rep, uint32_t k0, uint32_t k1) {
+  const int type = ev.type[j];
+  const uint32_t mask = tb.Emask[ev.select[j]];
+  const int n = ev.n[j];
+  if (type == SG_ENTER) {
+    const int first = __ffs(mask) - 1;  // first selected compartment
+#pragma unroll
+    for (int p = 0; p < C; ++p)
+      if (p == first) u[p] += n;
+    return 0;
+  }
+  long long total = 0;
+#pragma unroll
+  for (int p = 0; p < C; ++p)
+    if ((mask >> p) & 1u) total += u[p];
+  const long long k = n > 0 ? (long long)n : (long long)round(ev.proportion[j] * (double)total);
+  if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
+  int moved[C];
+#pragma unroll
+  for (int p = 0; p < C; ++p) moved[p] = 0;
+  if (k > 0) {
+    WordStream ws;
+    ws.init(((uint64_t)k1 << 32) | k0, ev.index[j], rep);
+    for (long long i = 0; i < k; ++i) {
+      uint32_t x = ws.below((uint32_t)(total - i));
+      bool taken = false;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        if (taken || !((mask >> p) & 1u)) continue;
+        const uint32_t rem = (uint32_t)(u[p] - moved[p]);
+        if (x < rem) {
+          ++moved[p];
+          taken = true;
+        } else {
+          x -= rem;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] -= moved[p];
+  if (type == SG_EXIT) return 0;
+  const int q = ev.shift[j];  // internal transfer: validated q >= 0
+#pragma unroll
+  for (int dst = 0; dst < C; ++dst) {
+    int add = 0;
+#pragma unroll
+    for (int p = 0; p < C; ++p)
+      if (p + tb.Nsh[q][p] == dst) add += moved[p];
+    u[dst] += add;
+  }
+  return 0;
+}
+
+// Post time step and recording for unit time Tf (the state after its
+// events).  Returns 0 or SG_ERR_PTS.
+template <int KIND>
+__device__ __forceinline__ int finish_step(int Tf, const int *u, double *v, const int *ends,
+                                           const SgTables &tb, const DayArgs &a, int rep,
+                                           int node) {
+  using M = ModelTraits<KIND>;
+  int code = 0;
+  if (M::NV > 0) {
+    const int r = post_step<KIND>(v, u, ends, tb.gdata, Tf);
+    if (r < 0) code = r;
+  }
+  const int m = a.rec[Tf - a.t0];
+  if (m >= 0) {
+    const long long base = ((long long)rep * a.M + m) * tb.n_nodes + node;
+    if (a.U) {
+#pragma unroll
+      for (int p = 0; p < M::C; ++p) a.U[base * M::C + p] = u[p];
+    }
+    if (a.V) {
+#pragma unroll
+      for (int q = 0; q < M::NV; ++q) a.V[base * M::NV + q] = v[q];
+    }
+    record_sparse<M::C, M::NV>(a.out, m, rep, node, u, v);
+  }
+  return code;
+}
+
+// The day kernel: one thread per (replicate, node) for a run of days
+// T_begin .. T_end - 1 with no external transfers before T_end - 1.  Per day:
+// rates, SSA (thread, then warp for heavy nodes), the node's E1 events, and
+// (unless a kernel boundary follows) the post time step and recording.
+template <int KIND, bool AEM>
+__global__ void __launch_bounds__(kDayBlock)
+k_days(const SgTables tb, const DayArgs a) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
+  __shared__ HeavySlot<C, NK> s_heavy[AEM ? 1 : kDayBlock];
+  __shared__ int s_nheavy;
+  pdl_trigger();
+  const int Nn = tb.n_nodes;
+  const long long gid = (long long)blockIdx.x * a.npb + threadIdx.x;
+  const long long total = (long long)Nn * a.n_rep;
+  const bool in_range = (int)threadIdx.x < a.npb && gid < total;
+  const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  unsigned long long fired = 0, drawn = 0, applied = 0;
+  int rep = 0, node = 0, code = 0, bad_day = 0;
+  long long bad_event = -1;
+  int u[C];
+  double v[NV > 0 ? NV : 1];
+  int ld[4] = {0, 0, 0, 0};  // season ends of the node (integer form)
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = 0;
+  v[0] = 0.0;
+  long long ecur = 0, ebase = 0, eend = 0;
+  int next_day = 0x7fffffff;
+  double ch_a[AEM ? T : 1], ch_tau[AEM ? T : 1];  // all events method channels
+  uint32_t ch_c[AEM ? T : 1];
+  // static inputs first (they overlap the previous kernel's tail)
+  if (in_range) {
+    rep = (int)(gid / Nn);
+    node = (int)(gid - (long long)rep * Nn);
+    if (NV > 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        ld[i] = season_end_int(a.ldata[(long long)node * tb.n_ldata + i]);
+    }
+    if (a.ev.e1_node_off) {
+      const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
+      ebase = a.ev.e1_node_off[key];
+      eend = a.ev.e1_node_off[key + 1];
+    }
+  }
+  pdl_wait();
+  const bool live = in_range && *(volatile int32_t *)&a.err->code == 0;
+  if (live) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+    if (a.ev.e1_node_off) {
+      ecur = ebase + a.e1_cur[gid];
+      if (ecur < eend) next_day = a.ev.e1_day[ecur];
+    }
+    if constexpr (AEM) {
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ch_a[j] = a.aem_a[j * total + gid];
+        ch_tau[j] = a.aem_tau[j * total + gid];
+        ch_c[j] = a.aem_cnt[j * total + gid];
+      }
+    }
+    if (a.finish_first) {
+      code = finish_step<KIND>(a.T_begin - 1, u, v, ld, tb, a, rep, node);
+      if (code) bad_day = a.T_begin - 1;
+    }
+  }
+  if (a.finish_first && a.out.prev) {
+    const int m = a.rec[a.T_begin - 1 - a.t0];
+    if (m >= 0)
+      prevalence_add<C>(a.out, in_range ? (long long)rep * a.M + m : -1, live && code == 0, u);
+  }
+  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
+  for (int Td = a.T_begin; Td < a.T_end; ++Td) {
+    const double Tn = (double)Td;
+    if constexpr (!AEM) {
+      if (threadIdx.x == 0) s_nheavy = 0;
+      __syncthreads();
+    }
+    int my = -1;
+    const bool emulated =
+        !AEM && live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
+    if (emulated) {
+      // the learned emulator's sampled one-day increments (SISe3 only):
+      // I_a += d_a, S_a -= d_a, each age class keeps its size
+#pragma unroll
+      for (int h = 0; h < C / 2; ++h) {
+        const int dlt = a.emu[gid * 4 + h];
+        u[2 * h] -= dlt;
+        u[2 * h + 1] += dlt;
+      }
+    }
+    if (AEM && live && code == 0) {
+      double kf[NK];
+      M::prepare(v, tb.gdata, kf);
+      code = aem_node_day<KIND>(u, kf, ch_a, ch_tau, ch_c, Tn, (uint32_t)node,
+                                (SG_STREAM_AEM << 24) | (uint32_t)rep, a.k0, a.k1, tb, fired,
+                                drawn);
+      if (code) bad_day = Td;
+    }
+    if (!AEM && live && code == 0 && !emulated) {
+      double kf[NK], w[T];
+      M::prepare(v, tb.gdata, kf);
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        w[j] = M::rate_k(j, u, kf, tb.gdata);
+        if (bad_rate(w[j])) code = SG_ERR_RATE;
+      }
+      if (code == 0) {
+        double t = (double)(Td - 1);
+        uint32_t c = 0;
+        const int r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag,
+                                       a.k0, a.k1, a.heavy_after, tb, fired);
+        drawn += c;
+        if (r == SSA_HEAVY) {
+          my = atomicAdd(&s_nheavy, 1);
+          HeavySlot<C, NK> &hs = s_heavy[my];
+          hs.t = t;
+#pragma unroll
+          for (int i = 0; i < NK; ++i) hs.kf[i] = kf[i];
+          hs.c = c;
+          hs.node = node;
+          hs.rep = rep;
+          hs.code = 0;
+#pragma unroll
+          for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+        } else if (r < 0) {
+          code = r;
+        }
+      }
+      if (code) bad_day = Td;
+    }
+    if constexpr (!AEM) {
+      __syncthreads();
+      const int nh = s_nheavy;
+      for (int h = warp; h < nh; h += nwarps)
+        ssa_warp<KIND>(s_heavy[h], Tn, (uint32_t)Td, a.k0, a.k1, tb, fired, drawn);
+      __syncthreads();
+    }
+    if (my >= 0) {
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = s_heavy[my].u[p];
+      if (s_heavy[my].code) {
+        code = s_heavy[my].code;
+        bad_day = Td;
+      }
+    }
+    // this node's E1 events of day Td, in (time, type, list index) order
+    const int d = Td - a.t0 - 1;
+    if (live && code == 0 && next_day == d) {
+      while (ecur < eend && a.ev.e1_day[ecur] == d) {
+        const int rc = apply_e1<C>(u, tb, a.ev, ecur, rep, a.k0, a.k1);
+        if (rc) {
+          code = rc;
+          bad_day = Td;
+          bad_event = a.ev.index[ecur];
+          break;
+        }
+        ++applied;
+        ++ecur;
+      }
+      next_day = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
+    }
+    if (live && code == 0 && (Td + 1 < a.T_end || a.finish_last)) {
+      code = finish_step<KIND>(Td, u, v, ld, tb, a, rep, node);
+      if (code) bad_day = Td;
+    }
+    if ((Td + 1 < a.T_end || a.finish_last) && a.out.prev) {
+      const int m = a.rec[Td - a.t0];
+      if (m >= 0)
+        prevalence_add<C>(a.out, in_range ? (long long)rep * a.M + m : -1, live && code == 0,
+                          u);
+    }
+  }
+  if (live) {
+    if (code) report(a.err, code, rep, node, bad_day, bad_event);
+#pragma unroll
+    for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.v[gid * NV + q] = v[q];
+    if (a.ev.e1_node_off) a.e1_cur[gid] = (int32_t)(ecur - ebase);
+    if constexpr (AEM) {
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        a.aem_a[j * total + gid] = ch_a[j];
+        a.aem_tau[j * total + gid] = ch_tau[j];
+        a.aem_cnt[j * total + gid] = ch_c[j];
+      }
+    }
+  }
+  // one atomic per warp for the counters
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fired += __shfl_down_sync(0xffffffffu, fired, off);
+    drawn += __shfl_down_sync(0xffffffffu, drawn, off);
+    applied += __shfl_down_sync(0xffffffffu, applied, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (drawn | fired) {
+      atomicAdd(&a.cnt->reactions, fired);
+      atomicAdd(&a.cnt->draws, drawn);
+    }
+    if (applied) atomicAdd(&a.cnt->events, applied);
+  }
+}
+
+struct EvArgs {
+  EvDev ev;
+  int *u;
+  int32_t n_rep;
+  uint32_t k0, k1;
+  int32_t day;  // unit time point T the events run at
+  SgDevError *err;
+  SgCounters *cnt;
+};
+
+// Block-wide copy of n 32-bit words with 16-byte accesses where both ends
+// are aligned, several loads in flight per thread.
+__device__ __forceinline__ void copy_words(int *dst, const int *src, int n) {
+  int head = 0;
+  if ((((uintptr_t)dst | (uintptr_t)src) & 15) == 0) {
+    const int n4 = n >> 2;
+    const int4 *s4 = reinterpret_cast<const int4 *>(src);
+    int4 *d4 = reinterpret_cast<int4 *>(dst);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
+    head = n4 << 2;
+  }
+#pragma unroll 4
+  for (int i = head + threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
+}
+
+constexpr int kE2Cap = 512;      // events staged in shared memory per chunk
+constexpr int kE2WaveCap = 128;  // wave bounds staged per chunk
+
+// E2 events of one day: block r runs replicate r's external transfers
+// (Sec. 3.3) wave by wave, with a block barrier between waves.  The block
+// first stages a chunk of events in shared memory together with the first
+// Philox block of each event's random stream (which does not depend on the
+// state); with SMEM_STATE the replicate's whole node state is also held in
+// shared memory for the day.  Several transfers of one wave may share a
+// destination, so additions are atomic; a wave never samples a node that
+// another event of the wave touches.
+template <int KIND, bool SMEM_STATE>
+__global__ void __launch_bounds__(kE2Block)
+k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_ev,
+            long long w_begin_shared, long long w_end_shared,
+            const int64_t *__restrict__ wave_off, int day_index, int slots) {
+  constexpr int C = ModelTraits<KIND>::C;
+  extern __shared__ __align__(16) int s_state[];
+  __shared__ int32_t s_node[kE2Cap], s_dest[kE2Cap], s_n[kE2Cap];
+  __shared__ uint8_t s_sel[kE2Cap];
+  __shared__ int8_t s_shift[kE2Cap];
+  __shared__ long long s_idx[kE2Cap];
+  __shared__ double s_prop[kE2Cap];
+  __shared__ uint4 s_w[kE2Cap];
+  __shared__ long long s_wave[kE2WaveCap + 1];
+  __shared__ int s_stop;
+  pdl_trigger();
+  const int rep = blockIdx.x;
+  const int Nn = tb.n_nodes;
+  long long w0 = w_begin_shared, w1 = w_end_shared;
+  if (slots > 1) {
+    w0 = wave_off[(long long)day_index * slots + rep];
+    w1 = wave_off[(long long)day_index * slots + rep + 1];
+  }
+  if (w0 >= w1) {
+    pdl_wait();
+    return;
+  }
+  int *gstate = a.u + (long long)rep * Nn * C;
+  int *state = SMEM_STATE ? s_state : gstate;
+  bool waited = false;
+  if (threadIdx.x == 0) s_stop = 0;
+  const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
+  const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
+  unsigned long long applied = 0;
+  long long w = w0;
+  long long pos = wave_ev[w0];
+  const long long pos_end = wave_ev[w1];
+  while (pos < pos_end) {
+    // stage the bounds of the next waves, then the events [pos, pend) they
+    // hold (at most kE2Cap; a wave may continue into the next chunk)
+    const long long wn = min(w1 - w, (long long)kE2WaveCap);
+    __syncthreads();
+    for (long long i = threadIdx.x; i <= wn; i += blockDim.x) s_wave[i] = wave_ev[w + i];
+    __syncthreads();
+    const long long pend = min(pos + (long long)kE2Cap, s_wave[wn]);
+    for (long long i = threadIdx.x; i < pend - pos; i += blockDim.x) {
+      const long long j = pos + i;
+      s_node[i] = a.ev.node[j];
+      s_dest[i] = a.ev.dest[j];
+      s_n[i] = a.ev.n[j];
+      s_sel[i] = a.ev.select[j];
+      s_shift[i] = a.ev.shift[j];
+      s_prop[i] = a.ev.proportion[j];
+      const long long idx = a.ev.index[j];
+      s_idx[i] = idx;
+      const U4 f = philox10(U4{0u, (uint32_t)(unsigned long long)idx,
+                               (uint32_t)((unsigned long long)idx >> 32), tag},
+                            a.k0, a.k1);
+      s_w[i] = make_uint4(f.x, f.y, f.z, f.w);
+    }
+    if (!waited) {
+      // the first chunk is staged: now wait for the day kernel's state
+      pdl_wait();
+      waited = true;
+      if (*(volatile int32_t *)&a.err->code != 0) s_stop = 1;
+      if (SMEM_STATE) copy_words(s_state, gstate, Nn * C);
+    }
+    __syncthreads();
+    if (s_stop) break;
+    // waves w .. (staged) intersecting [pos, pend)
+    long long wi = 0;
+    while (wi < wn && s_wave[wi] < pend) {
+      const long long lo = max(pos, s_wave[wi]), hi = min(pend, s_wave[wi + 1]);
+      for (long long q = lo + threadIdx.x; q < hi; q += blockDim.x) {
+        const int i = (int)(q - pos);
+        const int src = s_node[i];
+        int *un = state + (long long)src * C;
+        const uint32_t mask = tb.Emask[s_sel[i]];
+        int cur[C];
+        long long total = 0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          cur[p] = un[p];
+          if ((mask >> p) & 1u) total += cur[p];
+        }
+        const long long k = s_n[i] > 0 ? (long long)s_n[i]
+                                       : (long long)round(s_prop[i] * (double)total);
+        if (k < 0 || k > total) {
+          report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, a.day, s_idx[i]);
+          s_stop = 1;
+          continue;
+        }
+        int moved[C];
+#pragma unroll
+        for (int p = 0; p < C; ++p) moved[p] = 0;
+        if (k > 0) {
+          WordStream ws;
+          const uint4 f = s_w[i];
+          ws.init_with_first(seed, s_idx[i], rep, U4{f.x, f.y, f.z, f.w});
+          for (long long d = 0; d < k; ++d) {
+            uint32_t x = ws.below((uint32_t)(total - d));
+            bool taken = false;
+#pragma unroll
+            for (int p = 0; p < C; ++p) {
+              if (taken || !((mask >> p) & 1u)) continue;
+              const uint32_t rem = (uint32_t)(cur[p] - moved[p]);
+              if (x < rem) {
+                ++moved[p];
+                taken = true;
+              } else {
+                x -= rem;
+              }
+            }
+          }
+        }
+        const int q_sh = s_shift[i];
+        int *ud = state + (long long)s_dest[i] * C;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          if (moved[p] == 0) continue;
+          un[p] = cur[p] - moved[p];
+        }
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          if (moved[p] == 0) continue;
+          atomicAdd(ud + (q_sh >= 0 ? p + tb.Nsh[q_sh][p] : p), moved[p]);
+        }
+        ++applied;
+      }
+      __syncthreads();
+      if (s_stop) break;
+      if (s_wave[wi + 1] <= pend) ++wi;
+      else break;  // the wave continues in the next chunk
+    }
+    if (s_stop) break;
+    w += wi;
+    pos = pend;
+  }
+  if (!waited) pdl_wait();
+  if (SMEM_STATE && waited) {
+    __syncthreads();
+    copy_words(gstate, s_state, Nn * C);
+  }
+  if (applied) atomicAdd(&a.cnt->events, applied);
+}
+
+// U_sparse / V_sparse entries and prevalence counters of tspan slot 0 (the
+// initial state), one thread per (replicate, node).
+template <int C, int NV>
+__global__ void k_record0(const int32_t *__restrict__ u0, const double *__restrict__ v0, int Nn,
+                          int n_rep, int M, const OutDev o) {
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in_range = gid < (long long)Nn * n_rep;
+  int u[C];
+  double v[NV > 0 ? NV : 1];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = 0;
+  v[0] = 0.0;
+  int rep = 0;
+  if (in_range) {
+    rep = (int)(gid / Nn);
+    const int node = (int)(gid - (long long)rep * Nn);
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = u0[gid * C + p];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = v0[gid * NV + q];
+    record_sparse<C, NV>(o, 0, rep, node, u, v);
+  }
+  if (o.prev) prevalence_add<C>(o, in_range ? (long long)rep * M : -1, in_range, u);
+}
+
+}  // namespace sg
