@@ -77,7 +77,7 @@ def _base_workload(name):
         # thousands of transitions per node-day, so the oracle's sample is
         # sized by this relative cost per node-day
         w = W.config_predator_prey()
-        w.meta = {"oracle_cost": 400}
+        w.meta = {"oracle_cost": 400, "tune_days": 20}
         return w
     if name == "vaccination":
         return W.config_vaccination()
@@ -267,8 +267,12 @@ def bench_gpu(args):
 
     tuned = None
     if args.autotune:
-        # the work split changes speed only, never results
-        tuned = model.autotune(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
+        # the work split changes speed only, never results; workloads whose
+        # runs take seconds are tuned on a prefix of days (the buffers hold the
+        # full run)
+        td = w.meta.get("tune_days") if w.meta else None
+        tune_ts = w.tspan[:td + 1] if td and w.n_days > td else w.tspan
+        tuned = model.autotune(tune_ts, seed, n_rep, u0, v0, U, V, stream=stream)
 
     for _ in range(args.warmup):
         step()

@@ -268,7 +268,7 @@ int sg_set_kernel_timing(sg_model *m, int enable);
 int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 
 /* Autotuner: runs the given workload (arguments as sg_run) once for each of
- * nodes_per_block in {16, 32, 64, 128} x heavy_after in {0, 1, 2, 4, 8},
+ * nodes_per_block in {4, 8, 16, 32, 64, 128} x heavy_after in {0, 1, 2, 4, 8},
  * keeps the fastest setting in the model and reports it (outputs may be
  * NULL).  U and V hold the last run's (identical) results.  A shorter tspan
  * tunes a long workload on a prefix. */
@@ -334,6 +334,14 @@ typedef struct {
 } sg_output;
 
 int sg_set_output(sg_model *m, const sg_output *o);
+
+/* Where the external transfers of a day run.  enable = 1 (default): at the
+ * end of the day kernel, by the last block to finish each replicate's nodes
+ * (blocks count themselves off with an atomic after a device-wide fence; no
+ * block ever waits for another), saving one kernel launch per day with
+ * external transfers.  enable = 0: in a separate kernel, one block per
+ * replicate.  Results are identical. */
+int sg_set_fused_events(sg_model *m, int enable);
 
 /* Select the solver of later sg_run calls (SG_SOLVER_SSM by default).
  * SG_SOLVER_AEM keeps 20 bytes of channel state per (replicate, node,

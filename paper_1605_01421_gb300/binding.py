@@ -170,7 +170,8 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_gemm_bf16", "sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
            "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
-           "sg_set_output", "sg_model_create_parsed", "sg_model_tables"]
+           "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
+           "sg_set_fused_events"]
 
 _lock = threading.Lock()
 _lib = None
@@ -235,6 +236,8 @@ def lib(path: str | None = None):
         L.sg_model_create_parsed.restype = ctypes.c_int
         L.sg_model_tables.argtypes = [vp, vp, vp]
         L.sg_model_tables.restype = ctypes.c_int
+        L.sg_set_fused_events.argtypes = [vp, ctypes.c_int]
+        L.sg_set_fused_events.restype = ctypes.c_int
         L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
                                    i32, vp]
         L.sg_gemm_bf16.restype = ctypes.c_int
@@ -425,6 +428,13 @@ class Model:
             raise SimInfError(rc)
         self._out_refs = (u_values, v_values, prev_out)
         self.dense = bool(dense)
+
+    def set_fused_events(self, enable=True):
+        """External transfers inside the day kernel (default) or in their
+        own kernel; results are identical."""
+        rc = lib().sg_set_fused_events(self._h, 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
 
     def set_solver(self, solver):
         """0: split-step direct SSA ('ssm'), 1: all events method ('aem')."""

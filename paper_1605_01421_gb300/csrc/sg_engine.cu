@@ -323,6 +323,9 @@ struct sg_model {
   uint64_t out_version = 0;
   // SG_GENERIC: the kernels compiled at run time for the parsed model
   JitKernels jit;
+  // external transfers inside the day kernel (sg_set_fused_events)
+  bool fuse_e2 = true;
+  DevBuf<int32_t> e2_done;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -508,6 +511,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->out_u_colptr.release(); m->out_v_colptr.release();
   m->out_u_row.release(); m->out_v_row.release();
   jit_release(m->jit);
+  m->e2_done.release();
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
@@ -761,6 +765,7 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
   cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st);
   cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st);
   cudaMemsetAsync(m->e1_cur.p, 0, sizeof(int32_t) * (size_t)std::max(1, Nn * n_rep), st);
+  cudaMemsetAsync(m->e2_done.p, 0, sizeof(int32_t) * (size_t)n_rep, st);
   if (Nn > 0) {
     const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
     const unsigned g = (unsigned)std::min<long long>(4096, (nthreads + 255) / 256);
@@ -959,12 +964,22 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
       da.T_end = t0 + 1 + last + 1;
       da.finish_first = pending ? 1 : 0;
       da.finish_last = e2_today ? 0 : 1;
+      const bool fused = e2_today && m->fuse_e2;
+      da.e2_done = fused ? m->e2_done.p : nullptr;
+      if (fused) {
+        const long long b0 = (long long)last * slots, b1 = b0 + slots;
+        da.e2_wb = P.e2_wave_off[b0];
+        da.e2_we = P.e2_wave_off[b1];
+        da.e2_day_index = last;
+        waves += (int32_t)(da.e2_we - da.e2_wb);
+      }
       {
         LaunchTimer lt(m, st, 0);
         launch_days_kind(m, da, st);
       }
       ++launches;
-      if (e2_today) {
+      da.e2_done = nullptr;
+      if (e2_today && !fused) {
         ea.day = t0 + 1 + last;
         const long long b0 = (long long)last * slots, b1 = b0 + slots;
         const long long wb = P.e2_wave_off[b0], we = P.e2_wave_off[b1];
@@ -1030,6 +1045,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     return rc;
   if (tb.kind == SG_SISE_SP && (rc = m->v2.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))))
     return rc;
+  if ((rc = m->e2_done.ensure((size_t)n_rep))) return rc;
   const bool aem = m->solver == SG_SOLVER_AEM;
   if (aem && m->emu_on) return SG_ERR_ARG;  // the emulator replaces direct-method days only
   if (aem) {
@@ -1089,6 +1105,11 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     da.V = nullptr;
   }
   da.out = m->out;
+  da.wave_ev = m->wave_ev.p;
+  da.wave_off = m->wave_off.p;
+  da.e2_wb = da.e2_we = 0;
+  da.e2_day_index = 0;
+  da.e2_done = nullptr;
   da.aem_a = aem ? m->aem_a.p : nullptr;
   da.aem_tau = aem ? m->aem_tau.p : nullptr;
   da.aem_cnt = aem ? m->aem_cnt.p : nullptr;
@@ -1131,6 +1152,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                              1000033ull +
                          m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p +
                          m->out_version * 0x100000001b3ull +
+                         ((uint64_t)(uintptr_t)m->e2_done.p << 3) + (m->fuse_e2 ? 5 : 0) +
                          (aem ? 0x9e3779b97f4a7c15ull ^ (uint64_t)(uintptr_t)m->aem_tau.p ^
                                     ((uint64_t)(uintptr_t)m->aem_a.p << 1) ^
                                     ((uint64_t)(uintptr_t)m->aem_cnt.p << 2)
@@ -1496,6 +1518,10 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.cnt = d_cnt;
       da.aem_a = da.aem_tau = nullptr;
       da.aem_cnt = nullptr;
+      da.wave_ev = da.wave_off = nullptr;
+      da.e2_wb = da.e2_we = 0;
+      da.e2_day_index = 0;
+      da.e2_done = nullptr;
       const long long units = (long long)Nn * n_rep;
       const unsigned grid = (unsigned)std::max<long long>(1, (units + da.npb - 1) / da.npb);
       switch (k) {
@@ -1542,7 +1568,9 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
                            int32_t *d_U, double *d_V, void *stream, int32_t *npb_out,
                            int32_t *heavy_after_out, double *ms_out) {
   if (!m) return SG_ERR_ARG;
-  static const int32_t kNpb[] = {16, 32, 64, 128};
+  // 4 and 8 nodes per block give every heavy node its own warp (workloads
+  // where most node-days take thousands of draws)
+  static const int32_t kNpb[] = {4, 8, 16, 32, 64, 128};
   static const int32_t kHeavy[] = {0, 1, 2, 4, 8};
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
@@ -1658,6 +1686,15 @@ extern "C" int sg_set_output(sg_model *m, const sg_output *o) {
   m->out = d;
   m->out_dense = o->dense != 0;
   m->out_cols = (sparse || prev) ? o->n_tspan : -1;
+  return SG_OK;
+}
+
+extern "C" int sg_set_fused_events(sg_model *m, int enable) {
+  if (!m) return SG_ERR_ARG;
+  if ((enable != 0) != m->fuse_e2) {
+    m->fuse_e2 = enable != 0;
+    m->graph_ok = false;
+  }
   return SG_OK;
 }
 

@@ -171,7 +171,92 @@ struct DayArgs {
   double *aem_a, *aem_tau;
   uint32_t *aem_cnt;
   OutDev out;            // sparse output and prevalence (U, V may be null)
+  // external transfers of unit time T_end - 1 run inside this launch, by the
+  // last block to finish each replicate's nodes (null: none or by the E2
+  // kernel): wave bounds (wave_ev), the day's wave range [e2_wb, e2_we) when
+  // the events are shared, else per replicate from wave_off[day][slot], and
+  // a per-replicate count of finished blocks (zero between launches)
+  const int64_t *wave_ev, *wave_off;
+  long long e2_wb, e2_we;
+  int32_t e2_day_index;
+  int32_t *e2_done;
 };
+
+// The external transfers (Sec. 3.3) of replicate `rep` at unit time T, wave by
+// wave, by one block (a block barrier between waves), on the replicate's
+// state in global memory.  The state was written by other blocks of the same
+// launch, so it is read and written at L2 only (ld / st .cg) and added to
+// with atomics; a wave never samples a node another event of the wave
+// touches.  Same arithmetic and random stream as the E2 kernel.
+template <int C>
+__device__ void e2_rep_block(const SgTables &tb, const DayArgs &a, int rep, int T,
+                             long long w0, long long w1) {
+  // a run that already failed does nothing (one thread reads, the barrier
+  // makes the answer the block's)
+  if (__syncthreads_or(threadIdx.x == 0 && *(volatile int32_t *)&a.err->code != 0)) return;
+  int *state = a.u + (long long)rep * tb.n_nodes * C;
+  const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
+  unsigned long long applied = 0;
+  bool bad = false;
+  for (long long w = w0; w < w1; ++w) {
+    const long long lo = a.wave_ev[w], hi = a.wave_ev[w + 1];
+    for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
+      const int src = a.ev.node[j];
+      int *un = state + (long long)src * C;
+      const uint32_t mask = tb.Emask[a.ev.select[j]];
+      const long long idx = a.ev.index[j];
+      int cur[C];
+      long long total = 0;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        cur[p] = __ldcg(un + p);
+        if ((mask >> p) & 1u) total += cur[p];
+      }
+      const int n = a.ev.n[j];
+      const long long k =
+          n > 0 ? (long long)n : (long long)round(a.ev.proportion[j] * (double)total);
+      if (k < 0 || k > total) {
+        report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, T, idx);
+        bad = true;
+        continue;
+      }
+      int moved[C];
+#pragma unroll
+      for (int p = 0; p < C; ++p) moved[p] = 0;
+      if (k > 0) {
+        WordStream ws;
+        ws.init(seed, idx, rep);
+        for (long long d = 0; d < k; ++d) {
+          uint32_t x = ws.below((uint32_t)(total - d));
+          bool taken = false;
+#pragma unroll
+          for (int p = 0; p < C; ++p) {
+            if (taken || !((mask >> p) & 1u)) continue;
+            const uint32_t rem = (uint32_t)(cur[p] - moved[p]);
+            if (x < rem) {
+              ++moved[p];
+              taken = true;
+            } else {
+              x -= rem;
+            }
+          }
+        }
+      }
+      const int q_sh = a.ev.shift[j];
+      int *ud = state + (long long)a.ev.dest[j] * C;
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+        if (moved[p] != 0) __stcg(un + p, cur[p] - moved[p]);
+#pragma unroll
+      for (int p = 0; p < C; ++p)
+        if (moved[p] != 0) atomicAdd(ud + (q_sh >= 0 ? p + tb.Nsh[q_sh][p] : p), moved[p]);
+      ++applied;
+    }
+    // one barrier per wave; its result is the same for every thread
+    if (__syncthreads_or(bad)) break;
+  }
+  if (applied) atomicAdd(&a.cnt->events, applied);
+}
 
 // One transition (Appendix A, inversion and update): the smallest n with
 // target <= running sum of the positive rates (last positive one if rounding
@@ -469,39 +554,60 @@ __device__ __forceinline__ int aem_update(double t, double a_new, double &a, dou
   return 0;
 }
 
-// One node-day from Tn - 1 to Tn under the all events method, channel state
-// in registers.  Returns 0 or an error.
+// Day start (t = Tn - 1): every rate recomputed, the update rule applied.
 template <int KIND>
-__device__ __forceinline__ int aem_node_day(int *u, const double *kf, double *a, double *tau,
-                                            uint32_t *c, double Tn, uint32_t node, uint32_t tag,
-                                            uint32_t k0, uint32_t k1, const SgTables &tb,
-                                            unsigned long long &fired,
-                                            unsigned long long &drawn) {
+__device__ __forceinline__ int aem_day_start(const int *u, const double *kf, double *a,
+                                             double *tau, uint32_t *c, double Tn, uint32_t node,
+                                             uint32_t tag, uint32_t k0, uint32_t k1,
+                                             const SgTables &tb, unsigned long long &drawn) {
   using M = ModelTraits<KIND>;
-  constexpr int T = M::T;
-  const double inf = __longlong_as_double(0x7ff0000000000000ll);
-  double t = Tn - 1.0;
+  const double t = Tn - 1.0;
 #pragma unroll
-  for (int j = 0; j < T; ++j) {
+  for (int j = 0; j < M::T; ++j) {
     const double w = M::rate_k(j, u, kf, tb.gdata);
     if (bad_rate(w)) return SG_ERR_RATE;
     const int rc = aem_update(t, w, a[j], tau[j], c[j], node, (uint32_t)j, tag, k0, k1, drawn);
     if (rc) return rc;
   }
-  uint32_t nfired = 0;
-  for (;;) {
-    // the earliest channel, ties to the lowest index
-    int mu = -1;
-    double best = inf;
+  return 0;
+}
+
+enum { AEM_DONE = 0, AEM_HEAVY = 1 };
+
+// The earliest channel (ties to the lowest index); -1 if all sleep.
+template <int T>
+__device__ __forceinline__ int aem_earliest(const double *tau, double &best) {
+  int mu = -1;
+  best = __longlong_as_double(0x7ff0000000000000ll);
 #pragma unroll
-    for (int j = 0; j < T; ++j) {
-      if (tau[j] < best) {
-        best = tau[j];
-        mu = j;
-      }
+  for (int j = 0; j < T; ++j) {
+    if (tau[j] < best) {
+      best = tau[j];
+      mu = j;
     }
-    if (mu < 0 || best >= Tn) return 0;
+  }
+  return mu;
+}
+
+// Firings of one node until Tn, at most `budget` of them in this call.  The
+// fired channel and the woken ones take their Exp(1) draws from `draw(j,
+// E)` (computed on the spot by a thread, from a lane table by a warp).
+// Returns AEM_DONE, AEM_HEAVY (budget spent; state ready for a warp) or an
+// error.
+template <int KIND, typename Draw>
+__device__ __forceinline__ int aem_steps(int *u, const double *kf, double *a, double *tau,
+                                         uint32_t *c, double &t, uint32_t &nfired, double Tn,
+                                         const SgTables &tb, unsigned long long &fired,
+                                         int budget, Draw &&draw) {
+  using M = ModelTraits<KIND>;
+  constexpr int T = M::T;
+  const double inf = __longlong_as_double(0x7ff0000000000000ll);
+  for (int b = 0;; ++b) {
+    double best;
+    const int mu = aem_earliest<T>(tau, best);
+    if (mu < 0 || best >= Tn) return AEM_DONE;
     if (nfired >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+    if (b == budget) return AEM_HEAVY;
     ++nfired;
     t = best;
 #pragma unroll
@@ -518,22 +624,143 @@ __device__ __forceinline__ int aem_node_day(int *u, const double *kf, double *a,
         if (bad_rate(w)) return SG_ERR_RATE;
       }
       if (k == mu) {
+        // the fired channel always redraws
         a[k] = w;
         if (gt0(w)) {
           double E;
-          const int rc = aem_draw(c[k], node, (uint32_t)k, tag, k0, k1, E);
+          const int rc = draw(k, E);
           if (rc) return rc;
-          ++drawn;
           tau[k] = t + E / w;
         } else {
           tau[k] = inf;
         }
-      } else {
-        const int rc = aem_update(t, w, a[k], tau[k], c[k], node, (uint32_t)k, tag, k0, k1, drawn);
-        if (rc) return rc;
+      } else if (!(w == a[k])) {
+        if (gt0(a[k]) && gt0(w)) {
+          tau[k] = t + (a[k] / w) * (tau[k] - t);
+        } else if (gt0(w)) {
+          double E;
+          const int rc = draw(k, E);
+          if (rc) return rc;
+          tau[k] = t + E / w;
+        } else {
+          tau[k] = inf;
+        }
+        a[k] = w;
       }
     }
   }
+}
+
+// A node handed from its thread to a warp (all events method).
+template <int C, int NK, int T>
+struct AemSlot {
+  double t;
+  double kf[NK];
+  double a[T], tau[T];
+  uint32_t c[T];
+  uint32_t nfired;
+  int32_t node, rep, code;
+  int32_t u[C];
+};
+
+// Shared-memory slots for hand-offs (at most 24 KB, at most one per thread).
+template <int C, int NK, int T>
+struct AemSlots {
+  static constexpr int n = (int)(24576 / sizeof(AemSlot<C, NK, T>)) < kDayBlock
+                               ? (int)(24576 / sizeof(AemSlot<C, NK, T>))
+                               : kDayBlock;
+};
+
+// The rest of a heavy node-day by a whole warp.  Every channel's next draws
+// depend only on its counter, so lane l holds the Exp(1) value of draw
+// c_j + (l mod B) of channel j = l / B (B = 32 / T lanes per channel), all
+// computed at once; the firing loop runs on all lanes in step and takes a
+// channel's next value from its lane.  When a channel has used its B values
+// the table is recomputed from the current counters.  Same operations, in
+// the same order, as the thread path.
+template <int KIND>
+__device__ void aem_warp(AemSlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK,
+                                 ModelTraits<KIND>::T> &hs,
+                         double Tn, uint32_t k0, uint32_t k1, const SgTables &tb,
+                         unsigned long long &fired, unsigned long long &drawn) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NK = M::NK;
+  constexpr int B = 32 / T;
+  const int lane = threadIdx.x & 31;
+  const int jl = lane / B, il = lane - jl * B;
+  int u[C];
+  double kf[NK], a[T], tau[T];
+  uint32_t c[T];
+  int used[T];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = hs.u[p];
+#pragma unroll
+  for (int i = 0; i < NK; ++i) kf[i] = hs.kf[i];
+#pragma unroll
+  for (int j = 0; j < T; ++j) {
+    a[j] = hs.a[j];
+    tau[j] = hs.tau[j];
+    c[j] = hs.c[j];
+    used[j] = B;  // no table yet
+  }
+  double t = hs.t;
+  uint32_t nfired = hs.nfired;
+  const uint32_t node = (uint32_t)hs.node;
+  const uint32_t tag = (SG_STREAM_AEM << 24) | (uint32_t)hs.rep;
+  double myE = 0.0;
+  unsigned long long f = 0, dr = 0;
+  auto draw = [&](int j, double &E) -> int {
+    uint32_t cj = 0;
+    int uj = 0;
+#pragma unroll
+    for (int q = 0; q < T; ++q)
+      if (q == j) {
+        cj = c[q];
+        uj = used[q];
+      }
+    if (cj == 0xffffffffu) return SG_ERR_STEP_LIMIT;
+    if (uj == B) {
+      // recompute the table from every channel's current counter
+      if (jl < T) {
+        uint32_t cl = 0;
+#pragma unroll
+        for (int q = 0; q < T; ++q)
+          if (q == jl) cl = c[q];
+        const uint32_t ci = cl + (uint32_t)il;
+        // draws past the counter's end are never used (the counter check
+        // above stops first); compute something harmless for them
+        const U4 x = philox10(U4{ci < cl ? cl : ci, node, (uint32_t)jl, tag}, k0, k1);
+        myE = -log_pos(u01_open(x.x, x.y));
+      }
+#pragma unroll
+      for (int q = 0; q < T; ++q) used[q] = 0;
+      uj = 0;
+    }
+    E = __shfl_sync(0xffffffffu, myE, j * B + uj);
+#pragma unroll
+    for (int q = 0; q < T; ++q)
+      if (q == j) {
+        ++c[q];
+        ++used[q];
+      }
+    ++dr;
+    return 0;
+  };
+  const int rc = aem_steps<KIND>(u, kf, a, tau, c, t, nfired, Tn, tb, f, -1, draw);
+  if (lane == 0) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+#pragma unroll
+    for (int j = 0; j < T; ++j) {
+      hs.a[j] = a[j];
+      hs.tau[j] = tau[j];
+      hs.c[j] = c[j];
+    }
+    hs.code = rc < 0 ? rc : 0;
+    fired += f;
+    drawn += dr;
+  }
+  __syncwarp();
 }
 
 // One E1 event (exit, enter or internal transfer, Sec. 3.3) on a node whose
@@ -632,6 +859,8 @@ k_days(const SgTables tb, const DayArgs a) {
   using M = ModelTraits<KIND>;
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
   __shared__ HeavySlot<C, NK> s_heavy[AEM ? 1 : kDayBlock];
+  constexpr int kAemSlots = AEM ? AemSlots<C, NK, T>::n : 1;
+  __shared__ AemSlot<C, NK, T> s_aheavy[kAemSlots];
   __shared__ int s_nheavy;
   pdl_trigger();
   const int Nn = tb.n_nodes;
@@ -699,10 +928,8 @@ k_days(const SgTables tb, const DayArgs a) {
   const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
   for (int Td = a.T_begin; Td < a.T_end; ++Td) {
     const double Tn = (double)Td;
-    if constexpr (!AEM) {
-      if (threadIdx.x == 0) s_nheavy = 0;
-      __syncthreads();
-    }
+    if (threadIdx.x == 0) s_nheavy = 0;
+    __syncthreads();
     int my = -1;
     const bool emulated =
         !AEM && live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
@@ -719,9 +946,56 @@ k_days(const SgTables tb, const DayArgs a) {
     if (AEM && live && code == 0) {
       double kf[NK];
       M::prepare(v, tb.gdata, kf);
-      code = aem_node_day<KIND>(u, kf, ch_a, ch_tau, ch_c, Tn, (uint32_t)node,
-                                (SG_STREAM_AEM << 24) | (uint32_t)rep, a.k0, a.k1, tb, fired,
-                                drawn);
+      const uint32_t tag = (SG_STREAM_AEM << 24) | (uint32_t)rep;
+      code = aem_day_start<KIND>(u, kf, ch_a, ch_tau, ch_c, Tn, (uint32_t)node, tag, a.k0, a.k1,
+                                 tb, drawn);
+      double t = Tn - 1.0;
+      uint32_t nfired = 0;
+      if (code == 0) {
+        auto draw = [&](int j, double &E) -> int {
+          uint32_t cj = 0;
+#pragma unroll
+          for (int q = 0; q < T; ++q)
+            if (q == j) cj = ch_c[q];
+          const int rc = aem_draw(cj, (uint32_t)node, (uint32_t)j, tag, a.k0, a.k1, E);
+#pragma unroll
+          for (int q = 0; q < T; ++q)
+            if (q == j) ch_c[q] = cj;
+          if (rc == 0) ++drawn;
+          return rc;
+        };
+        const int r = aem_steps<KIND>(u, kf, ch_a, ch_tau, ch_c, t, nfired, Tn, tb, fired,
+                                      a.heavy_after, draw);
+        if (r == AEM_HEAVY) {
+          const int slot = atomicAdd(&s_nheavy, 1);
+          if (slot < kAemSlots) {
+            my = slot;
+            AemSlot<C, NK, T> &hs = s_aheavy[slot];
+            hs.t = t;
+#pragma unroll
+            for (int i = 0; i < NK; ++i) hs.kf[i] = kf[i];
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+              hs.a[j] = ch_a[j];
+              hs.tau[j] = ch_tau[j];
+              hs.c[j] = ch_c[j];
+            }
+            hs.nfired = nfired;
+            hs.node = node;
+            hs.rep = rep;
+            hs.code = 0;
+#pragma unroll
+            for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+          } else {
+            // no slot left: the thread finishes its node itself
+            const int r2 = aem_steps<KIND>(u, kf, ch_a, ch_tau, ch_c, t, nfired, Tn, tb, fired,
+                                           -1, draw);
+            if (r2 < 0) code = r2;
+          }
+        } else if (r < 0) {
+          code = r;
+        }
+      }
       if (code) bad_day = Td;
     }
     if (!AEM && live && code == 0 && !emulated) {
@@ -756,12 +1030,31 @@ k_days(const SgTables tb, const DayArgs a) {
       }
       if (code) bad_day = Td;
     }
+    __syncthreads();
     if constexpr (!AEM) {
-      __syncthreads();
       const int nh = s_nheavy;
       for (int h = warp; h < nh; h += nwarps)
         ssa_warp<KIND>(s_heavy[h], Tn, (uint32_t)Td, a.k0, a.k1, tb, fired, drawn);
-      __syncthreads();
+    } else {
+      const int nh = min(s_nheavy, kAemSlots);
+      for (int h = warp; h < nh; h += nwarps)
+        aem_warp<KIND>(s_aheavy[h], Tn, a.k0, a.k1, tb, fired, drawn);
+    }
+    __syncthreads();
+    if (AEM && my >= 0) {
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = s_aheavy[my].u[p];
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ch_a[j] = s_aheavy[my].a[j];
+        ch_tau[j] = s_aheavy[my].tau[j];
+        ch_c[j] = s_aheavy[my].c[j];
+      }
+      if (s_aheavy[my].code) {
+        code = s_aheavy[my].code;
+        bad_day = Td;
+      }
+      my = -1;
     }
     if (my >= 0) {
 #pragma unroll
@@ -812,6 +1105,35 @@ k_days(const SgTables tb, const DayArgs a) {
         a.aem_tau[j * total + gid] = ch_tau[j];
         a.aem_cnt[j * total + gid] = ch_c[j];
       }
+    }
+  }
+  if (a.e2_done) {
+    // the last block to finish a replicate's nodes runs its external
+    // transfers of T_end - 1 (threadfence-reduction pattern: no block waits)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    const long long g_lo = (long long)blockIdx.x * a.npb;
+    const long long g_hi = min(total, g_lo + a.npb) - 1;
+    for (int r = (int)(g_lo / Nn); r <= (int)(g_hi / Nn); ++r) {
+      if (threadIdx.x == 0) {
+        const long long b_first = (long long)r * Nn / a.npb;
+        const long long b_last = ((long long)(r + 1) * Nn - 1) / a.npb;
+        const int old = atomicAdd(&a.e2_done[r], 1);
+        s_last = old == (int)(b_last - b_first);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        long long w0 = a.e2_wb, w1 = a.e2_we;
+        if (a.slots > 1) {
+          w0 = a.wave_off[(long long)a.e2_day_index * a.slots + r];
+          w1 = a.wave_off[(long long)a.e2_day_index * a.slots + r + 1];
+        }
+        e2_rep_block<C>(tb, a, r, a.T_end - 1, w0, w1);
+        if (threadIdx.x == 0) a.e2_done[r] = 0;
+      }
+      __syncthreads();
     }
   }
   // one atomic per warp for the counters
@@ -881,7 +1203,6 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   __shared__ double s_prop[kE2Cap];
   __shared__ uint4 s_w[kE2Cap];
   __shared__ long long s_wave[kE2WaveCap + 1];
-  __shared__ int s_stop;
   pdl_trigger();
   const int rep = blockIdx.x;
   const int Nn = tb.n_nodes;
@@ -897,7 +1218,9 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   int *gstate = a.u + (long long)rep * Nn * C;
   int *state = SMEM_STATE ? s_state : gstate;
   bool waited = false;
-  if (threadIdx.x == 0) s_stop = 0;
+  // `bad`: this thread met an error; `stop`: the block's verdict, taken at a
+  // barrier (__syncthreads_or), so every thread leaves the loops together
+  bool bad = false, stop = false;
   const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
   const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
   unsigned long long applied = 0;
@@ -931,11 +1254,11 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
       // the first chunk is staged: now wait for the day kernel's state
       pdl_wait();
       waited = true;
-      if (*(volatile int32_t *)&a.err->code != 0) s_stop = 1;
+      if (threadIdx.x == 0 && *(volatile int32_t *)&a.err->code != 0) bad = true;
       if (SMEM_STATE) copy_words(s_state, gstate, Nn * C);
     }
-    __syncthreads();
-    if (s_stop) break;
+    stop = __syncthreads_or(bad);
+    if (stop) break;
     // waves w .. (staged) intersecting [pos, pend)
     long long wi = 0;
     while (wi < wn && s_wave[wi] < pend) {
@@ -956,7 +1279,7 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
                                        : (long long)round(s_prop[i] * (double)total);
         if (k < 0 || k > total) {
           report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, a.day, s_idx[i]);
-          s_stop = 1;
+          bad = true;
           continue;
         }
         int moved[C];
@@ -996,12 +1319,12 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
         }
         ++applied;
       }
-      __syncthreads();
-      if (s_stop) break;
+      stop = __syncthreads_or(bad);
+      if (stop) break;
       if (s_wave[wi + 1] <= pend) ++wi;
       else break;  // the wave continues in the next chunk
     }
-    if (s_stop) break;
+    if (stop) break;
     w += wi;
     pos = pend;
   }

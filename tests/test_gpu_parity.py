@@ -330,3 +330,25 @@ def test_sise_sp_replicates_and_sparse_tspan(orc, gpu):
                       "n_rep": 3, "u0": np.repeat(w.u0, 3, axis=0),
                       "v0": np.repeat(w.v0, 3, axis=0)})
     _compare(orc, gpu, w)
+
+
+@pytest.mark.parametrize("fused", [True, False], ids=["fused", "separate"])
+@pytest.mark.parametrize("tuning", [(1, 2), (48, 1), (128, 0)])
+def test_external_transfers_fused_or_separate(orc, gpu, fused, tuning):
+    # the day's external transfers run either at the end of the day kernel
+    # (last block of each replicate) or in their own kernel; with one node per
+    # block every replicate spans hundreds of blocks, with 48 a block spans a
+    # replicate boundary
+    w = W.config_sise3(n_nodes=350, days=60, gen_seed=41, n_rep=3, per_rep_events=True,
+                       median=50, sigma=1.0, hi=5000)
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == 0
+    m = gpu.Model(w)
+    m.set_fused_events(fused)
+    m.set_tuning(*tuning)
+    u0, v0, U, V = _dev(w)
+    rc, st, er = m.run(w.tspan, w.seed, w.n_rep, u0, v0, U, V)
+    assert np.array_equal(U.cpu().numpy(), U0)
+    assert np.array_equal(V.cpu().numpy().view(np.uint64), V0.view(np.uint64))
+    assert st["reactions"] == int(R0.sum())
+    m.close()
