@@ -335,12 +335,28 @@ typedef struct {
 
 int sg_set_output(sg_model *m, const sg_output *o);
 
-/* Where the external transfers of a day run.  enable = 1 (default): at the
- * end of the day kernel, by the last block to finish each replicate's nodes
- * (blocks count themselves off with an atomic after a device-wide fence; no
- * block ever waits for another), saving one kernel launch per day with
- * external transfers.  enable = 0: in a separate kernel, one block per
- * replicate.  Results are identical. */
+/* Persistent day loop (default off).  When the day kernel's grid fits on the
+ * device at once (cooperative launch), the whole run is one launch: each
+ * day's external transfers run inside it, between two grid-wide barriers
+ * (block counter and generation word in device memory, polled with a 20 s
+ * limit after which the run stops with SG_ERR_TIMEOUT), by the block that
+ * holds the replicate's first node.  Otherwise, and for models from
+ * transition strings, the run is split into day kernels and E2 kernels.
+ * enable = 0 (default) always splits: on the SISe benchmark workload the two
+ * grid barriers and the E2 block's unhidden event loads cost more per day
+ * (10.0 vs 7.9 ms per 365-day run) than the two launches they replace, which
+ * programmatic dependent launch already overlaps.  Results are identical. */
+int sg_set_persistent(sg_model *m, int enable);
+
+/* Where the external transfers of a day run.  enable = 0 (default): in a
+ * separate kernel, one block per replicate, which stages the day's events
+ * and their first random words while the day kernel is still running
+ * (programmatic dependent launch).  enable = 1: at the end of the day
+ * kernel, by the last block to finish each replicate's nodes (blocks count
+ * themselves off with an atomic after a device-wide fence; no block ever
+ * waits for another); one launch fewer per day, but the event loads are no
+ * longer hidden, and on the SISe benchmark workload this is slower (9.6 vs
+ * 8.0 ms per 365-day run).  Results are identical. */
 int sg_set_fused_events(sg_model *m, int enable);
 
 /* Select the solver of later sg_run calls (SG_SOLVER_SSM by default).

@@ -171,7 +171,7 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
            "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
            "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
-           "sg_set_fused_events"]
+           "sg_set_fused_events", "sg_set_persistent"]
 
 _lock = threading.Lock()
 _lib = None
@@ -238,6 +238,8 @@ def lib(path: str | None = None):
         L.sg_model_tables.restype = ctypes.c_int
         L.sg_set_fused_events.argtypes = [vp, ctypes.c_int]
         L.sg_set_fused_events.restype = ctypes.c_int
+        L.sg_set_persistent.argtypes = [vp, ctypes.c_int]
+        L.sg_set_persistent.restype = ctypes.c_int
         L.sg_gemm_bf16.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32, vp,
                                    i32, vp]
         L.sg_gemm_bf16.restype = ctypes.c_int
@@ -428,6 +430,13 @@ class Model:
             raise SimInfError(rc)
         self._out_refs = (u_values, v_values, prev_out)
         self.dense = bool(dense)
+
+    def set_persistent(self, enable=True):
+        """One cooperative launch for the whole run when it fits (default),
+        else day and E2 kernels; results are identical."""
+        rc = lib().sg_set_persistent(self._h, 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
 
     def set_fused_events(self, enable=True):
         """External transfers inside the day kernel (default) or in their

@@ -324,8 +324,11 @@ struct sg_model {
   // SG_GENERIC: the kernels compiled at run time for the parsed model
   JitKernels jit;
   // external transfers inside the day kernel (sg_set_fused_events)
-  bool fuse_e2 = true;
+  bool fuse_e2 = false;
   DevBuf<int32_t> e2_done;
+  // persistent day loop (sg_set_persistent) and its grid barrier words
+  bool persistent = false;
+  DevBuf<unsigned int> grid_bar;
 };
 
 extern "C" const char *sg_strerror(int code) {
@@ -512,6 +515,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->out_u_row.release(); m->out_v_row.release();
   jit_release(m->jit);
   m->e2_done.release();
+  m->grid_bar.release();
   if (m->h_err) cudaFreeHost(m->h_err);
   if (m->h_cnt) cudaFreeHost(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
@@ -643,6 +647,74 @@ static void launch_jit(cudaKernel_t k, unsigned grid, unsigned block, size_t sme
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelExC(&cfg, (const void *)k, args);
+}
+
+// Persistent day loop: one cooperative launch (every block resident) runs
+// every day, external transfers included.  Possible for the built-in kinds
+// when the grid fits on the device at once.
+template <int KIND>
+static bool coop_fits(bool aem, unsigned grid) {
+  int dev = 0, coop = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t e =
+      aem ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_days<KIND, true>, kDayBlock, 0)
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_days<KIND, false>, kDayBlock,
+                                                          0);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return coop != 0 && (long long)per_sm * sms >= (long long)grid;
+}
+
+template <int KIND>
+static void launch_days_coop(sg_model *m, const DayArgs &a, unsigned grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kDayBlock);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a.aem_tau)
+    cudaLaunchKernelEx(&cfg, k_days<KIND, true>, m->tb, a);
+  else
+    cudaLaunchKernelEx(&cfg, k_days<KIND, false>, m->tb, a);
+}
+
+static unsigned day_grid(const sg_model *m, const DayArgs &a) {
+  const long long units = (long long)m->tb.n_nodes * a.n_rep;
+  return (unsigned)std::max<long long>(1, (units + a.npb - 1) / a.npb);
+}
+
+// Whether the persistent form applies (built-in kind, grid resident at once).
+static bool persistent_fits(const sg_model *m, const DayArgs &a) {
+  const unsigned grid = day_grid(m, a);
+  const bool aem = a.aem_tau != nullptr;
+  switch (m->tb.kind) {
+    case SG_SIR: return coop_fits<SG_SIR>(aem, grid);
+    case SG_SIS: return coop_fits<SG_SIS>(aem, grid);
+    case SG_SISE: return coop_fits<SG_SISE>(aem, grid);
+    case SG_SISE3: return coop_fits<SG_SISE3>(aem, grid);
+    default: return false;
+  }
+}
+
+static void launch_days_persistent(sg_model *m, const DayArgs &a, cudaStream_t st) {
+  const unsigned grid = day_grid(m, a);
+  switch (m->tb.kind) {
+    case SG_SIR: launch_days_coop<SG_SIR>(m, a, grid, st); break;
+    case SG_SIS: launch_days_coop<SG_SIS>(m, a, grid, st); break;
+    case SG_SISE: launch_days_coop<SG_SISE>(m, a, grid, st); break;
+    default: launch_days_coop<SG_SISE3>(m, a, grid, st); break;
+  }
 }
 
 static void launch_days_kind(sg_model *m, const DayArgs &a, cudaStream_t st) {
@@ -951,6 +1023,24 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
       launch_days_kind(m, da, st);
       ++launches;
     }
+  } else if (Nn > 0 && days > 0 && m->persistent && persistent_fits(m, da)) {
+    // the whole run in one persistent launch
+    DayArgs dp = da;
+    dp.T_begin = t0 + 1;
+    dp.T_end = t_end + 1;
+    dp.finish_first = 0;
+    dp.finish_last = 1;
+    dp.grid_bar = m->grid_bar.p;
+    dp.n_blocks = (int32_t)std::max<long long>(1, ((long long)Nn * n_rep + da.npb - 1) / da.npb);
+    cudaMemsetAsync(m->grid_bar.p, 0, 2 * sizeof(unsigned int), st);
+    {
+      LaunchTimer lt(m, st, 0);
+      launch_days_persistent(m, dp, st);
+    }
+    ++launches;
+    for (int32_t d = 0; d < days; ++d)
+      waves += (int32_t)(P.e2_wave_off[(long long)(d + 1) * slots] -
+                         P.e2_wave_off[(long long)d * slots]);
   } else if (Nn > 0 && days > 0) {
     bool pending = false;  // the previous unit step still needs finishing
     int32_t d = 0;
@@ -1045,7 +1135,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     return rc;
   if (tb.kind == SG_SISE_SP && (rc = m->v2.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))))
     return rc;
-  if ((rc = m->e2_done.ensure((size_t)n_rep))) return rc;
+  if ((rc = m->e2_done.ensure((size_t)n_rep)) || (rc = m->grid_bar.ensure(2))) return rc;
   const bool aem = m->solver == SG_SOLVER_AEM;
   if (aem && m->emu_on) return SG_ERR_ARG;  // the emulator replaces direct-method days only
   if (aem) {
@@ -1110,6 +1200,8 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.e2_wb = da.e2_we = 0;
   da.e2_day_index = 0;
   da.e2_done = nullptr;
+  da.grid_bar = nullptr;
+  da.n_blocks = 0;
   da.aem_a = aem ? m->aem_a.p : nullptr;
   da.aem_tau = aem ? m->aem_tau.p : nullptr;
   da.aem_cnt = aem ? m->aem_cnt.p : nullptr;
@@ -1153,6 +1245,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                          m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p +
                          m->out_version * 0x100000001b3ull +
                          ((uint64_t)(uintptr_t)m->e2_done.p << 3) + (m->fuse_e2 ? 5 : 0) +
+                         ((uint64_t)(uintptr_t)m->grid_bar.p << 5) + (m->persistent ? 11 : 0) +
                          (aem ? 0x9e3779b97f4a7c15ull ^ (uint64_t)(uintptr_t)m->aem_tau.p ^
                                     ((uint64_t)(uintptr_t)m->aem_a.p << 1) ^
                                     ((uint64_t)(uintptr_t)m->aem_cnt.p << 2)
@@ -1522,6 +1615,8 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.e2_wb = da.e2_we = 0;
       da.e2_day_index = 0;
       da.e2_done = nullptr;
+      da.grid_bar = nullptr;
+      da.n_blocks = 0;
       const long long units = (long long)Nn * n_rep;
       const unsigned grid = (unsigned)std::max<long long>(1, (units + da.npb - 1) / da.npb);
       switch (k) {
@@ -1686,6 +1781,15 @@ extern "C" int sg_set_output(sg_model *m, const sg_output *o) {
   m->out = d;
   m->out_dense = o->dense != 0;
   m->out_cols = (sparse || prev) ? o->n_tspan : -1;
+  return SG_OK;
+}
+
+extern "C" int sg_set_persistent(sg_model *m, int enable) {
+  if (!m) return SG_ERR_ARG;
+  if ((enable != 0) != m->persistent) {
+    m->persistent = enable != 0;
+    m->graph_ok = false;
+  }
   return SG_OK;
 }
 

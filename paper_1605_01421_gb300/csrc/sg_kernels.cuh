@@ -180,7 +180,58 @@ struct DayArgs {
   long long e2_wb, e2_we;
   int32_t e2_day_index;
   int32_t *e2_done;
+  // persistent run (cooperative launch, every block resident): the days'
+  // external transfers run inside this launch between two grid barriers
+  // (arrival count, generation); null: not persistent
+  unsigned int *grid_bar;
+  int32_t n_blocks;
 };
+
+// %globaltimer (ns).
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A grid barrier must wait for the slowest block's whole day; a wait longer
+// than this is taken as a failure (SG_ERR_TIMEOUT) instead of a hang.
+constexpr unsigned long long kGridWaitNs = 20ull * 1000 * 1000 * 1000;
+
+// Grid-wide barrier for a cooperative launch (all blocks resident): thread 0
+// of each block reads the generation, fences, arrives; the last arrival
+// resets the count and advances the generation; the others poll the
+// generation with a time limit.  Returns false (the same in every thread of
+// the block) if this block gave up; the kernel must then leave.
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, int n_blocks, SgDevError *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = bar + 1;
+    const unsigned int g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == (unsigned int)n_blocks - 1u) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*gen == g) {
+        if (global_ns() - t0 > kGridWaitNs) {
+          ok = 0;
+          report(err, SG_ERR_TIMEOUT, -1, -1, -1, -1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
 
 // The external transfers (Sec. 3.3) of replicate `rep` at unit time T, wave by
 // wave, by one block (a block barrier between waves), on the replicate's
@@ -763,14 +814,41 @@ __device__ void aem_warp(AemSlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK,
   __syncwarp();
 }
 
+// The fields of one planned event and the first Philox block of its word
+// stream (a function of the seed, the list index and the replicate only), so
+// that they can be fetched and computed ahead of the event.
+struct E1Rec {
+  int type, n, shift;
+  uint32_t mask;
+  long long idx;
+  double prop;
+  U4 first;
+};
+
+__device__ __forceinline__ E1Rec load_e1(const SgTables &tb, const EvDev &ev, long long j, int rep,
+                                         uint32_t k0, uint32_t k1) {
+  E1Rec r;
+  r.type = ev.type[j];
+  r.mask = tb.Emask[ev.select[j]];
+  r.n = ev.n[j];
+  r.shift = ev.shift[j];
+  r.idx = ev.index[j];
+  r.prop = ev.proportion[j];
+  r.first = philox10(U4{0u, (uint32_t)(unsigned long long)r.idx,
+                        (uint32_t)((unsigned long long)r.idx >> 32),
+                        (SG_STREAM_EVENTS << 24) | (uint32_t)rep},
+                     k0, k1);
+  return r;
+}
+
 // One E1 event (exit, enter or internal transfer, Sec. 3.3) on a node whose
 // counts are in the calling thread's registers.  Returns 0 or an error.
 template <int C>
-__device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const EvDev &ev, long long j,
-                                        int rep, uint32_t k0, uint32_t k1) {
-  const int type = ev.type[j];
-  const uint32_t mask = tb.Emask[ev.select[j]];
-  const int n = ev.n[j];
+__device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const E1Rec &e, int rep,
+                                        uint32_t k0, uint32_t k1) {
+  const int type = e.type;
+  const uint32_t mask = e.mask;
+  const int n = e.n;
   if (type == SG_ENTER) {
     const int first = __ffs(mask) - 1;  // first selected compartment
 #pragma unroll
@@ -782,14 +860,14 @@ __device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const EvDev 
 #pragma unroll
   for (int p = 0; p < C; ++p)
     if ((mask >> p) & 1u) total += u[p];
-  const long long k = n > 0 ? (long long)n : (long long)round(ev.proportion[j] * (double)total);
+  const long long k = n > 0 ? (long long)n : (long long)round(e.prop * (double)total);
   if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
   int moved[C];
 #pragma unroll
   for (int p = 0; p < C; ++p) moved[p] = 0;
   if (k > 0) {
     WordStream ws;
-    ws.init(((uint64_t)k1 << 32) | k0, ev.index[j], rep);
+    ws.init_with_first(((uint64_t)k1 << 32) | k0, e.idx, rep, e.first);
     for (long long i = 0; i < k; ++i) {
       uint32_t x = ws.below((uint32_t)(total - i));
       bool taken = false;
@@ -809,7 +887,7 @@ __device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const EvDev 
 #pragma unroll
   for (int p = 0; p < C; ++p) u[p] -= moved[p];
   if (type == SG_EXIT) return 0;
-  const int q = ev.shift[j];  // internal transfer: validated q >= 0
+  const int q = e.shift;  // internal transfer: validated q >= 0
 #pragma unroll
   for (int dst = 0; dst < C; ++dst) {
     int add = 0;
@@ -931,6 +1009,12 @@ k_days(const SgTables tb, const DayArgs a) {
     if (threadIdx.x == 0) s_nheavy = 0;
     __syncthreads();
     int my = -1;
+    // the node's first E1 event of the day: fields and first random block
+    // fetched now, so that their latency overlaps the SSA
+    const int d = Td - a.t0 - 1;
+    const bool e1_today = live && code == 0 && next_day == d;
+    E1Rec pre;
+    if (e1_today) pre = load_e1(tb, a.ev, ecur, rep, a.k0, a.k1);
     const bool emulated =
         !AEM && live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
     if (emulated) {
@@ -1065,10 +1149,13 @@ k_days(const SgTables tb, const DayArgs a) {
       }
     }
     // this node's E1 events of day Td, in (time, type, list index) order
-    const int d = Td - a.t0 - 1;
-    if (live && code == 0 && next_day == d) {
+    if (e1_today && code == 0) {
+      bool first = true;
       while (ecur < eend && a.ev.e1_day[ecur] == d) {
-        const int rc = apply_e1<C>(u, tb, a.ev, ecur, rep, a.k0, a.k1);
+        const int rc = first ? apply_e1<C>(u, tb, pre, rep, a.k0, a.k1)
+                             : apply_e1<C>(u, tb, load_e1(tb, a.ev, ecur, rep, a.k0, a.k1),
+                                           rep, a.k0, a.k1);
+        first = false;
         if (rc) {
           code = rc;
           bad_day = Td;
@@ -1079,6 +1166,34 @@ k_days(const SgTables tb, const DayArgs a) {
         ++ecur;
       }
       next_day = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
+    }
+    if (a.grid_bar && a.wave_off) {
+      // persistent run: the day's external transfers between two grid
+      // barriers, by the block holding each replicate's first node, on the
+      // state in global memory
+      const long long wlo = a.wave_off[(long long)d * a.slots];
+      const long long whi = a.wave_off[(long long)(d + 1) * a.slots];
+      if (wlo < whi) {  // the same decision in every block
+        if (live) {
+#pragma unroll
+          for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+        }
+        __threadfence();
+        if (!grid_barrier(a.grid_bar, a.n_blocks, a.err)) break;
+        const long long g_lo = (long long)blockIdx.x * a.npb;
+        const long long g_hi = min(total, g_lo + a.npb) - 1;
+        for (int r = (int)((g_lo + Nn - 1) / Nn); (long long)r * Nn <= g_hi; ++r) {
+          // this block holds node 0 of replicate r
+          const long long k = (long long)d * a.slots + (a.slots > 1 ? r : 0);
+          e2_rep_block<C>(tb, a, r, Td, a.wave_off[k], a.wave_off[k + 1]);
+        }
+        __threadfence();
+        if (!grid_barrier(a.grid_bar, a.n_blocks, a.err)) break;
+        if (live) {
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = __ldcg(a.u + gid * C + p);
+        }
+      }
     }
     if (live && code == 0 && (Td + 1 < a.T_end || a.finish_last)) {
       code = finish_step<KIND>(Td, u, v, ld, tb, a, rep, node);

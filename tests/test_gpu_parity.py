@@ -332,19 +332,21 @@ def test_sise_sp_replicates_and_sparse_tspan(orc, gpu):
     _compare(orc, gpu, w)
 
 
-@pytest.mark.parametrize("fused", [True, False], ids=["fused", "separate"])
+@pytest.mark.parametrize("mode", ["persistent", "fused", "separate"])
 @pytest.mark.parametrize("tuning", [(1, 2), (48, 1), (128, 0)])
-def test_external_transfers_fused_or_separate(orc, gpu, fused, tuning):
-    # the day's external transfers run either at the end of the day kernel
-    # (last block of each replicate) or in their own kernel; with one node per
-    # block every replicate spans hundreds of blocks, with 48 a block spans a
-    # replicate boundary
+def test_external_transfers_every_schedule(orc, gpu, mode, tuning):
+    # the day's external transfers run inside one persistent launch between
+    # grid barriers, at the end of each day kernel (last block of each
+    # replicate) or in their own kernel; with one node per block every
+    # replicate spans hundreds of blocks, with 48 a block spans a replicate
+    # boundary
     w = W.config_sise3(n_nodes=350, days=60, gen_seed=41, n_rep=3, per_rep_events=True,
                        median=50, sigma=1.0, hi=5000)
     code, U0, V0, R0, err = orc.run(w)
     assert code == 0
     m = gpu.Model(w)
-    m.set_fused_events(fused)
+    m.set_persistent(mode == "persistent")
+    m.set_fused_events(mode == "fused")
     m.set_tuning(*tuning)
     u0, v0, U, V = _dev(w)
     rc, st, er = m.run(w.tspan, w.seed, w.n_rep, u0, v0, U, V)
@@ -352,3 +354,25 @@ def test_external_transfers_fused_or_separate(orc, gpu, fused, tuning):
     assert np.array_equal(V.cpu().numpy().view(np.uint64), V0.view(np.uint64))
     assert st["reactions"] == int(R0.sum())
     m.close()
+
+
+def test_persistent_and_split_runs_agree_on_the_benchmark_workload(orc, gpu):
+    # 1,600 SISe nodes x 365 days, ~200k events: one persistent launch and
+    # the split schedule give the oracle's trajectories, with graph replay
+    import torch
+    w = W.config_sise()
+    code, U0, V0, R0, err = orc.run(w)
+    s = torch.cuda.Stream()
+    for persistent in (True, False, True):
+        m = gpu.Model(w)
+        m.set_persistent(persistent)
+        u0, v0, U, V = _dev(w)
+        for _ in range(2):
+            U.fill_(-1)
+            rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=s)
+            s.synchronize()
+            assert np.array_equal(U.cpu().numpy(), U0)
+            assert np.array_equal(V.cpu().numpy().view(np.uint64), V0.view(np.uint64))
+            assert st["reactions"] == int(R0.sum())
+            assert (st["kernel_launches"] <= 3) == persistent
+        m.close()
