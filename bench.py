@@ -196,6 +196,24 @@ def time_oracle(w, budget_s=10.0, max_runs=50):
                       f"{t_total:.2f} s"}
 
 
+def max_over_ranks(total_ms, dist, device):
+    """The slowest rank's timed total (every rank gets it); the identity on
+    one process.  Replicas only: the ranks exchange nothing else."""
+    if not dist:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world, total_ms):
+    """Whole-job units per second: every rank ran `steps` steps of
+    `units_per_rank` units; the job took the slowest rank's time."""
+    return units_per_rank * steps * world / (total_ms * 1e-3)
+
+
 def bench_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -296,13 +314,9 @@ def bench_gpu(args):
     clocks = sampler.stop()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(total_ms, dist, dev)
     node_days = w.n_nodes * w.n_days * n_rep
-    value = node_days * args.steps * world / (total_ms * 1e-3)
+    value = job_throughput(node_days, args.steps, world, total_ms)
 
     # per-kernel device time in a second pass with timing events around every
     # launch (kept out of the timed region above)
