@@ -117,6 +117,13 @@ def lib():
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
             L.oracle_run.restype = ctypes.c_int
+            L.oracle_run_reps.argtypes = [
+                ctypes.POINTER(_Model), ctypes.POINTER(_Events),
+                ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+                ctypes.c_int, ctypes.c_int,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
+            L.oracle_run_reps.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -193,12 +200,14 @@ def _generic(w):
     return c.parsed.S, c.parsed.G, c.address
 
 
-def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
+def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None, rep0=0):
     """Run the oracle on a workload description (see
     ``paper_1605_01421_gb300.workloads.Workload``).
 
     ``solver`` (default ``w.solver``): 0 the direct-method split step
-    ('ssm'), 1 the all events method ('aem').
+    ('ssm'), 1 the all events method ('aem').  ``rep0`` > 0 runs replicates
+    rep0 .. rep0 + n_rep - 1 of the workload's w.n_rep (their own streams and
+    events) and returns only those.
 
     Returns ``(code, U, V, reactions, err)`` with U [R][M][Nn][C] int32,
     V [R][M][Nn][Nv] float64, reactions [R] int64 and err a dict.
@@ -206,8 +215,12 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
     L = lib()
     seed = w.seed if seed is None else seed
     n_rep = w.n_rep if n_rep is None else n_rep
-    u0 = _i32(w.u0 if u0 is None else u0)
-    v0 = _f64(w.v0 if v0 is None else v0)
+    if u0 is None:
+        u0 = w.u0[rep0:rep0 + n_rep] if rep0 else w.u0
+    if v0 is None:
+        v0 = w.v0[rep0:rep0 + n_rep] if rep0 else w.v0
+    u0 = _i32(u0)
+    v0 = _f64(v0)
     gen = _generic(w)
     S0, G0 = (gen[0], gen[1]) if gen else (w.S, w.G)
     S, G = _colmajor_i32(S0), _colmajor_i32(G0)
@@ -255,10 +268,18 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None):
     V = np.zeros((n_rep, M, n_nodes, int(w.n_v)), dtype=np.float64)
     reactions = np.zeros(n_rep, dtype=np.int64)
     err = _Error()
-    code = L.oracle_run(ctypes.byref(m), evp, _ptr(tspan), int(M), int(seed),
-                        int(n_rep), _ptr(u0), _ptr(v0) if v0.size else None,
-                        _ptr(U), _ptr(V) if V.size else None, _ptr(reactions),
-                        ctypes.byref(err))
+    if rep0 or (n_rep < w.n_rep and w.events is not None and w.events.get("rep") is not None):
+        # a range of the workload's replicates (events keep their replicate)
+        code = L.oracle_run_reps(ctypes.byref(m), evp, _ptr(tspan), int(M), int(seed),
+                                 int(rep0), int(n_rep), int(max(w.n_rep, rep0 + n_rep)), _ptr(u0),
+                                 _ptr(v0) if v0.size else None, _ptr(U),
+                                 _ptr(V) if V.size else None, _ptr(reactions),
+                                 ctypes.byref(err))
+    else:
+        code = L.oracle_run(ctypes.byref(m), evp, _ptr(tspan), int(M), int(seed),
+                            int(n_rep), _ptr(u0), _ptr(v0) if v0.size else None,
+                            _ptr(U), _ptr(V) if V.size else None, _ptr(reactions),
+                            ctypes.byref(err))
     del keep
     e = {"code": err.code, "rep": err.rep, "node": err.node,
          "event": err.event, "day": err.day}

@@ -770,12 +770,24 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
                const int *u0, const double *v0, int *U, double *V,
                int64_t *reactions, oracle_error *err)
 {
+    return oracle_run_reps(m, ev, tspan, n_tspan, seed, 0, n_rep, n_rep, u0,
+                           v0, U, V, reactions, err);
+}
+
+/* Replicates rep0 .. rep0 + n_rep - 1 of a run with n_rep_total replicates
+ * (each replicate's random streams and events depend on its index only);
+ * u0, v0, U, V, reactions hold those n_rep replicates. */
+int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
+                    const int *tspan, int n_tspan, uint64_t seed, int rep0,
+                    int n_rep, int n_rep_total, const int *u0, const double *v0,
+                    int *U, double *V, int64_t *reactions, oracle_error *err)
+{
     const int C = m->n_comp, Nv = m->n_v, Nn = m->n_nodes;
     const size_t ustride = (size_t)Nn * (size_t)C;
     const size_t vstride = (size_t)Nn * (size_t)Nv;
     ev_key *order = NULL;
     int64_t n_sorted = 0, e;
-    int rep, rc;
+    int r, rc;
     int *u = NULL;
     double *v = NULL, *v_new = NULL, *vtmp = NULL;
     double *aem_a = NULL, *aem_tau = NULL;
@@ -783,7 +795,11 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
     const size_t nch = (size_t)Nn * (size_t)m->n_trans;
 
     if (err) memset(err, 0, sizeof *err);
-    rc = validate(m, ev, tspan, n_tspan, n_rep, err);
+    if (rep0 < 0 || n_rep < 1 || rep0 + n_rep > n_rep_total) {
+        set_error(err, ORACLE_ERR_ARG, -1, -1, -1, -1);
+        return ORACLE_ERR_ARG;
+    }
+    rc = validate(m, ev, tspan, n_tspan, n_rep_total, err);
     if (rc) return rc;
 
     /* Events sorted by (time, type, list index): same-time events run in
@@ -818,12 +834,13 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
         return ORACLE_ERR_NOMEM;
     }
 
-    for (rep = 0; rep < n_rep; rep++) {
+    for (r = 0; r < n_rep; r++) {
+        const int rep = rep0 + r;
         int T, m_rec = 1, node;
         int64_t cursor = 0;
-        memcpy(u, u0 + (size_t)rep * ustride, ustride * sizeof *u);
-        if (vstride) memcpy(v, v0 + (size_t)rep * vstride, vstride * sizeof *v);
-        if (reactions) reactions[rep] = 0;
+        memcpy(u, u0 + (size_t)r * ustride, ustride * sizeof *u);
+        if (vstride) memcpy(v, v0 + (size_t)r * vstride, vstride * sizeof *v);
+        if (reactions) reactions[r] = 0;
         if (aem_a) {
             size_t q;
             for (q = 0; q < nch; q++) {
@@ -833,10 +850,10 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
             }
         }
         /* U[, 1] = u0 and V[, 1] = v0: the state at tspan[0]. */
-        memcpy(U + (size_t)rep * (size_t)n_tspan * ustride, u,
+        memcpy(U + (size_t)r * (size_t)n_tspan * ustride, u,
                ustride * sizeof *u);
         if (vstride)
-            memcpy(V + (size_t)rep * (size_t)n_tspan * vstride, v,
+            memcpy(V + (size_t)r * (size_t)n_tspan * vstride, v,
                    vstride * sizeof *v);
 
         for (T = tspan[0] + 1; T <= tspan[n_tspan - 1]; T++) {
@@ -860,7 +877,7 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
                     goto done;
                 }
             }
-            if (reactions) reactions[rep] += nr;
+            if (reactions) reactions[r] += nr;
 
             /* Events whose time has been reached: time <= T.  Reading: the
              * events dated tspan[0] or earlier run at the first unit of
@@ -917,10 +934,10 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
 
             /* (4) record when T reaches the next tspan point (Sec. 3.4.2) */
             if (m_rec < n_tspan && T == tspan[m_rec]) {
-                memcpy(U + ((size_t)rep * n_tspan + m_rec) * ustride, u,
+                memcpy(U + ((size_t)r * n_tspan + m_rec) * ustride, u,
                        ustride * sizeof *u);
                 if (vstride)
-                    memcpy(V + ((size_t)rep * n_tspan + m_rec) * vstride, v,
+                    memcpy(V + ((size_t)r * n_tspan + m_rec) * vstride, v,
                            vstride * sizeof *v);
                 m_rec++;
             }

@@ -107,5 +107,11 @@ int oracle_run(const oracle_model *m, const oracle_events *ev,
                const int *tspan, int n_tspan, uint64_t seed, int n_rep,
                const int *u0, const double *v0, int *U, double *V,
                int64_t *reactions, oracle_error *err);
+/* Replicates rep0 .. rep0 + n_rep - 1 of a run with n_rep_total replicates;
+ * u0, v0, U, V and reactions hold only those. */
+int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
+                    const int *tspan, int n_tspan, uint64_t seed, int rep0,
+                    int n_rep, int n_rep_total, const int *u0, const double *v0,
+                    int *U, double *V, int64_t *reactions, oracle_error *err);
 
 #endif

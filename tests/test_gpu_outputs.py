@@ -165,3 +165,49 @@ def test_run_host_without_dense_output(orc, gpu):
                None, None)
     assert np.array_equal(pout.cpu().numpy(), outputs.prevalence_counts(U0, [1], [0, 1]))
     m.close()
+
+
+def test_full_size_batched_on_sampled_replicates(orc, gpu):
+    # 256 replicates x 5,000 SISe3 nodes x 365 days, each replicate with its
+    # own ~175k events, tuned by the autotuner as the benchmark is; dense
+    # output off (it would be 11 GB), U_sparse holds every node at days 30 and
+    # 365, prevalence counters every day.  The oracle runs replicates 0, 101
+    # and 255 on their own; every replicate's population follows its events
+    import torch
+    w = W.config_batched()
+    R, M, Nn, C = w.n_rep, len(w.tspan), w.n_nodes, 6
+    m = gpu.Model(w)
+    cols = {30: np.arange(Nn * C, dtype=np.int32), 365: np.arange(Nn * C, dtype=np.int32)}
+    colptr, row = [0], []
+    for t in range(M):
+        row.extend(cols.get(t, []))
+        colptr.append(len(row))
+    up = (np.array(colptr, np.int64), np.array(row, np.int32))
+    uval = torch.full((R, len(row)), -1, dtype=torch.int32, device="cuda")
+    pout = torch.zeros((R, M, 4), dtype=torch.int64, device="cuda")
+    u0 = torch.as_tensor(np.ascontiguousarray(w.u0), device="cuda")
+    v0 = torch.as_tensor(np.ascontiguousarray(w.v0), device="cuda")
+    Ud = torch.empty((R, M, Nn, C), dtype=torch.int32, device="cuda")
+    Vd = torch.empty((R, M, Nn, 1), dtype=torch.float64, device="cuda")
+    m.autotune(w.tspan, w.seed, R, u0, v0, Ud, Vd)
+    del Ud, Vd
+    m.set_output(dense=False, n_tspan=M, u_pattern=up, u_values=uval,
+                 prevalence=([1, 3, 5], list(range(6))), prev_out=pout)
+    rc, st, er = m.run(w.tspan, w.seed, R, u0, v0, None, None)
+    assert st["node_days"] == R * Nn * 365
+    vals, prev = uval.cpu().numpy(), pout.cpu().numpy()
+    m.close()
+    for r in (0, 101, 255):
+        code, U0, V0, R0, err = orc.run(w, rep0=r, n_rep=1)
+        assert code == 0
+        assert np.array_equal(vals[r], outputs.sparse_values(U0, *up, C)[0])
+        assert np.array_equal(prev[r], outputs.prevalence_counts(U0, [1, 3, 5], range(6))[0])
+    # every replicate, every day: the population is u0 plus enters minus exits
+    ev = w.events
+    assert ev["n"].min() > 0 and ev["time"].min() >= 1
+    delta = np.zeros((R, M), np.int64)
+    for etype, sign in ((1, 1), (0, -1)):  # enter, exit
+        sel = ev["event"] == etype
+        np.add.at(delta, (ev["rep"][sel], ev["time"][sel]), sign * ev["n"][sel].astype(np.int64))
+    expected = w.u0.sum(axis=(1, 2)).astype(np.int64)[:, None] + np.cumsum(delta, axis=1)
+    assert np.array_equal(prev[:, :, 1], expected)

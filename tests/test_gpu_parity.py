@@ -376,3 +376,25 @@ def test_persistent_and_split_runs_agree_on_the_benchmark_workload(orc, gpu):
             assert st["reactions"] == int(R0.sum())
             assert (st["kernel_launches"] <= 3) == persistent
         m.close()
+
+
+def test_draw_limit_reports_the_same_error(orc, gpu):
+    # SIS with beta = gamma = 1e5: node 1 (S = I = 1000) flips between the
+    # two transitions at ~1e8 per day, so its first node-day needs more than
+    # 2^24 draws and both sides stop with SG_ERR_STEP_LIMIT at node 1, day 1
+    w = W.plain_model(W.SIS, [[10, 0], [1000, 1000], [5, 5]], np.arange(0, 3), [1e5, 1e5])
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == -9 and err["node"] == 1 and err["day"] == 1
+    m = gpu.Model(w)
+    u0, v0, U, V = _dev(w)
+    rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V, check=False)
+    assert rc == -9 and er["node"] == 1 and er["day"] == 1
+    m.close()
+
+
+def test_empty_model(orc, gpu):
+    w = W.plain_model(W.SIR, np.zeros((0, 3), np.int32), np.arange(0, 5), [0.5, 0.1])
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == 0 and U0.shape == (1, 5, 0, 3)
+    U1, V1, st = gpu.simulate(w)
+    assert U1.shape == (1, 5, 0, 3) and st["reactions"] == 0

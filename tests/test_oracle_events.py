@@ -217,3 +217,18 @@ def test_whole_pipeline_conserves_totals(orc):
         exits = ev["n"][sel & (ev["event"] == EXIT)].sum()
         assert tot[T] - tot[T - 1] == enters - exits
     assert np.all(U >= 0)
+
+
+def test_replicate_range_equals_the_slice_of_a_full_run(orc):
+    # each replicate's streams and events depend on its index only, so running
+    # replicates 1-2 or 3-4 alone gives the same trajectories as the full run
+    w = W.config_sise3(n_nodes=200, days=30, gen_seed=6, n_rep=5, per_rep_events=True,
+                       median=50, sigma=1.0, hi=5000)
+    code, U, V, R, err = orc.run(w)
+    assert code == 0
+    for r0 in (1, 3):
+        c2, U2, V2, R2, e2 = orc.run(w, rep0=r0, n_rep=2)
+        assert c2 == 0
+        assert np.array_equal(U2, U[r0:r0 + 2])
+        assert np.array_equal(V2.view(np.uint64), V[r0:r0 + 2].view(np.uint64))
+        assert np.array_equal(R2, R[r0:r0 + 2])
