@@ -44,6 +44,14 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal table figure)
 # logarithm (34), divide by the rate (1) and add to the time (1); a firing
 # compares the firing times (2), recomputes two rates (6) and rescales the
 # other dependent channel (4); a node-day adds the day-start rescale checks.
+# DRAM traffic of the day kernel per launch on the SISe workload, from the ncu
+# capture summarised in profiles/k_days_sise_1600x365_launches.md
+# (dram__bytes_read.sum + dram__bytes_write.sum, mean of the captured launches;
+# ncu flushes the caches between its passes, so it is the cold-cache figure).
+# It is reported only while the kernel sources hash to the captured ones.
+DAY_KERNEL_TRAFFIC = {"sources_sha1": "de676d70bcca63846a0f3324e7dc1fe176532e43",
+                      "bytes_per_launch": 665472}
+_KERNEL_SOURCES = ("sg_common.h", "sg_device.cuh", "sg_kernels.cuh")
 FP64_PER_DRAW_AEM = 42
 FP64_PER_REACTION_AEM = 12
 FP64_PER_NODE_DAY_AEM = 16
@@ -196,6 +204,21 @@ def time_oracle(w, budget_s=10.0, max_runs=50):
                       f"{t_total:.2f} s"}
 
 
+def _day_kernel_traffic(w, aem):
+    """The captured per-launch DRAM bytes of the day kernel, or None when the
+    workload, solver or kernel sources differ from the capture's."""
+    import hashlib
+    if aem or not w.name.startswith("SISe 1600 nodes x 365 days"):
+        return None
+    h = hashlib.sha1()
+    for f in _KERNEL_SOURCES:
+        with open(os.path.join(_ROOT, "paper_1605_01421_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != DAY_KERNEL_TRAFFIC["sources_sha1"]:
+        return None
+    return DAY_KERNEL_TRAFFIC["bytes_per_launch"]
+
+
 def max_over_ranks(total_ms, dist, device):
     """The slowest rank's timed total (every rank gets it); the identity on
     one process.  Replicas only: the ranks exchange nothing else."""
@@ -342,7 +365,8 @@ def bench_gpu(args):
     if dominant == "ssa":
         achieved = ssa_flops / (kt["ms_ssa"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "traffic": _day_kernel_traffic(w, aem),
                 "kernel": ("k_days<aem> (channels + post time step + recording)" if aem
                            else "k_days (SSA + post time step + recording)"),
                 "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s)",
@@ -377,6 +401,8 @@ def bench_gpu(args):
             t = time.perf_counter()
             m2 = binding.Model(w)  # tables + events: host validation, plan, upload
             m2.set_graphs(False)  # a single run: capturing a graph would not pay
+            if tuned:
+                m2.set_tuning(tuned[0], tuned[1])  # the split found for this workload
             m2.run_host(w.tspan, seed, n_rep, u0h, v0h, Uh, Vh, stream=stream)
             t_e2e += time.perf_counter() - t
             m2.close()

@@ -165,6 +165,10 @@ typedef struct {
   int64_t launches_ssa, launches_e1, launches_e2;
   double ms_mlp;          /* emulator kernels (features, GEMMs, sampling)    */
   int64_t launches_mlp;
+  double ms_host_plan;    /* host time of this call spent sorting, planning
+                             and uploading the events (0 when the plan of an
+                             earlier run was reused)                        */
+  double ms_host_total;   /* host time of the whole call                    */
 } sg_stats;
 
 /* Create a model from its tables (Sec. 3.2).  Validates the sizes against

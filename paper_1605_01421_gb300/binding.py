@@ -46,7 +46,7 @@ typedef unsigned long size_t;
 """
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", ARCH,
-              "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
+              "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-pthread",
               "-I" + _INCLUDE, "-I" + _CSRC, "-I" + _BUILD]
 
 OK = 0
@@ -122,7 +122,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB_PATH + ".tmp%d" % os.getpid()
-    cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-Xcompiler", "-fPIC", "-ldl"]
+    cmd = [nvcc, "-shared", ARCH, "-o", tmp] + objs + ["-Xcompiler", "-fPIC", "-ldl", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
@@ -157,7 +157,8 @@ class Stats(ctypes.Structure):
                 ("ms_ssa", ctypes.c_double), ("ms_e1", ctypes.c_double),
                 ("ms_e2", ctypes.c_double), ("launches_ssa", ctypes.c_int64),
                 ("launches_e1", ctypes.c_int64), ("launches_e2", ctypes.c_int64),
-                ("ms_mlp", ctypes.c_double), ("launches_mlp", ctypes.c_int64)]
+                ("ms_mlp", ctypes.c_double), ("launches_mlp", ctypes.c_int64),
+                ("ms_host_plan", ctypes.c_double), ("ms_host_total", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

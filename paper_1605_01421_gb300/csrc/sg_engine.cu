@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -260,11 +261,15 @@ struct sg_model {
   // planned events for the cached window
   bool plan_ok = false;
   Plan plan;
-  DevBuf<int8_t> e_type, e_shift;
-  DevBuf<uint8_t> e_select;
-  DevBuf<int32_t> e_node, e_dest, e_n, e1_day;
-  DevBuf<double> e_prop;
-  DevBuf<int64_t> e_index, wave_ev, wave_off, e1_node_off;
+  // the plan's device arrays: views into one arena (ev_arena), filled from
+  // one host staging buffer (ev_stage)
+  DevBuf<unsigned char> ev_arena;
+  std::vector<unsigned char> ev_stage;
+  int8_t *e_type = nullptr, *e_shift = nullptr;
+  uint8_t *e_select = nullptr;
+  int32_t *e_node = nullptr, *e_dest = nullptr, *e_n = nullptr, *e1_day = nullptr;
+  double *e_prop = nullptr;
+  int64_t *e_index = nullptr, *wave_ev = nullptr, *wave_off = nullptr, *e1_node_off = nullptr;
   int32_t heavy_after = -1;  // draws a thread takes before its warp takes
   int32_t npb = -1;          // nodes per block; -1 = chosen from the size
   // working memory
@@ -501,10 +506,8 @@ extern "C" int sg_model_tables(const sg_model *m, int32_t *S, int32_t *G) {
 extern "C" void sg_model_destroy(sg_model *m) {
   if (!m) return;
   m->ldata.release();
-  m->e_type.release(); m->e_shift.release(); m->e_select.release();
-  m->e_node.release(); m->e_dest.release(); m->e_n.release(); m->e1_day.release();
-  m->e1_node_off.release(); m->e1_cur.release();
-  m->e_prop.release(); m->e_index.release(); m->wave_ev.release(); m->wave_off.release();
+  m->ev_arena.release();
+  m->e1_cur.release();
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
@@ -566,31 +569,68 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
   Plan &P = m->plan;
   int rc = build_plan(m->ev, m->tb.n_nodes, t0, t_end, slots, &P);
   if (rc) return rc;
+  // every device array of the plan in one arena, filled in one host staging
+  // buffer and copied with one transfer
   const size_t n = P.order.size();
-  std::vector<int8_t> type(n), shift(n);
-  std::vector<uint8_t> sel(n);
-  std::vector<int32_t> nd(n), ds(n), cnt(n);
-  std::vector<double> prop(n);
-  std::vector<int64_t> idx(n);
-  const EventTable &ev = m->ev;
-  for (size_t i = 0; i < n; ++i) {
-    const int64_t e = P.order[i];
-    type[i] = (int8_t)ev.type[e];
-    shift[i] = (int8_t)(ev.shift[e] < 0 ? -1 : ev.shift[e]);
-    sel[i] = (uint8_t)ev.select[e];
-    nd[i] = ev.node[e];
-    ds[i] = ev.dest[e];
-    cnt[i] = ev.n[e];
-    prop[i] = ev.proportion[e];
-    idx[i] = e;
+  size_t off = 0;
+  auto place = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_type = place(n), o_shift = place(n), o_sel = place(n),
+               o_node = place(4 * n), o_dest = place(4 * n), o_cnt = place(4 * n),
+               o_prop = place(8 * n), o_idx = place(8 * n),
+               o_wev = place(8 * P.wave_ev.size()), o_woff = place(8 * P.e2_wave_off.size()),
+               o_e1d = place(4 * P.e1_day.size()), o_e1o = place(8 * P.e1_node_off.size());
+  const size_t total = std::max<size_t>(off, 256);
+  m->ev_stage.resize(total);
+  unsigned char *h = m->ev_stage.data();
+  {
+    int8_t *type = (int8_t *)(h + o_type), *shift = (int8_t *)(h + o_shift);
+    uint8_t *sel = h + o_sel;
+    int32_t *nd = (int32_t *)(h + o_node), *ds = (int32_t *)(h + o_dest),
+            *cnt = (int32_t *)(h + o_cnt);
+    double *prop = (double *)(h + o_prop);
+    int64_t *idx = (int64_t *)(h + o_idx);
+    const EventTable &ev = m->ev;
+    for (size_t i = 0; i < n; ++i) {
+      const int64_t e = P.order[i];
+      type[i] = (int8_t)ev.type[e];
+      shift[i] = (int8_t)(ev.shift[e] < 0 ? -1 : ev.shift[e]);
+      sel[i] = (uint8_t)ev.select[e];
+      nd[i] = ev.node[e];
+      ds[i] = ev.dest[e];
+      cnt[i] = ev.n[e];
+      prop[i] = ev.proportion[e];
+      idx[i] = e;
+    }
+    auto put = [&](size_t o, const void *src, size_t bytes) {
+      if (bytes) std::memcpy(h + o, src, bytes);
+    };
+    put(o_wev, P.wave_ev.data(), 8 * P.wave_ev.size());
+    put(o_woff, P.e2_wave_off.data(), 8 * P.e2_wave_off.size());
+    put(o_e1d, P.e1_day.data(), 4 * P.e1_day.size());
+    put(o_e1o, P.e1_node_off.data(), 8 * P.e1_node_off.size());
   }
-  if ((rc = upload(m->e_type, type)) || (rc = upload(m->e_shift, shift)) ||
-      (rc = upload(m->e_select, sel)) || (rc = upload(m->e_node, nd)) ||
-      (rc = upload(m->e_dest, ds)) || (rc = upload(m->e_n, cnt)) ||
-      (rc = upload(m->e_prop, prop)) || (rc = upload(m->e_index, idx)) ||
-      (rc = upload(m->wave_ev, P.wave_ev)) || (rc = upload(m->wave_off, P.e2_wave_off)) ||
-      (rc = upload(m->e1_day, P.e1_day)) || (rc = upload(m->e1_node_off, P.e1_node_off)))
-    return rc;
+  if ((rc = m->ev_arena.ensure(total))) return rc;
+  if (cudaMemcpy(m->ev_arena.p, h, total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    return SG_ERR_CUDA;
+  }
+  unsigned char *d = m->ev_arena.p;
+  m->e_type = (int8_t *)(d + o_type);
+  m->e_shift = (int8_t *)(d + o_shift);
+  m->e_select = d + o_sel;
+  m->e_node = (int32_t *)(d + o_node);
+  m->e_dest = (int32_t *)(d + o_dest);
+  m->e_n = (int32_t *)(d + o_cnt);
+  m->e_prop = (double *)(d + o_prop);
+  m->e_index = (int64_t *)(d + o_idx);
+  m->wave_ev = (int64_t *)(d + o_wev);
+  m->wave_off = (int64_t *)(d + o_woff);
+  m->e1_day = (int32_t *)(d + o_e1d);
+  m->e1_node_off = (int64_t *)(d + o_e1o);
   m->plan_ok = true;
   ++m->plan_version;
   return SG_OK;
@@ -778,10 +818,10 @@ static void launch_e2(sg_model *m, const EvArgs &ea, long long wb, long long we,
       attr_set |= 1ull << dev;
     }
     launch_pdl(k_events_e2<KIND, true>, (unsigned)n_rep, kE2Block, bytes, st, m->tb, ea,
-               (const int64_t *)m->wave_ev.p, wb, we, (const int64_t *)m->wave_off.p, day, slots);
+               (const int64_t *)m->wave_ev, wb, we, (const int64_t *)m->wave_off, day, slots);
   } else {
     launch_pdl(k_events_e2<KIND, false>, (unsigned)n_rep, kE2Block, 0, st, m->tb, ea,
-               (const int64_t *)m->wave_ev.p, wb, we, (const int64_t *)m->wave_off.p, day, slots);
+               (const int64_t *)m->wave_ev, wb, we, (const int64_t *)m->wave_off, day, slots);
   }
 }
 
@@ -796,7 +836,7 @@ static void launch_e2_kind(sg_model *m, const EvArgs &ea, long long wb, long lon
                            (int)kE2SmemStateMax);
     SgTables tb = m->tb;
     EvArgs a = ea;
-    const int64_t *wev = m->wave_ev.p, *woff = m->wave_off.p;
+    const int64_t *wev = m->wave_ev, *woff = m->wave_off;
     long long b = wb, e = we;
     int dd = day, sl = slots;
     void *args[] = {&tb, &a, &wev, &b, &e, &woff, &dd, &sl};
@@ -1120,11 +1160,14 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     if (dev != m->jit.device) return SG_ERR_ARG;  // kernels loaded on another device
   }
   cudaStream_t st = (cudaStream_t)stream;
+  const auto host_t0 = std::chrono::steady_clock::now();
   const int32_t t0 = tspan[0], t_end = tspan[n_tspan - 1];
   const int32_t days = t_end - t0;
   const int32_t slots = m->ev.per_rep ? n_rep : 1;
   int rc = ensure_plan(m, t0, t_end, slots);
   if (rc) return rc;
+  const double plan_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
   const Plan &P = m->plan;
 
   const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
@@ -1166,9 +1209,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     m->graph_ok = false;
   }
 
-  const EvDev evd{m->e_type.p, m->e_select.p, m->e_shift.p, m->e_node.p, m->e_dest.p,
-                  m->e_n.p,    m->e_prop.p,   m->e_index.p, m->e1_day.p,
-                  P.n_e1 > 0 ? m->e1_node_off.p : nullptr};
+  const EvDev evd{m->e_type, m->e_select, m->e_shift, m->e_node, m->e_dest,
+                  m->e_n,    m->e_prop,   m->e_index, m->e1_day,
+                  P.n_e1 > 0 ? m->e1_node_off : nullptr};
   DayArgs da;
   da.u = m->u.p;
   da.v = m->v.p;
@@ -1195,8 +1238,8 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     da.V = nullptr;
   }
   da.out = m->out;
-  da.wave_ev = m->wave_ev.p;
-  da.wave_off = m->wave_off.p;
+  da.wave_ev = m->wave_ev;
+  da.wave_off = m->wave_off;
   da.e2_wb = da.e2_we = 0;
   da.e2_day_index = 0;
   da.e2_done = nullptr;
@@ -1313,6 +1356,10 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     stats->kernel_launches = launches;
     stats->e2_waves = waves;
     stats->days = days;
+    stats->ms_host_plan = plan_ms;
+    stats->ms_host_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0)
+            .count();
   }
   const SgDevError &e = *m->h_err;
   if (e.code) {

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <numeric>
+#include <thread>
 
 namespace sg {
 
@@ -69,41 +70,62 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   };
   auto slot_of = [&](int64_t e) -> int64_t { return slots > 1 ? ev.rep[e] : 0; };
 
-  // 1. E1: stable counting sort by (slot, node), then (day, time, type,
-  //    index) inside each node's list.
-  std::vector<int64_t> e1_count(nk + 1, 0);
+  // The E1 and E2 parts write disjoint members of the plan and run in two
+  // threads.
   int64_t n_e1 = 0;
-  for (int64_t e = 0; e < n; ++e) {
-    if (ev.time[e] > t_end || ev.type[e] == SG_EXTERNAL_TRANSFER) continue;
-    const int64_t s = slot_of(e);
-    if (s >= slots) return SG_ERR_ARG;
-    ++e1_count[s * n_nodes + ev.node[e] + 1];
-    ++n_e1;
-  }
-  std::partial_sum(e1_count.begin(), e1_count.end(), e1_count.begin());
-  std::vector<int64_t> e1(n_e1);
-  {
-    std::vector<int64_t> fill(e1_count.begin(), e1_count.end() - 1);
+  std::vector<int64_t> e1, e2;
+  auto plan_e1 = [&]() -> int {
+    // 1. E1: ordered by (slot, node), then (day, time, type, list index), by
+    //    stable counting-sort passes over packed records taken in list order:
+    //    by type, then by day, then by (slot, node).  Every event of a day
+    //    d >= 1 has time t0 + 1 + d; day 0 also holds the earlier times, so
+    //    its runs are then ordered by time (stable, keeping type and index).
+    std::vector<int64_t> e1_count(nk + 1, 0);
     for (int64_t e = 0; e < n; ++e) {
       if (ev.time[e] > t_end || ev.type[e] == SG_EXTERNAL_TRANSFER) continue;
-      e1[fill[slot_of(e) * n_nodes + ev.node[e]]++] = e;
+      const int64_t s = slot_of(e);
+      if (s >= slots) return SG_ERR_ARG;
+      ++e1_count[s * n_nodes + ev.node[e] + 1];
+      ++n_e1;
     }
-  }
-  for (int64_t k = 0; k < nk; ++k) {
-    auto b = e1.begin() + e1_count[k], en = e1.begin() + e1_count[k + 1];
-    if (en - b > 1)
-      std::sort(b, en, [&](int64_t a, int64_t c) {
-        const int32_t da = day_of(a), dc = day_of(c);
-        if (da != dc) return da < dc;
-        if (ev.time[a] != ev.time[c]) return ev.time[a] < ev.time[c];
-        if (ev.type[a] != ev.type[c]) return ev.type[a] < ev.type[c];
-        return a < c;
-      });
-  }
-  P.e1_node_off = e1_count;
-  P.e1_day.resize(n_e1);
-  for (int64_t i = 0; i < n_e1; ++i) P.e1_day[i] = day_of(e1[i]);
-
+    std::partial_sum(e1_count.begin(), e1_count.end(), e1_count.begin());
+    struct Rec {
+      int64_t e;
+      int32_t day, type, key, time;
+    };
+    std::vector<Rec> ra, rb(n_e1);
+    ra.reserve(n_e1);
+    for (int64_t e = 0; e < n; ++e)
+      if (ev.time[e] <= t_end && ev.type[e] != SG_EXTERNAL_TRANSFER)
+        ra.push_back(Rec{e, day_of(e), ev.type[e], (int32_t)(slot_of(e) * n_nodes + ev.node[e]),
+                         ev.time[e]});
+    int64_t tc[5] = {0, 0, 0, 0, 0};  // by type (0 .. 3)
+    for (const Rec &r : ra) ++tc[r.type + 1];
+    for (int k = 0; k < 4; ++k) tc[k + 1] += tc[k];
+    for (const Rec &r : ra) rb[tc[r.type]++] = r;
+    std::vector<int64_t> dc((size_t)P.days + 1, 0);  // by day
+    for (const Rec &r : rb) ++dc[r.day + 1];
+    std::partial_sum(dc.begin(), dc.end(), dc.begin());
+    for (const Rec &r : rb) ra[dc[r.day]++] = r;
+    std::vector<int64_t> fill(e1_count.begin(), e1_count.end() - 1);  // by (slot, node)
+    for (const Rec &r : ra) rb[fill[r.key]++] = r;
+    for (int64_t k = 0; k < nk; ++k) {
+      auto lo = rb.begin() + e1_count[k], hi = rb.begin() + e1_count[k + 1];
+      auto z = lo;
+      while (z != hi && z->day == 0) ++z;
+      if (z - lo > 1)
+        std::stable_sort(lo, z, [](const Rec &x, const Rec &y) { return x.time < y.time; });
+    }
+    e1.resize(n_e1);
+    P.e1_day.resize(n_e1);
+    for (int64_t i = 0; i < n_e1; ++i) {
+      e1[i] = rb[i].e;
+      P.e1_day[i] = rb[i].day;
+    }
+    P.e1_node_off = e1_count;
+    return SG_OK;
+  };
+  auto plan_e2 = [&]() -> int {
   // 2. E2: stable bucketing by (day, slot), waves inside each bucket.
   std::vector<int64_t> count(nb + 1, 0);
   for (int64_t e = 0; e < n; ++e) {
@@ -121,7 +143,6 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
       bucketed[fill[(int64_t)day_of(e) * slots + slot_of(e)]++] = e;
     }
   }
-  std::vector<int64_t> e2;
   e2.reserve(bucketed.size());
   std::vector<int32_t> last_sample(n_nodes, 0), last_add(n_nodes, 0);
   std::vector<int64_t> stamp(n_nodes, -1);
@@ -130,8 +151,9 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   for (int64_t b = 0; b < nb; ++b) {
     tmp.assign(bucketed.begin() + count[b], bucketed.begin() + count[b + 1]);
     // list order is kept by the bucketing; only the first day can mix times
-    std::stable_sort(tmp.begin(), tmp.end(),
-                     [&](int64_t a, int64_t c) { return ev.time[a] < ev.time[c]; });
+    if (b < slots)
+      std::stable_sort(tmp.begin(), tmp.end(),
+                       [&](int64_t a, int64_t c) { return ev.time[a] < ev.time[c]; });
     wave_of.assign(tmp.size(), 0);
     int32_t n_w = 0;
     for (size_t i = 0; i < tmp.size(); ++i) {
@@ -161,6 +183,14 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     if (!tmp.empty()) P.day_has_e2[b / slots] = 1;
     P.max_waves_per_day = std::max(P.max_waves_per_day, n_w);
   }
+    return SG_OK;
+  };
+  int rc2 = SG_OK;
+  std::thread th([&] { rc2 = plan_e2(); });
+  const int rc1 = plan_e1();
+  th.join();
+  if (rc1) return rc1;
+  if (rc2) return rc2;
   P.n_e1 = n_e1;
   P.n_e2 = (int64_t)e2.size();
   P.n_waves = (int64_t)P.wave_ev.size() - 1;
