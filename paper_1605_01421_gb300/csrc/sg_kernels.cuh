@@ -390,6 +390,142 @@ struct HeavySlot {
   int32_t u[C];
 };
 
+// SISe3 heavy node-days, three draws per parallel round (see the comment
+// inside); returns false, doing nothing, for other kinds or another
+// dependency graph (the caller then takes the sequential loop).
+template <int KIND>
+__device__ __forceinline__ bool ssa_window3(int *u, double *w, const double *kf, double &t,
+                                            uint32_t &c, uint32_t &c0, double &nE, double &r2,
+                                            bool &have, unsigned long long &f, int &code,
+                                            uint32_t node, uint32_t Td, uint32_t tag, uint32_t k0,
+                                            uint32_t k1, long long Tkey, const SgTables &tb) {
+  if constexpr (KIND != SG_SISE3) {
+    return false;
+  } else {
+    using M = ModelTraits<KIND>;
+    constexpr int C = M::C, T = M::T;
+    if (!(tb.dep[0] == 3u && tb.dep[1] == 3u && tb.dep[2] == 12u && tb.dep[3] == 12u &&
+          tb.dep[4] == 48u && tb.dep[5] == 48u))
+      return false;
+    const int lane = threadIdx.x & 31;
+    // SISe3 with its block-diagonal dependency graph (each transition changes
+    // and is changed by its own age class only), so the rates of a state are
+    // the same however it was reached.  The states reachable within the next
+    // J = 3 draws are u plus at most two columns of S: the root (lane 0), one
+    // transition n (lanes 1 + n) and two transitions a <= b (lanes 7 +
+    // pair(a, b)), 28 in all.  Every lane evaluates its state's draw (draw
+    // c + depth): rates, lambda in index order, waiting-time divide and
+    // inversion; the walk then follows the fired transitions through the
+    // table.  Same operations and order as the sequential loop.
+    constexpr int J = 3;
+    constexpr int kT = ModelTraits<SG_SISE3>::T;  // 6
+    auto pair = [](int a, int b) { return a * kT - a * (a - 1) / 2 + (b - a); };
+    int depth = 0, ma = -1, mb = -1;  // this lane's state: root, {ma}, {ma, mb}
+    if (lane >= 1 && lane <= kT) {
+      depth = 1;
+      ma = lane - 1;
+    } else if (lane > kT && lane < 1 + kT + kT * (kT + 1) / 2) {
+      depth = 2;
+      int l = lane - 1 - kT, a = 0;
+      while (l >= kT - a) {
+        l -= kT - a;
+        ++a;
+      }
+      ma = a;
+      mb = a + l;
+    }
+    bool done = false;
+    while (!done && code == 0) {
+      if (!have || c + (uint32_t)J - c0 > 32u) {
+        c0 = c;
+        const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+        nE = -log_pos(u01_open(x.x, x.y));
+        r2 = u01_open(x.z, x.w);
+        have = true;
+      }
+      int us[C];
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        int x = u[p];
+        if (ma >= 0) x += tb.S[ma][p];
+        if (mb >= 0) x += tb.S[mb][p];
+        us[p] = x;
+      }
+      double ws[T];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ws[j] = M::rate_k(j, us, kf, tb.gdata);
+        bad = bad || bad_rate(ws[j]);
+      }
+      const int src = (int)(c - c0) + depth;  // lane holding draw c + depth
+      const double E = __shfl_sync(0xffffffffu, nE, src);
+      const double R2 = __shfl_sync(0xffffffffu, r2, src);
+      double lam = ws[0];
+#pragma unroll
+      for (int j = 1; j < T; ++j) lam = lam + ws[j];
+      const double tau = E / lam;
+      const double target = lam * R2;
+      // inversion exactly as fire(): running sum over the positive rates
+      double cum = 0.0;
+      int nsel = -1, last = -1;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        if (nsel < 0 && gt0(ws[j])) {
+          cum = last < 0 ? ws[j] : cum + ws[j];
+          last = j;
+          if (le_nonneg(target, cum)) nsel = j;
+        }
+      }
+      if (nsel < 0) nsel = last;
+      const unsigned pos_mask = __ballot_sync(0xffffffffu, gt0(lam));
+      const unsigned bad_mask = __ballot_sync(0xffffffffu, bad);
+      int L = 0, n1 = -1, j = 0;
+      for (; j < J; ++j) {
+        if (j > 0 && ((bad_mask >> L) & 1u)) {
+          code = SG_ERR_RATE;  // the transition into this state gave a bad rate
+          break;
+        }
+        if (!((pos_mask >> L) & 1u)) {
+          done = true;  // nothing can fire: jump to Tn
+          break;
+        }
+        if (c >= SG_MAX_DRAWS) {
+          code = SG_ERR_STEP_LIMIT;
+          break;
+        }
+        const double tauL = __shfl_sync(0xffffffffu, tau, L);
+        const int n = __shfl_sync(0xffffffffu, nsel, L);
+        ++c;
+        const double tt = t + tauL;
+        if (order_key(tt) >= Tkey) {
+          done = true;
+          break;
+        }
+        t = tt;
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] += tb.S[n][p];
+        ++f;
+        if (j == 0) {
+          n1 = n;
+          L = 1 + n;
+        } else if (j == 1) {
+          L = 1 + kT + (n1 <= n ? pair(n1, n) : pair(n, n1));
+        }
+      }
+      if (!done && code == 0) {
+        // j == J: a new window starts from the state after J transitions
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          w[k] = M::rate_k(k, u, kf, tb.gdata);
+          if (bad_rate(w[k])) code = SG_ERR_RATE;
+        }
+      }
+    }
+    return true;
+  }
+}
+
 // Direct SSA of one heavy node by a whole warp.  The draws depend only on
 // (seed, replicate, node, day, draw index), so lane l computes the Philox
 // words, uniforms and logarithm of draw c0 + l for 32 draws at once; the
@@ -508,7 +644,8 @@ __device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> 
         }
       }
     }
-  } else {
+  } else if (!ssa_window3<KIND>(u, w, kf, t, c, c0, nE, r2, have, f, code, node, Td, tag, k0,
+                                 k1, Tkey, tb)) {
   for (;;) {
     double lam = w[0];
 #pragma unroll
