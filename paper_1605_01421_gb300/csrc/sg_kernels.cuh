@@ -526,6 +526,180 @@ __device__ __forceinline__ bool ssa_window3(int *u, double *w, const double *kf,
   }
 }
 
+// Speculative window for heavy node-days of models from transition strings,
+// whose dependency graph is complete (the parser derives it from what each
+// propensity reads, so recomputing the rates G marks after a transition gives
+// the same rates as recomputing every rate from the counts).  The states reachable
+// within the next J draws are u plus a multiset of at most J - 1 columns of
+// S; lane l holds one such multiset (sorted transition indices a_1 <= ... ),
+// with J the largest for which they fit in a warp (T = 3: 4; T = 4..6: 3;
+// T = 7..31: 2).  Every lane evaluates its state's draw (draw c + depth):
+// rates from the counts, lambda in index order, waiting-time divide and
+// inversion; the walk then follows the fired transitions, finding the lane
+// of the state reached with a ballot, so J draws cost one parallel round
+// instead of J dependent rate updates and divides.  Same operations and
+// order as the sequential loop.  (SISe3 has a dedicated window with an
+// arithmetic walk, ssa_window3.)  Returns false, doing nothing, for other
+// kinds (the caller then takes the sequential loop).
+template <int KIND>
+__device__ __forceinline__ bool ssa_window(int *u, double *w, const double *kf, double &t,
+                                           uint32_t &c, uint32_t &c0, double &nE, double &r2,
+                                           bool &have, unsigned long long &f, int &code,
+                                           uint32_t node, uint32_t Td, uint32_t tag, uint32_t k0,
+                                           uint32_t k1, long long Tkey, const SgTables &tb) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T;
+  if constexpr (KIND != SG_GENERIC || T < 3 || T > 31) {
+    return false;
+  } else {
+    constexpr int J = T == 3 ? 4 : (T <= 6 ? 3 : 2);
+    constexpr int D = J - 1;  // largest multiset held by a lane
+    const int lane = threadIdx.x & 31;
+    // this lane's multiset: enumerate by depth, then lexicographically
+    int depth = 0, a[D > 0 ? D : 1];
+#pragma unroll
+    for (int i = 0; i < D; ++i) a[i] = -1;
+    {
+      int l = lane, d = 0, cur[D > 0 ? D : 1];
+      bool found = false;
+      // depth 0: lane 0
+      if (l == 0) {
+        found = true;
+      } else {
+        l -= 1;
+        for (d = 1; d <= D && !found; ++d) {
+          // multisets of size d in lexicographic order
+#pragma unroll
+          for (int i = 0; i < D; ++i) cur[i] = 0;
+          for (;;) {
+            if (l == 0) {
+              found = true;
+              depth = d;
+#pragma unroll
+              for (int i = 0; i < D; ++i) a[i] = i < d ? cur[i] : -1;
+              break;
+            }
+            --l;
+            // next non-decreasing tuple of length d over 0..T-1
+            int i = d - 1;
+            while (i >= 0 && cur[i] == T - 1) --i;
+            if (i < 0) break;
+            const int v = cur[i] + 1;
+            for (int k = i; k < d; ++k) cur[k] = v;
+          }
+        }
+      }
+      if (!found) depth = -1;  // a spare lane: evaluates nothing used
+    }
+    const int ev_depth = depth < 0 ? 0 : depth;
+    bool done = false;
+    while (!done && code == 0) {
+      if (!have || c + (uint32_t)J - c0 > 32u) {
+        c0 = c;
+        const U4 x = philox10(U4{c0 + (uint32_t)lane, node, Td, tag}, k0, k1);
+        nE = -log_pos(u01_open(x.x, x.y));
+        r2 = u01_open(x.z, x.w);
+        have = true;
+      }
+      int us[C];
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        int x = u[p];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+          if (a[i] >= 0) x += tb.S[a[i]][p];
+        us[p] = x;
+      }
+      double ws[T];
+      bool bad = false;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        ws[j] = M::rate_k(j, us, kf, tb.gdata);
+        bad = bad || bad_rate(ws[j]);
+      }
+      const int src = (int)(c - c0) + ev_depth;  // lane holding draw c + depth
+      const double E = __shfl_sync(0xffffffffu, nE, src);
+      const double R2 = __shfl_sync(0xffffffffu, r2, src);
+      double lam = ws[0];
+#pragma unroll
+      for (int j = 1; j < T; ++j) lam = lam + ws[j];
+      const double tau = E / lam;
+      const double target = lam * R2;
+      // inversion exactly as fire(): running sum over the positive rates
+      double cum = 0.0;
+      int nsel = -1, last = -1;
+#pragma unroll
+      for (int j = 0; j < T; ++j) {
+        if (nsel < 0 && gt0(ws[j])) {
+          cum = last < 0 ? ws[j] : cum + ws[j];
+          last = j;
+          if (le_nonneg(target, cum)) nsel = j;
+        }
+      }
+      if (nsel < 0) nsel = last;
+      const unsigned pos_mask = __ballot_sync(0xffffffffu, gt0(lam));
+      const unsigned bad_mask = __ballot_sync(0xffffffffu, bad);
+      int L = 0, j = 0;
+      int path[D > 0 ? D : 1];  // sorted transitions fired in this round
+#pragma unroll
+      for (int i = 0; i < D; ++i) path[i] = -1;
+      for (; j < J; ++j) {
+        if (j > 0 && ((bad_mask >> L) & 1u)) {
+          code = SG_ERR_RATE;  // the transition into this state gave a bad rate
+          break;
+        }
+        if (!((pos_mask >> L) & 1u)) {
+          done = true;  // nothing can fire: jump to Tn
+          break;
+        }
+        if (c >= SG_MAX_DRAWS) {
+          code = SG_ERR_STEP_LIMIT;
+          break;
+        }
+        const double tauL = __shfl_sync(0xffffffffu, tau, L);
+        const int n = __shfl_sync(0xffffffffu, nsel, L);
+        ++c;
+        const double tt = t + tauL;
+        if (order_key(tt) >= Tkey) {
+          done = true;
+          break;
+        }
+        t = tt;
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] += tb.S[n][p];
+        ++f;
+        if (j + 1 < J) {
+          // insert n into the sorted path, then find the lane holding it
+          int x = n;
+#pragma unroll
+          for (int i = 0; i < D; ++i) {
+            if (i <= j && path[i] >= 0 && path[i] > x) {
+              const int y = path[i];
+              path[i] = x;
+              x = y;
+            } else if (i == j) {
+              path[i] = x;
+            }
+          }
+          bool match = depth == j + 1;
+#pragma unroll
+          for (int i = 0; i < D; ++i) match = match && a[i] == path[i];
+          L = __ffs(__ballot_sync(0xffffffffu, match)) - 1;
+        }
+      }
+      if (!done && code == 0) {
+        // j == J: a new window starts from the state after J transitions
+#pragma unroll
+        for (int k = 0; k < T; ++k) {
+          w[k] = M::rate_k(k, u, kf, tb.gdata);
+          if (bad_rate(w[k])) code = SG_ERR_RATE;
+        }
+      }
+    }
+    return true;
+  }
+}
+
 // Direct SSA of one heavy node by a whole warp.  The draws depend only on
 // (seed, replicate, node, day, draw index), so lane l computes the Philox
 // words, uniforms and logarithm of draw c0 + l for 32 draws at once; the
@@ -645,7 +819,9 @@ __device__ void ssa_warp(HeavySlot<ModelTraits<KIND>::C, ModelTraits<KIND>::NK> 
       }
     }
   } else if (!ssa_window3<KIND>(u, w, kf, t, c, c0, nE, r2, have, f, code, node, Td, tag, k0,
-                                 k1, Tkey, tb)) {
+                                 k1, Tkey, tb) &&
+             !ssa_window<KIND>(u, w, kf, t, c, c0, nE, r2, have, f, code, node, Td, tag, k0,
+                               k1, Tkey, tb)) {
   for (;;) {
     double lam = w[0];
 #pragma unroll
