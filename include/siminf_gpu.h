@@ -429,6 +429,40 @@ int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t ldb, int32_
                  int32_t N, int32_t K, const float *bias, int32_t act, float *C32,
                  int32_t ldc32, void *C16, int32_t ldc16, void *stream);
 
+/* C = act(A8 . B8^T * a_scale * b_scale[n] + bias) with FP8 E4M3 operands
+ * on the tensor cores (tcgen05.mma kind::f8f6f4, FP32 accumulation in tensor
+ * memory).  A8: M x K, B8: N x K, bytes, row-major with K contiguous (K % 16
+ * == 0, lda and ldb multiples of 16, 16-byte aligned rows); a_scale scales
+ * the whole of A, b_scale (N floats) each row of B (dequantisation factors).
+ * Outputs (any may be NULL, not all): C32 (FP32, before the activation),
+ * C16 (BF16, after it), C8 (E4M3 bytes of the activated value times
+ * c8_inv_scale, rounded to nearest even and saturated to +-448).  act: 0
+ * identity, 1 GELU (tanh form).  Device pointers; the call waits for its
+ * stream.  SG_ERR_TIMEOUT if a tensor-core wait gave up. */
+int sg_gemm_fp8(const void *A8, int32_t lda, const void *B8, int32_t ldb, int32_t M, int32_t N,
+                int32_t K, float a_scale, const float *b_scale, const float *bias, int32_t act,
+                float *C32, int32_t ldc32, void *C16, int32_t ldc16, void *C8, int32_t ldc8,
+                float c8_inv_scale, void *stream);
+
+/* The same layer with BF16 operands (as sg_gemm_bf16) whose only output is
+ * C8: E4M3 bytes of act(A . Bt^T + bias) times c8_inv_scale, rounded to
+ * nearest even and saturated to +-448 (the input layer of an FP8 chain).
+ * Device pointers; the call waits for its stream. */
+int sg_gemm_bf16_to_fp8(const void *A, int32_t lda, const void *Bt, int32_t ldb, int32_t M,
+                        int32_t N, int32_t K, const float *bias, int32_t act, void *C8,
+                        int32_t ldc8, float c8_inv_scale, void *stream);
+
+/* FP8 quantisation helpers (device pointers, each waits for its stream):
+ *   sg_quant_fp8_rows: per row r of W (rows x cols, FP32): scale[r] = max |w|
+ *     / 448 (1 for a zero row), W8 = e4m3(w / scale[r]) (nearest even,
+ *     saturated);
+ *   sg_quant_fp8_bf16: out8[i] = e4m3(x[i] * inv_scale) for BF16 x;
+ *   sg_absmax_bf16:    *out = max_i |x[i]| for BF16 x. */
+int sg_quant_fp8_rows(const float *W, int32_t rows, int32_t cols, void *W8, float *scale,
+                      void *stream);
+int sg_quant_fp8_bf16(const void *x, int64_t n, float inv_scale, void *out8, void *stream);
+int sg_absmax_bf16(const void *x, int64_t n, float *out, void *stream);
+
 /* ---- Learned one-day emulator (an extension of the method: the paper has
  * no emulator).  For SISe3 nodes inside a validity range, a small MLP
  * predicts the distribution of each age class's one-day increment of I
@@ -481,6 +515,16 @@ int sg_emu_sample(const float *logits, int32_t ldl, const int32_t *u, const int3
  * [phi_lo, phi_hi] fall back to the SSA.  enable = 0 turns it off. */
 int sg_emulator_set(sg_model *m, const void *const *W, const float *const *b, int32_t max_herd,
                     double phi_lo, double phi_hi, int enable);
+
+/* FP8 inference for the emulator set with sg_emulator_set: layers 2-4 run on
+ * E4M3 operands (sg_gemm_fp8): W8[l] (E4M3 bytes, out x in, as W of layer l
+ * + 1) with per-row scales w_scale[l], and the input activations of layers
+ * 2-4 quantised with the static scales act_scale[0..2] (each = calibrated max
+ * |activation| / 448); layer 1 stays BF16 and writes E4M3 directly.  Device
+ * pointers (act_scale: 3 host floats), caller-owned, must outlive the runs.
+ * enable = 0 returns to BF16.  SG_ERR_ARG without an emulator. */
+int sg_emulator_set_fp8(sg_model *m, const void *const *W8, const float *const *w_scale,
+                        const float *act_scale, int enable);
 
 /* Device-side primitives, exported for parity checks of the random stream
  * and arithmetic (each fills a caller-owned device buffer on `stream` and

@@ -172,7 +172,8 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
            "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
            "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
-           "sg_set_fused_events", "sg_set_persistent"]
+           "sg_set_fused_events", "sg_set_persistent", "sg_gemm_fp8", "sg_quant_fp8_rows",
+           "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8", "sg_gemm_bf16_to_fp8"]
 
 _lock = threading.Lock()
 _lib = None
@@ -255,11 +256,22 @@ def lib(path: str | None = None):
         L.sg_emu_sample.argtypes = [vp, i32, vp, vp, i64, i32, u64, i32, vp, vp]
         L.sg_emulator_set.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, f64,
                                       f64, ctypes.c_int]
+        L.sg_gemm_fp8.argtypes = [vp, i32, vp, i32, i32, i32, i32, f32, vp, vp, i32, vp, i32,
+                                  vp, i32, vp, i32, f32, vp]
+        L.sg_gemm_bf16_to_fp8.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32,
+                                          f32, vp]
+        L.sg_quant_fp8_rows.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.sg_quant_fp8_bf16.argtypes = [vp, i64, f32, vp, vp]
+        L.sg_absmax_bf16.argtypes = [vp, i64, vp, vp]
+        L.sg_emulator_set_fp8.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                          ctypes.POINTER(f32), ctypes.c_int]
         L.sg_set_neighbors.argtypes = [vp, vp, vp, vp]
         L.sg_set_neighbors.restype = ctypes.c_int
         for nm in ("sg_mlp_ce_loss", "sg_gelu_backward", "sg_transpose_bf16",
                    "sg_colsum_bf16", "sg_adam_step", "sg_emu_features", "sg_emu_targets",
-                   "sg_emu_sample", "sg_emulator_set"):
+                   "sg_emu_sample", "sg_emulator_set", "sg_gemm_fp8", "sg_quant_fp8_rows",
+                   "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8",
+                   "sg_gemm_bf16_to_fp8"):
             getattr(L, nm).restype = ctypes.c_int
         _lib = L
         return L
@@ -547,6 +559,22 @@ class Model:
         if rc:
             raise SimInfError(rc)
 
+    def set_emulator_fp8(self, emu, enable=True):
+        """Switch the emulator's layers 2-4 to E4M3 operands (the emulator
+        must be quantised: emulator.Emulator.quantize_fp8); enable=False
+        returns to BF16."""
+        vp = ctypes.c_void_p
+        if enable:
+            W8 = (vp * 3)(*[ctypes.c_void_p(t.data_ptr()) for t in emu.W8])
+            sc = (vp * 3)(*[ctypes.c_void_p(t.data_ptr()) for t in emu.wscale])
+            act = (ctypes.c_float * 3)(*[float(a) for a in emu.act_scale])
+            self._emu_fp8_ref = emu
+        else:
+            W8 = sc = act = None
+        rc = lib().sg_emulator_set_fp8(self._h, W8, sc, act, 1 if enable else 0)
+        if rc:
+            raise SimInfError(rc)
+
     def set_graphs(self, enable=True):
         rc = lib().sg_set_graphs(self._h, 1 if enable else 0)
         if rc:
@@ -607,6 +635,85 @@ def gemm_bf16(A, Bt, bias=None, act=0, out32=True, out16=False, stream=None):
     if rc:
         raise SimInfError(rc)
     return C32, C16
+
+
+def gemm_fp8(A8, a_scale, B8, b_scale, bias=None, act=0, out32=True, out16=False,
+             out8_inv_scale=None, stream=None):
+    """C = act(A8 @ B8.T * a_scale * b_scale[n] + bias) with E4M3 operands
+    on the tensor cores.  A8 (M, K) and B8 (N, K) are contiguous uint8 CUDA
+    tensors holding E4M3 bytes, b_scale (N,) FP32; returns (C32, C16, C8),
+    each None unless requested (C8: E4M3 bytes of the activated value times
+    out8_inv_scale)."""
+    import torch
+    M, K = A8.shape
+    N = B8.shape[0]
+    dev = A8.device
+    C32 = torch.empty((M, N), dtype=torch.float32, device=dev) if out32 else None
+    C16 = torch.empty((M, N), dtype=torch.bfloat16, device=dev) if out16 else None
+    C8 = torch.empty((M, N), dtype=torch.uint8, device=dev) if out8_inv_scale else None
+    rc = lib().sg_gemm_fp8(
+        _dev_ptr(A8, torch.uint8, (M, K), "A8"), int(K),
+        _dev_ptr(B8, torch.uint8, (N, K), "B8"), int(K), int(M), int(N), int(K),
+        float(a_scale), _dev_ptr(b_scale, torch.float32, (N,), "b_scale"),
+        _dev_ptr(bias, torch.float32, (N,), "bias") if bias is not None else None, int(act),
+        _dev_ptr(C32), int(N), _dev_ptr(C16), int(N), _dev_ptr(C8), int(N),
+        float(out8_inv_scale or 0.0), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return C32, C16, C8
+
+
+def gemm_bf16_to_fp8(A, Bt, inv_scale, bias=None, act=0, stream=None):
+    """E4M3 bytes (uint8) of act(A @ Bt.T + bias) * inv_scale for BF16 A (M,
+    K) and Bt (N, K)."""
+    import torch
+    M, K = A.shape
+    N = Bt.shape[0]
+    C8 = torch.empty((M, N), dtype=torch.uint8, device=A.device)
+    rc = lib().sg_gemm_bf16_to_fp8(
+        _dev_ptr(A, torch.bfloat16, (M, K), "A"), int(K),
+        _dev_ptr(Bt, torch.bfloat16, (N, K), "Bt"), int(K), int(M), int(N), int(K),
+        _dev_ptr(bias, torch.float32, (N,), "bias") if bias is not None else None, int(act),
+        _dev_ptr(C8), int(N), float(inv_scale), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return C8
+
+
+def quant_fp8_rows(W, stream=None):
+    """Per-row E4M3 quantisation of an FP32 matrix: (W8 uint8, scale FP32)
+    with W ~ W8 * scale[:, None]."""
+    import torch
+    rows, cols = W.shape
+    W8 = torch.empty((rows, cols), dtype=torch.uint8, device=W.device)
+    sc = torch.empty((rows,), dtype=torch.float32, device=W.device)
+    rc = lib().sg_quant_fp8_rows(_dev_ptr(W, torch.float32, (rows, cols), "W"), int(rows),
+                                 int(cols), _dev_ptr(W8), _dev_ptr(sc), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return W8, sc
+
+
+def quant_fp8_bf16(x, inv_scale, stream=None):
+    """E4M3 bytes of x * inv_scale for a BF16 tensor x."""
+    import torch
+    out = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    rc = lib().sg_quant_fp8_bf16(_dev_ptr(x, torch.bfloat16), x.numel(), float(inv_scale),
+                                 _dev_ptr(out), _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return out
+
+
+def absmax_bf16(x, stream=None):
+    """max |x| of a BF16 tensor, as a Python float."""
+    import torch
+    out = torch.zeros((1,), dtype=torch.float32, device=x.device)
+    rc = lib().sg_absmax_bf16(_dev_ptr(x, torch.bfloat16), x.numel(), _dev_ptr(out),
+                              _stream_handle(stream))
+    if rc:
+        raise SimInfError(rc)
+    return float(out.item())
 
 
 def fp64_fma_probe(iters=20000, stream=None):

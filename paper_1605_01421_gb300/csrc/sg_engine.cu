@@ -307,6 +307,12 @@ struct sg_model {
   double emu_phi_lo = 0.0, emu_phi_hi = 0.0;
   uint64_t emu_version = 0;
   DevBuf<__nv_bfloat16> emu_feat, emu_ha, emu_hb;
+  // FP8 inference of layers 2-4 (sg_emulator_set_fp8)
+  bool emu_fp8 = false;
+  const uint8_t *emu_W8[3] = {};
+  const float *emu_wscale[3] = {};
+  float emu_act_scale[3] = {1.0f, 1.0f, 1.0f};
+  DevBuf<uint8_t> emu_h8a, emu_h8b;
   DevBuf<float> emu_logits;
   DevBuf<int32_t> emu_flag, emu_delta;
   // SISe_sp neighbour lists and the second phi buffer of the coupled step
@@ -511,6 +517,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
+  m->emu_h8a.release(); m->emu_h8b.release();
   m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
   m->nb_ptr.release(); m->nb_idx.release(); m->nb_dist.release(); m->v2.release();
   m->aem_a.release(); m->aem_tau.release(); m->aem_cnt.release();
@@ -1000,6 +1007,8 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
       const __nv_bfloat16 *in = m->emu_feat.p;
       int kin = kEmuIn;
       __nv_bfloat16 *outs[3] = {m->emu_ha.p, m->emu_hb.p, m->emu_ha.p};
+      uint8_t *outs8[3] = {m->emu_h8a.p, m->emu_h8b.p, m->emu_h8a.p};
+      const bool f8 = m->emu_fp8;
       for (int l = 0; l < 4; ++l) {
         GemmArgs g{};
         g.A = in;
@@ -1013,9 +1022,24 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
         g.act = l < 3 ? 1 : 0;
         g.C32 = l < 3 ? nullptr : m->emu_logits.p;
         g.ldc32 = kEmuOut;
-        g.C16 = l < 3 ? outs[l] : nullptr;
+        g.C16 = l < 3 && !f8 ? outs[l] : nullptr;
         g.ldc16 = kEmuHidden;
         g.err = nullptr;
+        if (f8) {
+          // layer 1 reads BF16 features and writes E4M3; layers 2-4 read E4M3
+          if (l > 0) {
+            g.f8 = 1;
+            g.A8 = outs8[l - 1];
+            g.B8 = m->emu_W8[l - 1];
+            g.a_scale = m->emu_act_scale[l - 1];
+            g.b_scale = m->emu_wscale[l - 1];
+          }
+          if (l < 3) {
+            g.C8 = outs8[l];
+            g.ldc8 = kEmuHidden;
+            g.c8_inv_scale = 1.0f / m->emu_act_scale[l];
+          }
+        }
         {
           LaunchTimer lt(m, st, 3);
           gemm_bf16(g, st);
@@ -1192,6 +1216,8 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
         (rc = m->emu_ha.ensure(units * kEmuHidden)) ||
         (rc = m->emu_hb.ensure(units * kEmuHidden)) ||
+        (m->emu_fp8 && ((rc = m->emu_h8a.ensure(units * kEmuHidden)) ||
+                        (rc = m->emu_h8b.ensure(units * kEmuHidden)))) ||
         (rc = m->emu_logits.ensure(units * kEmuOut)) || (rc = m->emu_flag.ensure(units)) ||
         (rc = m->emu_delta.ensure(units * 4)) || (rc = gemm_prepare()))
       return rc;
@@ -1883,6 +1909,30 @@ extern "C" int sg_emulator_set(sg_model *m, const void *const *W, const float *c
   m->emu_phi_lo = phi_lo;
   m->emu_phi_hi = phi_hi;
   m->emu_on = true;
+  ++m->emu_version;
+  m->graph_ok = false;
+  return SG_OK;
+}
+
+extern "C" int sg_emulator_set_fp8(sg_model *m, const void *const *W8,
+                                   const float *const *w_scale, const float *act_scale,
+                                   int enable) {
+  if (!m) return SG_ERR_ARG;
+  if (!enable) {
+    m->emu_fp8 = false;
+    ++m->emu_version;
+    m->graph_ok = false;
+    return SG_OK;
+  }
+  if (!m->emu_on || !W8 || !w_scale || !act_scale) return SG_ERR_ARG;
+  for (int l = 0; l < 3; ++l) {
+    if (!W8[l] || !w_scale[l] || ((uintptr_t)W8[l] & 15) != 0 || !(act_scale[l] > 0.0f))
+      return SG_ERR_ARG;
+    m->emu_W8[l] = (const uint8_t *)W8[l];
+    m->emu_wscale[l] = w_scale[l];
+    m->emu_act_scale[l] = act_scale[l];
+  }
+  m->emu_fp8 = true;
   ++m->emu_version;
   m->graph_ok = false;
   return SG_OK;

@@ -4,6 +4,7 @@
 // sampling).  The emulator is an extension of the method, not part of the
 // paper.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,11 +57,18 @@ __device__ __forceinline__ float gelu(float x) {
 // (4 per stage, K = 16 each) and commits them to the stage's mbarrier; in the
 // epilogue warp w reads TMEM lane quarter w % 4 (32 tile rows), columns of
 // half w / 4 of the tile.
+//
+// F8: A and B are FP8 E4M3 bytes instead (K = 128 per stage, the same 128
+// bytes per row; tcgen05.mma kind::f8f6f4 with K = 32 per instruction, the
+// same 32 bytes), and the accumulator is scaled by a_scale * b_scale[n].
+// Optional outputs: FP32 before the activation, BF16 after it, FP8 E4M3
+// after it (scaled by c8_inv_scale, saturated to the finite range).
 constexpr int kGemmThreads = 256;
-template <int BN>
+template <int BN, bool F8>
 __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  constexpr uint32_t kAStage = kBM * kBK * 2;  // 16 KB
+  constexpr int kStageK = F8 ? 2 * kBK : kBK;    // elements of K per stage
+  constexpr uint32_t kAStage = kBM * kBK * 2;  // 16 KB (128 bytes per row)
   constexpr uint32_t kBStage = BN * kBK * 2;
   unsigned char *sA[2] = {smem, smem + kAStage};
   unsigned char *sB[2] = {smem + 2 * kAStage, smem + 2 * kAStage + kBStage};
@@ -81,8 +89,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
   __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  constexpr uint32_t idesc = tc::idesc_bf16_f32(kBM, BN);
-  const int stages = (g.K + kBK - 1) / kBK;
+  constexpr uint32_t idesc = F8 ? tc::idesc_e4m3_f32(kBM, BN) : tc::idesc_bf16_f32(kBM, BN);
+  const int stages = (g.K + kStageK - 1) / kStageK;
   uint32_t uses[2] = {0, 0};
   bool ok = true;
 
@@ -90,20 +98,29 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
   // (cp.async) for stage s into buffer s & 1, rows past M / N and columns
   // past K are zero-filled.
   auto load_stage = [&](int s) {
-    const int b = s & 1, k0 = s * kBK;
+    const int b = s & 1, k0 = s * kStageK;
+    constexpr int kChunk = F8 ? 16 : 8;  // elements per 16-byte chunk
     const uint32_t a0 = tc::smem_u32(sA[b]), b0 = tc::smem_u32(sB[b]);
     for (int idx = tid; idx < kBM * 8; idx += kGemmThreads) {
       const int r = idx >> 3, kg = idx & 7;
-      const int m = m0 + r, k = k0 + kg * 8;
+      const int m = m0 + r, k = k0 + kg * kChunk;
       const bool in = m < g.M && k < g.K;
-      const __nv_bfloat16 *src = in ? g.A + (long long)m * g.lda + k : g.A;
+      const void *src;
+      if constexpr (F8)
+        src = in ? (const void *)(g.A8 + (long long)m * g.lda + k) : (const void *)g.A8;
+      else
+        src = in ? (const void *)(g.A + (long long)m * g.lda + k) : (const void *)g.A;
       cp_async16(a0 + stage_off(r, kg), src, in ? 16 : 0);
     }
     for (int idx = tid; idx < BN * 8; idx += kGemmThreads) {
       const int r = idx >> 3, kg = idx & 7;
-      const int n = n0 + r, k = k0 + kg * 8;
+      const int n = n0 + r, k = k0 + kg * kChunk;
       const bool in = n < g.N && k < g.K;
-      const __nv_bfloat16 *src = in ? g.Bt + (long long)n * g.ldb + k : g.Bt;
+      const void *src;
+      if constexpr (F8)
+        src = in ? (const void *)(g.B8 + (long long)n * g.ldb + k) : (const void *)g.B8;
+      else
+        src = in ? (const void *)(g.Bt + (long long)n * g.ldb + k) : (const void *)g.Bt;
       cp_async16(b0 + stage_off(r, kg), src, in ? 16 : 0);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
@@ -124,7 +141,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
         // two core matrices along K per MMA: +256 bytes per K step of 16
         const uint64_t ad = tc::smem_desc(a0 + kk * 256, 128, 1024);
         const uint64_t bd = tc::smem_desc(b0 + kk * 256, 128, 1024);
-        tc::mma_bf16(tmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+        if constexpr (F8)
+          tc::mma_e4m3(tmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
+        else
+          tc::mma_bf16(tmem, ad, bd, idesc, (s > 0 || kk > 0) ? 1u : 0u);
       }
       tc::mma_commit(&bar[b]);
     }
@@ -168,6 +188,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
       const int nb = n0 + c;
+      if constexpr (F8) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          v[i] *= g.a_scale * ((nb + i < g.N) ? __ldg(g.b_scale + nb + i) : 0.0f);
+      }
       if (g.bias) {
         if (nb + 16 <= g.N && (((uintptr_t)(g.bias + nb)) & 15) == 0) {
 #pragma unroll
@@ -193,18 +218,42 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
           for (int i = 0; i < 16 && nb + i < g.N; ++i) dst[i] = v[i];
         }
       }
+      if (g.C16 || g.C8) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (g.act == 1) v[i] = gelu(v[i]);
+      }
       if (g.C16) {
         uint32_t packed[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-          const float x0 = g.act == 1 ? gelu(v[i]) : v[i];
-          const float x1 = g.act == 1 ? gelu(v[i + 1]) : v[i + 1];
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i], v[i + 1]);
           packed[i / 2] = *reinterpret_cast<const uint32_t *>(&h2);
         }
         uint4 *sp = reinterpret_cast<uint4 *>(stage + lr * kPitch + c * 2);
         sp[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         sp[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      }
+      if (g.C8 && row < g.M) {
+        // 16 E4M3 values of this row, one 16-byte store when it fits
+        uint32_t packed[4];
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) {
+          const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+              make_float2(v[i] * g.c8_inv_scale, v[i + 1] * g.c8_inv_scale), __NV_SATFINITE,
+              __NV_E4M3);
+          const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+              make_float2(v[i + 2] * g.c8_inv_scale, v[i + 3] * g.c8_inv_scale), __NV_SATFINITE,
+              __NV_E4M3);
+          packed[i / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+        uint8_t *dst = g.C8 + (long long)row * g.ldc8 + nb;
+        if (nb + 16 <= g.N && (((uintptr_t)dst) & 15) == 0) {
+          *reinterpret_cast<uint4 *>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        } else {
+          const uint8_t *bytes = reinterpret_cast<const uint8_t *>(packed);
+          for (int i = 0; i < 16 && nb + i < g.N; ++i) dst[i] = bytes[i];
+        }
       }
     }
     if (g.C16) {
@@ -252,18 +301,19 @@ int gemm_err_buf(int **out) {
   return SG_OK;
 }
 
-template <int BN>
+template <int BN, bool F8>
 void launch_gemm(const GemmArgs &g, cudaStream_t st) {
   const size_t smem = 2 * ((size_t)kBM * kBK * 2 + (size_t)BN * kBK * 2);
   static unsigned long long attr_set = 0;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 64 && !((attr_set >> dev) & 1ull)) {
-    cudaFuncSetAttribute(k_gemm_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_gemm_tc<BN, F8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
     attr_set |= 1ull << dev;
   }
   const dim3 grid((unsigned)((g.M + kBM - 1) / kBM), (unsigned)((g.N + BN - 1) / BN));
-  k_gemm_tc<BN><<<grid, kGemmThreads, smem, st>>>(g);
+  k_gemm_tc<BN, F8><<<grid, kGemmThreads, smem, st>>>(g);
 }
 
 }  // namespace
@@ -272,21 +322,35 @@ namespace sg {
 
 int gemm_bf16(const GemmArgs &g0, cudaStream_t st) {
   GemmArgs g = g0;
-  if (g.M < 0 || g.N < 0 || g.K < 0 || (g.K % 8) != 0 || g.lda < g.K || g.ldb < g.K ||
-      (g.lda % 8) != 0 || (g.ldb % 8) != 0 || !g.A || !g.Bt || (!g.C32 && !g.C16) ||
-      (((uintptr_t)g.A | (uintptr_t)g.Bt) & 15) != 0)
+  const bool f8 = g.f8 != 0;
+  const int align = f8 ? 16 : 8;  // elements per 16 bytes
+  const void *A = f8 ? (const void *)g.A8 : (const void *)g.A;
+  const void *B = f8 ? (const void *)g.B8 : (const void *)g.Bt;
+  if (g.M < 0 || g.N < 0 || g.K < 0 || (g.K % align) != 0 || g.lda < g.K || g.ldb < g.K ||
+      (g.lda % align) != 0 || (g.ldb % align) != 0 || !A || !B ||
+      (!g.C32 && !g.C16 && !g.C8) || (((uintptr_t)A | (uintptr_t)B) & 15) != 0 ||
+      (f8 && !g.b_scale) || (g.C8 && g.ldc8 < g.N))
     return SG_ERR_ARG;
   if (g.M == 0 || g.N == 0) return SG_OK;
   if (!g.err) {
     int rc = gemm_err_buf(&g.err);
     if (rc) return rc;
   }
-  if (g.N <= 64)
-    launch_gemm<64>(g, st);
-  else if (g.N <= 128)
-    launch_gemm<128>(g, st);
-  else
-    launch_gemm<256>(g, st);
+  if (f8) {
+    if (g.N <= 64)
+      launch_gemm<64, true>(g, st);
+    else if (g.N <= 128)
+      launch_gemm<128, true>(g, st);
+    else
+      launch_gemm<256, true>(g, st);
+  } else {
+    if (g.N <= 64)
+      launch_gemm<64, false>(g, st);
+    else if (g.N <= 128)
+      launch_gemm<128, false>(g, st);
+    else
+      launch_gemm<256, false>(g, st);
+  }
   return SG_OK;
 }
 
@@ -331,6 +395,62 @@ extern "C" int sg_gemm_bf16(const void *A, int32_t lda, const void *Bt, int32_t 
   g.ldc32 = ldc32;
   g.C16 = (__nv_bfloat16 *)C16;
   g.ldc16 = ldc16;
+  g.err = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = sg::gemm_bf16(g, st);
+  if (rc) return rc;
+  return sg::gemm_check(st);
+}
+
+extern "C" int sg_gemm_bf16_to_fp8(const void *A, int32_t lda, const void *Bt, int32_t ldb,
+                                   int32_t M, int32_t N, int32_t K, const float *bias,
+                                   int32_t act, void *C8, int32_t ldc8, float c8_inv_scale,
+                                   void *stream) {
+  GemmArgs g{};
+  g.A = (const __nv_bfloat16 *)A;
+  g.lda = lda;
+  g.Bt = (const __nv_bfloat16 *)Bt;
+  g.ldb = ldb;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.bias = bias;
+  g.act = act;
+  g.C8 = (uint8_t *)C8;
+  g.ldc8 = ldc8;
+  g.c8_inv_scale = c8_inv_scale;
+  g.err = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int rc = sg::gemm_bf16(g, st);
+  if (rc) return rc;
+  return sg::gemm_check(st);
+}
+
+extern "C" int sg_gemm_fp8(const void *A8, int32_t lda, const void *B8, int32_t ldb, int32_t M,
+                           int32_t N, int32_t K, float a_scale, const float *b_scale,
+                           const float *bias, int32_t act, float *C32, int32_t ldc32,
+                           void *C16, int32_t ldc16, void *C8, int32_t ldc8,
+                           float c8_inv_scale, void *stream) {
+  GemmArgs g{};
+  g.f8 = 1;
+  g.A8 = (const uint8_t *)A8;
+  g.lda = lda;
+  g.B8 = (const uint8_t *)B8;
+  g.ldb = ldb;
+  g.M = M;
+  g.N = N;
+  g.K = K;
+  g.a_scale = a_scale;
+  g.b_scale = b_scale;
+  g.bias = bias;
+  g.act = act;
+  g.C32 = C32;
+  g.ldc32 = ldc32;
+  g.C16 = (__nv_bfloat16 *)C16;
+  g.ldc16 = ldc16;
+  g.C8 = (uint8_t *)C8;
+  g.ldc8 = ldc8;
+  g.c8_inv_scale = c8_inv_scale;
   g.err = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   const int rc = sg::gemm_bf16(g, st);
@@ -410,6 +530,50 @@ __global__ void k_transpose(const __nv_bfloat16 *__restrict__ src, int rows, int
     const int c = c0 + i, r = r0 + threadIdx.x;
     if (r < rows && c < cols) dst[(long long)c * rows + r] = tile[threadIdx.x][i];
   }
+}
+
+// FP8 quantisation.  Per row of W (rows x cols, FP32): scale = max |w| /
+// 448 (the largest finite E4M3 value; 1 for a zero row), W8 = e4m3(w /
+// scale) rounded to nearest even and saturated.  One block per row.
+__global__ void k_quant_rows_fp8(const float *__restrict__ W, int rows, int cols, uint8_t *W8,
+                                 float *scale) {
+  __shared__ float s_max[8];
+  const int r = blockIdx.x;
+  const float *w = W + (long long)r * cols;
+  float m = 0.0f;
+  for (int k = threadIdx.x; k < cols; k += blockDim.x) m = fmaxf(m, fabsf(w[k]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float mx = 0.0f;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) mx = fmaxf(mx, s_max[i]);
+  const float sc = mx > 0.0f ? mx / 448.0f : 1.0f;
+  if (threadIdx.x == 0) scale[r] = sc;
+  for (int k = threadIdx.x; k < cols; k += blockDim.x)
+    W8[(long long)r * cols + k] =
+        (uint8_t)__nv_cvt_float_to_fp8(w[k] / sc, __NV_SATFINITE, __NV_E4M3);
+}
+
+// x8 = e4m3(x * inv_scale) for BF16 x, saturated.
+__global__ void k_quant_bf16_fp8(const __nv_bfloat16 *__restrict__ x, long long n, float inv_scale,
+                                 uint8_t *out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (uint8_t)__nv_cvt_float_to_fp8(__bfloat162float(x[i]) * inv_scale, __NV_SATFINITE,
+                                            __NV_E4M3);
+}
+
+// *out = max |x_i| over BF16 x (out starts at 0; non-negative floats order
+// like their bit patterns).
+__global__ void k_absmax_bf16(const __nv_bfloat16 *__restrict__ x, long long n, float *out) {
+  float m = 0.0f;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(__bfloat162float(x[i])));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(out), __float_as_int(m));
 }
 
 __global__ void k_colsum(const __nv_bfloat16 *__restrict__ src, int rows, int cols, float *out) {
@@ -609,6 +773,36 @@ extern "C" int sg_colsum_bf16(const void *src, int32_t rows, int32_t cols, float
   if (rows < 0 || cols < 0 || (cols && (!src || !out))) return SG_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   if (cols) k_colsum<<<(cols + 127) / 128, 128, 0, st>>>((const __nv_bfloat16 *)src, rows, cols, out);
+  return finish(st);
+}
+
+extern "C" int sg_quant_fp8_rows(const float *W, int32_t rows, int32_t cols, void *W8,
+                                 float *scale, void *stream) {
+  if (rows < 0 || cols < 0 || (rows && (!W || !W8 || !scale))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (rows) k_quant_rows_fp8<<<rows, 256, 0, st>>>(W, rows, cols, (uint8_t *)W8, scale);
+  return finish(st);
+}
+
+extern "C" int sg_quant_fp8_bf16(const void *x, int64_t n, float inv_scale, void *out8,
+                                 void *stream) {
+  if (n < 0 || (n && (!x || !out8))) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n) {
+    const unsigned g = (unsigned)std::min<long long>(4096, (n + 255) / 256);
+    k_quant_bf16_fp8<<<g, 256, 0, st>>>((const __nv_bfloat16 *)x, n, inv_scale, (uint8_t *)out8);
+  }
+  return finish(st);
+}
+
+extern "C" int sg_absmax_bf16(const void *x, int64_t n, float *out, void *stream) {
+  if (n < 0 || !out || (n && !x)) return SG_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemsetAsync(out, 0, sizeof(float), st);
+  if (n) {
+    const unsigned g = (unsigned)std::min<long long>(4096, (n + 255) / 256);
+    k_absmax_bf16<<<g, 256, 0, st>>>((const __nv_bfloat16 *)x, n, out);
+  }
   return finish(st);
 }
 

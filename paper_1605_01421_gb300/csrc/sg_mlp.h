@@ -25,6 +25,18 @@ struct GemmArgs {
   __nv_bfloat16 *C16;
   int ldc16;
   int *err;  // device error word (SG_ERR_TIMEOUT if a wait gave up)
+  // FP8 operands (f8 != 0): A8 (M x K) and B8 (N x K) hold E4M3 bytes, K
+  // contiguous (K % 16 == 0); the accumulator is multiplied by a_scale *
+  // b_scale[n] before the bias.
+  int f8;
+  const uint8_t *A8, *B8;
+  float a_scale;
+  const float *b_scale;
+  // FP8 output after the activation: C8 = e4m3(act(..) * c8_inv_scale),
+  // saturated to the finite range (null: none)
+  uint8_t *C8;
+  int ldc8;
+  float c8_inv_scale;
 };
 
 int gemm_bf16(const GemmArgs &g, cudaStream_t st);

@@ -81,6 +81,40 @@ class Emulator:
                                       out32=True, out16=False)
         return logits, acts, pres
 
+    # -- FP8 inference ---------------------------------------------------------
+    def quantize_fp8(self, calib_feat16, margin=1.0):
+        """E4M3 copies of the weights of layers 2-4 (one scale per output row,
+        max |w| / 448) and static scales of their input activations (max
+        |activation| of the BF16 network over the calibration features, times
+        margin, / 448).  Layer 1 keeps BF16 operands (its inputs are the
+        features) and writes its output in E4M3."""
+        self.W8, self.wscale = [], []
+        for li in (1, 2, 3):
+            w8, sc = binding.quant_fp8_rows(self.W32[li])
+            self.W8.append(w8)
+            self.wscale.append(sc)
+        _, acts, _ = self.forward(calib_feat16)
+        f32 = np.float32
+        self.act_scale = [float(f32(max(binding.absmax_bf16(a), 1e-30) * margin) / f32(448.0))
+                          for a in acts[1:4]]
+
+    def _inv(self, li):
+        # the same single-precision reciprocal the engine takes
+        return float(np.float32(1.0) / np.float32(self.act_scale[li]))
+
+    def forward_fp8(self, feat16):
+        """Logits (B x 392 FP32) of the E4M3 network: the same kernels and
+        arguments the engine uses when FP8 inference is switched on."""
+        x8 = binding.gemm_bf16_to_fp8(feat16, self.W16[0], self._inv(0), bias=self.b32[0],
+                                      act=1)
+        for li in (1, 2):
+            _, _, x8 = binding.gemm_fp8(x8, self.act_scale[li - 1], self.W8[li - 1],
+                                        self.wscale[li - 1], bias=self.b32[li], act=1,
+                                        out32=False, out8_inv_scale=self._inv(li))
+        logits, _, _ = binding.gemm_fp8(x8, self.act_scale[2], self.W8[2], self.wscale[2],
+                                        bias=self.b32[3], act=0, out32=True)
+        return logits
+
     # -- backward ------------------------------------------------------------
     def gradients(self, feat16, targets):
         """Mean cross-entropy and its gradients (dW per layer FP32 out x in,
@@ -212,6 +246,19 @@ def features(u, phi, gdata, max_herd=2000, phi_lo=0.0, phi_hi=6.0):
     return feat, flag
 
 
+def sample_increments(logits, u, flag, seed, day, n_nodes=None):
+    """Sampled one-day increments (units x 4: dI_1..dI_3, used) of the
+    flagged units from the logits, with the engine's random stream for
+    `day` (unit i = replicate * n_nodes + node)."""
+    import torch
+    units = u.shape[0]
+    delta = torch.empty((units, 4), dtype=torch.int32, device="cuda")
+    _check(binding.lib().sg_emu_sample(_p(logits), int(logits.shape[1]), _p(u), _p(flag),
+                                        int(units), int(n_nodes or units),
+                                        ctypes.c_uint64(int(seed)), int(day), _p(delta), _s()))
+    return delta
+
+
 def make_dataset(n_nodes, n_batches, seed=0, max_herd=2000):
     """(features BF16, target bins int32) of n_nodes x n_batches one-day SSA
     outcomes, each batch with its own jittered rate parameters."""
@@ -237,13 +284,14 @@ def make_dataset(n_nodes, n_batches, seed=0, max_herd=2000):
 # Error against SSA ensembles: Wasserstein-1 and Kolmogorov-Smirnov.
 # ---------------------------------------------------------------------------
 
-def emulator_pmf(emu, u0, phi, gdata):
+def emulator_pmf(emu, u0, phi, gdata, fp8=False):
     """The emulator's law of each age class's increment (n x 3 x 129), with
-    the mass beyond -I_a .. S_a moved to those bounds as the sampler does."""
+    the mass beyond -I_a .. S_a moved to those bounds as the sampler does
+    (fp8: the E4M3 network)."""
     import torch
     ud = torch.as_tensor(u0, device="cuda")
     f, _ = features(ud, torch.as_tensor(phi, device="cuda"), gdata)
-    logits, _, _ = emu.forward(f)
+    logits = emu.forward_fp8(f) if fp8 else emu.forward(f)[0]
     lg = logits[:, :NUSED].double().cpu().numpy().reshape(-1, 3, BINS)
     lg = lg - lg.max(axis=2, keepdims=True)
     p = np.exp(lg)
@@ -263,7 +311,7 @@ def emulator_pmf(emu, u0, phi, gdata):
     return p
 
 
-def compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, max_herd=2000):
+def compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, max_herd=2000, fp8=False):
     """W1 and KS between the emulator's law and 1,000-replicate SSA ensembles
     at n_probes random in-range states, per age class's I (S moves by the
     same amount, so its distances are the same).  Returns a dict of mean and
@@ -273,7 +321,7 @@ def compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, max_herd=2000):
     g = random_params(rng)
     U, w = ssa_one_day(u0, phi, g, seed=777 + seed, n_rep=n_rep)
     Ua = U[:, 1].cpu().numpy()  # (n_rep, n, 6)
-    p = emulator_pmf(emu, u0, phi, g)
+    p = emulator_pmf(emu, u0, phi, g, fp8=fp8)
     d = np.arange(BINS) - HALF
     w1 = np.zeros((n_probes, 3))
     ks = np.zeros((n_probes, 3))

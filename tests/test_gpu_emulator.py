@@ -140,3 +140,51 @@ def test_training_and_emulated_run(env):
     for a in range(3):
         tot = Uc[:, :, 2 * a] + Uc[:, :, 2 * a + 1]
         assert np.all(tot == tot[0:1])
+
+
+def test_engine_day_equals_sampled_network_bf16_and_fp8(env):
+    # one day, every node inside the emulator's range: the engine's state
+    # after the day is the start state moved by the sampler's increments for
+    # the logits of the network computed on its own (BF16, then E4M3 layers
+    # 2-4 with static activation scales), bit for bit
+    torch, binding, emulator = env
+    rng = np.random.default_rng(21)
+    n, seed = 5000, 0x0123_4567_89AB
+    u0, phi = emulator.random_states(rng, n)
+    g = emulator.random_params(rng)
+    emu = emulator.Emulator(seed=3)
+    ud = torch.as_tensor(u0, device="cuda")
+    f, flag = emulator.features(ud, torch.as_tensor(phi, device="cuda"), g)
+    assert bool((flag == 1).all())
+    emu.quantize_fp8(f)
+    assert all(s > 0 for s in emu.act_scale)
+    l16 = emu.forward(f)[0]
+    l8 = emu.forward_fp8(f)
+    rel = ((l8 - l16).norm() / l16.norm()).item()
+    assert rel < 0.1, rel
+    for fp8, logits in ((False, l16), (True, l8)):
+        w = W.plain_model(W.SISE3, u0, np.array([0, 1]), g, seed=seed, v0=phi[:, None])
+        m = binding.Model(w)
+        m.set_emulator(emu, max_herd=2000)
+        if fp8:
+            m.set_emulator_fp8(emu)
+        u0d, v0d = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (w.u0, w.v0))
+        U = torch.empty((1, 2, n, 6), dtype=torch.int32, device="cuda")
+        V = torch.empty((1, 2, n, 1), dtype=torch.float64, device="cuda")
+        rc, st, er = m.run(w.tspan, seed, 1, u0d, v0d, U, V)
+        m.close()
+        delta = emulator.sample_increments(logits, ud, flag, seed, 1)
+        d = delta.cpu().numpy()
+        want = u0.astype(np.int64).copy()
+        for a in range(3):
+            want[:, 2 * a] -= d[:, a]
+            want[:, 2 * a + 1] += d[:, a]
+        assert np.array_equal(U.cpu().numpy()[0, 1], want), fp8
+    # switching FP8 off and on again through the API
+    m = binding.Model(w)
+    with pytest.raises(binding.SimInfError):
+        m.set_emulator_fp8(emu)  # no emulator set yet
+    m.set_emulator(emu, max_herd=2000)
+    m.set_emulator_fp8(emu)
+    m.set_emulator_fp8(emu, enable=False)
+    m.close()
