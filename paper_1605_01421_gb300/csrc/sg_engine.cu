@@ -312,7 +312,8 @@ struct sg_model {
   const uint8_t *emu_W8[3] = {};
   const float *emu_wscale[3] = {};
   float emu_act_scale[3] = {1.0f, 1.0f, 1.0f};
-  DevBuf<uint8_t> emu_h8a, emu_h8b;
+  DevBuf<uint8_t> emu_h8a, emu_h8b, emu_img;  // tiled E4M3 activations, weight images
+  DevBuf<float> emu_hvec;                     // head-padded output-layer bias, scales
   DevBuf<float> emu_logits;
   DevBuf<int32_t> emu_flag, emu_delta;
   // SISe_sp neighbour lists and the second phi buffer of the coupled step
@@ -517,7 +518,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
-  m->emu_h8a.release(); m->emu_h8b.release();
+  m->emu_h8a.release(); m->emu_h8b.release(); m->emu_img.release(); m->emu_hvec.release();
   m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
   m->nb_ptr.release(); m->nb_idx.release(); m->nb_dist.release(); m->v2.release();
   m->aem_a.release(); m->aem_tau.release(); m->aem_cnt.release();
@@ -987,6 +988,20 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     ep.phi_hi = m->emu_phi_hi;
     const unsigned gu = (unsigned)std::max<long long>(1, std::min<long long>(16384, (units + 255) / 256));
     const unsigned gw = (unsigned)std::max<long long>(1, std::min<long long>(1 << 20, (units * 32 + 255) / 256));
+    EmuChainWeights cw{};
+    if (m->emu_fp8) {
+      // weight images of the E4M3 chain, from the caller's current weights
+      cw.W0 = m->emu_W[0];
+      for (int l = 0; l < 3; ++l) {
+        cw.W8[l] = m->emu_W8[l];
+        cw.wscale[l] = m->emu_wscale[l];
+        cw.act_scale[l] = m->emu_act_scale[l];
+      }
+      for (int l = 0; l < 4; ++l) cw.b[l] = m->emu_b[l];
+      LaunchTimer lt(m, st, 3);
+      emu_chain_images(cw, m->emu_img.p, m->emu_hvec.p, st);
+      launches += 5;
+    }
     bool pending = false;
     for (int32_t d = 0; d < days; ++d) {
       const int32_t T = t0 + 1 + d;
@@ -999,63 +1014,56 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
         launch_days_kind(m, da, st);
         ++launches;
       }
-      {
+      if (m->emu_fp8) {
+        // the persistent E4M3 chain: features and layer 1, layers 2 and 3,
+        // layer 4 with the sampler
         LaunchTimer lt(m, st, 3);
-        k_emu_features<<<gu, 256, 0, st>>>(m->u.p, m->v.p, units, ep, m->emu_feat.p,
-                                           m->emu_flag.p);
-      }
-      const __nv_bfloat16 *in = m->emu_feat.p;
-      int kin = kEmuIn;
-      __nv_bfloat16 *outs[3] = {m->emu_ha.p, m->emu_hb.p, m->emu_ha.p};
-      uint8_t *outs8[3] = {m->emu_h8a.p, m->emu_h8b.p, m->emu_h8a.p};
-      const bool f8 = m->emu_fp8;
-      for (int l = 0; l < 4; ++l) {
-        GemmArgs g{};
-        g.A = in;
-        g.lda = kin;
-        g.Bt = m->emu_W[l];
-        g.ldb = kin;
-        g.M = (int)units;
-        g.N = l < 3 ? kEmuHidden : kEmuOut;
-        g.K = kin;
-        g.bias = m->emu_b[l];
-        g.act = l < 3 ? 1 : 0;
-        g.C32 = l < 3 ? nullptr : m->emu_logits.p;
-        g.ldc32 = kEmuOut;
-        g.C16 = l < 3 && !f8 ? outs[l] : nullptr;
-        g.ldc16 = kEmuHidden;
-        g.err = nullptr;
-        if (f8) {
-          // layer 1 reads BF16 features and writes E4M3; layers 2-4 read E4M3
-          if (l > 0) {
-            g.f8 = 1;
-            g.A8 = outs8[l - 1];
-            g.B8 = m->emu_W8[l - 1];
-            g.a_scale = m->emu_act_scale[l - 1];
-            g.b_scale = m->emu_wscale[l - 1];
+        emu_chain_day(cw, m->emu_img.p, m->emu_hvec.p, m->emu_h8a.p, m->emu_h8b.p, m->u.p,
+                      m->v.p, ep, units, Nn, da.k0, da.k1, T, m->emu_flag.p, m->emu_delta.p,
+                      st);
+        launches += 4;
+      } else {
+        {
+          LaunchTimer lt(m, st, 3);
+          k_emu_features<<<gu, 256, 0, st>>>(m->u.p, m->v.p, units, ep, m->emu_feat.p,
+                                             m->emu_flag.p);
+        }
+        const __nv_bfloat16 *in = m->emu_feat.p;
+        int kin = kEmuIn;
+        __nv_bfloat16 *outs[3] = {m->emu_ha.p, m->emu_hb.p, m->emu_ha.p};
+        for (int l = 0; l < 4; ++l) {
+          GemmArgs g{};
+          g.A = in;
+          g.lda = kin;
+          g.Bt = m->emu_W[l];
+          g.ldb = kin;
+          g.M = (int)units;
+          g.N = l < 3 ? kEmuHidden : kEmuOut;
+          g.K = kin;
+          g.bias = m->emu_b[l];
+          g.act = l < 3 ? 1 : 0;
+          g.C32 = l < 3 ? nullptr : m->emu_logits.p;
+          g.ldc32 = kEmuOut;
+          g.C16 = l < 3 ? outs[l] : nullptr;
+          g.ldc16 = kEmuHidden;
+          g.err = nullptr;
+          {
+            LaunchTimer lt(m, st, 3);
+            gemm_bf16(g, st);
           }
+          ++launches;
           if (l < 3) {
-            g.C8 = outs8[l];
-            g.ldc8 = kEmuHidden;
-            g.c8_inv_scale = 1.0f / m->emu_act_scale[l];
+            in = outs[l];
+            kin = kEmuHidden;
           }
         }
         {
           LaunchTimer lt(m, st, 3);
-          gemm_bf16(g, st);
+          k_emu_sample<<<gw, 256, 0, st>>>(m->emu_logits.p, kEmuOut, m->u.p, m->emu_flag.p,
+                                           units, Nn, da.k0, da.k1, T, m->emu_delta.p);
         }
-        ++launches;
-        if (l < 3) {
-          in = outs[l];
-          kin = kEmuHidden;
-        }
+        launches += 2;
       }
-      {
-        LaunchTimer lt(m, st, 3);
-        k_emu_sample<<<gw, 256, 0, st>>>(m->emu_logits.p, kEmuOut, m->u.p, m->emu_flag.p,
-                                         units, Nn, da.k0, da.k1, T, m->emu_delta.p);
-      }
-      launches += 2;
       const bool e2_today = P.day_has_e2[d] != 0;
       da.T_begin = T;
       da.T_end = T + 1;
@@ -1213,14 +1221,21 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   }
   if (m->emu_on) {
     const size_t units = (size_t)Nn * n_rep;
-    if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
-        (rc = m->emu_ha.ensure(units * kEmuHidden)) ||
-        (rc = m->emu_hb.ensure(units * kEmuHidden)) ||
-        (m->emu_fp8 && ((rc = m->emu_h8a.ensure(units * kEmuHidden)) ||
-                        (rc = m->emu_h8b.ensure(units * kEmuHidden)))) ||
-        (rc = m->emu_logits.ensure(units * kEmuOut)) || (rc = m->emu_flag.ensure(units)) ||
-        (rc = m->emu_delta.ensure(units * 4)) || (rc = gemm_prepare()))
+    const size_t tiles = (units + 127) / 128;
+    if ((rc = m->emu_flag.ensure(units)) || (rc = m->emu_delta.ensure(units * 4)) ||
+        (rc = gemm_prepare()))
       return rc;
+    if (m->emu_fp8) {
+      if ((rc = m->emu_h8a.ensure(tiles * kEmuTileBytes)) ||
+          (rc = m->emu_h8b.ensure(tiles * kEmuTileBytes)) ||
+          (rc = m->emu_img.ensure(kEmuImgBytes)) || (rc = m->emu_hvec.ensure(kEmuHeadVecFloats)))
+        return rc;
+    } else if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
+               (rc = m->emu_ha.ensure(units * kEmuHidden)) ||
+               (rc = m->emu_hb.ensure(units * kEmuHidden)) ||
+               (rc = m->emu_logits.ensure(units * kEmuOut))) {
+      return rc;
+    }
   }
   // tspan slot of every unit time, uploaded when it changes
   std::vector<int32_t> rec(days + 1, -1);
@@ -1301,7 +1316,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                      m->v.p,
                      m->e1_cur.p,
                      m->rec.p,
-                     m->emu_on ? (const void *)m->emu_logits.p : nullptr,
+                     m->emu_on ? (const void *)m->emu_delta.p : nullptr,
                      seed,
                      n_rep,
                      n_tspan,

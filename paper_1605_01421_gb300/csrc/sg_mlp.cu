@@ -604,34 +604,36 @@ __global__ void k_adam(float *p, const float *__restrict__ g, float *m, float *v
 
 namespace sg {
 
-// Input features of one SISe3 node for the emulator, and whether the node is
-// in the emulator's range (herd <= max_herd and phi_lo <= phi <= phi_hi).
+// Input features of one SISe3 node for the emulator (the BF16 values of the
+// 16 inputs), and whether the node is in the emulator's range (herd <=
+// max_herd and phi_lo <= phi <= phi_hi).
+__device__ __forceinline__ bool emu_feature_row(const int32_t *un, double phi,
+                                                const EmuParams &ep, __nv_bfloat16 *row) {
+  int herd = 0;
+#pragma unroll
+  for (int p = 0; p < 6; ++p) herd += un[p];
+  const bool in = herd <= ep.max_herd && phi >= ep.phi_lo && phi <= ep.phi_hi;
+  float f[16];
+#pragma unroll
+  for (int p = 0; p < 6; ++p) f[p] = log1pf((float)max(un[p], 0));
+  f[6] = (float)phi;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f[7 + a] = 50.0f * (float)ep.gdata[a];
+    f[10 + a] = 10.0f * (float)ep.gdata[3 + a];
+  }
+  f[13] = f[14] = f[15] = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) row[k] = __float2bfloat16_rn(f[k]);
+  return in;
+}
+
 __global__ void k_emu_features(const int32_t *__restrict__ u, const double *__restrict__ v,
                                long long units, EmuParams ep, __nv_bfloat16 *feat,
                                int32_t *flag) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < units;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int32_t *un = u + i * 6;
-    int herd = 0;
-#pragma unroll
-    for (int p = 0; p < 6; ++p) herd += un[p];
-    const double phi = v[i];
-    const bool in = herd <= ep.max_herd && phi >= ep.phi_lo && phi <= ep.phi_hi;
-    flag[i] = in ? 1 : 0;
-    float f[16];
-#pragma unroll
-    for (int p = 0; p < 6; ++p) f[p] = log1pf((float)max(un[p], 0));
-    f[6] = (float)phi;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      f[7 + a] = 50.0f * (float)ep.gdata[a];
-      f[10 + a] = 10.0f * (float)ep.gdata[3 + a];
-    }
-    f[13] = f[14] = f[15] = 0.0f;
-    __nv_bfloat16 *row = feat + i * 16;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) row[k] = __float2bfloat16_rn(f[k]);
-  }
+       i += (long long)gridDim.x * blockDim.x)
+    flag[i] = emu_feature_row(u + i * 6, v[i], ep, feat + i * 16) ? 1 : 0;
 }
 
 // Sample each in-range node's increments from the emulator's three heads:
@@ -723,6 +725,495 @@ __global__ void k_emu_targets(const int32_t *__restrict__ u0, const int32_t *__r
       tgt[i * 3 + a] = min(max(d + kHalf, 0), kBins - 1);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// The engine's FP8 inference chain: one persistent kernel per layer (one CTA
+// per SM), the layer's weights resident in shared memory, activations in a
+// tiled layout that one bulk copy moves, and (hidden layers) two tensor-memory
+// accumulators, so that the epilogue of one 128-row tile overlaps the MMAs of
+// the next.  Warp roles: producer warps (bulk copies, or the input features
+// computed in place), one MMA warp (one elected thread issues tcgen05.mma),
+// epilogue warps (tcgen05.ld, scale, bias, activation, store).
+//
+// Tiled layout of a matrix with rows padded to a multiple of 128 and Kb bytes
+// per row: tile t (rows 128 t .. 128 t + 127) occupies bytes [128 Kb t,
+// 128 Kb (t + 1)), as Kb / 16 chunks of 128 rows x 16 bytes (chunk c at
+// 2048 c, row r of it at 16 r).  Copied to shared memory this is the
+// no-swizzle K-major operand layout with 8-row core matrices 128 bytes apart
+// along M and 2048 bytes apart along K.  A weight image uses the same layout
+// with all of its N rows in one tile (chunk c at 16 N c).
+//
+// Layer kinds: 0, the input layer: features computed from the node states in
+// the kernel (BF16, K = 16), 256 outputs, GELU, E4M3 out; 1, a hidden layer:
+// E4M3 in (K = 256), 256 outputs, GELU, E4M3 out; 2, the output layer fused
+// with the sampler: E4M3 in, head h's 129 logits at accumulator columns
+// 144 h .. 144 h + 128, sampled as k_emu_sample samples them, bit for bit.
+// Every layer's arithmetic is that of k_gemm_tc on the same operands.
+// ---------------------------------------------------------------------------
+constexpr int kEmuHeadPitch = 144;               // accumulator columns per head
+constexpr int kEmuHeadCols = 3 * kEmuHeadPitch;  // 432 (MMAs of N = 256 and 176)
+constexpr uint32_t kEmuTmemCols = 512;
+constexpr uint32_t kEmuMinSmem = 120u * 1024u;   // one CTA per SM (its TMEM is 512 columns)
+
+template <int L>
+struct EmuLayerCfg;
+template <>
+struct EmuLayerCfg<0> {
+  static constexpr bool kF8 = false;
+  static constexpr int kKb = 32, kN = 256, kStages = 4, kAcc = 2, kProdWarps = 4,
+                       kEpiWarps = 8;
+};
+template <>
+struct EmuLayerCfg<1> {
+  static constexpr bool kF8 = true;
+  static constexpr int kKb = 256, kN = 256, kStages = 2, kAcc = 2, kProdWarps = 1,
+                       kEpiWarps = 8;
+};
+template <>
+struct EmuLayerCfg<2> {
+  static constexpr bool kF8 = true;
+  static constexpr int kKb = 256, kN = kEmuHeadCols, kStages = 2, kAcc = 1, kProdWarps = 1,
+                       kEpiWarps = 12;
+};
+
+template <int L>
+constexpr int emu_layer_threads() {
+  return (EmuLayerCfg<L>::kProdWarps + 1 + EmuLayerCfg<L>::kEpiWarps) * 32;
+}
+
+// weight image, A stages, per-column accumulator factor and bias
+template <int L>
+constexpr uint32_t emu_layer_smem() {
+  using C = EmuLayerCfg<L>;
+  return (uint32_t)C::kN * C::kKb + (uint32_t)C::kStages * 128u * C::kKb + 8u * C::kN;
+}
+
+__device__ __forceinline__ void emu_fail(volatile int *s_fail, int *err) {
+  *s_fail = 1;
+  atomicExch(err, SG_ERR_TIMEOUT);
+}
+
+template <int L>
+__global__ void __launch_bounds__(emu_layer_threads<L>(), 1) k_emu_layer(const EmuChainArgs a) {
+  using C = EmuLayerCfg<L>;
+  constexpr uint32_t kATile = 128u * C::kKb;
+  constexpr uint32_t kWBytes = (uint32_t)C::kN * C::kKb;
+  constexpr int kKSteps = C::kKb / 32;  // 32 bytes of K per MMA
+  constexpr int kMmaWarp = C::kProdWarps, kEpi0 = C::kProdWarps + 1;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sW = smem;
+  unsigned char *sA = smem + kWBytes;
+  float *sScale = reinterpret_cast<float *>(sA + C::kStages * kATile);
+  float *sBias = sScale + C::kN;
+  __shared__ __align__(8) uint64_t bar_w, bar_full[C::kStages], bar_empty[C::kStages],
+      bar_tfull[C::kAcc], bar_tempty[C::kAcc];
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar_w, 1);
+    for (int s = 0; s < C::kStages; ++s) {
+      tc::mbar_init(&bar_full[s], L == 0 ? 128 : 1);
+      tc::mbar_init(&bar_empty[s], 1);
+    }
+    for (int b = 0; b < C::kAcc; ++b) {
+      tc::mbar_init(&bar_tfull[b], 1);
+      tc::mbar_init(&bar_tempty[b], C::kEpiWarps);
+    }
+    tc::fence_mbar_init();
+    s_fail = 0;
+  }
+  // the accumulator's factor a_scale * w_scale[n] (E4M3 layers), the bias
+  for (int n = threadIdx.x; n < C::kN; n += blockDim.x) {
+    sScale[n] = C::kF8 ? a.a_scale * a.wscale[n] : 1.0f;
+    sBias[n] = a.bias[n];
+  }
+  if (warp == kMmaWarp) tc::tmem_alloc(&tmem_slot, kEmuTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const int my_tiles = (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1;
+
+  if (warp < C::kProdWarps) {
+    // ---- producer ----
+    if (threadIdx.x == 0) {
+      tc::mbar_arrive_expect_tx(&bar_w, kWBytes);
+      for (uint32_t off = 0; off < kWBytes; off += 16384u)
+        tc::bulk_g2s(sW + off, a.W + off, kWBytes - off < 16384u ? kWBytes - off : 16384u, &bar_w);
+    }
+    if constexpr (L == 0) {
+      // four warps, thread p writes row p of each tile: its 16 BF16
+      // features as two 16-byte pieces (chunks 0 and 1)
+      const int p = threadIdx.x;
+      for (int i = 0; i < my_tiles; ++i) {
+        const int s = i % C::kStages, k = i / C::kStages;
+        if (k > 0 && !tc::mbar_wait(&bar_empty[s], (k - 1) & 1, kWaitLimit)) {
+          emu_fail(&s_fail, a.err);
+          break;
+        }
+        if (s_fail) break;
+        const long long w = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128 + p;
+        __align__(16) __nv_bfloat16 row[16];
+        if (w < a.units) {
+          a.flag[w] = emu_feature_row(a.u + w * 6, a.v[w], a.ep, row) ? 1 : 0;
+        } else {
+#pragma unroll
+          for (int k2 = 0; k2 < 16; ++k2) row[k2] = __float2bfloat16_rn(0.0f);
+        }
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        unsigned char *stage = sA + s * kATile;
+        *reinterpret_cast<uint4 *>(stage + p * 16) = r4[0];
+        *reinterpret_cast<uint4 *>(stage + 2048 + p * 16) = r4[1];
+        tc::fence_async_smem();
+        tc::mbar_arrive(&bar_full[s]);
+      }
+      if (threadIdx.x == 0) tc::mbar_wait(&bar_w, 0, kWaitLimit);
+    } else {
+      if (lane == 0) {
+        int last[C::kStages];
+#pragma unroll
+        for (int s = 0; s < C::kStages; ++s) last[s] = -1;
+        for (int i = 0; i < my_tiles; ++i) {
+          const int s = i % C::kStages, k = i / C::kStages;
+          if (k > 0 && !tc::mbar_wait(&bar_empty[s], (k - 1) & 1, kWaitLimit)) {
+            emu_fail(&s_fail, a.err);
+            break;
+          }
+          if (s_fail) break;
+          const long long t = (long long)blockIdx.x + (long long)i * gridDim.x;
+          tc::mbar_arrive_expect_tx(&bar_full[s], kATile);
+          tc::bulk_g2s(sA + s * kATile, a.A + t * kATile, kATile, &bar_full[s]);
+          last[s] = k;
+        }
+        // no copy of ours may still be landing in shared memory at exit
+        tc::mbar_wait(&bar_w, 0, kWaitLimit);
+#pragma unroll
+        for (int s = 0; s < C::kStages; ++s)
+          if (last[s] >= 0) tc::mbar_wait(&bar_full[s], last[s] & 1, kWaitLimit);
+      }
+      __syncwarp();
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issue ----
+    if (lane == 0) {
+      int last_b = -1, last_kb = 0;
+      bool ok = tc::mbar_wait(&bar_w, 0, kWaitLimit);
+      const uint32_t a0 = tc::smem_u32(sA), w0 = tc::smem_u32(sW);
+      for (int i = 0; ok && i < my_tiles; ++i) {
+        const int s = i % C::kStages, k = i / C::kStages;
+        const int b = i % C::kAcc, kb = i / C::kAcc;
+        if (!tc::mbar_wait(&bar_full[s], k & 1, kWaitLimit) ||
+            (kb > 0 && !tc::mbar_wait(&bar_tempty[b], (kb - 1) & 1, kWaitLimit))) {
+          ok = false;
+          break;
+        }
+        tc::tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(b * 256);
+        const uint32_t as = a0 + (uint32_t)s * kATile;
+#pragma unroll
+        for (int ks = 0; ks < kKSteps; ++ks) {
+          const uint64_t ad = tc::smem_desc(as + ks * 4096, 2048, 128);
+          const uint64_t bd = tc::smem_desc(w0 + ks * 32 * C::kN, 16 * C::kN, 128);
+          if constexpr (L == 0) {
+            tc::mma_bf16(d, ad, bd, tc::idesc_bf16_f32(128, 256), ks > 0 ? 1u : 0u);
+          } else {
+            tc::mma_e4m3(d, ad, bd, tc::idesc_e4m3_f32(128, 256), ks > 0 ? 1u : 0u);
+            if constexpr (L == 2) {
+              const uint64_t bd2 = tc::smem_desc(w0 + 256 * 16 + ks * 32 * C::kN, 16 * C::kN, 128);
+              tc::mma_e4m3(d + 256, ad, bd2, tc::idesc_e4m3_f32(128, C::kN - 256),
+                           ks > 0 ? 1u : 0u);
+            }
+          }
+        }
+        tc::mma_commit(&bar_empty[s]);
+        tc::mma_commit(&bar_tfull[b]);
+        last_b = b;
+        last_kb = kb;
+      }
+      if (!ok) emu_fail(&s_fail, a.err);
+      // the tensor memory is freed only after our MMAs are done
+      if (last_b >= 0) tc::mbar_wait(&bar_tfull[last_b], last_kb & 1, kWaitLimit);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 ----
+    const int ew = warp - kEpi0;
+    const int q = warp & 3;
+    const int r = q * 32 + lane;  // tile row of this thread
+    if constexpr (L < 2) {
+      const int c0 = (ew >> 2) * 128;  // column half
+      for (int i = 0; i < my_tiles; ++i) {
+        const int b = i % C::kAcc, kb = i / C::kAcc;
+        if (!tc::mbar_wait(&bar_tfull[b], kb & 1, kWaitLimit)) {
+          emu_fail(&s_fail, a.err);
+          break;
+        }
+        tc::tc_fence_after();
+        const long long t = (long long)blockIdx.x + (long long)i * gridDim.x;
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
+        unsigned char *orow = a.out + t * (128 * 256) + r * 16;
+        for (int c = c0; c < c0 + 128; c += 16) {
+          float v[16];
+          tc::tmem_ld16(tb + (uint32_t)c, v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if constexpr (C::kF8) v[j] *= sScale[c + j];
+            v[j] += sBias[c + j];
+            v[j] = gelu(v[j]);
+          }
+          uint32_t packed[4];
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[j] * a.inv_out, v[j + 1] * a.inv_out), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
+                make_float2(v[j + 2] * a.inv_out, v[j + 3] * a.inv_out), __NV_SATFINITE,
+                __NV_E4M3);
+            packed[j / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
+          }
+          *reinterpret_cast<uint4 *>(orow + (c / 16) * 2048) =
+              make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bar_tempty[b]);
+      }
+    } else {
+      const int h = ew >> 2;  // head (age class) of this warp
+      const int col0 = h * kEmuHeadPitch;
+      for (int i = 0; i < my_tiles; ++i) {
+        if (!tc::mbar_wait(&bar_tfull[0], i & 1, kWaitLimit)) {
+          emu_fail(&s_fail, a.err);
+          break;
+        }
+        tc::tc_fence_after();
+        const long long w = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128 + r;
+        const bool live = w < a.units;
+        const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
+        // logit of bin j: accumulator x a_scale w_scale + bias; first their
+        // maximum, then the 32 partial sums of 5 bins' exp(logit - max)
+        float mx = -INFINITY;
+#pragma unroll
+        for (int c = 0; c < kEmuHeadPitch; c += 16) {
+          float x[16];
+          tc::tmem_ld16(tb + (uint32_t)c, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c + j < kBins) {
+              x[j] *= sScale[col0 + c + j];
+              x[j] += sBias[col0 + c + j];
+              mx = fmaxf(mx, x[j]);
+            }
+        }
+        float p[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) p[l] = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kEmuHeadPitch; c += 16) {
+          float x[16];
+          tc::tmem_ld16(tb + (uint32_t)c, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c + j < kBins) {
+              x[j] *= sScale[col0 + c + j];
+              x[j] += sBias[col0 + c + j];
+              p[(c + j) / 5] += expf(x[j] - mx);
+            }
+        }
+        // inclusive scan of the partial sums in the order of the warp's
+        // shuffle scan in k_emu_sample (steps 1, 2, 4, 8, 16)
+        float part[32];
+#pragma unroll
+        for (int l = 0; l < 32; ++l) part[l] = p[l];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+          for (int l = 31; l >= o; --l) p[l] += p[l - o];
+        const float total = p[31];
+        const long long rep = live ? w / a.n_nodes : 0;
+        const long long node = live ? w - rep * a.n_nodes : 0;
+        const U4 x4 = philox10(
+            U4{0u, (uint32_t)node, (uint32_t)a.T, (SG_STREAM_EMU << 24) | (uint32_t)rep}, a.k0,
+            a.k1);
+        const uint32_t word = h == 0 ? x4.x : (h == 1 ? x4.y : x4.z);
+        const float target = ((float)(word >> 8) + 0.5f) * (1.0f / 16777216.0f) * total;
+        // the first partial range that reaches the target, then the bin in it
+        int owner = 31;
+        float incl_o = p[31], part_o = part[31];
+#pragma unroll
+        for (int l = 30; l >= 0; --l)
+          if (p[l] >= target) {
+            owner = l;
+            incl_o = p[l];
+            part_o = part[l];
+          }
+        float e[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int c = 0; c < kEmuHeadPitch; c += 16) {
+          float x[16];
+          tc::tmem_ld16(tb + (uint32_t)c, x);
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c + j < kBins && (c + j) / 5 == owner) {
+              x[j] *= sScale[col0 + c + j];
+              x[j] += sBias[col0 + c + j];
+              e[(c + j) % 5] = expf(x[j] - mx);
+            }
+        }
+        float acc = incl_o - part_o;
+        int bin = min(owner * 5 + 4, kBins - 1);
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          acc += e[j];
+          if (acc >= target && owner * 5 + j < kBins) {
+            bin = owner * 5 + j;
+            break;
+          }
+        }
+        if (live) {
+          int32_t *o = a.delta + w * 4;
+          if (a.flag[w]) {
+            const int S = a.u[w * 6 + 2 * h], I = a.u[w * 6 + 2 * h + 1];
+            int d = bin - kHalf;
+            d = max(d, -I);
+            d = min(d, S);
+            o[h] = d;
+            if (h == 0) o[3] = 1;
+          } else if (h == 0) {
+            o[3] = 0;
+          }
+        }
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bar_tempty[0]);
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == kMmaWarp) tc::tmem_dealloc(tmem, kEmuTmemCols);
+}
+
+// Weight image of the chain: row n of the image is row n of W (src_rows x
+// Kb bytes, row-major), or with head_pad row 129 h + j for image row 144 h + j
+// (j < 129); other image rows are zero.
+__global__ void k_emu_image(const uint8_t *__restrict__ W, int src_rows, int Kb, int n_img,
+                            int head_pad, uint8_t *img) {
+  const int chunks = Kb / 16;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n_img * chunks;
+       idx += gridDim.x * blockDim.x) {
+    const int c = idx / n_img, n = idx - c * n_img;
+    int src = n;
+    if (head_pad) {
+      const int h = n / kEmuHeadPitch, j = n - h * kEmuHeadPitch;
+      src = j < kBins ? h * kBins + j : -1;
+    }
+    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+    if (src >= 0 && src < src_rows)
+      val = *reinterpret_cast<const uint4 *>(W + (size_t)src * Kb + c * 16);
+    *reinterpret_cast<uint4 *>(img + (size_t)idx * 16) = val;
+  }
+}
+
+// Bias and weight scales of the output layer in the head-padded order.
+__global__ void k_emu_head_vec(const float *__restrict__ b, const float *__restrict__ ws,
+                               float *bimg, float *wimg) {
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < kEmuHeadCols;
+       n += gridDim.x * blockDim.x) {
+    const int h = n / kEmuHeadPitch, j = n - h * kEmuHeadPitch;
+    const bool in = j < kBins;
+    bimg[n] = in ? b[h * kBins + j] : 0.0f;
+    wimg[n] = in ? ws[h * kBins + j] : 0.0f;
+  }
+}
+
+template <int L>
+static void launch_emu_layer(const EmuChainArgs &a, int grid, cudaStream_t st) {
+  const uint32_t smem = std::max(emu_layer_smem<L>(), kEmuMinSmem);
+  static bool attr_set = false;  // guarded by the caller's lock
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_emu_layer<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_emu_layer<L><<<grid, emu_layer_threads<L>(), smem, st>>>(a);
+}
+
+int emu_chain_images(const EmuChainWeights &cw, uint8_t *img, float *hvec, cudaStream_t st) {
+  k_emu_image<<<16, 256, 0, st>>>(reinterpret_cast<const uint8_t *>(cw.W0), kEmuHidden, 32,
+                                  kEmuHidden, 0, img + kEmuImgOff[0]);
+  k_emu_image<<<64, 256, 0, st>>>(cw.W8[0], kEmuHidden, 256, kEmuHidden, 0, img + kEmuImgOff[1]);
+  k_emu_image<<<64, 256, 0, st>>>(cw.W8[1], kEmuHidden, 256, kEmuHidden, 0, img + kEmuImgOff[2]);
+  k_emu_image<<<64, 256, 0, st>>>(cw.W8[2], kEmuOut, 256, kEmuHeadCols, 1, img + kEmuImgOff[3]);
+  k_emu_head_vec<<<2, 256, 0, st>>>(cw.b[3], cw.wscale[2], hvec, hvec + kEmuHeadCols);
+  return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+}
+
+int emu_chain_day(const EmuChainWeights &cw, const uint8_t *img, const float *hvec,
+                  uint8_t *act0, uint8_t *act1, const int32_t *u, const double *v,
+                  const EmuParams &ep, long long units, int n_nodes, uint32_t k0, uint32_t k1,
+                  int T, int32_t *flag, int32_t *delta, cudaStream_t st) {
+  if (units <= 0) return SG_OK;
+  static std::mutex mu;
+  static int n_sm = 0;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!n_sm) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n_sm <= 0) {
+      cudaGetLastError();
+      n_sm = 0;
+      return SG_ERR_CUDA;
+    }
+  }
+  int *err = nullptr;
+  int rc = gemm_err_buf(&err);
+  if (rc) return rc;
+  const long long tiles = (units + 127) / 128;
+  if (tiles > (1ll << 30)) return SG_ERR_ARG;
+  const int grid = (int)std::min<long long>(tiles, n_sm);
+  EmuChainArgs a{};
+  a.u = u;
+  a.v = v;
+  a.flag = flag;
+  a.delta = delta;
+  a.ep = ep;
+  a.units = units;
+  a.n_nodes = n_nodes;
+  a.k0 = k0;
+  a.k1 = k1;
+  a.T = T;
+  a.n_tiles = (int)tiles;
+  a.err = err;
+  // layer 1: features -> E4M3 activations (act0)
+  a.W = img + kEmuImgOff[0];
+  a.bias = cw.b[0];
+  a.inv_out = 1.0f / cw.act_scale[0];
+  a.out = act0;
+  launch_emu_layer<0>(a, grid, st);
+  // layers 2 and 3: act0 -> act1 -> act0
+  for (int l = 1; l <= 2; ++l) {
+    a.A = l == 1 ? act0 : act1;
+    a.out = l == 1 ? act1 : act0;
+    a.W = img + kEmuImgOff[l];
+    a.bias = cw.b[l];
+    a.wscale = cw.wscale[l - 1];
+    a.a_scale = cw.act_scale[l - 1];
+    a.inv_out = 1.0f / cw.act_scale[l];
+    launch_emu_layer<1>(a, grid, st);
+  }
+  // layer 4 and sampling: act0 -> delta
+  a.A = act0;
+  a.out = nullptr;
+  a.W = img + kEmuImgOff[3];
+  a.bias = hvec;
+  a.wscale = hvec + kEmuHeadCols;
+  a.a_scale = cw.act_scale[2];
+  launch_emu_layer<2>(a, grid, st);
+  return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
 }
 
 }  // namespace sg

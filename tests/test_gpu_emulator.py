@@ -140,6 +140,19 @@ def test_training_and_emulated_run(env):
     for a in range(3):
         tot = Uc[:, :, 2 * a] + Uc[:, :, 2 * a + 1]
         assert np.all(tot == tot[0:1])
+    # the same run with E4M3 layers 2-4 (the persistent tensor-core chain)
+    emu.quantize_fp8(feat[:65536].contiguous())
+    m.set_emulator_fp8(emu)
+    rc, st, er = m.run(w.tspan, w.seed, 1, u0, v0, U, V)
+    U8 = U.cpu().numpy()[0]
+    assert U8.min() >= 0 and not np.array_equal(U8, Uc)
+    for a in range(3):
+        tot = U8[:, :, 2 * a] + U8[:, :, 2 * a + 1]
+        assert np.all(tot == tot[0:1])
+    # the prevalence of the two runs stays close (both emulate the same law)
+    p16 = (Uc[-1, :, 1::2].sum(1) > 0).mean()
+    p8 = (U8[-1, :, 1::2].sum(1) > 0).mean()
+    assert abs(p16 - p8) < 0.05, (p16, p8)
 
 
 def test_engine_day_equals_sampled_network_bf16_and_fp8(env):
@@ -188,3 +201,45 @@ def test_engine_day_equals_sampled_network_bf16_and_fp8(env):
     m.set_emulator_fp8(emu)
     m.set_emulator_fp8(emu, enable=False)
     m.close()
+
+
+def test_fp8_chain_ragged_replicates_and_fallback(env, orc):
+    # 1,237 nodes (a ragged last tile), two replicates, 4% of the herds above
+    # the emulator's range: emulated nodes equal the sampled E4M3 network bit
+    # for bit, the others equal the oracle's SSA
+    torch, binding, emulator = env
+    rng = np.random.default_rng(33)
+    n, R, seed = 1237, 2, 0x5EED_0F_C4A1
+    u0, phi = emulator.random_states(rng, n)
+    big = rng.random(n) < 0.04
+    u0[big, 4] += 2500
+    g = emulator.random_params(rng)
+    emu = emulator.Emulator(seed=4)
+    uu = torch.as_tensor(np.tile(u0, (R, 1)), device="cuda")
+    ph = torch.as_tensor(np.tile(phi, R), device="cuda")
+    f, flag = emulator.features(uu, ph, g)
+    assert int(flag.sum()) == R * (n - big.sum())
+    emu.quantize_fp8(f)
+    logits = emu.forward_fp8(f)
+    delta = emulator.sample_increments(logits, uu, flag, seed, 1, n_nodes=n).cpu().numpy()
+    w = W.plain_model(W.SISE3, u0, np.array([0, 1]), g, seed=seed, v0=phi[:, None], n_rep=R)
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == 0
+    m = binding.Model(w)
+    m.set_emulator(emu, max_herd=2000)
+    m.set_emulator_fp8(emu)
+    u0d, v0d = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (w.u0, w.v0))
+    U = torch.empty((R, 2, n, 6), dtype=torch.int32, device="cuda")
+    V = torch.empty((R, 2, n, 1), dtype=torch.float64, device="cuda")
+    rc, st, er = m.run(w.tspan, seed, R, u0d, v0d, U, V)
+    m.close()
+    Ug = U.cpu().numpy()
+    for r in range(R):
+        d = delta[r * n:(r + 1) * n]
+        assert np.array_equal(d[:, 3] == 1, ~big)
+        want = u0.astype(np.int64).copy()
+        for a in range(3):
+            want[:, 2 * a] -= d[:, a]
+            want[:, 2 * a + 1] += d[:, a]
+        assert np.array_equal(Ug[r, 1][~big], want[~big]), r
+        assert np.array_equal(Ug[r, 1][big], U0[r, 1][big]), r
