@@ -502,7 +502,9 @@ int sg_emu_features(const int32_t *u, const double *v, int64_t units, const doub
 int sg_emu_targets(const int32_t *u_before, const int32_t *u_after, int64_t units,
                    int32_t *targets, void *stream);
 /* Sample increments for the flagged units from the logits: delta[i] =
- * (dI_1, dI_2, dI_3, used), each clamped to -I_a .. S_a; the uniforms come
+ * (dI_1, dI_2, dI_3, used), each clamped to -I_a .. S_a; a head's softmax
+ * weights are 2^(z - max z), z = logit log2 e (hardware 2^x), summed in
+ * groups of 5 bins and scanned over the groups; the uniforms come
  * from Philox with counter (0, node, day, (2 << 24) | replicate), unit i =
  * replicate * n_nodes + node. */
 int sg_emu_sample(const float *logits, int32_t ldl, const int32_t *u, const int32_t *flag,

@@ -45,9 +45,37 @@ __device__ __forceinline__ float tanh_fast(float x) {
   asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
-__device__ __forceinline__ float gelu(float x) {
-  const float u = 0.7978845608028654f * (x + 0.044715f * x * x * x);
-  return 0.5f * x * (1.0f + tanh_fast(u));
+
+// s GELU(x), given hs = s / 2: h (1 + tanh(u)) with h = hs x and u = x
+// (sqrt(2 / pi) + 0.044715 sqrt(2 / pi) x^2), in fused multiply-adds (s
+// folds an output scale into the activation).
+__device__ __forceinline__ float gelu_scaled(float x, float hs) {
+  const float u = x * __fmaf_rn(0.0356774081f, x * x, 0.7978845608f);
+  const float h = hs * x;
+  return __fmaf_rn(h, tanh_fast(u), h);
+}
+__device__ __forceinline__ float gelu(float x) { return gelu_scaled(x, 0.5f); }
+
+// 2^x with the hardware approximation (the sampler's softmax weights).
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+constexpr float kLog2e = 1.44269504088896341f;
+
+// 16 E4M3 bytes of y[0..15] (nearest even, saturated), y[0] in the lowest.
+__device__ __forceinline__ uint4 pack_e4m3_16(const float *y) {
+  uint32_t packed[4];
+#pragma unroll
+  for (int j = 0; j < 16; j += 4) {
+    const __nv_fp8x2_storage_t lo =
+        __nv_cvt_float2_to_fp8x2(make_float2(y[j], y[j + 1]), __NV_SATFINITE, __NV_E4M3);
+    const __nv_fp8x2_storage_t hi =
+        __nv_cvt_float2_to_fp8x2(make_float2(y[j + 2], y[j + 3]), __NV_SATFINITE, __NV_E4M3);
+    packed[j / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
+  }
+  return make_uint4(packed[0], packed[1], packed[2], packed[3]);
 }
 
 // C = act(A . Bt^T + bias) for one 128 x BN tile.  A: M x K, Bt: N x K, both
@@ -188,25 +216,27 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
       float v[16];
       tc::tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
       const int nb = n0 + c;
-      if constexpr (F8) {
+      // pre-activation: accumulator x a_scale b_scale[n] (E4M3) + bias[n],
+      // one fused multiply-add
+      float bs[16];
+      if (g.bias && nb + 16 <= g.N && (((uintptr_t)(g.bias + nb)) & 15) == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          v[i] *= g.a_scale * ((nb + i < g.N) ? __ldg(g.b_scale + nb + i) : 0.0f);
-      }
-      if (g.bias) {
-        if (nb + 16 <= g.N && (((uintptr_t)(g.bias + nb)) & 15) == 0) {
-#pragma unroll
-          for (int i = 0; i < 16; i += 4) {
-            const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + nb + i));
-            v[i] += b4.x;
-            v[i + 1] += b4.y;
-            v[i + 2] += b4.z;
-            v[i + 3] += b4.w;
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 16; ++i) v[i] += (nb + i < g.N) ? __ldg(g.bias + nb + i) : 0.0f;
+        for (int i = 0; i < 16; i += 4) {
+          const float4 b4 = __ldg(reinterpret_cast<const float4 *>(g.bias + nb + i));
+          bs[i] = b4.x;
+          bs[i + 1] = b4.y;
+          bs[i + 2] = b4.z;
+          bs[i + 3] = b4.w;
         }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) bs[i] = (g.bias && nb + i < g.N) ? __ldg(g.bias + nb + i) : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        float cs = 1.0f;
+        if constexpr (F8) cs = g.a_scale * ((nb + i < g.N) ? __ldg(g.b_scale + nb + i) : 0.0f);
+        v[i] = __fmaf_rn(v[i], cs, bs[i]);
       }
       if (g.C32 && row < g.M) {
         float *dst = g.C32 + (long long)row * g.ldc32 + nb;
@@ -218,16 +248,14 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
           for (int i = 0; i < 16 && nb + i < g.N; ++i) dst[i] = v[i];
         }
       }
-      if (g.C16 || g.C8) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (g.act == 1) v[i] = gelu(v[i]);
-      }
       if (g.C16) {
+        float y[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) y[i] = g.act == 1 ? gelu_scaled(v[i], 0.5f) : v[i];
         uint32_t packed[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(v[i], v[i + 1]);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(y[i], y[i + 1]);
           packed[i / 2] = *reinterpret_cast<const uint32_t *>(&h2);
         }
         uint4 *sp = reinterpret_cast<uint4 *>(stage + lr * kPitch + c * 2);
@@ -235,18 +263,15 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm_tc(const GemmArgs g) {
         sp[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
       if (g.C8 && row < g.M) {
-        // 16 E4M3 values of this row, one 16-byte store when it fits
-        uint32_t packed[4];
+        // 16 E4M3 values of this row (the output scale folded into the
+        // activation), one 16-byte store when it fits
+        const float hs = 0.5f * g.c8_inv_scale;
+        float y[16];
 #pragma unroll
-        for (int i = 0; i < 16; i += 4) {
-          const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-              make_float2(v[i] * g.c8_inv_scale, v[i + 1] * g.c8_inv_scale), __NV_SATFINITE,
-              __NV_E4M3);
-          const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-              make_float2(v[i + 2] * g.c8_inv_scale, v[i + 3] * g.c8_inv_scale), __NV_SATFINITE,
-              __NV_E4M3);
-          packed[i / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
-        }
+        for (int i = 0; i < 16; ++i)
+          y[i] = g.act == 1 ? gelu_scaled(v[i], hs) : v[i] * g.c8_inv_scale;
+        const uint4 pk = pack_e4m3_16(y);
+        const uint32_t packed[4] = {pk.x, pk.y, pk.z, pk.w};
         uint8_t *dst = g.C8 + (long long)row * g.ldc8 + nb;
         if (nb + 16 <= g.N && (((uintptr_t)dst) & 15) == 0) {
           *reinterpret_cast<uint4 *>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -637,7 +662,8 @@ __global__ void k_emu_features(const int32_t *__restrict__ u, const double *__re
 }
 
 // Sample each in-range node's increments from the emulator's three heads:
-// softmax over the 129 bins, inverse CDF at a uniform from the emulator's
+// softmax over the 129 bins (weights 2^(z - max z) with z = logit log2 e, the
+// hardware 2^x), inverse CDF at a uniform from the emulator's
 // Philox stream (seed, replicate, node, day), and clamp so that neither S_a
 // nor I_a becomes negative (each age class keeps its size within the day).
 // One warp per node; lane l holds bins 5 l .. 5 l + 4.
@@ -665,7 +691,7 @@ __global__ void k_emu_sample(const float *__restrict__ logits, int ldl,
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
       const int c = lane * 5 + j;
-      vals[j] = c < kBins ? lg[c] : -INFINITY;
+      vals[j] = c < kBins ? lg[c] * kLog2e : -INFINITY;
       mx = fmaxf(mx, vals[j]);
     }
 #pragma unroll
@@ -673,7 +699,7 @@ __global__ void k_emu_sample(const float *__restrict__ logits, int ldl,
     float part = 0.0f;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-      vals[j] = lane * 5 + j < kBins ? expf(vals[j] - mx) : 0.0f;
+      vals[j] = lane * 5 + j < kBins ? ex2_fast(vals[j] - mx) : 0.0f;
       part += vals[j];
     }
     // inclusive scan of the lane sums
@@ -762,13 +788,13 @@ template <>
 struct EmuLayerCfg<0> {
   static constexpr bool kF8 = false;
   static constexpr int kKb = 32, kN = 256, kStages = 4, kAcc = 2, kProdWarps = 4,
-                       kEpiWarps = 8;
+                       kEpiWarps = 16;
 };
 template <>
 struct EmuLayerCfg<1> {
   static constexpr bool kF8 = true;
   static constexpr int kKb = 256, kN = 256, kStages = 2, kAcc = 2, kProdWarps = 1,
-                       kEpiWarps = 8;
+                       kEpiWarps = 16;
 };
 template <>
 struct EmuLayerCfg<2> {
@@ -944,7 +970,8 @@ __global__ void __launch_bounds__(emu_layer_threads<L>(), 1) k_emu_layer(const E
     const int q = warp & 3;
     const int r = q * 32 + lane;  // tile row of this thread
     if constexpr (L < 2) {
-      const int c0 = (ew >> 2) * 128;  // column half
+      const int c0 = (ew >> 2) * 64;  // column quarter
+      const float hs = 0.5f * a.inv_out;
       for (int i = 0; i < my_tiles; ++i) {
         const int b = i % C::kAcc, kb = i / C::kAcc;
         if (!tc::mbar_wait(&bar_tfull[b], kb & 1, kWaitLimit)) {
@@ -955,28 +982,23 @@ __global__ void __launch_bounds__(emu_layer_threads<L>(), 1) k_emu_layer(const E
         const long long t = (long long)blockIdx.x + (long long)i * gridDim.x;
         const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 256);
         unsigned char *orow = a.out + t * (128 * 256) + r * 16;
-        for (int c = c0; c < c0 + 128; c += 16) {
-          float v[16];
-          tc::tmem_ld16(tb + (uint32_t)c, v);
+        tc::tmem_stream16<4>(tb + (uint32_t)c0, [&](int k, float *v) {
+          const int c = c0 + 16 * k;
+          const float4 *s4 = reinterpret_cast<const float4 *>(sScale + c);
+          const float4 *b4 = reinterpret_cast<const float4 *>(sBias + c);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            if constexpr (C::kF8) v[j] *= sScale[c + j];
-            v[j] += sBias[c + j];
-            v[j] = gelu(v[j]);
+          for (int j4 = 0; j4 < 4; ++j4) {
+            const float4 sc = s4[j4], bi = b4[j4];
+            float *x = v + 4 * j4;
+            x[0] = __fmaf_rn(x[0], sc.x, bi.x);
+            x[1] = __fmaf_rn(x[1], sc.y, bi.y);
+            x[2] = __fmaf_rn(x[2], sc.z, bi.z);
+            x[3] = __fmaf_rn(x[3], sc.w, bi.w);
           }
-          uint32_t packed[4];
 #pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(
-                make_float2(v[j] * a.inv_out, v[j + 1] * a.inv_out), __NV_SATFINITE, __NV_E4M3);
-            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(
-                make_float2(v[j + 2] * a.inv_out, v[j + 3] * a.inv_out), __NV_SATFINITE,
-                __NV_E4M3);
-            packed[j / 4] = (uint32_t)lo | ((uint32_t)hi << 16);
-          }
-          *reinterpret_cast<uint4 *>(orow + (c / 16) * 2048) =
-              make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        }
+          for (int j = 0; j < 16; ++j) v[j] = gelu_scaled(v[j], hs);
+          *reinterpret_cast<uint4 *>(orow + (c / 16) * 2048) = pack_e4m3_16(v);
+        });
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&bar_tempty[b]);
@@ -993,41 +1015,39 @@ __global__ void __launch_bounds__(emu_layer_threads<L>(), 1) k_emu_layer(const E
         const long long w = ((long long)blockIdx.x + (long long)i * gridDim.x) * 128 + r;
         const bool live = w < a.units;
         const uint32_t tb = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)col0;
-        // logit of bin j: accumulator x a_scale w_scale + bias; first their
-        // maximum, then the 32 partial sums of 5 bins' exp(logit - max)
+        // pass 1: the logits (accumulator x a_scale w_scale + bias) times
+        // log2 e, written back to the tensor memory, and their maximum
         float mx = -INFINITY;
+        tc::tmem_stream16<kEmuHeadPitch / 16>(tb, [&](int k, float *x) {
+          const int c = 16 * k;
+          const float4 *s4 = reinterpret_cast<const float4 *>(sScale + col0 + c);
+          const float4 *b4 = reinterpret_cast<const float4 *>(sBias + col0 + c);
 #pragma unroll
-        for (int c = 0; c < kEmuHeadPitch; c += 16) {
-          float x[16];
-          tc::tmem_ld16(tb + (uint32_t)c, x);
+          for (int j4 = 0; j4 < 4; ++j4) {
+            const float4 sc = s4[j4], bi = b4[j4];
+            float *y = x + 4 * j4;
+            y[0] = __fmaf_rn(y[0], sc.x, bi.x) * kLog2e;
+            y[1] = __fmaf_rn(y[1], sc.y, bi.y) * kLog2e;
+            y[2] = __fmaf_rn(y[2], sc.z, bi.z) * kLog2e;
+            y[3] = __fmaf_rn(y[3], sc.w, bi.w) * kLog2e;
+          }
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c + j < kBins) {
-              x[j] *= sScale[col0 + c + j];
-              x[j] += sBias[col0 + c + j];
-              mx = fmaxf(mx, x[j]);
-            }
-        }
+            if (c + j < kBins) mx = fmaxf(mx, x[j]);
+          tc::tmem_st16(tb + (uint32_t)c, x);
+        });
+        tc::tmem_wait_st();
+        // pass 2: the 32 partial sums of 5 bins' softmax weights 2^(z - max z)
         float p[32];
 #pragma unroll
         for (int l = 0; l < 32; ++l) p[l] = 0.0f;
-#pragma unroll
-        for (int c = 0; c < kEmuHeadPitch; c += 16) {
-          float x[16];
-          tc::tmem_ld16(tb + (uint32_t)c, x);
+        tc::tmem_stream16<kEmuHeadPitch / 16>(tb, [&](int k, float *x) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c + j < kBins) {
-              x[j] *= sScale[col0 + c + j];
-              x[j] += sBias[col0 + c + j];
-              p[(c + j) / 5] += expf(x[j] - mx);
-            }
-        }
+            if (16 * k + j < kBins) p[(16 * k + j) / 5] += ex2_fast(x[j] - mx);
+        });
         // inclusive scan of the partial sums in the order of the warp's
         // shuffle scan in k_emu_sample (steps 1, 2, 4, 8, 16)
-        float part[32];
-#pragma unroll
-        for (int l = 0; l < 32; ++l) part[l] = p[l];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
 #pragma unroll
@@ -1042,26 +1062,26 @@ __global__ void __launch_bounds__(emu_layer_threads<L>(), 1) k_emu_layer(const E
         const float target = ((float)(word >> 8) + 0.5f) * (1.0f / 16777216.0f) * total;
         // the first partial range that reaches the target, then the bin in it
         int owner = 31;
-        float incl_o = p[31], part_o = part[31];
+        float incl_o = p[31];
 #pragma unroll
         for (int l = 30; l >= 0; --l)
           if (p[l] >= target) {
             owner = l;
             incl_o = p[l];
-            part_o = part[l];
           }
-        float e[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int c = 0; c < kEmuHeadPitch; c += 16) {
-          float x[16];
-          tc::tmem_ld16(tb + (uint32_t)c, x);
+        // pass 3: the five values of that range, then their weights
+        float xo[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        tc::tmem_stream16<kEmuHeadPitch / 16>(tb, [&](int k, float *x) {
 #pragma unroll
           for (int j = 0; j < 16; ++j)
-            if (c + j < kBins && (c + j) / 5 == owner) {
-              x[j] *= sScale[col0 + c + j];
-              x[j] += sBias[col0 + c + j];
-              e[(c + j) % 5] = expf(x[j] - mx);
-            }
+            if (16 * k + j < kBins && (16 * k + j) / 5 == owner) xo[(16 * k + j) % 5] = x[j];
+        });
+        // the range's own partial sum, added in the same order as in pass 2
+        float e[5], part_o = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+          e[j] = owner * 5 + j < kBins ? ex2_fast(xo[j] - mx) : 0.0f;
+          part_o += e[j];
         }
         float acc = incl_o - part_o;
         int bin = min(owner * 5 + 4, kBins - 1);
