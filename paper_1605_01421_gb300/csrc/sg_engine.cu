@@ -595,24 +595,9 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
   m->ev_stage.resize(total);
   unsigned char *h = m->ev_stage.data();
   {
-    int8_t *type = (int8_t *)(h + o_type), *shift = (int8_t *)(h + o_shift);
-    uint8_t *sel = h + o_sel;
-    int32_t *nd = (int32_t *)(h + o_node), *ds = (int32_t *)(h + o_dest),
-            *cnt = (int32_t *)(h + o_cnt);
-    double *prop = (double *)(h + o_prop);
-    int64_t *idx = (int64_t *)(h + o_idx);
-    const EventTable &ev = m->ev;
-    for (size_t i = 0; i < n; ++i) {
-      const int64_t e = P.order[i];
-      type[i] = (int8_t)ev.type[e];
-      shift[i] = (int8_t)(ev.shift[e] < 0 ? -1 : ev.shift[e]);
-      sel[i] = (uint8_t)ev.select[e];
-      nd[i] = ev.node[e];
-      ds[i] = ev.dest[e];
-      cnt[i] = ev.n[e];
-      prop[i] = ev.proportion[e];
-      idx[i] = e;
-    }
+    gather_events(m->ev, P, (int8_t *)(h + o_type), (int8_t *)(h + o_shift), h + o_sel,
+                  (int32_t *)(h + o_node), (int32_t *)(h + o_dest), (int32_t *)(h + o_cnt),
+                  (double *)(h + o_prop), (int64_t *)(h + o_idx));
     auto put = [&](size_t o, const void *src, size_t bytes) {
       if (bytes) std::memcpy(h + o, src, bytes);
     };

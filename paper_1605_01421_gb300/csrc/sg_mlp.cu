@@ -54,7 +54,6 @@ __device__ __forceinline__ float gelu_scaled(float x, float hs) {
   const float h = hs * x;
   return __fmaf_rn(h, tanh_fast(u), h);
 }
-__device__ __forceinline__ float gelu(float x) { return gelu_scaled(x, 0.5f); }
 
 // 2^x with the hardware approximation (the sampler's softmax weights).
 __device__ __forceinline__ float ex2_fast(float x) {

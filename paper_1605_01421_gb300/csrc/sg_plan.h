@@ -56,4 +56,10 @@ struct Plan {
 int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
                int32_t slots, Plan *out);
 
+// The device image of the planned events, in plan order: type, shift (-1
+// for none), select, node, dest, n, proportion and the list index.
+void gather_events(const EventTable &ev, const Plan &P, int8_t *type, int8_t *shift,
+                   uint8_t *select, int32_t *node, int32_t *dest, int32_t *n, double *proportion,
+                   int64_t *index);
+
 }  // namespace sg
