@@ -570,6 +570,29 @@ extern "C" int sg_set_events(sg_model *m, int64_t n_events, const int32_t *event
 }
 
 // Build (or reuse) the device schedule of the events for a window.
+// Page-locked host staging for the plan upload, shared by every model of the
+// process (the copy from it is a DMA transfer; pinning a new buffer per
+// model would cost more than it saves).  Held under its lock from filling
+// to the end of the copy.
+static std::mutex g_stage_mu;
+static unsigned char *g_stage = nullptr;
+static size_t g_stage_cap = 0;
+
+static unsigned char *pinned_stage(size_t bytes) {
+  if (bytes <= g_stage_cap) return g_stage;
+  if (g_stage) cudaFreeHost(g_stage);
+  g_stage = nullptr;
+  g_stage_cap = 0;
+  const size_t cap = std::max<size_t>(bytes + bytes / 2, (size_t)1 << 20);
+  if (cudaHostAlloc((void **)&g_stage, cap, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    g_stage = nullptr;
+    return nullptr;
+  }
+  g_stage_cap = cap;
+  return g_stage;
+}
+
 static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
   if (m->plan_ok && m->plan.t0 == t0 && m->plan.t_end == t_end && m->plan.slots == slots)
     return SG_OK;
@@ -592,8 +615,12 @@ static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
                o_wev = place(8 * P.wave_ev.size()), o_woff = place(8 * P.e2_wave_off.size()),
                o_e1d = place(4 * P.e1_day.size()), o_e1o = place(8 * P.e1_node_off.size());
   const size_t total = std::max<size_t>(off, 256);
-  m->ev_stage.resize(total);
-  unsigned char *h = m->ev_stage.data();
+  std::lock_guard<std::mutex> stage_lock(g_stage_mu);
+  unsigned char *h = pinned_stage(total);
+  if (!h) {  // no page-locked memory: a pageable buffer of the model's own
+    m->ev_stage.resize(total);
+    h = m->ev_stage.data();
+  }
   {
     gather_events(m->ev, P, (int8_t *)(h + o_type), (int8_t *)(h + o_shift), h + o_sel,
                   (int32_t *)(h + o_node), (int32_t *)(h + o_dest), (int32_t *)(h + o_cnt),

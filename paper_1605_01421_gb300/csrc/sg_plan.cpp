@@ -2,8 +2,13 @@
 // (Sec. 3.3, Appendix A "Process E1 events" / "Process E2 events").
 #include "sg_plan.h"
 
+#include <unistd.h>
+
 #include <algorithm>
 #include <cmath>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -52,14 +57,74 @@ static int plan_threads(int64_t work) {
   return (int)std::max(1u, std::min(hc ? hc : 1u, 8u));
 }
 
-// f(t) for t = 0 .. T - 1, on T threads (the caller is thread 0).
+// Worker threads kept for the life of the process (created on first use,
+// again after a fork): run(T, f) runs f(t) for t = 0 .. T - 1, the caller
+// taking t = 0, and returns when every f(t) has returned.  One parallel
+// region at a time.
+class PlanPool {
+ public:
+  static PlanPool &get() {
+    static PlanPool *pool = new PlanPool();  // never destroyed: workers are detached
+    return *pool;
+  }
+  void run(int T, const std::function<void(int)> &f) {
+    if (T <= 1) {
+      f(0);
+      return;
+    }
+    std::lock_guard<std::mutex> region(region_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      if (pid_ != getpid()) {  // a forked child has none of the parent's workers
+        workers_ = 0;
+        pid_ = getpid();
+      }
+      while (workers_ < T - 1) {
+        const int id = ++workers_;
+        std::thread([this, id] { loop(id); }).detach();
+      }
+      job_ = &f;
+      active_ = T - 1;
+      remaining_ = T - 1;
+      ++gen_;
+    }
+    cv_.notify_all();
+    f(0);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_.wait(lk, [&] { return remaining_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  void loop(int id) {
+    const pid_t mine = getpid();
+    uint64_t seen = 0;
+    for (;;) {
+      const std::function<void(int)> *job = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+        if (pid_ != mine || id > active_) continue;
+        job = job_;
+      }
+      (*job)(id);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--remaining_ == 0) done_.notify_one();
+    }
+  }
+  std::mutex region_mu_, mu_;
+  std::condition_variable cv_, done_;
+  const std::function<void(int)> *job_ = nullptr;
+  int workers_ = 0, active_ = 0, remaining_ = 0;
+  uint64_t gen_ = 0;
+  pid_t pid_ = getpid();
+};
+
 template <class F>
 static void run_threads(int T, F &&f) {
-  std::vector<std::thread> th;
-  th.reserve(T > 1 ? T - 1 : 0);
-  for (int t = 1; t < T; ++t) th.emplace_back([&f, t] { f(t); });
-  f(0);
-  for (auto &x : th) x.join();
+  const std::function<void(int)> fn = [&f](int t) { f(t); };
+  PlanPool::get().run(T, fn);
 }
 
 // Split [0, nk) into T ranges of about equal weight, weight given by the
@@ -101,34 +166,88 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   };
   auto slot_of = [&](int64_t e) -> int64_t { return slots > 1 ? ev.rep[e] : 0; };
 
-  // 1. One pass in list order: E1 events bucketed by (slot, node), E2 events
-  //    by (day, slot); both stable, so list order is kept inside a bucket.
+  // 1. E1 events bucketed by (slot, node), E2 events by (day, slot), both
+  //    stable (list order kept inside a bucket): counts, offsets, scatter.
+  //    With several threads each takes a chunk of the list and its own
+  //    counts, so that its events land after those of the chunks before it.
+  const int T = plan_threads(n);
+  const bool par = T > 1 && n < ((int64_t)1 << 31) &&
+                   (int64_t)T * (nk + nb) <= std::max<int64_t>(n, (int64_t)1 << 20);
+  const int TB = par ? T : 1;
+  std::vector<std::vector<int32_t>> c1(TB), c2(TB);
+  std::vector<int> bad(TB, 0);
+  run_threads(TB, [&](int t) {
+    c1[t].assign(nk, 0);
+    c2[t].assign(nb, 0);
+    const int64_t lo = n * t / TB, hi = n * (t + 1) / TB;
+    for (int64_t e = lo; e < hi; ++e) {
+      if (ev.time[e] > t_end) continue;
+      const int64_t s = slot_of(e);
+      if (s >= slots) {
+        bad[t] = 1;
+        continue;
+      }
+      if (ev.type[e] == SG_EXTERNAL_TRANSFER)
+        ++c2[t][(int64_t)day_of(e) * slots + s];
+      else
+        ++c1[t][s * n_nodes + ev.node[e]];
+    }
+  });
+  for (int t = 0; t < TB; ++t)
+    if (bad[t]) return SG_ERR_ARG;
   std::vector<int64_t> e1_count(nk + 1, 0), e2_count(nb + 1, 0);
-  for (int64_t e = 0; e < n; ++e) {
-    if (ev.time[e] > t_end) continue;
-    const int64_t s = slot_of(e);
-    if (s >= slots) return SG_ERR_ARG;
-    if (ev.type[e] == SG_EXTERNAL_TRANSFER)
-      ++e2_count[(int64_t)day_of(e) * slots + s + 1];
-    else
-      ++e1_count[s * n_nodes + ev.node[e] + 1];
+  for (int t = 0; t < TB; ++t) {
+    for (int64_t k = 0; k < nk; ++k) e1_count[k + 1] += c1[t][k];
+    for (int64_t b = 0; b < nb; ++b) e2_count[b + 1] += c2[t][b];
   }
   std::partial_sum(e1_count.begin(), e1_count.end(), e1_count.begin());
   std::partial_sum(e2_count.begin(), e2_count.end(), e2_count.begin());
   const int64_t n_e1 = e1_count[nk], n_e2 = e2_count[nb];
+  // each thread's first position in each bucket
+  run_threads(TB, [&](int t) {
+    const int64_t k0 = nk * t / TB, k1 = nk * (t + 1) / TB;
+    for (int64_t k = k0; k < k1; ++k) {
+      int64_t run = e1_count[k];
+      for (int u = 0; u < TB; ++u) {
+        const int32_t x = c1[u][k];
+        c1[u][k] = (int32_t)run;
+        run += x;
+      }
+    }
+    const int64_t b0 = nb * t / TB, b1 = nb * (t + 1) / TB;
+    for (int64_t b = b0; b < b1; ++b) {
+      int64_t run = e2_count[b];
+      for (int u = 0; u < TB; ++u) {
+        const int32_t x = c2[u][b];
+        c2[u][b] = (int32_t)run;
+        run += x;
+      }
+    }
+  });
   P.order.resize(n_e1 + n_e2);
   int64_t *e1 = P.order.data(), *e2 = P.order.data() + n_e1;
-  {
-    std::vector<int64_t> f1(e1_count.begin(), e1_count.end() - 1);
-    std::vector<int64_t> f2(e2_count.begin(), e2_count.end() - 1);
-    for (int64_t e = 0; e < n; ++e) {
-      if (ev.time[e] > t_end) continue;
+  // E1 events travel with their sort keys: (day, time on day 0, type)
+  struct Rec1 {
+    int64_t e;
+    int32_t day, time0, type;  // time0: the time on day 0, else 0
+  };
+  std::vector<Rec1> rec1(n_e1);
+  run_threads(TB, [&](int t) {
+    std::vector<int32_t> &f1 = c1[t], &f2 = c2[t];
+    const int64_t lo = n * t / TB, hi = n * (t + 1) / TB;
+    for (int64_t e = lo; e < hi; ++e) {
+      const int32_t time = ev.time[e];
+      if (time > t_end) continue;
+      const int32_t day = day_of(e);
       if (ev.type[e] == SG_EXTERNAL_TRANSFER)
-        e2[f2[(int64_t)day_of(e) * slots + slot_of(e)]++] = e;
+        e2[f2[(int64_t)day * slots + slot_of(e)]++] = e;
       else
-        e1[f1[slot_of(e) * n_nodes + ev.node[e]]++] = e;
+        rec1[f1[slot_of(e) * n_nodes + ev.node[e]]++] = Rec1{e, day, day == 0 ? time : 0,
+                                                               ev.type[e]};
     }
-  }
+  });
+  c1.clear();
+  c2.clear();
   P.e1_day.resize(n_e1);
 
   // 2. In parallel over ranges of (slot, node) lists and of (day, slot)
@@ -138,22 +257,37 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   //    earlier times;
   //    E2: the first day's buckets ordered by time (stable), then waves, and
   //    the bucket ordered by wave (stable).
-  const int T = plan_threads(n_e1 + n_e2);
   const std::vector<int64_t> r1 = weighted_ranges(e1_count, nk, T);
   const std::vector<int64_t> r2 = weighted_ranges(e2_count, nb, T);
   std::vector<std::vector<int64_t>> wave_ends(T);  // per thread: wave ends, bucket by bucket
   std::vector<int32_t> n_waves_of(nb, 0);
   run_threads(T, [&](int t) {
-    auto before = [&](int64_t a, int64_t b) {
-      const int32_t da = day_of(a), db = day_of(b);
-      if (da != db) return da < db;
-      if (da == 0 && ev.time[a] != ev.time[b]) return ev.time[a] < ev.time[b];
-      return ev.type[a] < ev.type[b];
+    // sort keys of a list: (day, time on day 0, type, position in the list)
+    struct Key {
+      int32_t day, time, type, pos;
+      bool operator<(const Key &o) const {
+        if (day != o.day) return day < o.day;
+        if (time != o.time) return time < o.time;
+        if (type != o.type) return type < o.type;
+        return pos < o.pos;
+      }
     };
+    std::vector<Key> keys;
     for (int64_t k = r1[t]; k < r1[t + 1]; ++k) {
-      int64_t *lo = e1 + e1_count[k], *hi = e1 + e1_count[k + 1];
-      if (!std::is_sorted(lo, hi, before)) std::stable_sort(lo, hi, before);
-      for (int64_t *q = lo; q != hi; ++q) P.e1_day[q - e1] = day_of(*q);
+      const int64_t lo = e1_count[k];
+      const int32_t m = (int32_t)(e1_count[k + 1] - lo);
+      const Rec1 *rc = rec1.data() + lo;
+      keys.resize(m);
+      bool sorted = true;
+      for (int32_t i = 0; i < m; ++i) {
+        keys[i] = Key{rc[i].day, rc[i].time0, rc[i].type, i};
+        if (i > 0 && keys[i] < keys[i - 1]) sorted = false;
+      }
+      if (!sorted) std::sort(keys.begin(), keys.end());
+      for (int32_t i = 0; i < m; ++i) {
+        e1[lo + i] = rc[keys[i].pos].e;
+        P.e1_day[lo + i] = keys[i].day;
+      }
     }
     std::vector<int32_t> last_sample(n_nodes, 0), last_add(n_nodes, 0);
     std::vector<int64_t> stamp(n_nodes, -1);
