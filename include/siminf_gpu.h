@@ -229,6 +229,32 @@ int sg_set_events(sg_model *m, int64_t n_events, const int32_t *event,
                   const int32_t *select, const int32_t *shift,
                   const int32_t *rep);
 
+/* Host only (no device is touched): the schedule that sg_run builds from an
+ * event table for the window of unit steps T = t0 + 1 .. t_end (Sec. 3.3 and
+ * Appendix A, "Process E1 events" / "Process E2 events"), for inspection and
+ * tests.  Day d = T - t0 - 1 runs the events with time in (T - 1, T]; day 0
+ * also every earlier time; events after t_end never run.  Events as in
+ * sg_set_events (type, time, node, dest; rep NULL for slots = 1, else each
+ * event's replicate in 0 .. slots - 1).
+ *   E1 events (exit, enter, internal transfer): per (slot, node), ordered by
+ *     (day, time on day 0, type, list index);
+ *   E2 events (external transfers): per (day, slot), split into waves: an
+ *     event goes one wave after the last earlier event of its bucket that
+ *     sampled its source, added to its source or sampled its destination,
+ *     list order kept inside a wave.
+ * Two calls: with order == NULL, counts[0..2] = (n_e1, n_e2, n_waves); then,
+ * with caller arrays of those sizes, order[n_e1 + n_e2] (event indices: the
+ * E1 part by (slot, node), then the E2 part by (day, slot) and wave),
+ * e1_day[n_e1], e1_node_off[slots * n_nodes + 1] (into order),
+ * e2_wave_off[days * slots + 1] (into wave_ev) and wave_ev[n_waves + 1]
+ * (positions in order; wave w is wave_ev[w] .. wave_ev[w + 1]).  Errors:
+ * SG_ERR_ARG (a node, dest, type or rep out of range, t_end < t0). */
+int sg_plan_events(int64_t n_events, const int32_t *type, const int32_t *time,
+                   const int32_t *node, const int32_t *dest, const int32_t *rep,
+                   int32_t n_nodes, int32_t t0, int32_t t_end, int32_t slots, int64_t *counts,
+                   int64_t *order, int32_t *e1_day, int64_t *e1_node_off,
+                   int64_t *e2_wave_off, int64_t *wave_ev);
+
 /* Run n_rep independent trajectories over tspan (n_tspan >= 1 strictly
  * increasing integers; the simulation covers unit steps T = tspan[0] + 1 ..
  * tspan[n_tspan - 1]) with Philox key `seed`, on the caller's CUDA stream

@@ -173,7 +173,8 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_emu_sample", "sg_emulator_set", "sg_set_neighbors", "sg_set_solver",
            "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
            "sg_set_fused_events", "sg_set_persistent", "sg_gemm_fp8", "sg_quant_fp8_rows",
-           "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8", "sg_gemm_bf16_to_fp8"]
+           "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8", "sg_gemm_bf16_to_fp8",
+           "sg_plan_events"]
 
 _lock = threading.Lock()
 _lib = None
@@ -260,6 +261,10 @@ def lib(path: str | None = None):
                                   vp, i32, vp, i32, f32, vp]
         L.sg_gemm_bf16_to_fp8.argtypes = [vp, i32, vp, i32, i32, i32, i32, vp, i32, vp, i32,
                                           f32, vp]
+        ip64 = ctypes.POINTER(ctypes.c_int64)
+        L.sg_plan_events.argtypes = [i64, vp, vp, vp, vp, vp, i32, i32, i32, i32, ip64, vp, vp, vp,
+                                     vp, vp]
+        L.sg_plan_events.restype = ctypes.c_int
         L.sg_quant_fp8_rows.argtypes = [vp, i32, i32, vp, vp, vp]
         L.sg_quant_fp8_bf16.argtypes = [vp, i64, f32, vp, vp]
         L.sg_absmax_bf16.argtypes = [vp, i64, vp, vp]
@@ -661,6 +666,35 @@ def gemm_fp8(A8, a_scale, B8, b_scale, bias=None, act=0, out32=True, out16=False
     if rc:
         raise SimInfError(rc)
     return C32, C16, C8
+
+
+def plan_events(events, n_nodes, t0, t_end, slots=1):
+    """The engine's host schedule of an event table for the window of unit
+    steps t0 + 1 .. t_end (sg_plan_events): dict of numpy arrays order,
+    e1_day, e1_node_off, e2_wave_off, wave_ev and the counts n_e1, n_e2,
+    n_waves.  Runs on the host only."""
+    L = lib()
+    cols = [_i32(events[k]) for k in ("event", "time", "node", "dest")]
+    rep = _i32(events["rep"]) if slots > 1 else None
+    n = int(cols[0].size)
+    counts = (ctypes.c_int64 * 3)()
+    args = [n] + [_p(c) for c in cols] + [_p(rep) if rep is not None else None,
+                                          int(n_nodes), int(t0), int(t_end), int(slots)]
+    rc = L.sg_plan_events(*args, counts, None, None, None, None, None)
+    if rc:
+        raise SimInfError(rc)
+    n_e1, n_e2, n_w = (int(c) for c in counts)
+    days = int(t_end) - int(t0)
+    out = {"order": np.zeros(n_e1 + n_e2, np.int64), "e1_day": np.zeros(n_e1, np.int32),
+           "e1_node_off": np.zeros(slots * n_nodes + 1, np.int64),
+           "e2_wave_off": np.zeros(days * slots + 1, np.int64),
+           "wave_ev": np.zeros(n_w + 1, np.int64)}
+    rc = L.sg_plan_events(*args, counts, *[_p(out[k]) for k in ("order", "e1_day", "e1_node_off",
+                                                                 "e2_wave_off", "wave_ev")])
+    if rc:
+        raise SimInfError(rc)
+    out.update(n_e1=n_e1, n_e2=n_e2, n_waves=n_w)
+    return out
 
 
 def gemm_bf16_to_fp8(A, Bt, inv_scale, bias=None, act=0, stream=None):

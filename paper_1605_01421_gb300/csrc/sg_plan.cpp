@@ -367,3 +367,41 @@ void gather_events(const EventTable &ev, const Plan &P, int8_t *type, int8_t *sh
 }
 
 }  // namespace sg
+
+extern "C" int sg_plan_events(int64_t n_events, const int32_t *type, const int32_t *time,
+                              const int32_t *node, const int32_t *dest, const int32_t *rep,
+                              int32_t n_nodes, int32_t t0, int32_t t_end, int32_t slots,
+                              int64_t *counts, int64_t *order, int32_t *e1_day,
+                              int64_t *e1_node_off, int64_t *e2_wave_off, int64_t *wave_ev) {
+  if (n_events < 0 || n_nodes < 0 || slots < 1 || t_end < t0 || !counts ||
+      (n_events > 0 && (!type || !time || !node || !dest)) || (slots > 1 && !rep))
+    return SG_ERR_ARG;
+  sg::EventTable ev;
+  ev.type.assign(type, type + n_events);
+  ev.time.assign(time, time + n_events);
+  ev.node.assign(node, node + n_events);
+  ev.dest.assign(dest, dest + n_events);
+  ev.per_rep = slots > 1;
+  if (ev.per_rep) ev.rep.assign(rep, rep + n_events);
+  for (int64_t e = 0; e < n_events; ++e) {
+    const bool e2 = type[e] == SG_EXTERNAL_TRANSFER;
+    if (type[e] < SG_EXIT || type[e] > SG_EXTERNAL_TRANSFER || node[e] < 0 ||
+        node[e] >= n_nodes || (e2 && (dest[e] < 0 || dest[e] >= n_nodes)) ||
+        (ev.per_rep && (rep[e] < 0 || rep[e] >= slots)))
+      return SG_ERR_ARG;
+  }
+  sg::Plan P;
+  const int rc = sg::build_plan(ev, n_nodes, t0, t_end, slots, &P);
+  if (rc) return rc;
+  counts[0] = P.n_e1;
+  counts[1] = P.n_e2;
+  counts[2] = P.n_waves;
+  if (!order) return SG_OK;
+  if ((P.n_e1 > 0 && !e1_day) || !e1_node_off || !e2_wave_off || !wave_ev) return SG_ERR_ARG;
+  std::copy(P.order.begin(), P.order.end(), order);
+  std::copy(P.e1_day.begin(), P.e1_day.end(), e1_day);
+  std::copy(P.e1_node_off.begin(), P.e1_node_off.end(), e1_node_off);
+  std::copy(P.e2_wave_off.begin(), P.e2_wave_off.end(), e2_wave_off);
+  std::copy(P.wave_ev.begin(), P.wave_ev.end(), wave_ev);
+  return SG_OK;
+}
