@@ -439,8 +439,10 @@ def bench_gpu(args):
 def bench_emulator(args):
     """The learned one-day emulator on an SISe3 workload: train it on one-day
     SSA outcomes with the library's own kernels, measure its error against
-    1,000-replicate SSA ensembles (W1, KS), and compare node-days/s of the
-    run with the emulator (SSA fallback for herds > 2,000) to the plain SSA
+    1,000-replicate SSA ensembles (W1, KS) and the population's infected
+    fraction against a plain SSA run, and compare node-days/s of the run
+    with the emulator (SSA fallback for herds > 2,000 and for nodes below
+    the activity threshold) to the plain SSA
     on the same workload.  Prints one JSON line."""
     import torch
     from paper_1605_01421_gb300 import binding, emulator
@@ -448,21 +450,6 @@ def bench_emulator(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    t0 = time.perf_counter()
-    feat, tgt = emulator.make_dataset(1_000_000, args.emu_batches, seed=1)
-    t_data = time.perf_counter() - t0
-    emu = emulator.Emulator(seed=0)
-    t0 = time.perf_counter()
-    hist = emu.train(feat, tgt, steps=args.emu_steps, batch=8192, lr=2e-3)
-    t_train = time.perf_counter() - t0
-    err_bf16 = emulator.compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5)
-    # precision study: E4M3 weights (per-row scales) and activations (static
-    # per-layer scales calibrated on 262,144 training features) on the FP8
-    # tensor cores for layers 2-4
-    emu.quantize_fp8(feat[:262_144].contiguous())
-    del feat, tgt
-    err_fp8 = emulator.compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, fp8=True)
-
     from paper_1605_01421_gb300 import workloads as Wk
     if args.emu_workload == "endemic":
         w = Wk.config_endemic(days=args.emu_days)
@@ -474,6 +461,51 @@ def bench_emulator(args):
     U = torch.empty((1, M, w.n_nodes, 6), dtype=torch.int32, device="cuda")
     V = torch.empty((1, M, w.n_nodes, 1), dtype=torch.float64, device="cuda")
     node_days = w.n_nodes * w.n_days
+    mr = args.emu_min_rate
+
+    # training data: one-day SSA outcomes from random states (half) and from
+    # the in-range node-days of a plain SSA run of this workload (half; a
+    # different seed from the timed runs), 1,000,000 states per batch
+    t0 = time.perf_counter()
+    n_traj = args.emu_batches // 2
+    pilot = binding.Model(w)
+    pilot.run(w.tspan, w.seed + 1, 1, u0, v0, U, V, stream=stream)
+    pilot.close()
+    pool = emulator.trajectory_states(U, V, w.gdata, n_traj * 1_000_000 + 1000, seed=3,
+                                      min_rate=mr)
+    n_rand = args.emu_batches - n_traj if pool is not None else args.emu_batches
+    parts = [emulator.make_dataset(1_000_000, n_rand, seed=1)]
+    if pool is not None and n_traj:
+        parts.append(emulator.make_dataset_from_states(pool[0], pool[1], w.gdata, 1_000_000,
+                                                       n_traj, seed=2))
+    feat = torch.cat([p[0] for p in parts])
+    tgt = torch.cat([p[1] for p in parts])
+    del parts
+    t_data = time.perf_counter() - t0
+    emu = emulator.Emulator(seed=0)
+    t0 = time.perf_counter()
+    hist = emu.train(feat, tgt, steps=args.emu_steps, batch=8192, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    probes = None
+    if pool is not None:  # 1,000 trajectory states left out of training
+        probes = (pool[0][-1000:], pool[1][-1000:])
+
+    def errors(fp8):
+        e = {"random_states": emulator.compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5,
+                                                        fp8=fp8, min_rate=mr)}
+        if probes is not None:
+            e["trajectory_states"] = emulator.compare_at_states(
+                emu, probes[0], probes[1], w.gdata, n_rep=1000, seed=6, fp8=fp8)
+        e["w1_mean"] = max(v["w1_mean"] for v in e.values())
+        return e
+
+    err_bf16 = errors(False)
+    # precision study: E4M3 weights (per-row scales) and activations (static
+    # per-layer scales calibrated on 262,144 training features) on the FP8
+    # tensor cores for layers 2-4
+    emu.quantize_fp8(feat[:262_144].contiguous())
+    del feat, tgt
+    err_fp8 = errors(True)
 
     def timed(m, steps):
         for _ in range(2):
@@ -487,19 +519,30 @@ def bench_emulator(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / steps, st
 
+    def infected_fraction():
+        # the population's infected fraction at every tspan point, from the
+        # dense output of the last run
+        tot = U[0].sum(dim=(1, 2), dtype=torch.float64)
+        inf = U[0][:, :, 1::2].sum(dim=(1, 2), dtype=torch.float64)
+        return (inf / tot).cpu().numpy()
+
     plain = binding.Model(w)
     ms_plain, st_plain = timed(plain, args.steps)
+    f_plain = infected_fraction()
     m = binding.Model(w)
-    m.set_emulator(emu, max_herd=2000)
+    m.set_emulator(emu, max_herd=2000, min_rate=mr)
     ms_emu, st_emu = timed(m, args.steps)
+    f_bf16 = infected_fraction()
     m8 = binding.Model(w)
-    m8.set_emulator(emu, max_herd=2000)
+    m8.set_emulator(emu, max_herd=2000, min_rate=mr)
     m8.set_emulator_fp8(emu)
     ms_emu8, st_emu8 = timed(m8, args.steps)
+    f_fp8 = infected_fraction()
     m8.set_kernel_timing(True)
     rc, st_t8, er = m8.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=stream)
     m8.set_kernel_timing(False)
-    in_range = float((w.u0[0].sum(axis=1) <= 2000).mean())
+    a0 = emulator.total_rate(np.asarray(w.u0[0]), np.asarray(w.v0[0][:, 0]), w.gdata)
+    in_range = float(((w.u0[0].sum(axis=1) <= 2000) & (a0 >= mr)).mean())
 
     # tensor-core roofline: the emulator's launches timed with CUDA events
     # around each launch in one more run of each path (kernel timing on)
@@ -524,19 +567,29 @@ def bench_emulator(args):
                      "fallback",
             "data": "synthetic",
             "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
-                       "events": w.n_events, "in_range_fraction": in_range,
+                       "events": w.n_events, "in_range_fraction_day0": in_range,
+                       "min_rate_per_day": mr,
                        "mlp": "16-256-256-256-392 GELU, 3 heads x 129 bins",
                        "act_scale": emu.act_scale},
             "plain_ssa": {"value": node_days / (ms_plain * 1e-3), "ms_per_step": ms_plain,
                           "reactions": st_plain["reactions"]},
             "speedup_vs_plain_gpu_ssa": ms_plain / ms_emu8,
             "error_vs_ssa": err_fp8,
+            "population_vs_ssa": {
+                "what": "infected fraction of all animals at each tspan point, one run each",
+                "ssa_end": float(f_plain[-1]), "fp8_end": float(f_fp8[-1]),
+                "bf16_end": float(f_bf16[-1]),
+                "fp8_max_abs_diff": float(np.abs(f_fp8 - f_plain).max()),
+                "bf16_max_abs_diff": float(np.abs(f_bf16 - f_plain).max()),
+                "ssa_reactions": st_plain["reactions"],
+                "fp8_run_ssa_reactions": st_emu8["reactions"]},
             "bf16": {"value": node_days / (ms_emu * 1e-3), "ms_per_step": ms_emu,
                      "speedup_vs_plain_gpu_ssa": ms_plain / ms_emu, "error_vs_ssa": err_bf16,
                      "emulator_ms_per_day": gemm_ms,
                      "achieved_tflops": flops / (gemm_ms * 1e-3) / 1e12, "peak_tflops": peak,
                      "kernels": "features, k_gemm_tc x 4, k_emu_sample"},
             "training": {"node_days": int(args.emu_batches * 1_000_000), "steps": args.emu_steps,
+                         "from_trajectory": int((n_traj if pool is not None else 0) * 1_000_000),
                          "batch": 8192, "seconds": t_train, "data_seconds": t_data,
                          "loss_first": float(np.mean(hist[:20])),
                          "loss_last": float(np.mean(hist[-50:]))},
@@ -583,6 +636,8 @@ def main():
     ap.add_argument("--emu-nodes", type=int, default=37000)
     ap.add_argument("--emu-days", type=int, default=3650)
     ap.add_argument("--emu-workload", default="sise3", choices=["sise3", "endemic"])
+    ap.add_argument("--emu-min-rate", type=float, default=4.0,
+                    help="nodes with fewer expected transitions per day stay on the SSA")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
     ap.add_argument("--solver", default="ssm", choices=["ssm", "aem"],

@@ -520,10 +520,12 @@ int sg_adam_step(float *params, const float *grads, float *m, float *v, int64_t 
                  void *stream);
 /* Emulator features (units x 16 BF16) of SISe3 states u (units x 6 int32)
  * and phi (units doubles) with the model's gdata (11 host doubles); flag[i]
- * = 1 when herd <= max_herd and phi_lo <= phi <= phi_hi, else 0. */
+ * = 1 when herd <= max_herd, phi_lo <= phi <= phi_hi and the node's total
+ * transition rate sum_a (upsilon_a phi S_a + gamma_a I_a) >= min_rate
+ * (expected transitions per day), else 0. */
 int sg_emu_features(const int32_t *u, const double *v, int64_t units, const double *gdata,
-                    int32_t max_herd, double phi_lo, double phi_hi, void *feat,
-                    int32_t *flag, void *stream);
+                    int32_t max_herd, double phi_lo, double phi_hi, double min_rate,
+                    void *feat, int32_t *flag, void *stream);
 /* Training targets: bins clamp(I_a(after) - I_a(before) + 64, 0, 128). */
 int sg_emu_targets(const int32_t *u_before, const int32_t *u_after, int64_t units,
                    int32_t *targets, void *stream);
@@ -543,6 +545,14 @@ int sg_emu_sample(const float *logits, int32_t ldl, const int32_t *u, const int3
  * [phi_lo, phi_hi] fall back to the SSA.  enable = 0 turns it off. */
 int sg_emulator_set(sg_model *m, const void *const *W, const float *const *b, int32_t max_herd,
                     double phi_lo, double phi_hi, int enable);
+
+/* The emulator's activity threshold: a node whose total transition rate at
+ * the start of a day (sum_a upsilon_a phi S_a + gamma_a I_a, expected
+ * transitions per day) is below min_rate stays on the SSA that day (default
+ * 0: only the herd size and phi decide).  Quiet nodes are cheap for the SSA,
+ * and the emulator's rare-event probabilities are where its error
+ * accumulates over long runs.  SG_ERR_ARG for a negative or NaN min_rate. */
+int sg_emulator_set_min_rate(sg_model *m, double min_rate);
 
 /* FP8 inference for the emulator set with sg_emulator_set: layers 2-4 run on
  * E4M3 operands (sg_gemm_fp8): W8[l] (E4M3 bytes, out x in, as W of layer l

@@ -174,7 +174,7 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
            "sg_set_fused_events", "sg_set_persistent", "sg_gemm_fp8", "sg_quant_fp8_rows",
            "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8", "sg_gemm_bf16_to_fp8",
-           "sg_plan_events"]
+           "sg_plan_events", "sg_emulator_set_min_rate"]
 
 _lock = threading.Lock()
 _lib = None
@@ -252,7 +252,9 @@ def lib(path: str | None = None):
         L.sg_transpose_bf16.argtypes = [vp, i32, i32, vp, vp]
         L.sg_colsum_bf16.argtypes = [vp, i32, i32, vp, vp]
         L.sg_adam_step.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp, vp]
-        L.sg_emu_features.argtypes = [vp, vp, i64, vp, i32, f64, f64, vp, vp, vp]
+        L.sg_emu_features.argtypes = [vp, vp, i64, vp, i32, f64, f64, f64, vp, vp, vp]
+        L.sg_emulator_set_min_rate.argtypes = [vp, f64]
+        L.sg_emulator_set_min_rate.restype = ctypes.c_int
         L.sg_emu_targets.argtypes = [vp, vp, i64, vp, vp]
         L.sg_emu_sample.argtypes = [vp, i32, vp, vp, i64, i32, u64, i32, vp, vp]
         L.sg_emulator_set.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i32, f64,
@@ -549,9 +551,12 @@ class Model:
             raise SimInfError(rc)
         return npb.value, ha.value, ms.value
 
-    def set_emulator(self, emu, max_herd=2000, phi_lo=0.0, phi_hi=6.0, enable=True):
+    def set_emulator(self, emu, max_herd=2000, phi_lo=0.0, phi_hi=6.0, enable=True,
+                     min_rate=0.0):
         """Let sg_run use a trained emulator (emulator.Emulator) for the
-        in-range nodes; the emulator's tensors must outlive the runs."""
+        in-range nodes (herd <= max_herd, phi_lo <= phi <= phi_hi, total
+        transition rate >= min_rate per day); the emulator's tensors must
+        outlive the runs."""
         vp = ctypes.c_void_p
         if enable:
             W = (vp * 4)(*[ctypes.c_void_p(t.data_ptr()) for t in emu.W16])
@@ -563,6 +568,10 @@ class Model:
                                    float(phi_hi), 1 if enable else 0)
         if rc:
             raise SimInfError(rc)
+        if enable:
+            rc = lib().sg_emulator_set_min_rate(self._h, float(min_rate))
+            if rc:
+                raise SimInfError(rc)
 
     def set_emulator_fp8(self, emu, enable=True):
         """Switch the emulator's layers 2-4 to E4M3 operands (the emulator

@@ -304,7 +304,7 @@ struct sg_model {
   const __nv_bfloat16 *emu_W[4] = {};
   const float *emu_b[4] = {};
   int32_t emu_max_herd = 2000;
-  double emu_phi_lo = 0.0, emu_phi_hi = 0.0;
+  double emu_phi_lo = 0.0, emu_phi_hi = 0.0, emu_min_rate = 0.0;
   uint64_t emu_version = 0;
   DevBuf<__nv_bfloat16> emu_feat, emu_ha, emu_hb;
   // FP8 inference of layers 2-4 (sg_emulator_set_fp8)
@@ -998,6 +998,7 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     ep.max_herd = m->emu_max_herd;
     ep.phi_lo = m->emu_phi_lo;
     ep.phi_hi = m->emu_phi_hi;
+    ep.min_rate = m->emu_min_rate;
     const unsigned gu = (unsigned)std::max<long long>(1, std::min<long long>(16384, (units + 255) / 256));
     const unsigned gw = (unsigned)std::max<long long>(1, std::min<long long>(1 << 20, (units * 32 + 255) / 256));
     EmuChainWeights cw{};
@@ -1936,6 +1937,14 @@ extern "C" int sg_emulator_set(sg_model *m, const void *const *W, const float *c
   m->emu_phi_lo = phi_lo;
   m->emu_phi_hi = phi_hi;
   m->emu_on = true;
+  ++m->emu_version;
+  m->graph_ok = false;
+  return SG_OK;
+}
+
+extern "C" int sg_emulator_set_min_rate(sg_model *m, double min_rate) {
+  if (!m || !(min_rate >= 0.0)) return SG_ERR_ARG;
+  m->emu_min_rate = min_rate;
   ++m->emu_version;
   m->graph_ok = false;
   return SG_OK;

@@ -630,13 +630,20 @@ namespace sg {
 
 // Input features of one SISe3 node for the emulator (the BF16 values of the
 // 16 inputs), and whether the node is in the emulator's range (herd <=
-// max_herd and phi_lo <= phi <= phi_hi).
+// max_herd, phi_lo <= phi <= phi_hi, total transition rate >= min_rate).
 __device__ __forceinline__ bool emu_feature_row(const int32_t *un, double phi,
                                                 const EmuParams &ep, __nv_bfloat16 *row) {
   int herd = 0;
 #pragma unroll
   for (int p = 0; p < 6; ++p) herd += un[p];
-  const bool in = herd <= ep.max_herd && phi >= ep.phi_lo && phi <= ep.phi_hi;
+  // total transition rate: S_a -> I_a at upsilon_a phi S_a, I_a -> S_a at
+  // gamma_a I_a
+  double a0 = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    a0 += ep.gdata[a] * phi * (double)un[2 * a] + ep.gdata[3 + a] * (double)un[2 * a + 1];
+  const bool in = herd <= ep.max_herd && phi >= ep.phi_lo && phi <= ep.phi_hi &&
+                  a0 >= ep.min_rate;
   float f[16];
 #pragma unroll
   for (int p = 0; p < 6; ++p) f[p] = log1pf((float)max(un[p], 0));
@@ -1330,13 +1337,15 @@ extern "C" int sg_adam_step(float *params, const float *grads, float *m, float *
 
 extern "C" int sg_emu_features(const int32_t *u, const double *v, int64_t units,
                                const double *gdata, int32_t max_herd, double phi_lo,
-                               double phi_hi, void *feat, int32_t *flag, void *stream) {
+                               double phi_hi, double min_rate, void *feat, int32_t *flag,
+                               void *stream) {
   if (units < 0 || !gdata || (units && (!u || !v || !feat || !flag))) return SG_ERR_ARG;
   EmuParams ep{};
   for (int i = 0; i < 11; ++i) ep.gdata[i] = gdata[i];
   ep.max_herd = max_herd;
   ep.phi_lo = phi_lo;
   ep.phi_hi = phi_hi;
+  ep.min_rate = min_rate;
   cudaStream_t st = (cudaStream_t)stream;
   if (units)
     k_emu_features<<<grid_n(units, 256), 256, 0, st>>>(u, v, units, ep, (__nv_bfloat16 *)feat,

@@ -50,6 +50,7 @@ struct EmuParams {
   double gdata[11];
   int32_t max_herd;
   double phi_lo, phi_hi;
+  double min_rate;  // least total transition rate (per day) of an emulated node
 };
 
 // The engine's FP8 inference chain (layers 2-4 with E4M3 operands, the

@@ -232,7 +232,7 @@ def ssa_one_day(u0, phi, gdata, seed, n_rep=1):
     return U, w
 
 
-def features(u, phi, gdata, max_herd=2000, phi_lo=0.0, phi_hi=6.0):
+def features(u, phi, gdata, max_herd=2000, phi_lo=0.0, phi_hi=6.0, min_rate=0.0):
     """Emulator features (BF16, n x 16) and range flags from device state."""
     import torch
     n = u.shape[0]
@@ -241,9 +241,17 @@ def features(u, phi, gdata, max_herd=2000, phi_lo=0.0, phi_hi=6.0):
     g = np.ascontiguousarray(gdata, dtype=np.float64)
     _check(binding.lib().sg_emu_features(_p(u), _p(phi), n,
                                           ctypes.c_void_p(g.ctypes.data), int(max_herd),
-                                          float(phi_lo), float(phi_hi), _p(feat), _p(flag),
-                                          _s()))
+                                          float(phi_lo), float(phi_hi), float(min_rate),
+                                          _p(feat), _p(flag), _s()))
     return feat, flag
+
+
+def total_rate(u0, phi, gdata):
+    """A node's total transition rate per day (numpy): sum over age classes
+    of upsilon_a phi S_a + gamma_a I_a."""
+    g = np.asarray(gdata, dtype=np.float64)
+    S, I = u0[:, 0::2].astype(np.float64), u0[:, 1::2].astype(np.float64)
+    return (g[None, 0:3] * phi[:, None] * S + g[None, 3:6] * I).sum(axis=1)
 
 
 def sample_increments(logits, u, flag, seed, day, n_nodes=None):
@@ -280,6 +288,45 @@ def make_dataset(n_nodes, n_batches, seed=0, max_herd=2000):
     return torch.cat(feats), torch.cat(tgts)
 
 
+def trajectory_states(U, V, gdata, n, seed=0, max_herd=2000, phi_hi=6.0, min_rate=0.0):
+    """n node-day start states (u int32 (n, 6), phi (n,)) drawn uniformly,
+    with replacement, from the in-range node-days of an SSA trajectory
+    (device U (1, M, N, 6) int32 and V (1, M, N, 1) float64 of one run): the
+    states the emulator meets on that workload.  None if none is in range."""
+    import torch
+    u = U[0, :-1].reshape(-1, 6)
+    phi = V[0, :-1].reshape(-1)
+    g = torch.as_tensor(np.asarray(gdata, np.float64), device=U.device)
+    a0 = (g[0:3] * phi[:, None] * u[:, 0::2].double() + g[3:6] * u[:, 1::2].double()).sum(1)
+    ok = (u.sum(1) <= max_herd) & (phi >= 0) & (phi <= phi_hi) & (a0 >= min_rate)
+    idx = torch.nonzero(ok).flatten()
+    if idx.numel() == 0:
+        return None
+    gen = torch.Generator(device=U.device).manual_seed(seed)
+    pick = idx[torch.randint(0, idx.numel(), (n,), device=U.device, generator=gen)]
+    return u[pick].cpu().numpy().astype(np.int32), phi[pick].cpu().numpy()
+
+
+def make_dataset_from_states(u_pool, phi_pool, gdata, n_nodes, n_batches, seed=0,
+                             max_herd=2000):
+    """(features, target bins) of one-day SSA outcomes from given start
+    states (consecutive slices of the pools, n_nodes per batch) under the
+    workload's own rate parameters."""
+    import torch
+    feats, tgts = [], []
+    for b in range(n_batches):
+        u0 = np.ascontiguousarray(u_pool[b * n_nodes:(b + 1) * n_nodes])
+        phi = np.ascontiguousarray(phi_pool[b * n_nodes:(b + 1) * n_nodes])
+        U, w = ssa_one_day(u0, phi, gdata, seed=20_000 + 7919 * seed + b)
+        ub, ua = U[0, 0].contiguous(), U[0, 1].contiguous()
+        f, _ = features(ub, torch.as_tensor(phi, device="cuda"), gdata, max_herd)
+        t = torch.empty((len(u0), 3), dtype=torch.int32, device="cuda")
+        _check(binding.lib().sg_emu_targets(_p(ub), _p(ua), len(u0), _p(t), _s()))
+        feats.append(f)
+        tgts.append(t)
+    return torch.cat(feats), torch.cat(tgts)
+
+
 # ---------------------------------------------------------------------------
 # Error against SSA ensembles: Wasserstein-1 and Kolmogorov-Smirnov.
 # ---------------------------------------------------------------------------
@@ -311,14 +358,33 @@ def emulator_pmf(emu, u0, phi, gdata, fp8=False):
     return p
 
 
-def compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, max_herd=2000, fp8=False):
+def compare_with_ssa(emu, n_probes=1000, n_rep=1000, seed=5, max_herd=2000, fp8=False,
+                     min_rate=0.0):
     """W1 and KS between the emulator's law and 1,000-replicate SSA ensembles
-    at n_probes random in-range states, per age class's I (S moves by the
-    same amount, so its distances are the same).  Returns a dict of mean and
-    max over probes."""
+    at n_probes random in-range states (total rate >= min_rate), per age
+    class's I (S moves by the same amount, so its distances are the same).
+    Returns a dict of mean and max over probes."""
     rng = np.random.default_rng(seed)
-    u0, phi = random_states(rng, n_probes, max_herd)
     g = random_params(rng)
+    us, ps, have = [], [], 0
+    while have < n_probes:
+        u, p = random_states(rng, 4 * n_probes, max_herd)
+        keep = total_rate(u, p, g) >= min_rate
+        us.append(u[keep])
+        ps.append(p[keep])
+        have += int(keep.sum())
+    u0 = np.concatenate(us)[:n_probes]
+    phi = np.concatenate(ps)[:n_probes]
+    res = compare_at_states(emu, u0, phi, g, n_rep=n_rep, seed=seed, fp8=fp8)
+    res["min_rate"] = float(min_rate)
+    return res
+
+
+def compare_at_states(emu, u0, phi, g, n_rep=1000, seed=5, fp8=False):
+    """W1 and KS between the emulator's law and n_rep-replicate SSA
+    ensembles at the given start states (rate parameters g), per age
+    class's I."""
+    n_probes = len(u0)
     U, w = ssa_one_day(u0, phi, g, seed=777 + seed, n_rep=n_rep)
     Ua = U[:, 1].cpu().numpy()  # (n_rep, n, 6)
     p = emulator_pmf(emu, u0, phi, g, fp8=fp8)

@@ -203,22 +203,28 @@ def test_engine_day_equals_sampled_network_bf16_and_fp8(env):
     m.close()
 
 
-def test_fp8_chain_ragged_replicates_and_fallback(env, orc):
+@pytest.mark.parametrize("min_rate", [0.0, 3.0])
+def test_fp8_chain_ragged_replicates_and_fallback(env, orc, min_rate):
     # 1,237 nodes (a ragged last tile), two replicates, 4% of the herds above
-    # the emulator's range: emulated nodes equal the sampled E4M3 network bit
-    # for bit, the others equal the oracle's SSA
+    # the emulator's range and (min_rate 3) the nodes with fewer than three
+    # expected transitions a day on the SSA: emulated nodes equal the sampled
+    # E4M3 network bit for bit, the others equal the oracle's SSA
     torch, binding, emulator = env
     rng = np.random.default_rng(33)
     n, R, seed = 1237, 2, 0x5EED_0F_C4A1
     u0, phi = emulator.random_states(rng, n)
+    g = emulator.random_params(rng)
+    quiet = emulator.total_rate(u0, phi, g) < min_rate
     big = rng.random(n) < 0.04
     u0[big, 4] += 2500
-    g = emulator.random_params(rng)
+    big |= quiet
+    if min_rate > 0:
+        assert 0.1 < quiet.mean() < 0.9
     emu = emulator.Emulator(seed=4)
     uu = torch.as_tensor(np.tile(u0, (R, 1)), device="cuda")
     ph = torch.as_tensor(np.tile(phi, R), device="cuda")
-    f, flag = emulator.features(uu, ph, g)
-    assert int(flag.sum()) == R * (n - big.sum())
+    f, flag = emulator.features(uu, ph, g, min_rate=min_rate)
+    assert np.array_equal(flag.cpu().numpy() == 1, np.tile(~big, R))
     emu.quantize_fp8(f)
     logits = emu.forward_fp8(f)
     delta = emulator.sample_increments(logits, uu, flag, seed, 1, n_nodes=n).cpu().numpy()
@@ -226,7 +232,7 @@ def test_fp8_chain_ragged_replicates_and_fallback(env, orc):
     code, U0, V0, R0, err = orc.run(w)
     assert code == 0
     m = binding.Model(w)
-    m.set_emulator(emu, max_herd=2000)
+    m.set_emulator(emu, max_herd=2000, min_rate=min_rate)
     m.set_emulator_fp8(emu)
     u0d, v0d = (torch.as_tensor(np.ascontiguousarray(a), device="cuda") for a in (w.u0, w.v0))
     U = torch.empty((R, 2, n, 6), dtype=torch.int32, device="cuda")
