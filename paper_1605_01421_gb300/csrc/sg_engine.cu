@@ -314,6 +314,10 @@ struct sg_model {
   float emu_act_scale[3] = {1.0f, 1.0f, 1.0f};
   DevBuf<uint8_t> emu_h8a, emu_h8b, emu_img;  // tiled E4M3 activations, weight images
   DevBuf<float> emu_hvec;                     // head-padded output-layer bias, scales
+  // side stream of the emulator day (the SSA part beside the chain) and its
+  // fork / join events
+  cudaStream_t side_st = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
   DevBuf<float> emu_logits;
   DevBuf<int32_t> emu_flag, emu_delta;
   // SISe_sp neighbour lists and the second phi buffer of the coupled step
@@ -519,6 +523,9 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
   m->emu_h8a.release(); m->emu_h8b.release(); m->emu_img.release(); m->emu_hvec.release();
+  if (m->side_st) cudaStreamDestroy(m->side_st);
+  if (m->side_fork) cudaEventDestroy(m->side_fork);
+  if (m->side_join) cudaEventDestroy(m->side_join);
   m->emu_logits.release(); m->emu_flag.release(); m->emu_delta.release();
   m->nb_ptr.release(); m->nb_idx.release(); m->nb_dist.release(); m->v2.release();
   m->aem_a.release(); m->aem_tau.release(); m->aem_cnt.release();
@@ -1027,13 +1034,42 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
         launch_days_kind(m, da, st);
         ++launches;
       }
+      const bool split = m->emu_fp8 && m->side_st != nullptr;
       if (m->emu_fp8) {
-        // the persistent E4M3 chain: features and layer 1, layers 2 and 3,
-        // layer 4 with the sampler
-        LaunchTimer lt(m, st, 3);
-        emu_chain_day(cw, m->emu_img.p, m->emu_hvec.p, m->emu_h8a.p, m->emu_h8b.p, m->u.p,
-                      m->v.p, ep, units, Nn, da.k0, da.k1, T, m->emu_flag.p, m->emu_delta.p,
-                      st);
+        // the persistent E4M3 chain: features, flags and layer 1; then the
+        // SSA of the units outside the emulator's range on the side stream,
+        // beside layers 2 and 3 and layer 4 with the sampler
+        {
+          LaunchTimer lt(m, st, 3);
+          emu_chain_day(cw, m->emu_img.p, m->emu_hvec.p, m->emu_h8a.p, m->emu_h8b.p, m->u.p,
+                        m->v.p, ep, units, Nn, da.k0, da.k1, T, m->emu_flag.p, m->emu_delta.p,
+                        st, 0);
+        }
+        if (split) {
+          cudaEventRecord(m->side_fork, st);
+          cudaStreamWaitEvent(m->side_st, m->side_fork, 0);
+          DayArgs db = da;
+          db.T_begin = T;
+          db.T_end = T + 1;
+          db.finish_first = 0;
+          db.finish_last = P.day_has_e2[d] != 0 ? 0 : 1;
+          db.emu = nullptr;
+          db.emu_flag = m->emu_flag.p;
+          db.emu_part = 1;
+          {
+            LaunchTimer lt(m, m->side_st, 0);
+            launch_days_kind(m, db, m->side_st);
+          }
+          cudaEventRecord(m->side_join, m->side_st);
+          ++launches;
+        }
+        {
+          LaunchTimer lt(m, st, 3);
+          emu_chain_day(cw, m->emu_img.p, m->emu_hvec.p, m->emu_h8a.p, m->emu_h8b.p, m->u.p,
+                        m->v.p, ep, units, Nn, da.k0, da.k1, T, m->emu_flag.p, m->emu_delta.p,
+                        st, 1);
+        }
+        if (split) cudaStreamWaitEvent(st, m->side_join, 0);
         launches += 4;
       } else {
         {
@@ -1083,10 +1119,12 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
       da.finish_first = 0;
       da.finish_last = e2_today ? 0 : 1;
       da.emu = m->emu_delta.p;
+      da.emu_part = split ? 2 : 0;  // split: the SSA part ran on the side stream
       {
         LaunchTimer lt(m, st, 0);
         launch_days_kind(m, da, st);
       }
+      da.emu_part = 0;
       ++launches;
       if (e2_today) {
         ea.day = T;
@@ -1243,6 +1281,19 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
           (rc = m->emu_h8b.ensure(tiles * kEmuTileBytes)) ||
           (rc = m->emu_img.ensure(kEmuImgBytes)) || (rc = m->emu_hvec.ensure(kEmuHeadVecFloats)))
         return rc;
+      if (!m->side_st) {
+        // side stream of the emulator day; without it the day runs in order
+        if (cudaStreamCreateWithFlags(&m->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&m->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&m->side_join, cudaEventDisableTiming) != cudaSuccess) {
+          cudaGetLastError();
+          if (m->side_st) cudaStreamDestroy(m->side_st);
+          if (m->side_fork) cudaEventDestroy(m->side_fork);
+          if (m->side_join) cudaEventDestroy(m->side_join);
+          m->side_st = nullptr;
+          m->side_fork = m->side_join = nullptr;
+        }
+      }
     } else if ((rc = m->emu_feat.ensure(units * kEmuIn)) ||
                (rc = m->emu_ha.ensure(units * kEmuHidden)) ||
                (rc = m->emu_hb.ensure(units * kEmuHidden)) ||
@@ -1266,7 +1317,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   const EvDev evd{m->e_type, m->e_select, m->e_shift, m->e_node, m->e_dest,
                   m->e_n,    m->e_prop,   m->e_index, m->e1_day,
                   P.n_e1 > 0 ? m->e1_node_off : nullptr};
-  DayArgs da;
+  DayArgs da{};
   da.u = m->u.p;
   da.v = m->v.p;
   da.ldata = m->ldata.p;
@@ -1686,7 +1737,7 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
                                             n_tspan, n_rep);
     ++launches;
     if (days > 0) {
-      DayArgs da;
+      DayArgs da{};
       da.u = d_u;
       da.v = d_v;
       da.ldata = d_ldata;

@@ -163,6 +163,12 @@ struct DayArgs {
                            // threads of the block only serve heavy nodes
   const int32_t *emu;      // [R][Nn][4]: emulated increments of I_1..I_3 and
                            // a flag (1 = use them instead of the SSA), or null
+  // the emulator's node split across two launches of a day: 0 every node;
+  // 1 only the nodes outside the emulator's range (emu_flag[gid] == 0, the
+  // SSA part, run beside the emulator); 2 only the emulated nodes (emu[gid]
+  // flag set)
+  const int32_t *emu_flag;
+  int32_t emu_part;
   uint32_t k0, k1;         // Philox key (seed)
   SgDevError *err;
   SgCounters *cnt;
@@ -1288,7 +1294,9 @@ k_days(const SgTables tb, const DayArgs a) {
     }
   }
   pdl_wait();
-  const bool live = in_range && *(volatile int32_t *)&a.err->code == 0;
+  bool live = in_range && *(volatile int32_t *)&a.err->code == 0;
+  if (live && a.emu_part == 1) live = a.emu_flag[gid] == 0;
+  if (live && a.emu_part == 2) live = a.emu[gid * 4 + 3] != 0;
   if (live) {
 #pragma unroll
     for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];

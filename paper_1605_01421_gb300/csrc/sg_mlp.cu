@@ -1180,7 +1180,7 @@ int emu_chain_images(const EmuChainWeights &cw, uint8_t *img, float *hvec, cudaS
 int emu_chain_day(const EmuChainWeights &cw, const uint8_t *img, const float *hvec,
                   uint8_t *act0, uint8_t *act1, const int32_t *u, const double *v,
                   const EmuParams &ep, long long units, int n_nodes, uint32_t k0, uint32_t k1,
-                  int T, int32_t *flag, int32_t *delta, cudaStream_t st) {
+                  int T, int32_t *flag, int32_t *delta, cudaStream_t st, int part) {
   if (units <= 0) return SG_OK;
   static std::mutex mu;
   static int n_sm = 0;
@@ -1214,12 +1214,15 @@ int emu_chain_day(const EmuChainWeights &cw, const uint8_t *img, const float *hv
   a.T = T;
   a.n_tiles = (int)tiles;
   a.err = err;
-  // layer 1: features -> E4M3 activations (act0)
-  a.W = img + kEmuImgOff[0];
-  a.bias = cw.b[0];
-  a.inv_out = 1.0f / cw.act_scale[0];
-  a.out = act0;
-  launch_emu_layer<0>(a, grid, st);
+  if (part == 0) {
+    // layer 1: features -> E4M3 activations (act0), range flags
+    a.W = img + kEmuImgOff[0];
+    a.bias = cw.b[0];
+    a.inv_out = 1.0f / cw.act_scale[0];
+    a.out = act0;
+    launch_emu_layer<0>(a, grid, st);
+    return cudaPeekAtLastError() == cudaSuccess ? SG_OK : SG_ERR_CUDA;
+  }
   // layers 2 and 3: act0 -> act1 -> act0
   for (int l = 1; l <= 2; ++l) {
     a.A = l == 1 ? act0 : act1;

@@ -95,10 +95,15 @@ constexpr size_t kEmuHeadVecFloats = 2 * 432;
 constexpr size_t kEmuTileBytes = 128 * 256;  // one tile of tiled E4M3 activations
 
 int emu_chain_images(const EmuChainWeights &cw, uint8_t *img, float *hvec, cudaStream_t st);
+// One emulator day in two parts: part 0 computes the features and range
+// flags of every unit from the day-start state (the input layer), part 1 the
+// other layers and the sampled increments; the SSA of the units outside the
+// range may run between them on another stream (it never touches a flagged
+// unit, and part 1 reads only flagged units' state).
 int emu_chain_day(const EmuChainWeights &cw, const uint8_t *img, const float *hvec,
                   uint8_t *act0, uint8_t *act1, const int32_t *u, const double *v,
                   const EmuParams &ep, long long units, int n_nodes, uint32_t k0, uint32_t k1,
-                  int T, int32_t *flag, int32_t *delta, cudaStream_t st);
+                  int T, int32_t *flag, int32_t *delta, cudaStream_t st, int part);
 
 __global__ void k_emu_features(const int32_t *u, const double *v, long long units, EmuParams ep,
                                __nv_bfloat16 *feat, int32_t *flag);
