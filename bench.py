@@ -49,8 +49,8 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal table figure)
 # (dram__bytes_read.sum + dram__bytes_write.sum, mean of the captured launches;
 # ncu flushes the caches between its passes, so it is the cold-cache figure).
 # It is reported only while the kernel sources hash to the captured ones.
-DAY_KERNEL_TRAFFIC = {"sources_sha1": "b818c45beaa3bdcea8b4f16b4a85ea7d73003cb9",
-                      "bytes_per_launch": 661504}
+DAY_KERNEL_TRAFFIC = {"sources_sha1": "b9cede1af8d73e079a9e3cda85bc0bd2385fb1d1",
+                      "bytes_per_launch": 661632}
 _KERNEL_SOURCES = ("sg_common.h", "sg_device.cuh", "sg_kernels.cuh")
 FP64_PER_DRAW_AEM = 42
 FP64_PER_REACTION_AEM = 12
