@@ -297,11 +297,13 @@ int sg_set_kernel_timing(sg_model *m, int enable);
  * nodes_per_block <= 0 or heavy_after < 0 restore the size-based defaults. */
 int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 
-/* Autotuner: runs the given workload (arguments as sg_run) once for each of
- * nodes_per_block in {4, 8, 16, 32, 64, 128} x heavy_after in {0, 1, 2, 4, 8},
- * keeps the fastest setting in the model and reports it (outputs may be
- * NULL).  U and V hold the last run's (identical) results.  A shorter tspan
- * tunes a long workload on a prefix. */
+/* Autotuner: for each of nodes_per_block in {4, 8, 16, 32, 64, 128} x
+ * heavy_after in {0, 1, 2, 4, 8} runs the given workload (arguments as
+ * sg_run) once untimed (capturing its graph when graphs are on) and twice
+ * timed, keeps the setting with the fastest timed run in the model and
+ * reports it and its time (outputs may be NULL).  U and V hold the last
+ * run's (identical) results.  A shorter tspan tunes a long workload on a
+ * prefix. */
 int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
                 int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
                 double *d_V, void *stream, int32_t *nodes_per_block,

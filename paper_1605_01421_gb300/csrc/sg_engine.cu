@@ -1835,14 +1835,23 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
     for (int32_t h : kHeavy) {
       m->npb = npb;
       m->heavy_after = h;
-      cudaEventRecord(e0, st);
+      // one untimed run (it captures the candidate's graph when graphs are
+      // on), then the faster of two timed runs
       rc = sg_run(m, tspan, n_tspan, seed, n_rep, d_u0, d_v0, d_U, d_V, stream, nullptr,
                   nullptr);
-      cudaEventRecord(e1, st);
       if (rc) break;
-      float ms = 0.f;
-      cudaEventSynchronize(e1);
-      cudaEventElapsedTime(&ms, e0, e1);
+      float ms = 3.0e38f;
+      for (int rep = 0; rep < 2 && rc == SG_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = sg_run(m, tspan, n_tspan, seed, n_rep, d_u0, d_v0, d_U, d_V, stream, nullptr,
+                    nullptr);
+        cudaEventRecord(e1, st);
+        float t = 0.f;
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (rc) break;
       if (ms < best) {
         best = ms;
         best_npb = npb;
