@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -199,25 +200,105 @@ __global__ void k_fp64_fma(double *out, int iters) {
 // Host runtime
 // ---------------------------------------------------------------------------
 
+// Memory kept for reuse by the models of the process: blocks freed by one
+// model are handed to the next (creating and freeing CUDA memory costs tens
+// to hundreds of microseconds a call and synchronises the device).  Blocks
+// are matched by (device, size rounded up to 256 bytes), best fit up to
+// twice the size asked for; at most kCap bytes stay cached, the rest is
+// freed.  A block goes back to the pool only when its model is destroyed or
+// grows it, after sg_run has synchronised its stream.
+class MemPool {
+ public:
+  explicit MemPool(bool pinned) : pinned_(pinned) {}
+  void *get(size_t bytes) {
+    bytes = round(bytes);
+    const int dev = device();
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      auto it = free_.lower_bound(Key{dev, bytes});
+      if (it != free_.end() && it->first.dev == dev && it->first.bytes <= 2 * bytes) {
+        void *p = it->second;
+        cached_ -= it->first.bytes;
+        owner_[p] = it->first;
+        free_.erase(it);
+        return p;
+      }
+    }
+    void *p = nullptr;
+    const cudaError_t e = pinned_ ? cudaMallocHost(&p, bytes) : cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu_);
+    owner_[p] = Key{dev, bytes};
+    return p;
+  }
+  void put(void *p) {
+    if (!p) return;
+    std::unique_lock<std::mutex> lock(mu_);
+    auto it = owner_.find(p);
+    const Key k = it == owner_.end() ? Key{0, 0} : it->second;
+    if (it != owner_.end()) owner_.erase(it);
+    if (k.bytes && cached_ + k.bytes <= kCap) {
+      free_.emplace(k, p);
+      cached_ += k.bytes;
+      return;
+    }
+    lock.unlock();
+    if (pinned_)
+      cudaFreeHost(p);
+    else
+      cudaFree(p);
+  }
+
+ private:
+  struct Key {
+    int dev;
+    size_t bytes;
+    bool operator<(const Key &o) const { return dev != o.dev ? dev < o.dev : bytes < o.bytes; }
+  };
+  static constexpr size_t kCap = (size_t)1 << 30;
+  static size_t round(size_t b) { return ((b ? b : 1) + 255) & ~(size_t)255; }
+  static int device() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess) {
+      cudaGetLastError();
+      d = 0;
+    }
+    return d;
+  }
+  const bool pinned_;
+  std::mutex mu_;
+  std::multimap<Key, void *> free_;
+  std::map<void *, Key> owner_;  // blocks in use: device and size
+  size_t cached_ = 0;
+};
+
+static MemPool &device_pool() {
+  static MemPool *p = new MemPool(false);  // never destroyed (outlives every model)
+  return *p;
+}
+static MemPool &pinned_pool() {
+  static MemPool *p = new MemPool(true);
+  return *p;
+}
+
 template <typename T>
 struct DevBuf {
   T *p = nullptr;
   size_t n = 0;
   int ensure(size_t want) {
     if (want <= n && p) return SG_OK;
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
+    release();
     if (want == 0) want = 1;
-    if (cudaMalloc(&p, want * sizeof(T)) != cudaSuccess) {
-      cudaGetLastError();
-      return SG_ERR_NOMEM;
-    }
+    p = static_cast<T *>(device_pool().get(want * sizeof(T)));
+    if (!p) return SG_ERR_NOMEM;
     n = want;
     return SG_OK;
   }
   void release() {
-    if (p) cudaFree(p);
+    device_pool().put(p);
     p = nullptr;
     n = 0;
   }
@@ -439,8 +520,10 @@ static int model_create(const sg_desc *d, sg_model **out, bool generic) {
   int rc = upload(m->ldata, ld);
   if (!rc) rc = m->err.ensure(1);
   if (!rc) rc = m->cnt.ensure(1);
-  if (!rc && cudaMallocHost(&m->h_err, sizeof(SgDevError)) != cudaSuccess) rc = SG_ERR_NOMEM;
-  if (!rc && cudaMallocHost(&m->h_cnt, sizeof(SgCounters)) != cudaSuccess) rc = SG_ERR_NOMEM;
+  if (!rc && !(m->h_err = static_cast<SgDevError *>(pinned_pool().get(sizeof(SgDevError)))))
+    rc = SG_ERR_NOMEM;
+  if (!rc && !(m->h_cnt = static_cast<SgCounters *>(pinned_pool().get(sizeof(SgCounters)))))
+    rc = SG_ERR_NOMEM;
   if (rc) {
     cudaGetLastError();
     sg_model_destroy(m);
@@ -534,8 +617,8 @@ extern "C" void sg_model_destroy(sg_model *m) {
   jit_release(m->jit);
   m->e2_done.release();
   m->grid_bar.release();
-  if (m->h_err) cudaFreeHost(m->h_err);
-  if (m->h_cnt) cudaFreeHost(m->h_cnt);
+  pinned_pool().put(m->h_err);
+  pinned_pool().put(m->h_cnt);
   for (cudaEvent_t e : m->evpool) cudaEventDestroy(e);
   if (m->graph_exec) cudaGraphExecDestroy(m->graph_exec);
   delete m;
