@@ -635,19 +635,7 @@ extern "C" int sg_set_events(sg_model *m, int64_t n_events, const int32_t *event
     return SG_ERR_ARG;
   EventTable ev;
   try {
-    ev.type.assign(event, event + n_events);
-    ev.time.assign(time, time + n_events);
-    ev.node.assign(node, node + n_events);
-    ev.dest.assign(dest, dest + n_events);
-    ev.n.assign(n, n + n_events);
-    ev.proportion.assign(proportion, proportion + n_events);
-    ev.select.assign(select, select + n_events);
-    ev.shift.assign(shift, shift + n_events);
-    if (rep) {
-      ev.rep.assign(rep, rep + n_events);
-      ev.per_rep = true;
-      for (int64_t e = 0; e < n_events; ++e) ev.max_rep = std::max(ev.max_rep, rep[e]);
-    }
+    copy_events(&ev, n_events, event, time, node, dest, n, proportion, select, shift, rep);
   } catch (const std::bad_alloc &) {
     return SG_ERR_NOMEM;
   }

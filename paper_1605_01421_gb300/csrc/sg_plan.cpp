@@ -14,9 +14,10 @@
 
 namespace sg {
 
-int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad) {
-  const int64_t n = ev.size();
-  for (int64_t e = 0; e < n; ++e) {
+// Checks of events lo .. hi - 1; the first offending one in *bad (-1: none).
+static int validate_range(const SgTables &tb, const EventTable &ev, int64_t lo, int64_t hi,
+                          int64_t *bad) {
+  for (int64_t e = lo; e < hi; ++e) {
     const int type = ev.type[e], s = ev.select[e], q = ev.shift[e];
     bool ok = type >= SG_EXIT && type <= SG_EXTERNAL_TRANSFER;
     ok = ok && ev.node[e] >= 0 && ev.node[e] < tb.n_nodes;
@@ -231,7 +232,7 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     int64_t e;
     int32_t day, time0, type;  // time0: the time on day 0, else 0
   };
-  std::vector<Rec1> rec1(n_e1);
+  std::unique_ptr<Rec1[]> rec1(new Rec1[n_e1 > 0 ? n_e1 : 1]);  // left unset: all written below
   run_threads(TB, [&](int t) {
     std::vector<int32_t> &f1 = c1[t], &f2 = c2[t];
     const int64_t lo = n * t / TB, hi = n * (t + 1) / TB;
@@ -276,7 +277,7 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     for (int64_t k = r1[t]; k < r1[t + 1]; ++k) {
       const int64_t lo = e1_count[k];
       const int32_t m = (int32_t)(e1_count[k + 1] - lo);
-      const Rec1 *rc = rec1.data() + lo;
+      const Rec1 *rc = rec1.get() + lo;
       keys.resize(m);
       bool sorted = true;
       for (int32_t i = 0; i < m; ++i) {
@@ -364,6 +365,49 @@ void gather_events(const EventTable &ev, const Plan &P, int8_t *type, int8_t *sh
       index[i] = e;
     }
   });
+}
+
+int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad) {
+  const int64_t n = ev.size();
+  const int T = plan_threads(n);
+  std::vector<int> rc(T, SG_OK);
+  std::vector<int64_t> first(T, -1);
+  run_threads(T, [&](int t) {
+    rc[t] = validate_range(tb, ev, n * t / T, n * (t + 1) / T, &first[t]);
+  });
+  // the first offending event of the list: in the first slice that has one
+  for (int t = 0; t < T; ++t)
+    if (rc[t]) {
+      *bad = first[t];
+      return rc[t];
+    }
+  *bad = -1;
+  return SG_OK;
+}
+
+void copy_events(EventTable *out, int64_t n, const int32_t *type, const int32_t *time,
+                 const int32_t *node, const int32_t *dest, const int32_t *cnt,
+                 const double *proportion, const int32_t *select, const int32_t *shift,
+                 const int32_t *rep) {
+  EventTable &ev = *out;
+  plan_vector<int32_t> *cols[8] = {&ev.type, &ev.time, &ev.node, &ev.dest,
+                                   &ev.n,    &ev.select, &ev.shift, &ev.rep};
+  const int32_t *src[8] = {type, time, node, dest, cnt, select, shift, rep};
+  for (int c = 0; c < 8; ++c) cols[c]->resize(src[c] ? (size_t)n : 0);
+  ev.proportion.resize((size_t)n);
+  ev.per_rep = rep != nullptr;
+  const int T = plan_threads(n);
+  std::vector<int32_t> max_rep(T, -1);
+  run_threads(T, [&](int t) {
+    const int64_t lo = n * t / T, hi = n * (t + 1) / T;
+    for (int c = 0; c < 8; ++c)
+      if (src[c] && hi > lo) std::copy(src[c] + lo, src[c] + hi, cols[c]->data() + lo);
+    if (hi > lo) std::copy(proportion + lo, proportion + hi, ev.proportion.data() + lo);
+    if (rep)
+      for (int64_t e = lo; e < hi; ++e) max_rep[t] = std::max(max_rep[t], rep[e]);
+  });
+  ev.max_rep = -1;
+  for (int t = 0; t < T; ++t) ev.max_rep = std::max(ev.max_rep, max_rep[t]);
 }
 
 }  // namespace sg

@@ -4,20 +4,56 @@
 
 #include <stdint.h>
 
+#include <memory>
+#include <new>
+#include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "sg_common.h"
 
 namespace sg {
 
+// Allocator whose default construction leaves trivial elements unset: the
+// planner's large arrays are written exactly once by its threads, which then
+// also touch their pages first (a value-initialised vector would zero them
+// on one thread beforehand).
+template <class T>
+struct DefaultInitAllocator : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = DefaultInitAllocator<U>;
+  };
+  DefaultInitAllocator() noexcept = default;
+  template <class U>
+  DefaultInitAllocator(const DefaultInitAllocator<U> &) noexcept {}
+  template <class U>
+  void construct(U *p) noexcept(std::is_nothrow_default_constructible<U>::value) {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <class U, class... Args>
+  void construct(U *p, Args &&...args) {
+    ::new (static_cast<void *>(p)) U(std::forward<Args>(args)...);
+  }
+};
+template <class T>
+using plan_vector = std::vector<T, DefaultInitAllocator<T>>;
+
 // The caller's event table, copied (0-based; shift < 0 = no shift).
 struct EventTable {
-  std::vector<int32_t> type, time, node, dest, n, select, shift, rep;
-  std::vector<double> proportion;
+  plan_vector<int32_t> type, time, node, dest, n, select, shift, rep;
+  plan_vector<double> proportion;
   bool per_rep = false;  // rep[] given
   int32_t max_rep = -1;
   int64_t size() const { return (int64_t)type.size(); }
 };
+
+// The caller's columns copied into *ev (rep may be NULL), in parallel over
+// slices of the table.
+void copy_events(EventTable *ev, int64_t n, const int32_t *type, const int32_t *time,
+                 const int32_t *node, const int32_t *dest, const int32_t *cnt,
+                 const double *proportion, const int32_t *select, const int32_t *shift,
+                 const int32_t *rep);
 
 // Checks of the event table against the model (Sec. 3.3 constraints and the
 // readings of the engine): returns SG_OK or the error code, and the index of
@@ -43,8 +79,8 @@ int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad);
 // additions in list order.
 struct Plan {
   int32_t t0 = 0, t_end = 0, slots = 1, days = 0, n_nodes = 0;
-  std::vector<int64_t> order;        // E1 part, then E2 part (EventTable indices)
-  std::vector<int32_t> e1_day;       // [n_e1] day index of each E1 event
+  plan_vector<int64_t> order;        // E1 part, then E2 part (EventTable indices)
+  plan_vector<int32_t> e1_day;       // [n_e1] day index of each E1 event
   std::vector<int64_t> e1_node_off;  // [slots * n_nodes + 1] into order
   std::vector<int64_t> e2_wave_off;  // [days * slots + 1] into wave_ev
   std::vector<int64_t> wave_ev;      // [n_waves + 1] positions in order
