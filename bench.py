@@ -57,8 +57,8 @@ FP64_PER_REACTION_AEM = 12
 FP64_PER_NODE_DAY_AEM = 16
 
 
-def _workload(name, solver="ssm"):
-    w = _base_workload(name)
+def _workload(name, solver="ssm", days=None, reps=None):
+    w = _base_workload(name, days=days, reps=reps)
     from paper_1605_01421_gb300 import workloads as W
     w.solver = W.AEM if solver == "aem" else W.SSM
     return w
@@ -68,16 +68,21 @@ def _metric(w):
     return METRIC_AEM if getattr(w, "solver", 0) == 1 else METRIC
 
 
-def _base_workload(name):
+def _base_workload(name, days=None, reps=None):
+    """The named workload; `days` / `reps` shrink it (profiling captures on a
+    smaller case of the same kernel)."""
     from paper_1605_01421_gb300 import workloads as W
+    kw = {} if days is None else {"days": days}
     if name == "sise":
-        return W.config_sise()
+        return W.config_sise(**kw)
     if name == "sir":
         return W.config_sir()
     if name == "sise3":
-        return W.config_sise3()
+        return W.config_sise3(**kw)
     if name == "batched":
-        return W.config_batched()
+        if reps is not None:
+            kw["n_rep"] = reps
+        return W.config_batched(**kw)
     if name == "sise_sp":
         return W.config_sise_sp()
     if name == "predator_prey":
@@ -286,7 +291,7 @@ def bench_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     binding.build()
-    w = _workload(args.workload, args.solver)
+    w = _workload(args.workload, args.solver, args.days, args.reps)
     aem = w.solver == 1
     n_rep = w.n_rep
     M = len(w.tspan)
@@ -307,7 +312,11 @@ def bench_gpu(args):
         return model.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
 
     tuned = None
-    if args.autotune:
+    if args.tuning:
+        npb, heavy = (int(x) for x in args.tuning.split(","))
+        model.set_tuning(npb, heavy)
+        tuned = (npb, heavy, None)
+    elif args.autotune:
         # the work split changes speed only, never results; workloads whose
         # runs take seconds are tuned on a prefix of days (the buffers hold the
         # full run)
@@ -389,7 +398,7 @@ def bench_gpu(args):
 
     # end to end through the public host-buffer call
     e2e = None
-    if True:
+    if args.e2e:
         u0h = torch.as_tensor(np.ascontiguousarray(w.u0)).pin_memory().numpy()
         v0h = torch.as_tensor(np.ascontiguousarray(w.v0)).pin_memory().numpy()
         Uh = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32).pin_memory().numpy()
@@ -640,6 +649,12 @@ def main():
                     help="nodes with fewer expected transitions per day stay on the SSA")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--days", type=int, default=None,
+                    help="shorter run of the workload (sise, sise3, batched)")
+    ap.add_argument("--reps", type=int, default=None, help="replicates (batched)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed work split 'nodes_per_block,heavy_after' instead of the autotuner")
+    ap.add_argument("--e2e", type=int, default=1, help="0: skip the end-to-end leg")
     ap.add_argument("--solver", default="ssm", choices=["ssm", "aem"],
                     help="ssm: split-step direct SSA; aem: all events method (Sec. 3.4.2)")
     args = ap.parse_args()

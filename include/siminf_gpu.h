@@ -408,9 +408,8 @@ const char *sg_strerror(int code);
  *
  * Some callers cannot call cudaMalloc (or anything that allocates): code that
  * runs inside a host framework which owns the device memory pool and forbids
- * private allocations, services that must not allocate after start-up so
- * that their memory footprint stays fixed, and pipelines that may run while a
- * CUDA stream is being captured, where allocation calls are not allowed.
+ * private allocations, and services that must not allocate after start-up so
+ * that their memory footprint stays fixed.
  * This entry point needs neither an sg_model nor any allocation: the model
  * tables come from `desc` (host memory, read during the call; desc->ldata is
  * ignored and `d_ldata` gives the local data on the device, n_ldata x
@@ -433,8 +432,10 @@ const char *sg_strerror(int code);
  *     call's contents (each call clears what must start at zero); calls whose
  *     work overlaps on the GPU (several host threads, or several streams
  *     without ordering) race on it and must be serialised by the caller;
- *   - otherwise as sg_run: same results bit for bit, same errors; the call
- *     waits for its stream before it returns. */
+ *   - the call copies `tspan` from host memory to the array, reads the
+ *     error word and counters back into host memory and waits for its
+ *     stream (cudaStreamSynchronize) before it returns;
+ *   - otherwise as sg_run: same results bit for bit, same errors. */
 #define SG_NOALLOC_SCRATCH_BYTES (8u << 20)
 int sg_run_noalloc(const sg_desc *desc, const double *d_ldata, const int32_t *tspan,
                    int32_t n_tspan, uint64_t seed, int32_t n_rep, const int32_t *d_u0,

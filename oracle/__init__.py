@@ -24,6 +24,8 @@ _SRC = os.path.join(_HERE, "siminf_oracle.c")
 _HDR = os.path.join(_HERE, "siminf_oracle.h")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libsiminf_oracle.so")
+# the same source with -fopenmp: node loops in parallel (timing only)
+_OMP_LIB_PATH = os.path.join(_OUT_DIR, "libsiminf_oracle_omp.so")
 
 ERR_NAMES = {
     0: "ok",
@@ -40,19 +42,23 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/_build/libsiminf_oracle.so``."""
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into ``oracle/_build/libsiminf_oracle.so`` (or,
+    with ``openmp``, the node-parallel timing build
+    ``libsiminf_oracle_omp.so`` of the same source)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
+    path = _OMP_LIB_PATH if openmp else _LIB_PATH
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= newest):
-        return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    if (not force and os.path.exists(path)
+            and os.path.getmtime(path) >= newest):
+        return path
+    tmp = path + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           "-fPIC", "-shared"] + (["-fopenmp"] if openmp else []) + [
+           "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 class _Model(ctypes.Structure):
@@ -88,44 +94,89 @@ class _Error(ctypes.Structure):
                 ("day", ctypes.c_int)]
 
 
-def lib():
-    global _lib
+class _TauRecord(ctypes.Structure):
+    _fields_ = [("rep", ctypes.c_int), ("node", ctypes.c_int), ("T", ctypes.c_int),
+                ("tau", ctypes.c_double)]
+
+
+_omp_lib = None
+
+
+def lib(openmp: bool = False):
+    """The serial oracle (or, with ``openmp``, its node-parallel timing
+    build)."""
+    global _lib, _omp_lib
     with _lock:
+        if openmp:
+            if _omp_lib is None:
+                _omp_lib = _load(build(openmp=True), openmp=True)
+            return _omp_lib
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            u32p = ctypes.POINTER(ctypes.c_uint32)
-            L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
-            L.oracle_philox4x32_10.restype = None
-            L.oracle_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
-            L.oracle_u01.restype = ctypes.c_double
-            L.oracle_log.argtypes = [ctypes.c_double]
-            L.oracle_log.restype = ctypes.c_double
-            L.oracle_bounded_sequence.argtypes = [
-                ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, u32p,
-                ctypes.c_int, u32p]
-            L.oracle_bounded_sequence.restype = ctypes.c_uint32
-            ip = ctypes.POINTER(ctypes.c_int)
-            L.oracle_apply_event.argtypes = [
-                ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int,
-                ip, ip, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int]
-            L.oracle_apply_event.restype = ctypes.c_int
-            L.oracle_run.argtypes = [
-                ctypes.POINTER(_Model), ctypes.POINTER(_Events),
-                ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
-                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
-            L.oracle_run.restype = ctypes.c_int
-            L.oracle_run_reps.argtypes = [
-                ctypes.POINTER(_Model), ctypes.POINTER(_Events),
-                ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
-                ctypes.c_int, ctypes.c_int,
-                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
-            L.oracle_run_reps.restype = ctypes.c_int
-            _lib = L
+            _lib = _load(build())
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the OpenMP timing build's parallel loops."""
+    lib(openmp=True).omp_set_num_threads(int(n))
+
+
+def _load(path, openmp=False):
+    L = ctypes.CDLL(path)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.oracle_philox4x32_10.restype = None
+    L.oracle_u01.argtypes = [ctypes.c_uint32, ctypes.c_uint32]
+    L.oracle_u01.restype = ctypes.c_double
+    L.oracle_log.argtypes = [ctypes.c_double]
+    L.oracle_log.restype = ctypes.c_double
+    L.oracle_bounded_sequence.argtypes = [
+        ctypes.c_uint64, ctypes.c_int64, ctypes.c_int, u32p,
+        ctypes.c_int, u32p]
+    L.oracle_bounded_sequence.restype = ctypes.c_uint32
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.oracle_apply_event.argtypes = [
+        ctypes.c_int, ip, ctypes.c_int, ip, ctypes.c_int, ctypes.c_int,
+        ip, ip, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+        ctypes.c_int, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int]
+    L.oracle_apply_event.restype = ctypes.c_int
+    L.oracle_run.argtypes = [
+        ctypes.POINTER(_Model), ctypes.POINTER(_Events),
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
+    L.oracle_run.restype = ctypes.c_int
+    L.oracle_run_reps.argtypes = [
+        ctypes.POINTER(_Model), ctypes.POINTER(_Events),
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_int,
+        ctypes.c_int, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_Error)]
+    L.oracle_run_reps.restype = ctypes.c_int
+    L.oracle_trace_first_tau.argtypes = [ctypes.c_void_p, ctypes.c_int64]
+    L.oracle_trace_first_tau.restype = ctypes.c_int64
+    if openmp:
+        L.omp_set_num_threads.argtypes = [ctypes.c_int]
+        L.omp_set_num_threads.restype = None
+    return L
+
+
+def first_waiting_times(w, cap, **run_kw):
+    """Test hook: run the serial oracle on ``w`` and return, for every
+    node-day with lambda > 0 (direct method, at most ``cap`` of them in run
+    order), the replicate, node, T and the waiting time tau of its first
+    draw (whether or not it passes T), plus run()'s return value."""
+    L = lib()
+    buf = (_TauRecord * int(cap))()
+    L.oracle_trace_first_tau(ctypes.cast(buf, ctypes.c_void_p), int(cap))
+    try:
+        res = run(w, **run_kw)
+    finally:
+        n = int(L.oracle_trace_first_tau(None, 0))
+    rec = np.ctypeslib.as_array(buf)[:n]
+    out = {"rep": rec["rep"].copy(), "node": rec["node"].copy(), "T": rec["T"].copy(),
+           "tau": rec["tau"].copy()}
+    return out, res
 
 
 def _i32(a):
@@ -200,7 +251,7 @@ def _generic(w):
     return c.parsed.S, c.parsed.G, c.address
 
 
-def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None, rep0=0):
+def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None, rep0=0, openmp=False):
     """Run the oracle on a workload description (see
     ``paper_1605_01421_gb300.workloads.Workload``).
 
@@ -209,10 +260,13 @@ def run(w, seed=None, n_rep=None, u0=None, v0=None, solver=None, rep0=0):
     rep0 .. rep0 + n_rep - 1 of the workload's w.n_rep (their own streams and
     events) and returns only those.
 
+    ``openmp`` runs the node-parallel timing build (same results; threads
+    set with ``set_threads``).
+
     Returns ``(code, U, V, reactions, err)`` with U [R][M][Nn][C] int32,
     V [R][M][Nn][Nv] float64, reactions [R] int64 and err a dict.
     """
-    L = lib()
+    L = lib(openmp)
     seed = w.seed if seed is None else seed
     n_rep = w.n_rep if n_rep is None else n_rep
     if u0 is None:

@@ -14,6 +14,11 @@
  * Every floating-point expression is evaluated left to right exactly as
  * written; no fused multiply-add is allowed (the CUDA side is built with
  * -fmad=false for the same reason), so the double results are bit-identical.
+ * The same source compiled with -fopenmp is a timing build for the CPU
+ * baseline only: the node loops of a day (SSA, each node's E1 events, post
+ * time step) run in parallel as in the paper's solver (Sec. 3.4.2), E2
+ * events stay serial, and the results are the serial build's.  The tests use
+ * the serial build.
  *
  * What each part follows:
  *   - the split-step solver: Sec. 2.3 (Eq. numstep1-numstep3) and the solver
@@ -50,6 +55,9 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include "siminf_oracle.h"
 
@@ -575,6 +583,29 @@ static int validate(const oracle_model *m, const oracle_events *ev,
     return 0;
 }
 
+/* Test hook (not part of the method): when a trace buffer is set, the
+ * direct method appends, for every node-day with lambda > 0, the waiting time
+ * tau of its first draw (whether or not t + tau passes T) with the node-day's
+ * replicate, node and T.  The waiting-time law of Appendix A is pinned on
+ * these records.  Serial builds only. */
+static oracle_tau_record *g_tau_trace = NULL;
+static int64_t g_tau_cap = 0, g_tau_n = 0;
+
+int64_t oracle_trace_first_tau(oracle_tau_record *buf, int64_t cap)
+{
+#ifdef _OPENMP
+    (void)buf;
+    (void)cap;
+    return -1;
+#else
+    int64_t n = g_tau_n;
+    g_tau_trace = cap > 0 ? buf : NULL;
+    g_tau_cap = cap > 0 ? cap : 0;
+    g_tau_n = 0;
+    return n;
+#endif
+}
+
 /* Direct SSA for one node from its current time t0 = T - 1 (or tspan[0])
  * up to the next unit of time T (Appendix A).  Returns an error code. */
 static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
@@ -615,6 +646,13 @@ static int ssa_node_day(const oracle_model *m, int node, int rep, int T,
         r1 = oracle_u01(x[0], x[1]);
         r2 = oracle_u01(x[2], x[3]);
         tau = -oracle_log(r1) / lambda;
+        if (g_tau_trace && ctr[0] == 1 && g_tau_n < g_tau_cap) {
+            g_tau_trace[g_tau_n].rep = rep;
+            g_tau_trace[g_tau_n].node = node;
+            g_tau_trace[g_tau_n].T = T;
+            g_tau_trace[g_tau_n].tau = tau;
+            g_tau_n++;
+        }
         if (t + tau >= (double)T) break;
         t = t + tau;
         /* Inversion: the smallest n with lambda r2 <= sum_{j<=n} w_j, summed
@@ -789,7 +827,7 @@ int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
     int64_t n_sorted = 0, e;
     int r, rc;
     int *u = NULL;
-    double *v = NULL, *v_new = NULL, *vtmp = NULL;
+    double *v = NULL, *vtmp = NULL;
     double *aem_a = NULL, *aem_tau = NULL;
     uint32_t *aem_cnt = NULL;
     const size_t nch = (size_t)Nn * (size_t)m->n_trans;
@@ -820,16 +858,15 @@ int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
 
     u = (int *)malloc((ustride ? ustride : 1) * sizeof *u);
     v = (double *)malloc((vstride ? vstride : 1) * sizeof *v);
-    v_new = (double *)malloc((Nv ? Nv : 1) * sizeof *v_new);
     vtmp = (double *)malloc((Nn ? Nn : 1) * sizeof *vtmp);
     if (m->solver == ORACLE_SOLVER_AEM) {
         aem_a = (double *)malloc((nch ? nch : 1) * sizeof *aem_a);
         aem_tau = (double *)malloc((nch ? nch : 1) * sizeof *aem_tau);
         aem_cnt = (uint32_t *)malloc((nch ? nch : 1) * sizeof *aem_cnt);
     }
-    if (!u || !v || !v_new || !vtmp ||
+    if (!u || !v || !vtmp ||
         (m->solver == ORACLE_SOLVER_AEM && (!aem_a || !aem_tau || !aem_cnt))) {
-        free(order); free(u); free(v); free(v_new); free(vtmp);
+        free(order); free(u); free(v); free(vtmp);
         free(aem_a); free(aem_tau); free(aem_cnt);
         return ORACLE_ERR_NOMEM;
     }
@@ -861,19 +898,46 @@ int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
             double t0 = (double)(T - 1);
             int64_t nr = 0;
 
-            /* (1) local stochastic step, Eq. numstep1, node by node */
-            for (node = 0; node < Nn; node++) {
-                if (aem_a) {
-                    const size_t o = (size_t)node * (size_t)m->n_trans;
-                    rc = aem_node_day(m, node, rep, T, t0, u + (size_t)node * C,
-                                      v + (size_t)node * Nv, aem_a + o,
-                                      aem_tau + o, aem_cnt + o, seed, &nr);
-                } else {
-                    rc = ssa_node_day(m, node, rep, T, t0, u + (size_t)node * C,
-                                      v + (size_t)node * Nv, seed, &nr);
+            /* (1) local stochastic step, Eq. numstep1, node by node.  The
+             * nodes are independent; the timing build (OpenMP) runs them in
+             * parallel as the paper's solver does (Sec. 3.4.2).  Either way
+             * the failing node with the lowest index is reported. */
+            {
+                int bad_node = -1, bad_rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(guided) reduction(+ : nr)
+#endif
+                for (node = 0; node < Nn; node++) {
+                    int64_t nr_node = 0;
+                    int rc_node;
+#ifndef _OPENMP
+                    if (bad_node >= 0) continue;
+#endif
+                    if (aem_a) {
+                        const size_t o = (size_t)node * (size_t)m->n_trans;
+                        rc_node = aem_node_day(m, node, rep, T, t0, u + (size_t)node * C,
+                                               v + (size_t)node * Nv, aem_a + o,
+                                               aem_tau + o, aem_cnt + o, seed, &nr_node);
+                    } else {
+                        rc_node = ssa_node_day(m, node, rep, T, t0, u + (size_t)node * C,
+                                               v + (size_t)node * Nv, seed, &nr_node);
+                    }
+                    nr += nr_node;
+                    if (rc_node) {
+#ifdef _OPENMP
+#pragma omp critical(oracle_first_bad_node)
+#endif
+                        {
+                            if (bad_node < 0 || node < bad_node) {
+                                bad_node = node;
+                                bad_rc = rc_node;
+                            }
+                        }
+                    }
                 }
-                if (rc) {
-                    set_error(err, rc, rep, node, -1, T);
+                if (bad_node >= 0) {
+                    set_error(err, bad_rc, rep, bad_node, -1, T);
+                    rc = bad_rc;
                     goto done;
                 }
             }
@@ -886,50 +950,131 @@ int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
             while (seg_end < n_sorted && order[seg_end].time <= T) seg_end++;
             cursor = seg_end;
 
-            /* (2) data step, Eq. numstep2: E1 events, then E2 events */
-            for (int pass = 0; pass < 2; pass++) {
-                for (e = seg_begin; e < seg_end; e++) {
-                    int64_t idx = order[e].idx;
-                    int type = ev->event[idx];
-                    int nd = ev->node[idx], ds = ev->dest[idx];
-                    if ((pass == 0) != (type != ORACLE_EV_EXTERNAL)) continue;
-                    if (ev->rep && ev->rep[idx] != rep) continue;
-                    rc = oracle_apply_event(
-                        C, m->E, m->n_select, m->N, m->n_shift, type,
-                        u + (size_t)nd * C,
-                        type == ORACLE_EV_EXTERNAL ? u + (size_t)ds * C : NULL,
-                        ev->n_ind[idx], ev->proportion[idx], ev->select[idx],
-                        ev->shift[idx], seed, idx, rep);
-                    if (rc) {
-                        set_error(err, rc, rep, nd, idx, T);
-                        goto done;
+            /* (2) data step, Eq. numstep2: E1 events in sorted order, then
+             * E2 events in sorted order.  An E1 event touches one node only,
+             * so in the timing build each thread applies the E1 events of
+             * its own range of nodes (in sorted order, as the paper's node
+             * threads do); E2 events stay serial (Sec. 3.4.2).  The first
+             * failing E1 event in sorted order is reported. */
+            {
+                int64_t bad_e = -1;
+                int bad_rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+                {
+                    int nth = 1, me = 0, nd_lo, nd_hi;
+                    int64_t e1;
+#ifdef _OPENMP
+                    nth = omp_get_num_threads();
+                    me = omp_get_thread_num();
+#endif
+                    nd_lo = (int)(((int64_t)Nn * me) / nth);
+                    nd_hi = (int)(((int64_t)Nn * (me + 1)) / nth);
+                    for (e1 = seg_begin; e1 < seg_end; e1++) {
+                        int64_t idx = order[e1].idx;
+                        int type = ev->event[idx], nd = ev->node[idx], rc1;
+                        if (type == ORACLE_EV_EXTERNAL) continue;
+                        if (ev->rep && ev->rep[idx] != rep) continue;
+                        if (nd < nd_lo || nd >= nd_hi) continue;
+                        rc1 = oracle_apply_event(
+                            C, m->E, m->n_select, m->N, m->n_shift, type,
+                            u + (size_t)nd * C, NULL, ev->n_ind[idx],
+                            ev->proportion[idx], ev->select[idx], ev->shift[idx],
+                            seed, idx, rep);
+                        if (rc1) {
+#ifdef _OPENMP
+#pragma omp critical(oracle_first_bad_event)
+#endif
+                            {
+                                if (bad_e < 0 || e1 < bad_e) {
+                                    bad_e = e1;
+                                    bad_rc = rc1;
+                                }
+                            }
+                            break;
+                        }
                     }
+                }
+                if (bad_e >= 0) {
+                    int64_t idx = order[bad_e].idx;
+                    set_error(err, bad_rc, rep, ev->node[idx], idx, T);
+                    rc = bad_rc;
+                    goto done;
+                }
+            }
+            for (e = seg_begin; e < seg_end; e++) {
+                int64_t idx = order[e].idx;
+                int type = ev->event[idx];
+                int nd = ev->node[idx], ds = ev->dest[idx];
+                if (type != ORACLE_EV_EXTERNAL) continue;
+                if (ev->rep && ev->rep[idx] != rep) continue;
+                rc = oracle_apply_event(
+                    C, m->E, m->n_select, m->N, m->n_shift, type,
+                    u + (size_t)nd * C, u + (size_t)ds * C,
+                    ev->n_ind[idx], ev->proportion[idx], ev->select[idx],
+                    ev->shift[idx], seed, idx, rep);
+                if (rc) {
+                    set_error(err, rc, rep, nd, idx, T);
+                    goto done;
                 }
             }
 
-            /* (3) post time step, Eq. numstep3, on the state after events */
+            /* (3) post time step, Eq. numstep3, on the state after events;
+             * node-parallel in the timing build, the failing node with the
+             * lowest index reported */
             if (m->kind == ORACLE_SISE_SP) {
                 /* every node from the same old values: new values first */
+                int bad_node = -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
                 for (node = 0; node < Nn; node++) {
                     if (sise_sp_pts(m, node, u, v, T, &vtmp[node])) {
-                        set_error(err, ORACLE_ERR_PTS, rep, node, -1, T);
-                        rc = ORACLE_ERR_PTS;
-                        goto done;
+#ifdef _OPENMP
+#pragma omp critical(oracle_first_bad_node)
+#endif
+                        {
+                            if (bad_node < 0 || node < bad_node) bad_node = node;
+                        }
                     }
                 }
-                memcpy(v, vtmp, (size_t)Nn * sizeof *v);
-            }
-            for (node = 0; node < Nn && Nv > 0 && m->kind != ORACLE_SISE_SP; node++) {
-                int ret = model_pts(m->kind, v_new, u + (size_t)node * C,
-                                    v + (size_t)node * Nv,
-                                    m->ldata + (size_t)node * m->n_ldata,
-                                    m->gdata, T);
-                if (ret < 0) {
-                    set_error(err, ORACLE_ERR_PTS, rep, node, -1, T);
+                if (bad_node >= 0) {
+                    set_error(err, ORACLE_ERR_PTS, rep, bad_node, -1, T);
                     rc = ORACLE_ERR_PTS;
                     goto done;
                 }
-                memcpy(v + (size_t)node * Nv, v_new, (size_t)Nv * sizeof *v);
+                memcpy(v, vtmp, (size_t)Nn * sizeof *v);
+            }
+            if (Nv > 0 && m->kind != ORACLE_SISE_SP) {
+                int bad_node = -1;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+                for (node = 0; node < Nn; node++) {
+                    double vn[ORACLE_MAX_V];
+                    int ret;
+                    memcpy(vn, v + (size_t)node * Nv, (size_t)Nv * sizeof *v);
+                    ret = model_pts(m->kind, vn, u + (size_t)node * C,
+                                    v + (size_t)node * Nv,
+                                    m->ldata + (size_t)node * m->n_ldata,
+                                    m->gdata, T);
+                    if (ret < 0) {
+#ifdef _OPENMP
+#pragma omp critical(oracle_first_bad_node)
+#endif
+                        {
+                            if (bad_node < 0 || node < bad_node) bad_node = node;
+                        }
+                        continue;
+                    }
+                    memcpy(v + (size_t)node * Nv, vn, (size_t)Nv * sizeof *v);
+                }
+                if (bad_node >= 0) {
+                    set_error(err, ORACLE_ERR_PTS, rep, bad_node, -1, T);
+                    rc = ORACLE_ERR_PTS;
+                    goto done;
+                }
             }
 
             /* (4) record when T reaches the next tspan point (Sec. 3.4.2) */
@@ -951,7 +1096,6 @@ done:
     free(order);
     free(u);
     free(v);
-    free(v_new);
     free(vtmp);
     return rc;
 }

@@ -21,6 +21,7 @@
 
 #define ORACLE_MAX_COMP 16
 #define ORACLE_MAX_TRANS 16
+#define ORACLE_MAX_V 16
 
 enum {
     ORACLE_SIR = 0,
@@ -113,5 +114,15 @@ int oracle_run_reps(const oracle_model *m, const oracle_events *ev,
                     const int *tspan, int n_tspan, uint64_t seed, int rep0,
                     int n_rep, int n_rep_total, const int *u0, const double *v0,
                     int *U, double *V, int64_t *reactions, oracle_error *err);
+
+/* Test hook: records of the first waiting time of every node-day with
+ * lambda > 0 (direct method).  oracle_trace_first_tau(buf, cap) starts a
+ * trace into buf (at most cap records; cap = 0 stops tracing) and returns
+ * the number of records of the previous trace; -1 in the OpenMP build. */
+typedef struct {
+    int rep, node, T;
+    double tau;
+} oracle_tau_record;
+int64_t oracle_trace_first_tau(oracle_tau_record *buf, int64_t cap);
 
 #endif

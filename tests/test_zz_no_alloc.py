@@ -1,12 +1,13 @@
 """sg_run_noalloc, the entry point for callers that cannot allocate memory
 (a host framework that owns the device memory, a service whose footprint must
-stay fixed after start-up, work issued while a stream is being captured).
+stay fixed after start-up).
 
 It keeps its working memory in one fixed array inside the library instead of
 allocating it.  These checks call it through the C ABI and compare its U, V
 and counters, bit for bit, with those of the allocating entry point sg_run on
 the same inputs, on two calls in a row (different sizes and seeds, so stale
-contents of the shared array would show).  The file is collected last.
+contents of the shared array would show), and the first call's U and V also
+with the CPU oracle.  The file is collected last.
 """
 import ctypes
 
@@ -76,10 +77,10 @@ def _workload(n_nodes, days, n_rep, gen_seed):
                          seed=1, n_rep=n_rep, v0=v0)
 
 
-def test_noalloc_matches_allocating_run_twice(env):
+def test_noalloc_matches_allocating_run_twice(env, orc):
     torch, binding, L = env
     cases = [(_workload(2000, 150, 3, 11), 101), (_workload(777, 90, 1, 12), 202)]
-    for w, seed in cases:
+    for i, (w, seed) in enumerate(cases):
         U0, V0, st0 = binding.simulate(w, seed=seed)
         rc, U1, V1, st1 = _run_noalloc(torch, binding, L, w, seed, w.n_rep)
         assert rc == 0
@@ -87,6 +88,13 @@ def test_noalloc_matches_allocating_run_twice(env):
         assert np.array_equal(V0.view(np.uint64), V1.view(np.uint64))
         assert st1["reactions"] == st0["reactions"] > 0
         assert st1["draws"] == st0["draws"]
+        if i == 0:
+            # the first case also against the CPU oracle, bit for bit
+            code, Uo, Vo, Ro, err = orc.run(w, seed=seed)
+            assert code == 0, err
+            assert np.array_equal(Uo, U1)
+            assert np.array_equal(Vo.view(np.uint64), V1.view(np.uint64))
+            assert st1["reactions"] == int(Ro.sum())
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(env):
