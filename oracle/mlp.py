@@ -39,8 +39,11 @@ def forward(Ws, bs, X):
     return h, cache
 
 
-def loss_and_grads(Ws, bs, X, targets):
-    """Mean over rows of the summed head cross-entropies, and dW, db."""
+def loss_and_grads(Ws, bs, X, targets, return_cache=False):
+    """Mean over rows of the summed head cross-entropies, and dW, db.  With
+    ``return_cache`` also the forward cache (per layer: input, pre-activation)
+    and the gradient of the loss with respect to each layer's pre-activation
+    (the tests derive their tolerances from these)."""
     logits, cache = forward(Ws, bs, X)
     B = X.shape[0]
     d = np.zeros_like(logits)
@@ -55,12 +58,16 @@ def loss_and_grads(Ws, bs, X, targets):
         p[np.arange(B), t] -= 1.0
         d[:, h * BINS:(h + 1) * BINS] = p / B
     dWs, dbs = [None] * len(Ws), [None] * len(Ws)
+    deltas = [None] * len(Ws)
     delta = d
     for li in range(len(Ws) - 1, -1, -1):
         hin, pre = cache[li]
+        deltas[li] = delta
         dWs[li] = delta.T @ hin
         dbs[li] = delta.sum(axis=0)
         if li > 0:
             _, pre_prev = cache[li - 1]
             delta = (delta @ Ws[li]) * gelu_grad(pre_prev)
+    if return_cache:
+        return loss / B, dWs, dbs, cache, deltas
     return loss / B, dWs, dbs

@@ -1,6 +1,8 @@
-"""The learned one-day emulator: gradients of the tensor-core training path
-against the FP64 oracle network, the optimiser, the sampler, training on
-SSA-generated data, and the engine's use of the emulator with SSA fallback."""
+"""The learned one-day emulator: logits of the BF16 and E4M3 networks and the
+gradients of the tensor-core training path against the FP64 oracle network,
+element by element (tolerances from tests/mlp_tolerance.py), the optimiser,
+the sampler, training on SSA-generated data to the W1 <= 0.5 target, and the
+engine's use of the emulator with SSA fallback."""
 import numpy as np
 import pytest
 
@@ -19,25 +21,90 @@ def env():
     return torch, binding, emulator
 
 
-def test_gradients_match_fp64_oracle(env):
+def _net_inputs(torch, emulator, emu, n, seed):
+    """Features of random in-range SISe3 states (the emulator's own inputs)
+    and random biases (the initial ones are zero), so that every term of
+    each layer is exercised."""
+    rng = np.random.default_rng(seed)
+    u0, phi = emulator.random_states(rng, n)
+    g = emulator.random_params(rng)
+    f, flag = emulator.features(torch.as_tensor(u0, device="cuda"),
+                                torch.as_tensor(phi, device="cuda"), g)
+    for li, b in enumerate(emu.b32):
+        b.copy_(torch.as_tensor(rng.normal(0, 0.2, b.numel()), dtype=torch.float32))
+    return f, rng
+
+
+def _oracle_weights(emu):
+    return ([w.double().cpu().numpy() for w in emu.W16],
+            [b.double().cpu().numpy() for b in emu.b32])
+
+
+def test_bf16_logits_match_fp64_oracle_per_element(env):
+    # the BF16 network (four tcgen05 GEMMs with bias and GELU epilogues) vs
+    # the FP64 network on the same BF16 weights and inputs, every logit
+    # within its propagated rounding tolerance
     torch, binding, emulator = env
     from oracle import mlp
+    import mlp_tolerance as tol
     emu = emulator.Emulator(seed=1)
-    rng = np.random.default_rng(2)
-    B = 512
-    X = torch.as_tensor(rng.normal(0, 1, (B, 16)), dtype=torch.float32).to(torch.bfloat16).cuda()
-    t = torch.as_tensor(rng.integers(40, 90, (B, 3)), dtype=torch.int32).cuda()
-    loss, dW, db = emu.gradients(X, t)
-    Ws = [w.double().cpu().numpy() for w in emu.W16]
+    f, _ = _net_inputs(torch, emulator, emu, 3000, 41)  # 23 full tiles + a ragged one
+    logits = emu.forward(f)[0].double().cpu().numpy()
+    Ws, bs = _oracle_weights(emu)
+    X = f.double().cpu().numpy()
+    ref, _ = mlp.forward(Ws, bs, X)
+    Vz, _ = tol.forward_variances(Ws, bs, X, "bf16")
+    tol.check(logits[:, :mlp.HEADS * mlp.BINS], ref[:, :mlp.HEADS * mlp.BINS],
+              Vz[-1][:, :mlp.HEADS * mlp.BINS], "BF16 logits")
+
+
+def test_fp8_logits_match_fp64_oracle_per_element(env):
+    # the E4M3 network (layer 1 BF16 operands, E4M3 output; layers 2-4 E4M3
+    # operands with per-row weight scales and static activation scales) vs
+    # the FP64 network on the dequantised weights, every logit within its
+    # propagated rounding tolerance (E4M3 storage of the activations
+    # dominates).  The engine's persistent chain samples from exactly these
+    # logits (tested bit for bit below).
+    torch, binding, emulator = env
+    from oracle import mlp
+    import mlp_tolerance as tol
+    emu = emulator.Emulator(seed=2)
+    f, _ = _net_inputs(torch, emulator, emu, 3000, 42)
+    emu.quantize_fp8(f)
+    logits = emu.forward_fp8(f).double().cpu().numpy()
+    Ws = [emu.W16[0].double().cpu().numpy()]
+    for li in range(3):
+        w8 = emu.W8[li].cpu().view(torch.float8_e4m3fn).double()
+        Ws.append((w8 * emu.wscale[li].cpu().double()[:, None]).numpy())
     bs = [b.double().cpu().numpy() for b in emu.b32]
-    ref_loss, rdW, rdb = mlp.loss_and_grads(Ws, bs, X.double().cpu().numpy(),
-                                            t.cpu().numpy())
-    assert abs(loss - ref_loss) < 2e-2 * abs(ref_loss)
+    X = f.double().cpu().numpy()
+    ref, _ = mlp.forward(Ws, bs, X)
+    Vz, _ = tol.forward_variances(Ws, bs, X, "e4m3", emu.act_scale)
+    n = mlp.HEADS * mlp.BINS
+    tol.check(logits[:, :n], ref[:, :n], Vz[-1][:, :n], "E4M3 logits")
+
+
+def test_gradients_match_fp64_oracle_per_element(env):
+    # loss, dW and db of the training path (BF16 storage, FP32 accumulation:
+    # loss kernel, transposes, GEMMs, GELU backward, column sums) vs the FP64
+    # oracle's backpropagation, element by element within the propagated
+    # rounding tolerance
+    torch, binding, emulator = env
+    import mlp_tolerance as tol
+    emu = emulator.Emulator(seed=1)
+    f, rng = _net_inputs(torch, emulator, emu, 512, 43)
+    t = torch.as_tensor(rng.integers(40, 90, (512, 3)), dtype=torch.int32).cuda()
+    loss, dW, db = emu.gradients(f, t)
+    Ws, bs = _oracle_weights(emu)
+    (ref_loss, rdW, rdb), VdW, Vdb = tol.gradient_variances(Ws, bs, f.double().cpu().numpy(),
+                                                            t.cpu().numpy())
+    # the loss (about 3 ln 129 per row, a mean over 512 rows of sums of
+    # logits whose errors are ~1e-3 each) is expected within ~1e-4
+    # relative; 1e-3 leaves room for the FP32 exponentials and logarithms
+    assert abs(loss - ref_loss) <= 1e-3 * abs(ref_loss), (loss, ref_loss)
     for li in range(4):
-        g, r = dW[li].double().cpu().numpy(), rdW[li]
-        assert np.linalg.norm(g - r) <= 5e-2 * np.linalg.norm(r) + 1e-6, li
-        g, r = db[li].double().cpu().numpy(), rdb[li]
-        assert np.linalg.norm(g - r) <= 5e-2 * np.linalg.norm(r) + 1e-6, li
+        tol.check(dW[li].double().cpu().numpy(), rdW[li], VdW[li], f"dW layer {li + 1}")
+        tol.check(db[li].double().cpu().numpy(), rdb[li], Vdb[li], f"db layer {li + 1}")
 
 
 def test_adam_step_matches_definition(env):
@@ -120,12 +187,14 @@ def test_engine_without_emulated_nodes_equals_ssa(env, orc):
 
 def test_training_and_emulated_run(env):
     torch, binding, emulator = env
-    feat, tgt = emulator.make_dataset(200_000, 4, seed=1)
+    feat, tgt = emulator.make_dataset(500_000, 8, seed=1)
     emu = emulator.Emulator(seed=0)
-    hist = emu.train(feat, tgt, steps=600, batch=4096, lr=2e-3)
+    hist = emu.train(feat, tgt, steps=2500, batch=8192, lr=2e-3)
     assert np.mean(hist[-50:]) < 0.7 * np.mean(hist[:10])
-    res = emulator.compare_with_ssa(emu, n_probes=200, n_rep=500, seed=9)
-    assert res["w1_mean"] < 1.5, res
+    # the target: W1 <= 0.5 individuals per compartment per node-day against
+    # SSA ensembles
+    res = emulator.compare_with_ssa(emu, n_probes=200, n_rep=1000, seed=9)
+    assert res["w1_mean"] <= 0.5, res
     # the engine with the emulator: populations per age class stay exact
     w = W.config_sise3(n_nodes=3000, days=60, gen_seed=15, events_per_node_day=0)
     m = binding.Model(w)
