@@ -1,21 +1,31 @@
 """Benchmark of the SimInf split-step engine on one GB300.
 
-One step = one complete simulation of the SISe workload with scheduled
-events (1,600 nodes, log-normal herds, 365 days, ~200k enter / exit /
-external-transfer events): per-node direct SSA, E1 and E2 events, post time
-step (phi) and recording of U and V at every day, all through the C ABI.
+One step = one complete simulation of the batched SISe3 workload: 256
+independent replicates x 5,000 log-normal herds x 365 days, each replicate
+with its own ~175k scheduled events (exit, enter, ageing internal transfers,
+external transfers on a power-law network), per-node direct SSA, E1 and E2
+events, post time step (phi) and recording of U and V at every day, all
+through the C ABI, the run replayed as one CUDA graph.
 
 Prints one JSON line.  `value` is node-days/s over the timed steps (inputs
 resident in HBM); `e2e` is the same metric through the public host-buffer
 call (model creation, event upload and planning, host-to-device copy of the
-initial state, run, device-to-host copy of U and V).  `--impl reference`
-times the CPU oracle on the same workload instead.
+initial state, run, device-to-host copy of U and V).  At one GPU the line
+also carries the SISe3 37,000-herd 10-year workload (`sise3_37000x3650`)
+and the learned emulator on it (`emulator`: node-days/s with E4M3 and BF16
+inference, speed-up over the plain GPU SSA, W1 / KS against SSA ensembles).
+Under torchrun each rank runs its own range of the replicates (the global
+replicate index keys every random stream, so the ranks together run exactly
+the one-GPU job).  `--impl reference` times the CPU oracle on the same
+workload instead.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -32,29 +42,33 @@ METRIC_AEM = ("node-days/s (all events method: per-channel streams, next reactio
               " + scheduled events + post time step + recording)")
 UNIT = "node-days/s"
 L2_BYTES = 129 * 2 ** 20
-# FP64 ops (adds, multiplies, divides, conversions each counted once) of one
-# SSA draw in the SISe rate loop: two uniforms (6), logarithm (34), waiting
-# time (1 divide), rate sum (2), time update and comparison (1); a draw that
-# fires a transition adds the inversion (3) and two rate recomputations (6).
-FP64_PER_DRAW = 44
-FP64_PER_REACTION = 9
-FP64_PER_NODE_DAY = 14  # day-start rates (6) + post time step (8)
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 dense FP64 (nominal table figure)
-# The same counts for the all events method: a channel draw is a uniform (6),
-# logarithm (34), divide by the rate (1) and add to the time (1); a firing
-# compares the firing times (2), recomputes two rates (6) and rescales the
-# other dependent channel (4); a node-day adds the day-start rescale checks.
-# DRAM traffic of the day kernel per launch on the SISe workload, from the ncu
-# capture summarised in profiles/k_days_sise_1600x365_launches.md
-# (dram__bytes_read.sum + dram__bytes_write.sum, mean of the captured launches;
-# ncu flushes the caches between its passes, so it is the cold-cache figure).
-# It is reported only while the kernel sources hash to the captured ones.
-DAY_KERNEL_TRAFFIC = {"sources_sha1": "b9cede1af8d73e079a9e3cda85bc0bd2385fb1d1",
-                      "bytes_per_launch": 661632}
-_KERNEL_SOURCES = ("sg_common.h", "sg_device.cuh", "sg_kernels.cuh")
-FP64_PER_DRAW_AEM = 42
-FP64_PER_REACTION_AEM = 12
-FP64_PER_NODE_DAY_AEM = 16
+
+# Algorithmic FP64 operations of the direct method, counted from the oracle's
+# definitions (each add, subtract, multiply, divide and integer-to-double
+# conversion once; comparisons not counted):
+#   per draw: two open-interval uniforms (3 each), the logarithm (38:
+#     reduction 6, atanh series in Estrin form 23, reconstruction 9), the
+#     waiting-time divide and the time update (2) = 46;
+#   per node-day: the day-start rates and their sum, plus the post time step
+#     (SISe3: rates 15, lambda 5, phi step 24; SISe: 5 + 1 + 10; SIS: 6 + 1;
+#     SIR: 10 + 1);
+#   per transition fired: target lambda r2 (1), the running sum of the
+#     inversion (T - 1 at most), the rates column n of G marks and the new
+#     lambda (SISe3: 1 + 5 + 5 + 5; SISe: 1 + 1 + 5 + 1; SIS 1 + 1 + 6 + 1;
+#     SIR 1 + 1 + 10 + 1).
+# Parsed models (transition strings) have no fixed count: no FP64 roofline.
+FP64_OPS = {  # kind: (per node-day, per draw, per transition)
+    0: (11, 46, 13),   # SIR
+    1: (7, 46, 9),     # SIS
+    2: (16, 46, 8),    # SISe
+    3: (44, 46, 16),   # SISe3
+    4: (6, 46, 8),     # SISe_sp (the coupled phi step runs in its own kernel)
+}
+# The same for the all events method (SISe): a channel draw is a uniform (3),
+# the logarithm (38), the divide by the rate and the add to the time (2); a
+# firing compares firing times, recomputes two rates (5) and rescales the
+# other dependent channel (4); a node-day adds the day-start rate updates.
+FP64_OPS_AEM = {2: (16, 43, 12)}
 
 
 def _workload(name, solver="ssm", days=None, reps=None):
@@ -78,7 +92,9 @@ def _base_workload(name, days=None, reps=None):
     if name == "sir":
         return W.config_sir()
     if name == "sise3":
-        return W.config_sise3(**kw)
+        w = W.config_sise3(**kw)
+        w.meta["tune_days"] = 30
+        return w
     if name == "batched":
         if reps is not None:
             kw["n_rep"] = reps
@@ -186,42 +202,96 @@ def _cpu_cores():
         return os.cpu_count()
 
 
-def time_oracle(w, budget_s=10.0, max_runs=50):
-    """Run the CPU oracle on (a bounded sample of) the workload repeatedly for
-    ~budget_s (at least once); node-days/s and reactions/s."""
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _time_oracle_runs(w, budget_s, max_runs, threads):
+    """Repeated oracle runs on w for ~budget_s (at least one): total seconds,
+    runs, reactions.  threads = None: the serial build; else the OpenMP
+    timing build with that many threads."""
     import oracle
-    oracle.build()
-    w, desc = _oracle_sample(w, max_node_days=1.5e6 * budget_s / w.meta.get("oracle_cost", 1))
-    node_days = w.n_nodes * w.n_days * w.n_rep
+    if threads is not None:
+        oracle.set_threads(threads)
     runs, t_total, reactions = 0, 0.0, 0
     while runs < max_runs and (runs == 0 or t_total < budget_s):
         t = time.perf_counter()
-        code, U, V, R, err = oracle.run(w)
+        code, U, V, R, err = oracle.run(w, openmp=threads is not None)
         t_total += time.perf_counter() - t
         assert code == 0, err
         reactions += int(R.sum())
         runs += 1
-    return {"value": node_days * runs / t_total, "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "reactions_per_s": reactions / t_total,
-            "sample": f"{runs} run(s) of " + (", ".join(desc) if desc else "the whole workload")
-                      + f" ({node_days} node-days each), serial C oracle, 1 thread, "
-                      f"{t_total:.2f} s"}
+    return t_total, runs, reactions
 
 
-def _day_kernel_traffic(w, aem):
-    """The captured per-launch DRAM bytes of the day kernel, or None when the
-    workload, solver or kernel sources differ from the capture's."""
-    import hashlib
-    if aem or not w.name.startswith("SISe 1600 nodes x 365 days"):
-        return None
+def time_oracle(w, budget_s=10.0, max_runs=50):
+    """The CPU oracle on a bounded sample of the workload, on the host's
+    cores: the node-parallel OpenMP timing build on every core (the paper's
+    solver design: nodes in parallel, E2 events serial) and the serial
+    build on one.  node-days/s and reactions/s."""
+    import oracle
+    oracle.build()
+    w, desc = _oracle_sample(w, max_node_days=1.5e6 * budget_s / w.meta.get("oracle_cost", 1))
+    node_days = w.n_nodes * w.n_days * w.n_rep
+    sample = ((", ".join(desc) if desc else "the whole workload")
+              + f" ({node_days} node-days per run)")
+    t1, r1, re1 = _time_oracle_runs(w, budget_s / 2, max_runs, None)
+    single = {"value": node_days * r1 / t1, "reactions_per_s": re1 / t1, "cores": 1,
+              "runs": r1, "seconds": t1}
+    cores = _cpu_cores()
+    out = {"value": single["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+           "reactions_per_s": single["reactions_per_s"], "cpu_model": _cpu_model(),
+           "host_cores": cores, "single_thread": single,
+           "sample": f"{r1} run(s) of {sample}, serial C oracle, 1 thread, {t1:.2f} s"}
+    try:
+        oracle.build(openmp=True)
+        tn, rn, ren = _time_oracle_runs(w, budget_s / 2, max_runs, cores)
+        out.update({"value": node_days * rn / tn, "cores": cores,
+                    "reactions_per_s": ren / tn,
+                    "sample": f"{rn} run(s) of {sample}, OpenMP oracle (nodes in parallel, "
+                              f"E2 serial), {cores} threads, {tn:.2f} s; 1 thread: "
+                              f"{r1} run(s), {t1:.2f} s"})
+        out["all_cores"] = {"value": node_days * rn / tn, "reactions_per_s": ren / tn,
+                            "cores": cores, "runs": rn, "seconds": tn}
+    except Exception as e:  # no OpenMP compiler: the serial figure stands
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def _kernel_sources_sha1():
     h = hashlib.sha1()
-    for f in _KERNEL_SOURCES:
+    for f in ("sg_common.h", "sg_device.cuh", "sg_kernels.cuh"):
         with open(os.path.join(_ROOT, "paper_1605_01421_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != DAY_KERNEL_TRAFFIC["sources_sha1"]:
+    return h.hexdigest()
+
+
+# Counters of one limited ncu capture of the day kernel on the batched
+# workload shortened to 8 days (256 replicates x 5,000 herds per launch, the
+# same launch as in the timed run); reported only while the kernel sources
+# hash to the captured ones (otherwise null).  The capture command:
+#   python bench.py --workload batched --days 8 --steps 1 --warmup 1
+#       --cpu-seconds 0 --e2e 0 --extras 0 --tuning <split>, under
+#   ncu --section SpeedOfLight --section ComputeWorkloadAnalysis
+#       --section MemoryWorkloadAnalysis --section WarpStateStats
+#       --section SchedulerStats --section Occupancy --section LaunchStats
+#       --section InstructionStats --clock-control none -k regex:k_days -s 2 -c 2
+DAY_KERNEL_NCU = None
+
+
+def _day_kernel_ncu(w):
+    c = DAY_KERNEL_NCU
+    if (c is None or not w.name.startswith("SISe3 256 replicates x 5000 nodes")
+            or c["sources_sha1"] != _kernel_sources_sha1()):
         return None
-    return DAY_KERNEL_TRAFFIC["bytes_per_launch"]
+    return c
 
 
 def max_over_ranks(total_ms, dist, device):
@@ -242,26 +312,45 @@ def job_throughput(units_per_rank, steps, world, total_ms):
     return units_per_rank * steps * world / (total_ms * 1e-3)
 
 
+def shard_replicates(n_rep, rank, world):
+    """Replicates [rep0, rep0 + n) of rank `rank` out of `world`: contiguous
+    ranges that tile 0 .. n_rep - 1, sizes differing by at most one."""
+    rep0 = (n_rep * rank) // world
+    return rep0, (n_rep * (rank + 1)) // world - rep0
+
+
 def bench_reference(args):
+    """The reference arm: the CPU oracle (the paper's method restated in
+    plain C) on the host's cores, node-parallel (OpenMP build, E2 serial),
+    on a bounded sample of the same workload per step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    w_full = _workload(args.workload, args.solver)
+    w_full = _workload(args.workload, args.solver, args.days, args.reps)
     w, desc = _oracle_sample(w_full, max_node_days=3e6 / w_full.meta.get("oracle_cost", 1))
     node_days = w.n_nodes * w.n_days * w.n_rep
     import oracle
     oracle.build()
+    cores = _cpu_cores()
+    try:
+        oracle.build(openmp=True)
+        oracle.set_threads(cores)
+        omp = True
+    except Exception:
+        omp, cores = False, 1
     for _ in range(args.warmup):
-        oracle.run(w)
+        oracle.run(w, openmp=omp)
     times, reactions = [], 0
     for _ in range(args.steps):
         t = time.perf_counter()
-        code, U, V, R, err = oracle.run(w)
+        code, U, V, R, err = oracle.run(w, openmp=omp)
         times.append(time.perf_counter() - t)
         assert code == 0, err
         reactions += int(R.sum())
     total = sum(times)
     value = node_days * args.steps / total
+    what = (f"OpenMP oracle (nodes in parallel, E2 serial), {cores} threads" if omp
+            else "serial C oracle, 1 thread")
     line = {"impl": "reference", "metric": _metric(w_full), "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
@@ -270,17 +359,143 @@ def bench_reference(args):
             "config": {"workload": w_full.name, "nodes": w_full.n_nodes,
                        "days": w_full.n_days, "replicates": w_full.n_rep,
                        "events": w_full.n_events, "seed": w_full.seed},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "cpu_model": _cpu_model(),
                              "sample": f"{args.steps} run(s) of "
-                                       + (", ".join(desc) if desc else "the whole workload")},
+                                       + (", ".join(desc) if desc else "the whole workload")
+                                       + f", {what}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
+def _fp64_roofline(w, aem, kt, fp64_fma_tflops):
+    """Algorithmic FP64 operations of the day kernel per second against the
+    measured FP64 instruction rate (the FMA probe's flops / 2: one FMA lane
+    instruction = one operation here)."""
+    table = FP64_OPS_AEM if aem else FP64_OPS
+    if w.kind not in table:
+        return None
+    per_nd, per_draw, per_fire = table[w.kind]
+    ops = (per_nd * kt["node_days"] + per_draw * kt["draws"] + per_fire * kt["reactions"])
+    sec = kt["ms_ssa"] * 1e-3
+    achieved = ops / sec / 1e12
+    peak = fp64_fma_tflops / 2.0
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "kernel": ("k_days<aem> (channels + post time step + recording)" if aem
+                       else "k_days (SSA + E1 events + post time step + recording)"),
+            "peak_source": "measured: FP64 FMA lane instructions per second of this GPU "
+                           f"(sg_fp64_fma_probe {fp64_fma_tflops:.4f} TFLOP/s / 2)",
+            "ops_per_launch": ops / max(1, kt["launches_ssa"]),
+            "ops_counted": "FP64 add, multiply, divide, conversion once each (oracle's "
+                           "definitions): per node-day / draw / transition "
+                           f"{per_nd} / {per_draw} / {per_fire}",
+            "avg_launch_ms": kt["ms_ssa"] / max(1, kt["launches_ssa"])}
+
+
+def measure_gpu(w, args, stream, dev, steps, warmup, rep0=0, seed=None, tune=True,
+                kernel_pass_steps=None, dist=None, world=1, clocks=True):
+    """Time `steps` runs of w (after autotuning the work split and `warmup`
+    untimed runs) with CUDA events on `stream`; then one pass with per-launch
+    timing events for the roofline.  Returns a dict."""
+    import torch
+    from paper_1605_01421_gb300 import binding
+    aem = w.solver == 1
+    n_rep = w.n_rep
+    M = len(w.tspan)
+    seed = w.seed if seed is None else seed
+    model = binding.Model(w)
+    if w.meta.get("rep_total"):
+        model.set_replicate_range(rep0, w.meta["rep_total"])
+    u0 = torch.as_tensor(np.array(w.u0, dtype=np.int32, order="C"), device=dev)
+    v0 = torch.as_tensor(np.array(w.v0, dtype=np.float64, order="C"), device=dev)
+    U = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32, device=dev)
+    V = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        return model.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
+
+    tuned = None
+    if args.tuning:
+        npb, heavy = (int(x) for x in args.tuning.split(","))
+        model.set_tuning(npb, heavy)
+        tuned = (npb, heavy, None)
+    elif tune and args.autotune:
+        # the work split changes speed only, never results; workloads whose
+        # runs take seconds are tuned on a prefix of days (the buffers hold
+        # the full run)
+        td = w.meta.get("tune_days") if w.meta else None
+        tune_ts = w.tspan[:td + 1] if td and w.n_days > td else w.tspan
+        tuned = model.autotune(tune_ts, seed, n_rep, u0, v0, U, V, stream=stream)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(dev.index or 0) if clocks else None
+    if sampler:
+        sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    reactions = draws = launches = 0
+    for i in range(steps):
+        flush.zero_()  # L2 flush outside the timed interval of the step
+        starts[i].record(stream)
+        rc, st, er = step()
+        ends[i].record(stream)
+        reactions += st["reactions"]
+        draws += st["draws"]
+        launches += st["kernel_launches"]
+    torch.cuda.synchronize()
+    clk = sampler.stop() if sampler else None
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    total_ms = max_over_ranks(total_ms, dist, dev)
+    node_days = w.n_nodes * w.n_days * n_rep
+    out = {"value": job_throughput(node_days, steps, world, total_ms),
+           "ms_per_step": total_ms / steps,
+           "reactions_per_s": reactions * world / (total_ms * 1e-3),
+           "draws_per_step": draws / steps, "reactions_per_step": reactions / steps,
+           "gpu_launches": launches, "clocks": clk,
+           "tuning": ({"nodes_per_block": tuned[0], "heavy_after": tuned[1],
+                       "autotune_best_ms": tuned[2]} if tuned else None)}
+    # per-kernel device time in a second pass with timing events around every
+    # launch (kept out of the timed region above)
+    kps = steps if kernel_pass_steps is None else kernel_pass_steps
+    model.set_kernel_timing(True)
+    kt = {"ms_ssa": 0.0, "ms_e1": 0.0, "ms_e2": 0.0, "launches_ssa": 0,
+          "launches_e1": 0, "launches_e2": 0, "draws": 0, "reactions": 0,
+          "node_days": 0}
+    for _ in range(kps):
+        flush.zero_()
+        rc, st, er = step()
+        for k in kt:
+            kt[k] += st[k]
+    model.set_kernel_timing(False)
+    shares = {k: kt[f"ms_{k}"] for k in ("ssa", "e1", "e2")}
+    roof = _fp64_roofline(w, aem, kt, binding.fp64_fma_probe())
+    if roof is not None:
+        roof["kernel_ms_share"] = {k: v / max(1e-9, sum(shares.values()))
+                                   for k, v in shares.items()}
+        # the U / V write stream of the day kernel, for context (HBM is not
+        # its bound): bytes written per launch / launch time
+        rec = (w.n_comp * 4 + w.n_v * 8) * w.n_nodes * n_rep * (M - 1) * kps
+        roof["record_stream_gbs"] = rec / (kt["ms_ssa"] * 1e-3) / 1e9
+        ncu = _day_kernel_ncu(w)
+        roof["traffic"] = ncu["dram_bytes_per_launch"] if ncu else None
+        roof["ncu"] = ncu
+    out["roofline"] = roof
+    out["kernel_ms_per_step"] = {k: v / kps for k, v in shares.items()}
+    out["_model"] = model
+    out["_buffers"] = (u0, v0, U, V, flush)
+    return out
+
+
 def bench_gpu(args):
     import torch
     from paper_1605_01421_gb300 import binding
+    from paper_1605_01421_gb300 import workloads as W
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,174 +506,161 @@ def bench_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     binding.build()
-    w = _workload(args.workload, args.solver, args.days, args.reps)
-    aem = w.solver == 1
-    n_rep = w.n_rep
-    M = len(w.tspan)
+    w_full = _workload(args.workload, args.solver, args.days, args.reps)
     dev = torch.device("cuda", local)
     # a non-default stream, so that each run is one replayed CUDA graph
     stream = torch.cuda.Stream(dev)
     torch.cuda.set_stream(stream)
-    model = binding.Model(w)
-    u0 = torch.as_tensor(np.array(w.u0, dtype=np.int32, order="C"), device=dev)
-    v0 = torch.as_tensor(np.array(w.v0, dtype=np.float64, order="C"), device=dev)
-    U = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32, device=dev)
-    V = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64, device=dev)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
-    # replicas only: every rank runs the same workload with its own seed
-    seed = w.seed + rank
-
-    def step():
-        return model.run(w.tspan, seed, n_rep, u0, v0, U, V, stream=stream)
-
-    tuned = None
-    if args.tuning:
-        npb, heavy = (int(x) for x in args.tuning.split(","))
-        model.set_tuning(npb, heavy)
-        tuned = (npb, heavy, None)
-    elif args.autotune:
-        # the work split changes speed only, never results; workloads whose
-        # runs take seconds are tuned on a prefix of days (the buffers hold the
-        # full run)
-        td = w.meta.get("tune_days") if w.meta else None
-        tune_ts = w.tspan[:td + 1] if td and w.n_days > td else w.tspan
-        tuned = model.autotune(tune_ts, seed, n_rep, u0, v0, U, V, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    sampler = ClockSampler(local)
-    sampler.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    reactions = draws = launches = 0
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush outside the timed interval of the step
-        starts[i].record(stream)
-        rc, st, er = step()
-        ends[i].record(stream)
-        reactions += st["reactions"]
-        draws += st["draws"]
-        launches += st["kernel_launches"]
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(ms)
-    total_ms = max_over_ranks(total_ms, dist, dev)
-    node_days = w.n_nodes * w.n_days * n_rep
-    value = job_throughput(node_days, args.steps, world, total_ms)
-
-    # per-kernel device time in a second pass with timing events around every
-    # launch (kept out of the timed region above)
-    model.set_kernel_timing(True)
-    kt = {"ms_ssa": 0.0, "ms_e1": 0.0, "ms_e2": 0.0, "launches_ssa": 0,
-          "launches_e1": 0, "launches_e2": 0, "draws": 0, "reactions": 0,
-          "node_days": 0}
-    for _ in range(args.steps):
-        flush.zero_()
-        rc, st, er = step()
-        for k in kt:
-            kt[k] += st[k]
-    model.set_kernel_timing(False)
-    shares = {k: kt[f"ms_{k}"] for k in ("ssa", "e1", "e2")}
-    dominant = max(shares, key=shares.get)
-    fp64_measured = binding.fp64_fma_probe()
-    if aem:
-        ssa_flops = (FP64_PER_DRAW_AEM * kt["draws"] + FP64_PER_REACTION_AEM * kt["reactions"]
-                     + FP64_PER_NODE_DAY_AEM * kt["node_days"])
+    rep0, seed = 0, w_full.seed
+    if world > 1 and w_full.n_rep > 1:
+        # replicas only, sharded: this rank's range of the replicates with
+        # their own events; the global replicate index keys every stream
+        rep0, n_loc = shard_replicates(w_full.n_rep, rank, world)
+        w = W.replicate_range(w_full, rep0, n_loc)
+        parallelism = f"replicate shards x{world} (ranks run replicates {rep0}..)"
     else:
-        ssa_flops = (FP64_PER_DRAW * kt["draws"] + FP64_PER_REACTION * kt["reactions"]
-                     + FP64_PER_NODE_DAY * kt["node_days"])
-    if dominant == "ssa":
-        achieved = ssa_flops / (kt["ms_ssa"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "traffic": _day_kernel_traffic(w, aem),
-                "kernel": ("k_days<aem> (channels + post time step + recording)" if aem
-                           else "k_days (SSA + post time step + recording)"),
-                "peak_source": "nominal GB300 dense FP64 (1.25 TFLOP/s)",
-                "fp64_fma_measured_tflops": fp64_measured,
-                "frac_of_measured_fp64": achieved / fp64_measured,
-                "avg_launch_ms": kt["ms_ssa"] / max(1, kt["launches_ssa"])}
-    else:
-        # event kernels: algorithmic bytes = event record (35 B) + read/write of
-        # the touched node states (2 x 4 C B per node, 2 nodes for E2)
-        C = w.n_comp
-        ev_bytes = w.n_events * n_rep * (35 + (2 * 2 * 4 * C if dominant == "e2" else 2 * 4 * C))
-        ms_k = kt[f"ms_{dominant}"]
-        from_peaks = _measured_peaks()
-        achieved = ev_bytes / (ms_k * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": from_peaks,
-                "unit": "GB/s", "frac": achieved / from_peaks, "traffic": None,
-                "kernel": f"k_events_{dominant}",
-                "avg_launch_ms": ms_k / max(1, kt[f"launches_{dominant}"])}
-    roof["kernel_ms_share"] = {k: v / max(1e-9, sum(shares.values())) for k, v in shares.items()}
+        # one replicate: independent replicas, one seed per rank
+        w = w_full
+        seed = w_full.seed + rank
+        parallelism = f"replicas{world}"
+    res = measure_gpu(w, args, stream, dev, args.steps, args.warmup, rep0=rep0, seed=seed,
+                      dist=dist, world=world)
+    if world > 1 and w_full.n_rep > 1:
+        # every rank ran its own replicate range: the job's node-days are the
+        # full workload's (shards may differ by one replicate)
+        node_days = w_full.n_nodes * w_full.n_days * w_full.n_rep
+        res["value"] = node_days * args.steps / (res["ms_per_step"] * args.steps * 1e-3)
+    model = res.pop("_model")
+    u0, v0, U, V, flush = res.pop("_buffers")
+    n_rep, M = w.n_rep, len(w.tspan)
+    tuned = res["tuning"]
 
-    # end to end through the public host-buffer call
+    # end to end through the public host-buffer call: model creation (event
+    # table copy, validation, planning, upload), host-to-device copy of u0
+    # and v0 from page-locked memory, the run, device-to-host copy of U and V
     e2e = None
     if args.e2e:
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
         u0h = torch.as_tensor(np.ascontiguousarray(w.u0)).pin_memory().numpy()
         v0h = torch.as_tensor(np.ascontiguousarray(w.v0)).pin_memory().numpy()
         Uh = torch.empty((n_rep, M, w.n_nodes, w.n_comp), dtype=torch.int32).pin_memory().numpy()
         Vh = torch.empty((n_rep, M, w.n_nodes, w.n_v), dtype=torch.float64).pin_memory().numpy()
+        del U, V  # the device buffers of the timed runs are not needed any more
         t_e2e = 0.0
-        for i in range(args.steps):
+        for i in range(n_e2e):
             flush.zero_()
             torch.cuda.synchronize()
             t = time.perf_counter()
             m2 = binding.Model(w)  # tables + events: host validation, plan, upload
+            if w.meta.get("rep_total"):
+                m2.set_replicate_range(rep0, w.meta["rep_total"])
             m2.set_graphs(False)  # a single run: capturing a graph would not pay
             if tuned:
-                m2.set_tuning(tuned[0], tuned[1])  # the split found for this workload
+                m2.set_tuning(tuned["nodes_per_block"], tuned["heavy_after"])
             m2.run_host(w.tspan, seed, n_rep, u0h, v0h, Uh, Vh, stream=stream)
             t_e2e += time.perf_counter() - t
             m2.close()
-        ev_bytes_h2d = w.n_events * 35
-        e2e = {"value": node_days * args.steps / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": int(u0h.nbytes + v0h.nbytes + ev_bytes_h2d),
-               "d2h_bytes_per_step": int(Uh.nbytes + Vh.nbytes)}
+        t_e2e = max_over_ranks(t_e2e * 1e3, dist, dev) * 1e-3
+        sharded = world > 1 and w_full.n_rep > 1
+        node_days_job = (w_full.n_nodes * w_full.n_days * w_full.n_rep if sharded
+                         else w.n_nodes * w.n_days * n_rep * world)
+        e2e = {"value": node_days_job * n_e2e / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(u0h.nbytes + v0h.nbytes + w.n_events * 35),
+               "d2h_bytes_per_step": int(Uh.nbytes + Vh.nbytes), "steps": n_e2e,
+               "what": "sg_run_host with model creation, event upload and planning per step"}
+        del Uh, Vh
+    model.close()
+    del model, u0, v0
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    cpu = time_oracle(w, budget_s=args.cpu_seconds) if world == 1 and args.cpu_seconds > 0 else None
-    line = {"metric": _metric(w), "value": value, "unit": UNIT, "n_gpus": world,
+    cpu = (time_oracle(w_full, budget_s=args.cpu_seconds)
+           if world == 1 and args.cpu_seconds > 0 else None)
+    line = {"metric": _metric(w), "value": res["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64+int32",
-            "data": "synthetic",
-            "reactions_per_s": reactions * world / (total_ms * 1e-3),
-            "config": {"workload": w.name, "nodes": w.n_nodes, "days": w.n_days,
-                       "replicates": n_rep, "events": w.n_events, "seed": w.seed,
-                       "solver": "aem" if aem else "ssm",
-                       "l2": "flushed between steps (512 MiB write)",
-                       "parallelism": f"replicas{world}"},
-            "gpu_launches": launches,
-            "tuning": {"nodes_per_block": tuned[0], "heavy_after": tuned[1],
-                       "autotune_best_ms": tuned[2]} if tuned else None,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks}
+            "ms_per_step": res["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak" if not (world > 1 and w_full.n_rep > 1) else "strong",
+            "vs_baseline": None, "dtype": "f64+int32", "data": "synthetic",
+            "reactions_per_s": res["reactions_per_s"],
+            "config": {"workload": w_full.name, "nodes": w_full.n_nodes,
+                       "days": w_full.n_days, "replicates": w_full.n_rep,
+                       "events": w_full.n_events, "seed": w_full.seed,
+                       "solver": "aem" if w.solver == 1 else "ssm",
+                       "l2": "flushed between steps (512 MiB write); U and V alone "
+                             "exceed L2",
+                       "parallelism": parallelism},
+            "gpu_launches": res["gpu_launches"], "tuning": res["tuning"],
+            "draws_per_step": res["draws_per_step"],
+            "reactions_per_step": res["reactions_per_step"],
+            "kernel_ms_per_step": res["kernel_ms_per_step"],
+            "roofline": res["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": res["clocks"]}
+    if world == 1 and args.extras:
+        line["sise3_37000x3650"] = _extra_sise3(args, stream, dev)
+        line["emulator"] = _extra_emulator(args)
     print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
 
 
-def bench_emulator(args):
+def _extra_sise3(args, stream, dev):
+    """The paper's application scale (about 40,000 herds, about ten years of
+    events, Sec. 1): SISe3 on 37,000 herds for 3,650 days."""
+    try:
+        w = _workload("sise3")
+        r = measure_gpu(w, argparse.Namespace(**{**vars(args), "tuning": None}), stream, dev,
+                        steps=args.extra_steps, warmup=1, kernel_pass_steps=1)
+        r.pop("_model").close()
+        r.pop("_buffers")
+        return {"workload": w.name, "events": w.n_events, "value": r["value"], "unit": UNIT,
+                "ms_per_step": r["ms_per_step"], "steps": args.extra_steps,
+                "reactions_per_s": r["reactions_per_s"], "tuning": r["tuning"],
+                "roofline": r["roofline"], "clocks": r["clocks"]}
+    except Exception as e:  # reported, not fatal to the headline
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def _extra_emulator(args):
+    """The learned emulator on the 37,000-herd 10-year SISe3 workload: E4M3
+    and BF16 node-days/s, speed-up over the plain GPU SSA on the same
+    workload, W1 and KS against 1,000-replicate SSA ensembles."""
+    try:
+        import torch
+        e = bench_emulator(args, timed_steps=args.extra_steps)
+        torch.cuda.empty_cache()
+        err = e["error_vs_ssa"]
+        return {"workload": e["config"]["workload"], "value_e4m3": e["value"],
+                "value_bf16": e["bf16"]["value"], "plain_gpu_ssa": e["plain_ssa"]["value"],
+                "unit": UNIT, "speedup_e4m3": e["speedup_vs_plain_gpu_ssa"],
+                "speedup_bf16": e["bf16"]["speedup_vs_plain_gpu_ssa"],
+                "w1_mean_e4m3": err["w1_mean"], "w1_mean_bf16": e["bf16"]["error_vs_ssa"]["w1_mean"],
+                "w1_target": 0.5, "meets_w1_target": err["w1_mean"] <= 0.5,
+                "error_vs_ssa_e4m3": err, "error_vs_ssa_bf16": e["bf16"]["error_vs_ssa"],
+                "population_vs_ssa": e["population_vs_ssa"], "training": e["training"],
+                "roofline": e["roofline"], "steps": e["steps"],
+                "ms_per_step_e4m3": e["ms_per_step"], "config": e["config"]}
+    except Exception as ex:
+        return {"error": f"{type(ex).__name__}: {ex}"[:300]}
+
+
+def bench_emulator(args, timed_steps=None):
     """The learned one-day emulator on an SISe3 workload: train it on one-day
     SSA outcomes with the library's own kernels, measure its error against
     1,000-replicate SSA ensembles (W1, KS) and the population's infected
     fraction against a plain SSA run, and compare node-days/s of the run
     with the emulator (SSA fallback for herds > 2,000 and for nodes below
     the activity threshold) to the plain SSA
-    on the same workload.  Prints one JSON line."""
+    on the same workload.  Returns the JSON line (a dict)."""
     import torch
     from paper_1605_01421_gb300 import binding, emulator
     binding.build()
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
+    n_timed = args.steps if timed_steps is None else timed_steps
     from paper_1605_01421_gb300 import workloads as Wk
     if args.emu_workload == "endemic":
         w = Wk.config_endemic(days=args.emu_days)
@@ -536,16 +738,16 @@ def bench_emulator(args):
         return (inf / tot).cpu().numpy()
 
     plain = binding.Model(w)
-    ms_plain, st_plain = timed(plain, args.steps)
+    ms_plain, st_plain = timed(plain, n_timed)
     f_plain = infected_fraction()
     m = binding.Model(w)
     m.set_emulator(emu, max_herd=2000, min_rate=mr)
-    ms_emu, st_emu = timed(m, args.steps)
+    ms_emu, st_emu = timed(m, n_timed)
     f_bf16 = infected_fraction()
     m8 = binding.Model(w)
     m8.set_emulator(emu, max_herd=2000, min_rate=mr)
     m8.set_emulator_fp8(emu)
-    ms_emu8, st_emu8 = timed(m8, args.steps)
+    ms_emu8, st_emu8 = timed(m8, n_timed)
     f_fp8 = infected_fraction()
     m8.set_kernel_timing(True)
     rc, st_t8, er = m8.run(w.tspan, w.seed, 1, u0, v0, U, V, stream=stream)
@@ -570,7 +772,7 @@ def bench_emulator(args):
     peak8 = 2.0 * peak
     line = {"metric": "node-days/s with the learned emulator (SSA fallback for herds > 2000)",
             "value": node_days / (ms_emu8 * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": 2, "ms_per_step": ms_emu8,
+            "steps": n_timed, "warmup": 2, "ms_per_step": ms_emu8,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "e4m3 MLP layers 2-4, bf16 layer 1 (fp32 accumulation) + f64/int32 SSA "
                      "fallback",
@@ -612,7 +814,9 @@ def bench_emulator(args):
                          "mlp_share_of_run": st_t8["ms_mlp"] / max(1e-9, st_t8["ms_mlp"]
                                                                     + st_t8["ms_ssa"]
                                                                     + st_t8["ms_e2"])}}
-    print(json.dumps(line))
+    for mm in (plain, m, m8):
+        mm.close()
+    return line
 
 
 def _measured_bf16_tflops():
@@ -637,9 +841,21 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="sise",
+    ap.add_argument("--workload", default="batched",
                     choices=["sise", "sir", "sise3", "batched", "emulator", "sise_sp",
                              "predator_prey", "vaccination"])
+    ap.add_argument("--days", type=int, default=None,
+                    help="shorter run of the workload (sise, sise3, batched)")
+    ap.add_argument("--reps", type=int, default=None, help="replicates (batched)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed work split 'nodes_per_block,heavy_after' instead of the autotuner")
+    ap.add_argument("--e2e", type=int, default=1, help="0: skip the end-to-end leg")
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="end-to-end steps (at most --steps)")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="at one GPU, also the 37,000-herd 10-year SISe3 workload and the "
+                         "emulator on it")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed steps of the extras")
     ap.add_argument("--emu-batches", type=int, default=50)
     ap.add_argument("--emu-steps", type=int, default=4000)
     ap.add_argument("--emu-nodes", type=int, default=37000)
@@ -649,19 +865,13 @@ def main():
                     help="nodes with fewer expected transitions per day stay on the SSA")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--autotune", type=int, default=1)
-    ap.add_argument("--days", type=int, default=None,
-                    help="shorter run of the workload (sise, sise3, batched)")
-    ap.add_argument("--reps", type=int, default=None, help="replicates (batched)")
-    ap.add_argument("--tuning", default=None,
-                    help="fixed work split 'nodes_per_block,heavy_after' instead of the autotuner")
-    ap.add_argument("--e2e", type=int, default=1, help="0: skip the end-to-end leg")
     ap.add_argument("--solver", default="ssm", choices=["ssm", "aem"],
                     help="ssm: split-step direct SSA; aem: all events method (Sec. 3.4.2)")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
     elif args.workload == "emulator":
-        bench_emulator(args)
+        print(json.dumps(bench_emulator(args)))
     else:
         bench_gpu(args)
 

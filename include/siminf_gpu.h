@@ -288,22 +288,49 @@ int sg_run_host(sg_model *m, const int32_t *tspan, int32_t n_tspan,
  * sg_stats.  Off by default (the events add host work per launch). */
 int sg_set_kernel_timing(sg_model *m, int enable);
 
-/* Work split of the SSA day kernel.  Each block of 128 threads owns
- * nodes_per_block (1..128) (replicate, node) pairs, one per thread; a node
- * whose SSA needs more than heavy_after draws in a day is handed to one of
- * the block's warps, whose 32 lanes compute 32 draws' random numbers at
- * once.  Results are identical for every setting (the random stream is a
- * function of replicate, node, day and draw index only); only speed changes.
- * nodes_per_block <= 0 or heavy_after < 0 restore the size-based defaults. */
+/* Run a shard of a job with several replicates (replicas only across GPUs:
+ * replicates are independent trajectories, Sec. 3.4.2 runs one realisation
+ * per call).  After this call, sg_run's n_rep replicates are the job's
+ * global replicates rep0 .. rep0 + n_rep - 1 out of rep_total: every random
+ * stream (SSA draws, event sampling, 'aem' channels) and every error report
+ * uses the global index, so the shards of one job together reproduce the
+ * whole job's run bit for bit; u0 / v0 / U / V hold the shard's n_rep
+ * replicates only.  With per-replicate events (sg_set_events with a
+ * replicate column) the event table may be the whole job's: the events of
+ * other replicates are left out.  rep_total = 0 (and rep0 = 0) restores a
+ * whole job (the default).  Returns SG_ERR_ARG for rep0 < 0, rep0 >=
+ * rep_total, rep_total > 2^24, or a learned emulator set (the emulator
+ * runs whole jobs only); sg_run returns SG_ERR_ARG when rep0 + n_rep >
+ * rep_total or an event's replicate is >= rep_total. */
+int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total);
+
+/* Work split of the SSA day kernel.  With nodes_per_block in 1..128 each
+ * block of 128 threads owns that many (replicate, node) pairs, one per
+ * thread, kept in registers for a run of days; a node whose SSA needs more
+ * than heavy_after draws in a day is handed to one of the block's warps,
+ * whose 32 lanes compute 32 draws' random numbers at once.  With
+ * nodes_per_block > 128 (up to 2^22; the direct method on the built-in
+ * kinds without emulator, persistent or fused schedules -- elsewhere it
+ * means 128) the sparse-activity schedule runs instead: each block of 256
+ * threads owns nodes_per_block pairs in device memory, skips the days that
+ * are certainly empty (no infected animal and phi == +0, with finite model
+ * parameters), and runs the SSA of the pairs with a positive total rate from
+ * a compact list, one thread each, handing those that need more than
+ * heavy_after draws to warps.  Results are identical for every setting (the
+ * random stream is a function of replicate, node, day and draw index only);
+ * only speed changes.  nodes_per_block <= 0 or heavy_after < 0 restore the
+ * size-based defaults. */
 int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 
 /* Autotuner: for each of nodes_per_block in {4, 8, 16, 32, 64, 128} x
- * heavy_after in {0, 1, 2, 4, 8} runs the given workload (arguments as
- * sg_run) once untimed (capturing its graph when graphs are on) and twice
- * timed, keeps the setting with the fastest timed run in the model and
- * reports it and its time (outputs may be NULL).  U and V hold the last
- * run's (identical) results.  A shorter tspan tunes a long workload on a
- * prefix. */
+ * heavy_after in {0, 1, 2, 4, 8}, and, where the sparse-activity schedule
+ * applies, nodes_per_block = the pairs spread over 1, 2 or 4 blocks per SM
+ * and 1,024 (when above 128) x heavy_after in {2, 8, 32}, runs the given
+ * workload (arguments as sg_run) once untimed (capturing its graph when
+ * graphs are on) and twice timed, keeps the setting with the fastest timed
+ * run in the model and reports it and its time (outputs may be NULL).  U and
+ * V hold the last run's (identical) results.  A shorter tspan tunes a long
+ * workload on a prefix. */
 int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64_t seed,
                 int32_t n_rep, const int32_t *d_u0, const double *d_v0, int32_t *d_U,
                 double *d_V, void *stream, int32_t *nodes_per_block,

@@ -174,7 +174,7 @@ EXPORTS = ["sg_model_create", "sg_set_events", "sg_run", "sg_run_host",
            "sg_set_output", "sg_model_create_parsed", "sg_model_tables",
            "sg_set_fused_events", "sg_set_persistent", "sg_gemm_fp8", "sg_quant_fp8_rows",
            "sg_quant_fp8_bf16", "sg_absmax_bf16", "sg_emulator_set_fp8", "sg_gemm_bf16_to_fp8",
-           "sg_plan_events", "sg_emulator_set_min_rate"]
+           "sg_plan_events", "sg_emulator_set_min_rate", "sg_set_replicate_range"]
 
 _lock = threading.Lock()
 _lib = None
@@ -223,6 +223,8 @@ def lib(path: str | None = None):
         L.sg_run_noalloc.restype = ctypes.c_int
         L.sg_set_tuning.argtypes = [vp, i32, i32]
         L.sg_set_tuning.restype = ctypes.c_int
+        L.sg_set_replicate_range.argtypes = [vp, i32, i32]
+        L.sg_set_replicate_range.restype = ctypes.c_int
         ip32 = ctypes.POINTER(ctypes.c_int32)
         L.sg_autotune.argtypes = [vp, vp, i32, u64, i32, vp, vp, vp, vp, vp, ip32, ip32,
                                   ctypes.POINTER(ctypes.c_double)]
@@ -532,6 +534,14 @@ class Model:
         if rc and check:
             raise SimInfError(rc, er.as_dict())
         return rc, st.as_dict(), er.as_dict()
+
+    def set_replicate_range(self, rep0, rep_total):
+        """Runs cover the job's global replicates rep0 .. rep0 + n_rep - 1 of
+        rep_total (a shard: streams keyed by the global index, other
+        replicates' events left out); (0, 0) = a whole job."""
+        rc = lib().sg_set_replicate_range(self._h, int(rep0), int(rep_total))
+        if rc:
+            raise SimInfError(rc)
 
     def set_tuning(self, nodes_per_block=-1, heavy_after=-1):
         rc = lib().sg_set_tuning(self._h, int(nodes_per_block), int(heavy_after))

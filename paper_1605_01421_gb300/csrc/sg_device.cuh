@@ -176,6 +176,74 @@ struct WordStream {
   }
 };
 
+// Events that move at least this many individuals are sampled by a whole
+// warp (urn_warp); smaller ones by one thread (WordStream::below + walk).
+constexpr int kUrnWarp = 32;
+
+// The urn of one event, sampled by the 32 lanes of a warp together (every
+// lane passes the same arguments and gets the same moved[]).  k individuals
+// are drawn without replacement from the compartments of `mask` with counts
+// cur[] (total of them: `total`): draw j takes a uniform index below
+// total - j from the event's word stream by Lemire's multiply-shift with
+// rejection, and walks the compartments in row order -- the same words,
+// the same indices and the same walk as the thread urn, so moved[] is
+// identical.  Lane l tests draw j0 + l on word i0 + l (words i: component
+// i % 4 of Philox block i / 4); a ballot finds the first rejected draw r,
+// draws j0 .. j0 + r - 1 are final, the rejected word is skipped and the
+// next round starts at draw j0 + r with word i0 + r + 1 (the thread urn's
+// retry).  The walk then takes the final indices in order (a shuffle each).
+template <int C>
+__device__ __forceinline__ void urn_warp(const int *cur, uint32_t mask, uint32_t k,
+                                         uint32_t total, uint64_t seed, long long index, int rep,
+                                         int *moved) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint32_t ilo = (uint32_t)(unsigned long long)index;
+  const uint32_t ihi = (uint32_t)((unsigned long long)index >> 32);
+  const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
+  int rem[C];
+#pragma unroll
+  for (int p = 0; p < C; ++p) {
+    moved[p] = 0;
+    rem[p] = ((mask >> p) & 1u) ? cur[p] : 0;
+  }
+  uint32_t j0 = 0, i0 = 0;
+  while (j0 < k) {
+    const uint32_t j = j0 + (uint32_t)lane;
+    const uint32_t wi = i0 + (uint32_t)lane;
+    const U4 b = philox10(U4{wi >> 2, ilo, ihi, tag}, k0, k1);
+    const uint32_t q = wi & 3u;
+    const uint32_t word = q == 0 ? b.x : q == 1 ? b.y : q == 2 ? b.z : b.w;
+    const bool live = j < k;
+    const uint32_t s = live ? total - j : 1u;  // >= 1 for the draws of this event
+    const unsigned long long m = (unsigned long long)word * s;
+    const uint32_t lo = (uint32_t)m;
+    const bool reject = live && lo < s && lo < (0u - s) % s;
+    const unsigned rmask = __ballot_sync(0xffffffffu, reject);
+    const uint32_t ok = rmask ? (uint32_t)(__ffs(rmask) - 1) : 32u;
+    const uint32_t nd = min(ok, k - j0);
+    const uint32_t x = (uint32_t)(m >> 32);
+    for (uint32_t d = 0; d < nd; ++d) {
+      uint32_t xd = __shfl_sync(0xffffffffu, x, (int)d);
+      bool taken = false;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        if (taken || !((mask >> p) & 1u)) continue;
+        const uint32_t r = (uint32_t)rem[p];
+        if (xd < r) {
+          ++moved[p];
+          --rem[p];
+          taken = true;
+        } else {
+          xd -= r;
+        }
+      }
+    }
+    j0 += nd;
+    i0 += nd + (ok < 32u && j0 < k ? 1u : 0u);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Transition-rate functions (TRFun, Sec. 3.4.1), one set per kind.
 // ---------------------------------------------------------------------------

@@ -51,6 +51,7 @@ struct PtsSpArgs {
   double *V;
   const int32_t *rec;
   int32_t t0, M, n_rep, T;
+  int32_t rep0;  // global index of local replicate 0 (error reports)
   SgDevError *err;
   OutDev out;
 };
@@ -86,7 +87,7 @@ __device__ __forceinline__ void pts_sp_node(const SgTables &tb, const PtsSpArgs 
   const double beta = season_decay(a.T, ends, g + 3);
   const double nv = phi + ((shed + coupling) - beta * phi);
   a.v_new[gid] = nv;
-  if (!isfinite(nv)) report(a.err, SG_ERR_PTS, rep, node, a.T, -1);
+  if (!isfinite(nv)) report(a.err, SG_ERR_PTS, a.rep0 + rep, node, a.T, -1);
   uu[0] = S;
   uu[1] = I;
   if (m >= 0) {
@@ -325,11 +326,12 @@ struct GraphKey {
   const void *u0, *v0, *U, *V;
   const void *u, *v, *cur, *rec, *emu;
   uint64_t seed;
-  int32_t n_rep, n_tspan, t0, t_end, npb, heavy_after;
+  int32_t n_rep, n_tspan, t0, t_end, npb, heavy_after, rep0;
   uint64_t plan_version;
   bool operator==(const GraphKey &o) const {
     return u0 == o.u0 && v0 == o.v0 && U == o.U && V == o.V && u == o.u && v == o.v &&
            cur == o.cur && rec == o.rec && emu == o.emu && seed == o.seed && n_rep == o.n_rep &&
+           rep0 == o.rep0 &&
            n_tspan == o.n_tspan && t0 == o.t0 && t_end == o.t_end && npb == o.npb &&
            heavy_after == o.heavy_after && plan_version == o.plan_version;
   }
@@ -353,6 +355,9 @@ struct sg_model {
   int64_t *e_index = nullptr, *wave_ev = nullptr, *wave_off = nullptr, *e1_node_off = nullptr;
   int32_t heavy_after = -1;  // draws a thread takes before its warp takes
   int32_t npb = -1;          // nodes per block; -1 = chosen from the size
+  // sg_set_replicate_range: the runs cover global replicates rep0 .. rep0 +
+  // n_rep - 1 of a job with rep_total replicates (0: a whole job, rep0 = 0)
+  int32_t rep0 = 0, rep_total = 0;
   // working memory
   DevBuf<int32_t> e1_cur;
   DevBuf<int> u;
@@ -672,11 +677,15 @@ static unsigned char *pinned_stage(size_t bytes) {
 }
 
 static int ensure_plan(sg_model *m, int32_t t0, int32_t t_end, int32_t slots) {
-  if (m->plan_ok && m->plan.t0 == t0 && m->plan.t_end == t_end && m->plan.slots == slots)
+  // a shard of a job with per-replicate events plans its own replicates
+  const bool shard = m->rep_total > 0 && m->ev.per_rep;
+  const int32_t rep_lo = shard ? m->rep0 : 0;
+  if (m->plan_ok && m->plan.t0 == t0 && m->plan.t_end == t_end && m->plan.slots == slots &&
+      m->plan.rep_lo == rep_lo && m->plan.shard == shard)
     return SG_OK;
   m->plan_ok = false;
   Plan &P = m->plan;
-  int rc = build_plan(m->ev, m->tb.n_nodes, t0, t_end, slots, &P);
+  int rc = build_plan(m->ev, m->tb.n_nodes, t0, t_end, slots, &P, rep_lo, shard);
   if (rc) return rc;
   // every device array of the plan in one arena, filled in one host staging
   // buffer and copied with one transfer
@@ -764,10 +773,16 @@ template <int KIND>
 static void launch_days(sg_model *m, const DayArgs &a, cudaStream_t st) {
   const long long units = (long long)m->tb.n_nodes * a.n_rep;
   const unsigned grid = (unsigned)std::max<long long>(1, (units + a.npb - 1) / a.npb);
-  if (a.aem_tau)
+  if (a.aem_tau) {
     launch_pdl(k_days<KIND, true>, grid, kDayBlock, 0, st, m->tb, a);
-  else
+  } else if (a.npb > kDayBlock) {
+    // sparse-activity schedule (sg_run only sets npb > kDayBlock where it
+    // applies: direct method, built-in kinds without a coupled post step)
+    if constexpr (KIND == SG_SIR || KIND == SG_SIS || KIND == SG_SISE || KIND == SG_SISE3)
+      launch_pdl(k_days_sparse<KIND>, grid, kSparseBlock, 0, st, m->tb, a);
+  } else {
     launch_pdl(k_days<KIND, false>, grid, kDayBlock, 0, st, m->tb, a);
+  }
 }
 
 // Launch of a kernel compiled at run time (SG_GENERIC), with programmatic
@@ -1033,6 +1048,7 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     pa.t0 = t0;
     pa.M = n_tspan;
     pa.n_rep = n_rep;
+    pa.rep0 = da0.rep0;
     pa.err = m->err.p;
     const long long units = (long long)Nn * n_rep;
     for (int32_t d = 0; d < days; ++d) {
@@ -1304,10 +1320,16 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   if (Nn > 0 && (!d_u0 || (NV > 0 && !d_v0))) return SG_ERR_ARG;
   if (Nn > 0 && m->out_dense && (!d_U || (NV > 0 && !d_V))) return SG_ERR_ARG;
   if (m->out_cols >= 0 && m->out_cols != n_tspan) return SG_ERR_ARG;
-  if (m->ev.per_rep && m->ev.max_rep >= n_rep) {
+  // a shard (sg_set_replicate_range) runs global replicates rep0 .. rep0 +
+  // n_rep - 1 of a job with rep_total; a whole job needs every event's
+  // replicate below n_rep
+  const int32_t rep_total = m->rep_total > 0 ? m->rep_total : n_rep;
+  if (m->rep0 + (long long)n_rep > rep_total) return SG_ERR_ARG;
+  if (m->ev.per_rep && m->ev.max_rep >= rep_total) {
     fill_error(err, SG_ERR_ARG, m->ev.max_rep, -1, -1, -1);
     return SG_ERR_ARG;
   }
+  if (m->rep0 > 0 && m->emu_on) return SG_ERR_ARG;  // the emulator runs whole jobs only
   if (tb.kind == SG_GENERIC) {
     int dev = -1;
     cudaGetDevice(&dev);
@@ -1401,8 +1423,23 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.M = n_tspan;
   da.n_rep = n_rep;
   da.slots = slots;
+  da.rep0 = m->rep0;
   da.heavy_after = m->heavy_after >= 0 ? m->heavy_after : 2;
   da.npb = m->npb > 0 ? m->npb : default_npb((long long)Nn * n_rep);
+  // the sparse-activity schedule (nodes_per_block > kDayBlock) is for the
+  // direct method on the built-in kinds with the day / E2 kernel pair;
+  // elsewhere such a split falls back to full thread-per-node blocks
+  const bool sparse_ok = !aem && !m->emu_on && !m->fuse_e2 && !m->persistent &&
+                         (tb.kind == SG_SIR || tb.kind == SG_SIS || tb.kind == SG_SISE ||
+                          tb.kind == SG_SISE3);
+  if (da.npb > kDayBlock && !sparse_ok) da.npb = kDayBlock;
+  {
+    // a unit with no infected animal and phi == +0 has an empty day only
+    // when every parameter is finite (0 times inf or NaN is not 0)
+    bool finite = true;
+    for (int i = 0; i < SG_MAX_GDATA; ++i) finite = finite && std::isfinite(tb.gdata[i]);
+    da.quiet = finite ? 1 : 0;
+  }
   da.k0 = (uint32_t)seed;
   da.k1 = (uint32_t)(seed >> 32);
   da.err = m->err.p;
@@ -1429,6 +1466,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   ea.ev = evd;
   ea.u = m->u.p;
   ea.n_rep = n_rep;
+  ea.rep0 = m->rep0;
   ea.k0 = da.k0;
   ea.k1 = da.k1;
   ea.day = 0;
@@ -1459,6 +1497,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                      t_end,
                      da.npb,
                      da.heavy_after,
+                     m->rep0,
                      (m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)) *
                              1000033ull +
                          m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p +
@@ -1874,8 +1913,18 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
   return SG_OK;
 }
 
+extern "C" int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total) {
+  if (!m || rep0 < 0 || rep_total < 0 || (rep_total > 0 && rep0 >= rep_total) ||
+      (rep_total == 0 && rep0 != 0) || rep_total > (1 << 24))
+    return SG_ERR_ARG;
+  if (rep0 > 0 && m->emu_on) return SG_ERR_ARG;
+  m->rep0 = rep0;
+  m->rep_total = rep_total;
+  return SG_OK;
+}
+
 extern "C" int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after) {
-  if (!m || nodes_per_block > kDayBlock || heavy_after > (1 << 20)) return SG_ERR_ARG;
+  if (!m || nodes_per_block > (1 << 22) || heavy_after > (1 << 20)) return SG_ERR_ARG;
   m->npb = nodes_per_block > 0 ? nodes_per_block : -1;
   m->heavy_after = heavy_after >= 0 ? heavy_after : -1;
   return SG_OK;
@@ -1887,9 +1936,34 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
                            int32_t *heavy_after_out, double *ms_out) {
   if (!m) return SG_ERR_ARG;
   // 4 and 8 nodes per block give every heavy node its own warp (workloads
-  // where most node-days take thousands of draws)
-  static const int32_t kNpb[] = {4, 8, 16, 32, 64, 128};
-  static const int32_t kHeavy[] = {0, 1, 2, 4, 8};
+  // where most node-days take thousands of draws); more than kDayBlock
+  // selects the sparse-activity schedule: units spread over 1, 2 or 4
+  // blocks per SM, or fixed 1,024-unit blocks
+  std::vector<std::pair<int32_t, int32_t>> cand;
+  for (int32_t npb : {4, 8, 16, 32, 64, 128})
+    for (int32_t h : {0, 1, 2, 4, 8}) cand.emplace_back(npb, h);
+  {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    const long long units = (long long)m->tb.n_nodes * n_rep;
+    std::vector<int32_t> sp;
+    for (int per_sm : {1, 2, 4}) {
+      const long long b = (units + (long long)sms * per_sm - 1) / ((long long)sms * per_sm);
+      if (b > kDayBlock && b <= (1 << 22)) sp.push_back((int32_t)b);
+    }
+    if (units > 2LL * kDayBlock * sms) sp.push_back(1024);
+    const int k = m->tb.kind;
+    const bool sparse_ok = m->solver != SG_SOLVER_AEM && !m->emu_on && !m->fuse_e2 &&
+                           !m->persistent &&
+                           (k == SG_SIR || k == SG_SIS || k == SG_SISE || k == SG_SISE3);
+    if (!sparse_ok) sp.clear();
+    for (int32_t npb : sp)
+      for (int32_t h : {2, 8, 32}) cand.emplace_back(npb, h);
+  }
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -1902,8 +1976,9 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
   double best = 1e300;
   int32_t best_npb = -1, best_heavy = -1;
   int rc = SG_OK;
-  for (int32_t npb : kNpb) {
-    for (int32_t h : kHeavy) {
+  for (const auto &ch : cand) {
+    {
+      const int32_t npb = ch.first, h = ch.second;
       m->npb = npb;
       m->heavy_after = h;
       // one untimed run (it captures the candidate's graph when graphs are

@@ -155,6 +155,13 @@ struct DayArgs {
   int32_t *e1_cur;     // [R][Nn]: next E1 event, relative to the node's list
   EvDev ev;
   int32_t t0, M, n_rep, slots;
+  // global index of the run's replicate 0 (a shard of a larger job): every
+  // random stream and error report uses rep0 + the local replicate, state
+  // and outputs the local one
+  int32_t rep0;
+  // 1: the model's parameters are finite, so a unit without infected
+  // animals and with phi == +0 has an empty day (k_days_sparse skips it)
+  int32_t quiet;
   int32_t T_begin, T_end;  // SSA toward T = T_begin .. T_end - 1
   int32_t finish_first;    // finish unit step T_begin - 1 before the SSA
   int32_t finish_last;     // finish unit step T_end - 1 after the SSA
@@ -253,8 +260,14 @@ __device__ void e2_rep_block(const SgTables &tb, const DayArgs &a, int rep, int 
   if (__syncthreads_or(threadIdx.x == 0 && *(volatile int32_t *)&a.err->code != 0)) return;
   int *state = a.u + (long long)rep * tb.n_nodes * C;
   const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
+  constexpr int kHv = 256;  // large transfers of a wave left to the warps
+  __shared__ long long s_hv[kHv];
+  __shared__ int s_nhv;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   unsigned long long applied = 0;
   bool bad = false;
+  if (threadIdx.x == 0) s_nhv = 0;
+  __syncthreads();
   for (long long w = w0; w < w1; ++w) {
     const long long lo = a.wave_ev[w], hi = a.wave_ev[w + 1];
     for (long long j = lo + threadIdx.x; j < hi; j += blockDim.x) {
@@ -273,16 +286,25 @@ __device__ void e2_rep_block(const SgTables &tb, const DayArgs &a, int rep, int 
       const long long k =
           n > 0 ? (long long)n : (long long)round(a.ev.proportion[j] * (double)total);
       if (k < 0 || k > total) {
-        report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, T, idx);
+        report(a.err, SG_ERR_EVENT_UNDERFLOW, a.rep0 + rep, src, T, idx);
         bad = true;
         continue;
+      }
+      if (k >= kUrnWarp) {
+        // a large transfer: sampled by a warp after this pass (in this
+        // thread when the list is full)
+        const int slot = atomicAdd(&s_nhv, 1);
+        if (slot < kHv) {
+          s_hv[slot] = j;
+          continue;
+        }
       }
       int moved[C];
 #pragma unroll
       for (int p = 0; p < C; ++p) moved[p] = 0;
       if (k > 0) {
         WordStream ws;
-        ws.init(seed, idx, rep);
+        ws.init(seed, idx, a.rep0 + rep);
         for (long long d = 0; d < k; ++d) {
           uint32_t x = ws.below((uint32_t)(total - d));
           bool taken = false;
@@ -311,6 +333,45 @@ __device__ void e2_rep_block(const SgTables &tb, const DayArgs &a, int rep, int 
     }
     // one barrier per wave; its result is the same for every thread
     if (__syncthreads_or(bad)) break;
+    const int nhv = min(s_nhv, kHv);  // the same in every thread
+    if (nhv > 0) {
+      __syncthreads();  // every thread has read the count
+      if (threadIdx.x == 0) s_nhv = 0;
+      // the wave's large transfers, one warp each (no other event of the
+      // wave touches their source nodes)
+      for (int h = warp; h < nhv; h += nwarps) {
+        const long long j = s_hv[h];
+        const int src = a.ev.node[j];
+        int *un = state + (long long)src * C;
+        const uint32_t mask = tb.Emask[a.ev.select[j]];
+        int cur[C];
+        long long total = 0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) {
+          cur[p] = __ldcg(un + p);
+          if ((mask >> p) & 1u) total += cur[p];
+        }
+        const int n = a.ev.n[j];
+        const long long k =
+            n > 0 ? (long long)n : (long long)round(a.ev.proportion[j] * (double)total);
+        int moved[C];
+        urn_warp<C>(cur, mask, (uint32_t)k, (uint32_t)total, seed, a.ev.index[j], a.rep0 + rep,
+                    moved);
+        if (lane == 0) {
+          const int q_sh = a.ev.shift[j];
+          int *ud = state + (long long)a.ev.dest[j] * C;
+#pragma unroll
+          for (int p = 0; p < C; ++p)
+            if (moved[p] != 0) __stcg(un + p, cur[p] - moved[p]);
+#pragma unroll
+          for (int p = 0; p < C; ++p)
+            if (moved[p] != 0) atomicAdd(ud + (q_sh >= 0 ? p + tb.Nsh[q_sh][p] : p), moved[p]);
+          ++applied;
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
   }
   if (applied) atomicAdd(&a.cnt->events, applied);
 }
@@ -1218,6 +1279,63 @@ __device__ __forceinline__ int apply_e1(int *u, const SgTables &tb, const E1Rec 
   return 0;
 }
 
+// The number of individuals an E1 event draws (exit or internal transfer;
+// 0 for an enter, -1 for one that moves more than exist).
+template <int C>
+__device__ __forceinline__ long long e1_draws(const int *u, const SgTables &tb, const E1Rec &e) {
+  if (e.type == SG_ENTER) return 0;
+  long long total = 0;
+#pragma unroll
+  for (int p = 0; p < C; ++p)
+    if ((e.mask >> p) & 1u) total += u[p];
+  const long long k = e.n > 0 ? (long long)e.n : (long long)round(e.prop * (double)total);
+  return (k < 0 || k > total) ? -1 : k;
+}
+
+// The E1 event `e` of lane `owner` (an exit or internal transfer drawing at
+// least kUrnWarp individuals), applied by the whole warp: the owner's counts
+// and event fields are broadcast, the warp samples the urn (urn_warp, the
+// same draws as apply_e1), and the owner's counts are updated.  Every lane
+// calls it with the same owner; returns the owner's result in every lane.
+template <int C>
+__device__ __forceinline__ int apply_e1_warp(int *u, const SgTables &tb, const E1Rec &e,
+                                             int owner, int rep, uint32_t k0, uint32_t k1) {
+  const int lane = threadIdx.x & 31;
+  int cu[C];
+#pragma unroll
+  for (int p = 0; p < C; ++p) cu[p] = __shfl_sync(0xffffffffu, u[p], owner);
+  const int type = __shfl_sync(0xffffffffu, e.type, owner);
+  const uint32_t mask = __shfl_sync(0xffffffffu, e.mask, owner);
+  const int n = __shfl_sync(0xffffffffu, e.n, owner);
+  const int shift = __shfl_sync(0xffffffffu, e.shift, owner);
+  const long long idx = __shfl_sync(0xffffffffu, e.idx, owner);
+  const double prop = __shfl_sync(0xffffffffu, e.prop, owner);
+  const int r = __shfl_sync(0xffffffffu, rep, owner);
+  long long total = 0;
+#pragma unroll
+  for (int p = 0; p < C; ++p)
+    if ((mask >> p) & 1u) total += cu[p];
+  const long long k = n > 0 ? (long long)n : (long long)round(prop * (double)total);
+  if (k < 0 || k > total) return SG_ERR_EVENT_UNDERFLOW;
+  int moved[C];
+  urn_warp<C>(cu, mask, (uint32_t)k, (uint32_t)total, ((uint64_t)k1 << 32) | k0, idx, r, moved);
+  if (lane == owner) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] -= moved[p];
+    if (type != SG_EXIT) {
+#pragma unroll
+      for (int dst = 0; dst < C; ++dst) {
+        int add = 0;
+#pragma unroll
+        for (int p = 0; p < C; ++p)
+          if (p + tb.Nsh[shift][p] == dst) add += moved[p];
+        u[dst] += add;
+      }
+    }
+  }
+  return 0;
+}
+
 // Post time step and recording for unit time Tf (the state after its
 // events).  Returns 0 or SG_ERR_PTS.
 template <int KIND>
@@ -1324,7 +1442,8 @@ k_days(const SgTables tb, const DayArgs a) {
     if (m >= 0)
       prevalence_add<C>(a.out, in_range ? (long long)rep * a.M + m : -1, live && code == 0, u);
   }
-  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)rep;
+  const int grep = a.rep0 + rep;  // global replicate: streams, error reports
+  const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)grep;
   for (int Td = a.T_begin; Td < a.T_end; ++Td) {
     const double Tn = (double)Td;
     if (threadIdx.x == 0) s_nheavy = 0;
@@ -1335,7 +1454,7 @@ k_days(const SgTables tb, const DayArgs a) {
     const int d = Td - a.t0 - 1;
     const bool e1_today = live && code == 0 && next_day == d;
     E1Rec pre;
-    if (e1_today) pre = load_e1(tb, a.ev, ecur, rep, a.k0, a.k1);
+    if (e1_today) pre = load_e1(tb, a.ev, ecur, grep, a.k0, a.k1);
     const bool emulated =
         !AEM && live && code == 0 && a.emu != nullptr && a.emu[gid * 4 + 3] != 0;
     if (emulated) {
@@ -1351,7 +1470,7 @@ k_days(const SgTables tb, const DayArgs a) {
     if (AEM && live && code == 0) {
       double kf[NK];
       M::prepare(v, tb.gdata, kf);
-      const uint32_t tag = (SG_STREAM_AEM << 24) | (uint32_t)rep;
+      const uint32_t tag = (SG_STREAM_AEM << 24) | (uint32_t)grep;
       code = aem_day_start<KIND>(u, kf, ch_a, ch_tau, ch_c, Tn, (uint32_t)node, tag, a.k0, a.k1,
                                  tb, drawn);
       double t = Tn - 1.0;
@@ -1387,7 +1506,7 @@ k_days(const SgTables tb, const DayArgs a) {
             }
             hs.nfired = nfired;
             hs.node = node;
-            hs.rep = rep;
+            hs.rep = grep;
             hs.code = 0;
 #pragma unroll
             for (int p = 0; p < C; ++p) hs.u[p] = u[p];
@@ -1425,7 +1544,7 @@ k_days(const SgTables tb, const DayArgs a) {
           for (int i = 0; i < NK; ++i) hs.kf[i] = kf[i];
           hs.c = c;
           hs.node = node;
-          hs.rep = rep;
+          hs.rep = grep;
           hs.code = 0;
 #pragma unroll
           for (int p = 0; p < C; ++p) hs.u[p] = u[p];
@@ -1469,24 +1588,57 @@ k_days(const SgTables tb, const DayArgs a) {
         bad_day = Td;
       }
     }
-    // this node's E1 events of day Td, in (time, type, list index) order
-    if (e1_today && code == 0) {
+    // this node's E1 events of day Td, in (time, type, list index) order:
+    // each round every lane with an event left takes its next one, applied
+    // in the thread, or by the whole warp when it draws kUrnWarp or more
+    // individuals (every thread of the block reaches this loop)
+    {
+      bool pend = e1_today && code == 0;
       bool first = true;
-      while (ecur < eend && a.ev.e1_day[ecur] == d) {
-        const int rc = first ? apply_e1<C>(u, tb, pre, rep, a.k0, a.k1)
-                             : apply_e1<C>(u, tb, load_e1(tb, a.ev, ecur, rep, a.k0, a.k1),
-                                           rep, a.k0, a.k1);
-        first = false;
-        if (rc) {
-          code = rc;
-          bad_day = Td;
-          bad_event = a.ev.index[ecur];
-          break;
+      const int lane = threadIdx.x & 31;
+      while (__any_sync(0xffffffffu, pend)) {
+        E1Rec e;
+        bool heavy = false;
+        if (pend) {
+          if (ecur < eend && a.ev.e1_day[ecur] == d) {
+            e = first ? pre : load_e1(tb, a.ev, ecur, grep, a.k0, a.k1);
+            first = false;
+            heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
+            if (!heavy) {
+              const int rc = apply_e1<C>(u, tb, e, grep, a.k0, a.k1);
+              if (rc) {
+                code = rc;
+                bad_day = Td;
+                bad_event = a.ev.index[ecur];
+                pend = false;
+              } else {
+                ++applied;
+                ++ecur;
+              }
+            }
+          } else {
+            pend = false;
+          }
         }
-        ++applied;
-        ++ecur;
+        unsigned hm = __ballot_sync(0xffffffffu, heavy);
+        while (hm) {
+          const int L = __ffs(hm) - 1;
+          hm &= hm - 1;
+          const int rc = apply_e1_warp<C>(u, tb, e, L, grep, a.k0, a.k1);
+          if (lane == L) {
+            if (rc) {
+              code = rc;
+              bad_day = Td;
+              bad_event = a.ev.index[ecur];
+              pend = false;
+            } else {
+              ++applied;
+              ++ecur;
+            }
+          }
+        }
       }
-      next_day = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
+      if (e1_today) next_day = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
     }
     if (a.grid_bar && a.wave_off) {
       // persistent run: the day's external transfers between two grid
@@ -1528,7 +1680,7 @@ k_days(const SgTables tb, const DayArgs a) {
     }
   }
   if (live) {
-    if (code) report(a.err, code, rep, node, bad_day, bad_event);
+    if (code) report(a.err, code, a.rep0 + rep, node, bad_day, bad_event);
 #pragma unroll
     for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
 #pragma unroll
@@ -1588,10 +1740,380 @@ k_days(const SgTables tb, const DayArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Day kernel for sparse activity (the direct method on the built-in kinds).
+// On cattle-shaped workloads only a few percent of the node-days have a
+// positive total rate; the rest take no draw, and on the thread-per-node
+// schedule above their threads still compute every rate and the post time
+// step in FP64 (GB300's weakest pipe) and wait at block barriers for the
+// block's few active nodes.  Here a block owns a contiguous range of
+// `npb` (> kDayBlock) (replicate, node) units whose state stays in global
+// memory (L2), and each day it
+//   1. visits every unit: finishes the previous day when the launch starts
+//      with it, and tests whether the unit's day is certainly empty
+//      (quiescent<>: no infected animal and phi exactly +0, with finite
+//      parameters every rate is then +-0 and the post time step leaves phi
+//      at +0, so skipping them changes no bit); the other units get their
+//      rates, and those with lambda > 0 go to a shared list;
+//   2. runs the SSA of the listed units, one thread each (dense lanes), a
+//      unit needing more than heavy_after draws handed to a warp (32 draws'
+//      random numbers at once, as above);
+//   3. visits every unit again: its E1 events of the day (per-unit cursor)
+//      and, unless the day's external transfers follow in their own kernel,
+//      the post time step and recording.
+// Units are taken in chunks of kSparseChunk so that the list fits in shared
+// memory.  Every unit's operations and random draws are the ones of the
+// thread-per-node schedule, so the results are identical.
+// ---------------------------------------------------------------------------
+constexpr int kSparseBlock = 256;   // threads of the sparse-schedule day kernel
+constexpr int kSparseChunk = 4096;  // units per pass through the active list
+constexpr int kSparseHeavy = 64;    // warp hand-off slots per pass
+
+// A unit whose day is certainly empty: no infected animal and phi == +0
+// (bit pattern 0).  Exact only with finite model parameters (DayArgs::quiet).
+template <int KIND>
+__device__ __forceinline__ bool quiescent(const int *u, const double *v) {
+  if constexpr (KIND == SG_SIR || KIND == SG_SIS) {
+    return u[1] == 0;
+  } else if constexpr (KIND == SG_SISE) {
+    return u[1] == 0 && __double_as_longlong(v[0]) == 0;
+  } else if constexpr (KIND == SG_SISE3) {
+    return (u[1] | u[3] | u[5]) == 0 && __double_as_longlong(v[0]) == 0;
+  } else {
+    return false;
+  }
+}
+
+__device__ __forceinline__ void load_ends(const DayArgs &a, const SgTables &tb, int node,
+                                          int *ld) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ld[i] = season_end_int(a.ldata[(long long)node * tb.n_ldata + i]);
+}
+
+// Post time step and recording of unit time Tf for one unit of the sparse
+// schedule (counts u, continuous state v, stored back); a quiescent unit's
+// post time step is skipped (phi stays +0).  Returns 0 or SG_ERR_PTS.
+template <int KIND>
+__device__ __forceinline__ int sparse_finish(int Tf, const int *u, double *v, bool quiet,
+                                             const SgTables &tb, const DayArgs &a, int rep,
+                                             int node, long long gid) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, NV = M::NV;
+  if (quiet && quiescent<KIND>(u, v)) {
+    const int m = a.rec[Tf - a.t0];
+    if (m >= 0) {
+      const long long base = ((long long)rep * a.M + m) * tb.n_nodes + node;
+      if (a.U) {
+#pragma unroll
+        for (int p = 0; p < C; ++p) a.U[base * C + p] = u[p];
+      }
+      if (a.V) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) a.V[base * NV + q] = v[q];
+      }
+      record_sparse<C, NV>(a.out, m, rep, node, u, v);
+    }
+    return 0;
+  }
+  int ld[4] = {0, 0, 0, 0};
+  if (NV > 0) load_ends(a, tb, node, ld);
+  const int code = finish_step<KIND>(Tf, u, v, ld, tb, a, rep, node);
+  if (code) report(a.err, code, a.rep0 + rep, node, Tf, -1);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) a.v[gid * NV + q] = v[q];
+  return code;
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kSparseBlock)
+k_days_sparse(const SgTables tb, const DayArgs a) {
+  using M = ModelTraits<KIND>;
+  constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
+  __shared__ int32_t s_act[kSparseChunk];
+  __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
+  __shared__ int s_nact, s_nheavy, s_stop;
+  pdl_trigger();
+  const int Nn = tb.n_nodes;
+  const long long total = (long long)Nn * a.n_rep;
+  const long long g0 = (long long)blockIdx.x * a.npb;
+  const int nub = (int)max(0LL, min((long long)a.npb, total - g0));
+  const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const bool quiet = a.quiet != 0;
+  const uint32_t k0 = a.k0, k1 = a.k1;
+  unsigned long long fired = 0, drawn = 0, applied = 0;
+  pdl_wait();
+  if (a.finish_first && a.T_begin >= a.T_end &&
+      *(volatile int32_t *)&a.err->code == 0) {
+    // a launch that only finishes unit time T_begin - 1 (the run's last
+    // step after its external transfers)
+    const int Tf = a.T_begin - 1;
+    for (int i0 = 0; i0 < nub; i0 += kSparseBlock) {
+      const int i = i0 + tid;
+      const bool in = i < nub;
+      const long long gid = g0 + i;
+      int u[C];
+      double v[NV > 0 ? NV : 1];
+      int rep = 0, node = 0, code = 0;
+      v[0] = 0.0;
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = 0;
+      if (in) {
+        rep = (int)(gid / Nn);
+        node = (int)(gid - (long long)rep * Nn);
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+        code = sparse_finish<KIND>(Tf, u, v, quiet, tb, a, rep, node, gid);
+      }
+      if (a.out.prev) {
+        const int m = a.rec[Tf - a.t0];
+        if (m >= 0)
+          prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+      }
+    }
+  }
+  for (int Td = a.T_begin; Td < a.T_end; ++Td) {
+    // a failed run stops at the next day boundary (the block's verdict)
+    if (tid == 0) s_stop = *(volatile int32_t *)&a.err->code != 0;
+    __syncthreads();
+    if (s_stop) break;
+    const double Tn = (double)Td;
+    const int d = Td - a.t0 - 1;
+    const bool fin_prev = Td == a.T_begin && a.finish_first;
+    for (int c0 = 0; c0 < nub; c0 += kSparseChunk) {
+      const int cn = min(kSparseChunk, nub - c0);
+      if (tid == 0) {
+        s_nact = 0;
+        s_nheavy = 0;
+      }
+      __syncthreads();
+      // 1. every unit of the chunk: finish of Td - 1 (launch start only),
+      //    quiescence test, rates, list of the units with lambda > 0
+      for (int i0 = 0; i0 < cn; i0 += kSparseBlock) {
+        const int i = i0 + tid;
+        const bool in = i < cn;
+        const long long gid = g0 + c0 + i;
+        int u[C];
+        double v[NV > 0 ? NV : 1];
+        int rep = 0, node = 0, code = 0;
+        v[0] = 0.0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] = 0;
+        if (in) {
+          rep = (int)(gid / Nn);
+          node = (int)(gid - (long long)rep * Nn);
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+          if (fin_prev) code = sparse_finish<KIND>(Td - 1, u, v, quiet, tb, a, rep, node, gid);
+          if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
+            double kf[NK], w[T];
+            M::prepare(v, tb.gdata, kf);
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+              w[j] = M::rate_k(j, u, kf, tb.gdata);
+              bad = bad || bad_rate(w[j]);
+            }
+            double lam = w[0];
+#pragma unroll
+            for (int j = 1; j < T; ++j) lam = lam + w[j];
+            if (bad) {
+              report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
+            } else if (gt0(lam)) {
+              s_act[atomicAdd(&s_nact, 1)] = c0 + i;
+            }
+          }
+        }
+        if (fin_prev && a.out.prev) {
+          const int m = a.rec[Td - 1 - a.t0];
+          if (m >= 0)
+            prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+        }
+      }
+      __syncthreads();
+      // 2. the listed units' SSA, one thread each
+      const int na = s_nact;
+      for (int i = tid; i < na; i += kSparseBlock) {
+        const long long gid = g0 + s_act[i];
+        const int rep = (int)(gid / Nn);
+        const int node = (int)(gid - (long long)rep * Nn);
+        const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)(a.rep0 + rep);
+        int u[C];
+        double v[NV > 0 ? NV : 1];
+        v[0] = 0.0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+        double kf[NK], w[T];
+        M::prepare(v, tb.gdata, kf);
+#pragma unroll
+        for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
+        double t = (double)(Td - 1);
+        uint32_t c = 0;
+        int r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag, k0, k1,
+                                 a.heavy_after, tb, fired);
+        if (r == SSA_HEAVY) {
+          const int slot = atomicAdd(&s_nheavy, 1);
+          if (slot < kSparseHeavy) {
+            HeavySlot<C, NK> &hs = s_heavy[slot];
+            hs.t = t;
+#pragma unroll
+            for (int k = 0; k < NK; ++k) hs.kf[k] = kf[k];
+            hs.c = c;
+            hs.node = node;
+            hs.rep = a.rep0 + rep;
+            hs.code = (int32_t)(gid - g0);  // the unit, until the warp reports
+#pragma unroll
+            for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+            drawn += c;
+            continue;
+          }
+          // no slot left: the thread finishes its unit itself
+          r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag, k0, k1, -1,
+                               tb, fired);
+        }
+        drawn += c;
+        if (r < 0) report(a.err, r, a.rep0 + rep, node, Td, -1);
+#pragma unroll
+        for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+      }
+      __syncthreads();
+      // heavy units, one warp each
+      const int nh = min(s_nheavy, kSparseHeavy);
+      for (int h = warp; h < nh; h += nwarps) {
+        HeavySlot<C, NK> &hs = s_heavy[h];
+        const long long gid = g0 + hs.code;  // the unit (ssa_warp sets the code)
+        __syncwarp();
+        ssa_warp<KIND>(hs, Tn, (uint32_t)Td, k0, k1, tb, fired, drawn);
+        if ((tid & 31) == 0) {
+          if (hs.code) report(a.err, hs.code, hs.rep, hs.node, Td, -1);
+#pragma unroll
+          for (int p = 0; p < C; ++p) a.u[gid * C + p] = hs.u[p];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+    // 3. every unit: E1 events of day Td in (time, type, list index) order,
+    //    then (unless deferred to the next launch) the post time step and
+    //    recording of Td
+    const bool fin = Td + 1 < a.T_end || a.finish_last;
+    for (int i0 = 0; i0 < nub; i0 += kSparseBlock) {
+      const int i = i0 + tid;
+      const bool in = i < nub;
+      const long long gid = g0 + i;
+      int u[C];
+      double v[NV > 0 ? NV : 1];
+      int rep = 0, node = 0, code = 0;
+      long long ecur = 0, eend = 0, ebase = 0;
+      bool has = false;
+      v[0] = 0.0;
+#pragma unroll
+      for (int p = 0; p < C; ++p) u[p] = 0;
+      if (in) {
+        rep = (int)(gid / Nn);
+        node = (int)(gid - (long long)rep * Nn);
+        if (a.ev.e1_node_off) {
+          const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
+          ebase = a.ev.e1_node_off[key];
+          eend = a.ev.e1_node_off[key + 1];
+          ecur = ebase + a.e1_cur[gid];
+          has = ecur < eend && a.ev.e1_day[ecur] == d;
+        }
+        if (has || fin) {
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+        }
+      }
+      // E1 events, every lane with an event left taking its next one per
+      // round, applied in the thread or (kUrnWarp or more individuals
+      // drawn) by the whole warp; the loop is warp-uniform
+      {
+        const int grep = a.rep0 + rep;
+        const int lane = tid & 31;
+        bool pend = has;
+        while (__any_sync(0xffffffffu, pend)) {
+          E1Rec e;
+          bool heavy = false;
+          if (pend) {
+            if (ecur < eend && a.ev.e1_day[ecur] == d) {
+              e = load_e1(tb, a.ev, ecur, grep, k0, k1);
+              heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
+              if (!heavy) {
+                const int rc = apply_e1<C>(u, tb, e, grep, k0, k1);
+                if (rc) {
+                  code = rc;
+                  report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
+                  pend = false;
+                } else {
+                  ++applied;
+                  ++ecur;
+                }
+              }
+            } else {
+              pend = false;
+            }
+          }
+          unsigned hm = __ballot_sync(0xffffffffu, heavy);
+          while (hm) {
+            const int L = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const int rc = apply_e1_warp<C>(u, tb, e, L, grep, k0, k1);
+            if (lane == L) {
+              if (rc) {
+                code = rc;
+                report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
+                pend = false;
+              } else {
+                ++applied;
+                ++ecur;
+              }
+            }
+          }
+        }
+        if (has) {
+#pragma unroll
+          for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+          a.e1_cur[gid] = (int32_t)(ecur - ebase);
+        }
+      }
+      if (in && fin && code == 0)
+        code = sparse_finish<KIND>(Td, u, v, quiet, tb, a, rep, node, gid);
+      if (fin && a.out.prev) {
+        const int m = a.rec[Td - a.t0];
+        if (m >= 0)
+          prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+      }
+    }
+    __syncthreads();
+  }
+  // one atomic per warp for the counters
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    fired += __shfl_down_sync(0xffffffffu, fired, off);
+    drawn += __shfl_down_sync(0xffffffffu, drawn, off);
+    applied += __shfl_down_sync(0xffffffffu, applied, off);
+  }
+  if ((tid & 31) == 0) {
+    if (drawn | fired) {
+      atomicAdd(&a.cnt->reactions, fired);
+      atomicAdd(&a.cnt->draws, drawn);
+    }
+    if (applied) atomicAdd(&a.cnt->events, applied);
+  }
+}
+
 struct EvArgs {
   EvDev ev;
   int *u;
   int32_t n_rep;
+  int32_t rep0;  // global index of local replicate 0 (streams, error reports)
   uint32_t k0, k1;
   int32_t day;  // unit time point T the events run at
   SgDevError *err;
@@ -1639,8 +2161,12 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   __shared__ double s_prop[kE2Cap];
   __shared__ uint4 s_w[kE2Cap];
   __shared__ long long s_wave[kE2WaveCap + 1];
+  __shared__ int16_t s_hv[kE2Cap];  // the wave's events left to the warps
+  __shared__ int s_nhv;
   pdl_trigger();
   const int rep = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) s_nhv = 0;
   const int Nn = tb.n_nodes;
   long long w0 = w_begin_shared, w1 = w_end_shared;
   if (slots > 1) {
@@ -1658,7 +2184,7 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
   // barrier (__syncthreads_or), so every thread leaves the loops together
   bool bad = false, stop = false;
   const uint64_t seed = ((uint64_t)a.k1 << 32) | a.k0;
-  const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)rep;
+  const uint32_t tag = (SG_STREAM_EVENTS << 24) | (uint32_t)(a.rep0 + rep);
   unsigned long long applied = 0;
   long long w = w0;
   long long pos = wave_ev[w0];
@@ -1714,8 +2240,13 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
         const long long k = s_n[i] > 0 ? (long long)s_n[i]
                                        : (long long)round(s_prop[i] * (double)total);
         if (k < 0 || k > total) {
-          report(a.err, SG_ERR_EVENT_UNDERFLOW, rep, src, a.day, s_idx[i]);
+          report(a.err, SG_ERR_EVENT_UNDERFLOW, a.rep0 + rep, src, a.day, s_idx[i]);
           bad = true;
+          continue;
+        }
+        if (k >= kUrnWarp) {
+          // a large transfer: sampled by a warp after this pass
+          s_hv[atomicAdd(&s_nhv, 1)] = (int16_t)i;
           continue;
         }
         int moved[C];
@@ -1724,7 +2255,7 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
         if (k > 0) {
           WordStream ws;
           const uint4 f = s_w[i];
-          ws.init_with_first(seed, s_idx[i], rep, U4{f.x, f.y, f.z, f.w});
+          ws.init_with_first(seed, s_idx[i], a.rep0 + rep, U4{f.x, f.y, f.z, f.w});
           for (long long d = 0; d < k; ++d) {
             uint32_t x = ws.below((uint32_t)(total - d));
             bool taken = false;
@@ -1757,6 +2288,44 @@ k_events_e2(const SgTables tb, const EvArgs a, const int64_t *__restrict__ wave_
       }
       stop = __syncthreads_or(bad);
       if (stop) break;
+      const int nhv = s_nhv;  // the same in every thread (read after the barrier)
+      if (nhv > 0) {
+        __syncthreads();  // every thread has read the count
+        if (threadIdx.x == 0) s_nhv = 0;
+        // the wave's large transfers, one warp each: no other event of the
+        // wave touches their source nodes, so the order does not matter
+        for (int h = warp; h < nhv; h += nwarps) {
+          const int i = s_hv[h];
+          const int src = s_node[i];
+          int *un = state + (long long)src * C;
+          const uint32_t mask = tb.Emask[s_sel[i]];
+          int cur[C];
+          long long total = 0;
+#pragma unroll
+          for (int p = 0; p < C; ++p) {
+            cur[p] = un[p];
+            if ((mask >> p) & 1u) total += cur[p];
+          }
+          const long long k = s_n[i] > 0 ? (long long)s_n[i]
+                                         : (long long)round(s_prop[i] * (double)total);
+          int moved[C];
+          urn_warp<C>(cur, mask, (uint32_t)k, (uint32_t)total, seed, s_idx[i], a.rep0 + rep,
+                      moved);
+          if (lane == 0) {
+            const int q_sh = s_shift[i];
+            int *ud = state + (long long)s_dest[i] * C;
+#pragma unroll
+            for (int p = 0; p < C; ++p)
+              if (moved[p] != 0) un[p] = cur[p] - moved[p];
+#pragma unroll
+            for (int p = 0; p < C; ++p)
+              if (moved[p] != 0) atomicAdd(ud + (q_sh >= 0 ? p + tb.Nsh[q_sh][p] : p), moved[p]);
+            ++applied;
+          }
+          __syncwarp();
+        }
+        __syncthreads();
+      }
       if (s_wave[wi + 1] <= pend) ++wi;
       else break;  // the wave continues in the next chunk
     }

@@ -143,12 +143,14 @@ static std::vector<int64_t> weighted_ranges(const std::vector<int64_t> &off, int
 }
 
 int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
-               int32_t slots, Plan *out) {
+               int32_t slots, Plan *out, int32_t rep_lo, bool shard) {
   Plan &P = *out;
   P = Plan();
   P.t0 = t0;
   P.t_end = t_end;
   P.slots = slots;
+  P.rep_lo = rep_lo;
+  P.shard = shard;
   P.n_nodes = n_nodes;
   P.days = std::max(0, t_end - t0);
   const int64_t nb = (int64_t)P.days * slots;
@@ -165,7 +167,13 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
   auto day_of = [&](int64_t e) {
     return (int32_t)std::max<int64_t>(0, (int64_t)ev.time[e] - t0 - 1);
   };
-  auto slot_of = [&](int64_t e) -> int64_t { return slots > 1 ? ev.rep[e] : 0; };
+  // a shard plans the replicates rep_lo .. rep_lo + slots - 1 of a
+  // per-replicate table (slot = replicate - rep_lo; the other replicates'
+  // events are left out); otherwise slot = replicate when slots > 1
+  auto slot_of = [&](int64_t e) -> int64_t {
+    if (shard) return (int64_t)ev.rep[e] - rep_lo;
+    return slots > 1 ? ev.rep[e] : 0;
+  };
 
   // 1. E1 events bucketed by (slot, node), E2 events by (day, slot), both
   //    stable (list order kept inside a bucket): counts, offsets, scatter.
@@ -184,8 +192,8 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     for (int64_t e = lo; e < hi; ++e) {
       if (ev.time[e] > t_end) continue;
       const int64_t s = slot_of(e);
-      if (s >= slots) {
-        bad[t] = 1;
+      if (s < 0 || s >= slots) {
+        if (!shard) bad[t] = 1;
         continue;
       }
       if (ev.type[e] == SG_EXTERNAL_TRANSFER)
@@ -239,12 +247,14 @@ int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
     for (int64_t e = lo; e < hi; ++e) {
       const int32_t time = ev.time[e];
       if (time > t_end) continue;
+      const int64_t s = slot_of(e);
+      if (s < 0 || s >= slots) continue;  // another shard's replicate
       const int32_t day = day_of(e);
       if (ev.type[e] == SG_EXTERNAL_TRANSFER)
-        e2[f2[(int64_t)day * slots + slot_of(e)]++] = e;
+        e2[f2[(int64_t)day * slots + s]++] = e;
       else
-        rec1[f1[slot_of(e) * n_nodes + ev.node[e]]++] = Rec1{e, day, day == 0 ? time : 0,
-                                                               ev.type[e]};
+        rec1[f1[s * n_nodes + ev.node[e]]++] = Rec1{e, day, day == 0 ? time : 0,
+                                                    ev.type[e]};
     }
   });
   c1.clear();

@@ -79,6 +79,8 @@ int validate_events(const SgTables &tb, const EventTable &ev, int64_t *bad);
 // additions in list order.
 struct Plan {
   int32_t t0 = 0, t_end = 0, slots = 1, days = 0, n_nodes = 0;
+  int32_t rep_lo = 0;  // a shard's first replicate (slot = replicate - rep_lo)
+  bool shard = false;
   plan_vector<int64_t> order;        // E1 part, then E2 part (EventTable indices)
   plan_vector<int32_t> e1_day;       // [n_e1] day index of each E1 event
   std::vector<int64_t> e1_node_off;  // [slots * n_nodes + 1] into order
@@ -89,8 +91,11 @@ struct Plan {
   int32_t max_waves_per_day = 0;
 };
 
+// shard: plan only the replicates rep_lo .. rep_lo + slots - 1 of a
+// per-replicate table (the others' events are left out); otherwise an
+// event whose replicate is >= slots (with slots > 1) is an argument error.
 int build_plan(const EventTable &ev, int32_t n_nodes, int32_t t0, int32_t t_end,
-               int32_t slots, Plan *out);
+               int32_t slots, Plan *out, int32_t rep_lo = 0, bool shard = false);
 
 // The device image of the planned events, in plan order: type, shift (-1
 // for none), select, node, dest, n, proportion and the list index.

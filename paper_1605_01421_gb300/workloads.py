@@ -646,6 +646,19 @@ def config_batched(n_rep=256, n_nodes=5000, days=365, gen_seed=1004, seed=42,
     return w
 
 
+def replicate_range(w, rep0, n):
+    """The shard of workload w that holds its replicates rep0 .. rep0 + n - 1:
+    their initial states; the event table stays the whole job's (each event
+    keeps its replicate and list index, which key its random stream).  Run it
+    with the model's replicate range set to (rep0, w.n_rep)."""
+    if not (0 <= rep0 and n >= 1 and rep0 + n <= w.n_rep):
+        raise ValueError(f"replicates {rep0}..{rep0 + n - 1} outside 0..{w.n_rep - 1}")
+    out = Workload(**{**w.__dict__, "u0": w.u0[rep0:rep0 + n].copy(),
+                      "v0": w.v0[rep0:rep0 + n].copy(), "n_rep": n,
+                      "meta": {**w.meta, "rep0": rep0, "rep_total": w.n_rep}})
+    return out
+
+
 def config_endemic(n_nodes=100_000, days=365, gen_seed=1005, seed=42):
     """SISe3 without events on large endemic herds: herd sizes log-uniform
     in [200, 2000], 40% of each age class infected, phi at its equilibrium

@@ -211,3 +211,54 @@ def test_full_size_batched_on_sampled_replicates(orc, gpu):
         np.add.at(delta, (ev["rep"][sel], ev["time"][sel]), sign * ev["n"][sel].astype(np.int64))
     expected = w.u0.sum(axis=(1, 2)).astype(np.int64)[:, None] + np.cumsum(delta, axis=1)
     assert np.array_equal(prev[:, :, 1], expected)
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_replicate_shards_reproduce_the_whole_job(orc, gpu, solver):
+    # a job of 6 replicates with their own events, run whole and as shards
+    # 0..1, 2..4, 5..5 (global replicate index in every stream, the whole
+    # job's event table given to every shard): every shard's U and V equal
+    # the whole run's rows bit for bit, and the middle shard equals the
+    # oracle's run of those replicates
+    import torch
+    w = W.config_batched(n_rep=6, n_nodes=300, days=40, gen_seed=77)
+    w.solver = solver
+    U_all, V_all, st_all = gpu.simulate(w)
+    for rep0, n in ((0, 2), (2, 3), (5, 1)):
+        s = W.replicate_range(w, rep0, n)
+        m = gpu.Model(s)
+        m.set_replicate_range(rep0, w.n_rep)
+        M = len(s.tspan)
+        u0 = torch.as_tensor(np.ascontiguousarray(s.u0), device="cuda")
+        v0 = torch.as_tensor(np.ascontiguousarray(s.v0), device="cuda")
+        U = torch.empty((n, M, s.n_nodes, 6), dtype=torch.int32, device="cuda")
+        V = torch.empty((n, M, s.n_nodes, 1), dtype=torch.float64, device="cuda")
+        rc, st, er = m.run(s.tspan, s.seed, n, u0, v0, U, V)
+        m.close()
+        assert np.array_equal(U.cpu().numpy(), U_all[rep0:rep0 + n])
+        assert np.array_equal(V.cpu().numpy().view(np.uint64),
+                              V_all[rep0:rep0 + n].view(np.uint64))
+        if rep0 == 2:
+            code, Uo, Vo, Ro, err = orc.run(w, rep0=rep0, n_rep=n)
+            assert code == 0
+            assert np.array_equal(Uo, U.cpu().numpy())
+            assert st["reactions"] == int(Ro.sum())
+
+
+def test_replicate_range_arguments(gpu):
+    w = W.config_batched(n_rep=4, n_nodes=50, days=5, gen_seed=78)
+    s = W.replicate_range(w, 1, 2)
+    m = gpu.Model(s)
+    with pytest.raises(gpu.SimInfError):
+        m.set_replicate_range(4, 4)  # rep0 beyond the job
+    with pytest.raises(gpu.SimInfError):
+        m.set_replicate_range(1, 0)  # an offset without a job size
+    m.set_replicate_range(3, 4)  # 3 + 2 replicates > 4: rejected by the run
+    import torch
+    u0 = torch.as_tensor(np.ascontiguousarray(s.u0), device="cuda")
+    v0 = torch.as_tensor(np.ascontiguousarray(s.v0), device="cuda")
+    U = torch.empty((2, len(s.tspan), 50, 6), dtype=torch.int32, device="cuda")
+    V = torch.empty((2, len(s.tspan), 50, 1), dtype=torch.float64, device="cuda")
+    rc, st, er = m.run(s.tspan, s.seed, 2, u0, v0, U, V, check=False)
+    assert rc == -1
+    m.close()

@@ -398,3 +398,35 @@ def test_empty_model(orc, gpu):
     assert code == 0 and U0.shape == (1, 5, 0, 3)
     U1, V1, st = gpu.simulate(w)
     assert U1.shape == (1, 5, 0, 3) and st["reactions"] == 0
+
+
+@pytest.mark.parametrize("tuning", [(64, 2), (2000, 2)])
+def test_large_events_sampled_by_warps(orc, gpu, tuning):
+    # events that move thousands of animals are sampled by a whole warp
+    # (32 draws per round): exits, ageing internal transfers and external
+    # transfers by count and by proportion (80%, 25%, 20%) on herds of 10^4,
+    # and on two herds of about 2e9 animals, where Lemire's method rejects
+    # 2-7% of the words (2^32 mod s is large for s near 2e9), so rounds end
+    # early and the retry takes the next word; every outcome equals the
+    # oracle's sequential urn bit for bit
+    n = 40
+    big = 2_000_000_000
+    u0 = np.tile([[6000, 2000, 5000, 1000, 9000, 3000]], (n, 1)).astype(np.int32)
+    u0[0] = [big, 100_000_000, 10, 0, 10, 0]
+    u0[1] = [big, 0, 0, 0, 0, 0]
+    rows = []
+    for t in range(1, 6):
+        rows.append((EXIT, t, 0, 0, 4000 + t, 0.0, 3, -1))          # 4,000 draws at s ~ 2.1e9
+        rows.append((EXTERNAL, t, 1, 2 + t, 3000, 0.0, 0, -1))       # 3,000 draws at s ~ 2e9
+        for i in range(2, n):
+            rows.append((EXIT, t, i, 0, 0, 0.25, 3 + (i % 3), -1))
+            rows.append((INTERNAL, t, i, 0, 0, 0.8, 3 + (i % 2), i % 2))
+            rows.append((EXTERNAL, t, i, (i + 7) % n, 0, 0.2, 3 + (i % 3), -1))
+            rows.append((EXTERNAL, t, i, (i + 3) % n, 40 + i, 0.0, 5, -1))
+    gd = W.sise3_gdata(upsilons=(0.0,) * 3, gammas=(0.0,) * 3, alpha=0.0, betas=(0.0,) * 4)
+    w = W.plain_model(W.SISE3, u0, np.arange(0, 7), gd, seed=99, events=W.make_events(rows))
+    code, U0, V0, R0, err = orc.run(w)
+    assert code == 0, err
+    U1, V1, st = gpu.simulate(w, tuning=tuning)
+    assert np.array_equal(U0, U1)
+    assert st["events_applied"] == len(rows)
