@@ -325,7 +325,7 @@ int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 /* Autotuner: for each of nodes_per_block in {4, 8, 16, 32, 64, 128} x
  * heavy_after in {0, 1, 2, 4, 8}, and, where the sparse-activity schedule
  * applies, nodes_per_block = the pairs spread over 1, 2 or 4 blocks per SM
- * and 1,024 (when above 128) x heavy_after in {2, 8, 32}, runs the given
+ * and 1,024 (when above 128) x heavy_after in {2, 8, 32, 128}, runs the given
  * workload (arguments as sg_run) once untimed (capturing its graph when
  * graphs are on) and twice timed, keeps the setting with the fastest timed
  * run in the model and reports it and its time (outputs may be NULL).  U and

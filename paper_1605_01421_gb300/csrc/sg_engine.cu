@@ -360,6 +360,12 @@ struct sg_model {
   int32_t rep0 = 0, rep_total = 0;
   // working memory
   DevBuf<int32_t> e1_cur;
+  DevBuf<int32_t> e1_next;  // sparse schedule: day of each unit's next E1 event
+  // the external transfers of a replicate-day touch a sizeable share of its
+  // nodes (on average at least one node in 16 as a source): the E2 kernel
+  // then stages the replicate's state in shared memory, else it works on
+  // the state in device memory (L2)
+  bool e2_dense = true;
   DevBuf<int> u;
   DevBuf<double> v;
   DevBuf<int32_t> rec;
@@ -607,6 +613,7 @@ extern "C" void sg_model_destroy(sg_model *m) {
   m->ldata.release();
   m->ev_arena.release();
   m->e1_cur.release();
+  m->e1_next.release();
   m->u.release(); m->v.release(); m->rec.release(); m->err.release(); m->cnt.release();
   m->hu0.release(); m->hU.release(); m->hv0.release(); m->hV.release();
   m->emu_feat.release(); m->emu_ha.release(); m->emu_hb.release();
@@ -921,7 +928,7 @@ template <int KIND>
 static void launch_e2(sg_model *m, const EvArgs &ea, long long wb, long long we, int day,
                       int slots, int n_rep, cudaStream_t st) {
   const size_t bytes = sizeof(int) * (size_t)m->tb.n_nodes * ModelTraits<KIND>::C;
-  if (bytes <= kE2SmemStateMax) {
+  if (bytes <= kE2SmemStateMax && m->e2_dense) {
     static unsigned long long attr_set = 0;  // one bit per device
     int dev = 0;
     cudaGetDevice(&dev);
@@ -942,7 +949,7 @@ static void launch_e2_kind(sg_model *m, const EvArgs &ea, long long wb, long lon
                            int slots, int n_rep, cudaStream_t st) {
   if (m->tb.kind == SG_GENERIC) {
     const size_t bytes = sizeof(int) * (size_t)m->tb.n_nodes * m->tb.n_comp;
-    const bool in_smem = bytes <= kE2SmemStateMax;
+    const bool in_smem = bytes <= kE2SmemStateMax && m->e2_dense;
     cudaKernel_t k = m->jit.k[in_smem ? JitKernels::kE2Smem : JitKernels::kE2];
     if (in_smem)
       cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -990,6 +997,14 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
   cudaMemsetAsync(m->err.p, 0, sizeof(SgDevError), st);
   cudaMemsetAsync(m->cnt.p, 0, sizeof(SgCounters), st);
   cudaMemsetAsync(m->e1_cur.p, 0, sizeof(int32_t) * (size_t)std::max(1, Nn * n_rep), st);
+  if (da0.npb > kDayBlock && da0.ev.e1_node_off && Nn > 0) {
+    // the sparse schedule's per-unit day of the next E1 event
+    const long long units = (long long)Nn * n_rep;
+    const unsigned g = (unsigned)std::min<long long>(4096, (units + 255) / 256);
+    k_e1_next_init<<<std::max(1u, g), 256, 0, st>>>(da0.ev.e1_node_off, da0.ev.e1_day, Nn,
+                                                     n_rep, da0.slots, m->e1_next.p);
+    ++launches;
+  }
   cudaMemsetAsync(m->e2_done.p, 0, sizeof(int32_t) * (size_t)n_rep, st);
   if (Nn > 0) {
     const long long nthreads = per_rep_u * n_rep + per_rep_v * n_rep;
@@ -1345,11 +1360,13 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   const double plan_ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
   const Plan &P = m->plan;
+  m->e2_dense = days > 0 && P.n_e2 * 16 >= (long long)days * slots * Nn;
 
   const long long per_rep_u = (long long)Nn * C, per_rep_v = (long long)Nn * NV;
   if ((rc = m->u.ensure((size_t)(per_rep_u * n_rep))) ||
       (rc = m->v.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))) ||
       (rc = m->e1_cur.ensure((size_t)std::max(1, Nn * n_rep))) ||
+      (rc = m->e1_next.ensure((size_t)std::max(1, Nn * n_rep))) ||
       (rc = m->rec.ensure((size_t)days + 1)))
     return rc;
   if (tb.kind == SG_SISE_SP && (rc = m->v2.ensure((size_t)std::max<long long>(1, per_rep_v * n_rep))))
@@ -1418,6 +1435,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.V = d_V;
   da.rec = m->rec.p;
   da.e1_cur = m->e1_cur.p;
+  da.e1_next = m->e1_next.p;
   da.ev = evd;
   da.t0 = t0;
   da.M = n_tspan;
@@ -1501,6 +1519,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
                      (m->plan_version * 1000003ull + (m->emu_on ? m->emu_version + 1 : 0)) *
                              1000033ull +
                          m->nb_version * 7ull + (uint64_t)(uintptr_t)m->v2.p +
+                         ((uint64_t)(uintptr_t)m->e1_next.p << 7) +
                          m->out_version * 0x100000001b3ull +
                          ((uint64_t)(uintptr_t)m->e2_done.p << 3) + (m->fuse_e2 ? 5 : 0) +
                          ((uint64_t)(uintptr_t)m->grid_bar.p << 5) + (m->persistent ? 11 : 0) +
@@ -1962,7 +1981,7 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
                            (k == SG_SIR || k == SG_SIS || k == SG_SISE || k == SG_SISE3);
     if (!sparse_ok) sp.clear();
     for (int32_t npb : sp)
-      for (int32_t h : {2, 8, 32}) cand.emplace_back(npb, h);
+      for (int32_t h : {2, 8, 32, 128}) cand.emplace_back(npb, h);
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -153,6 +153,7 @@ struct DayArgs {
   double *V;           // [R][M][Nn][NV]
   const int32_t *rec;  // [days + 1]: tspan slot of T = t0 + i, or -1
   int32_t *e1_cur;     // [R][Nn]: next E1 event, relative to the node's list
+  int32_t *e1_next;    // [R][Nn]: day index of that event (sparse schedule)
   EvDev ev;
   int32_t t0, M, n_rep, slots;
   // global index of the run's replicate 0 (a shard of a larger job): every
@@ -445,6 +446,37 @@ __device__ __forceinline__ int ssa_thread(int *u, double *w, const double *kf, d
     ++fired;
     if (rc) return rc;
   }
+}
+
+// One iteration of ssa_thread's loop (one draw of the direct method,
+// Appendix A): returns SSA_STEP_FIRED (a transition fired, t and u moved on),
+// SSA_DONE (lambda = 0 or the next event falls at or after Tn),
+// SSA_HEAVY (hand_off set and a draw is due: state unchanged, for a warp) or
+// an error.  The same operations in the same order as ssa_thread.
+enum { SSA_STEP_FIRED = 2 };
+template <int KIND>
+__device__ __forceinline__ int ssa_step(int *u, double *w, const double *kf, double &t,
+                                        uint32_t &c, long long Tkey, uint32_t node, uint32_t Td,
+                                        uint32_t tag, uint32_t k0, uint32_t k1, bool hand_off,
+                                        const SgTables &tb, unsigned long long &fired) {
+  using M = ModelTraits<KIND>;
+  double lam = w[0];
+#pragma unroll
+  for (int j = 1; j < M::T; ++j) lam = lam + w[j];
+  if (!gt0(lam)) return SSA_DONE;
+  if (c >= SG_MAX_DRAWS) return SG_ERR_STEP_LIMIT;
+  if (hand_off) return SSA_HEAVY;
+  const U4 x = philox10(U4{c, node, Td, tag}, k0, k1);
+  ++c;
+  const double r1 = u01_open(x.x, x.y);
+  const double r2 = u01_open(x.z, x.w);
+  const double tau = -log_pos(r1) / lam;
+  const double tt = t + tau;
+  if (order_key(tt) >= Tkey) return SSA_DONE;
+  t = tt;
+  const int rc = fire<KIND>(u, w, lam * r2, kf, tb);
+  ++fired;
+  return rc ? rc : SSA_STEP_FIRED;
 }
 
 // A node handed from its thread to a warp.
@@ -1824,6 +1856,23 @@ __device__ __forceinline__ int sparse_finish(int Tf, const int *u, double *v, bo
   return code;
 }
 
+// (replicate, node) of a unit index, advanced by a stride without dividing
+// (the passes over a block's units step by kSparseBlock).
+struct UnitPos {
+  int rep, node;
+  __device__ __forceinline__ void set(long long gid, int Nn) {
+    rep = (int)(gid / Nn);
+    node = (int)(gid - (long long)rep * Nn);
+  }
+  __device__ __forceinline__ void advance(int by, int Nn) {
+    node += by;
+    while (node >= Nn) {
+      node -= Nn;
+      ++rep;
+    }
+  }
+};
+
 template <int KIND>
 __global__ void __launch_bounds__(kSparseBlock)
 k_days_sparse(const SgTables tb, const DayArgs a) {
@@ -1831,15 +1880,18 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
   __shared__ int32_t s_act[kSparseChunk];
   __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
-  __shared__ int s_nact, s_nheavy, s_stop;
+  __shared__ int s_nact, s_nheavy, s_stop, s_next;
   pdl_trigger();
   const int Nn = tb.n_nodes;
   const long long total = (long long)Nn * a.n_rep;
   const long long g0 = (long long)blockIdx.x * a.npb;
   const int nub = (int)max(0LL, min((long long)a.npb, total - g0));
-  const int tid = threadIdx.x, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const bool quiet = a.quiet != 0;
   const uint32_t k0 = a.k0, k1 = a.k1;
+  // a unit whose expected transitions in the day (lambda times one day) reach
+  // this goes to a warp at once
+  const double heavy_rate = (double)max(a.heavy_after, 1);
   unsigned long long fired = 0, drawn = 0, applied = 0;
   pdl_wait();
   if (a.finish_first && a.T_begin >= a.T_end &&
@@ -1847,7 +1899,9 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
     // a launch that only finishes unit time T_begin - 1 (the run's last
     // step after its external transfers)
     const int Tf = a.T_begin - 1;
-    for (int i0 = 0; i0 < nub; i0 += kSparseBlock) {
+    UnitPos pos;
+    pos.set(g0 + tid, Nn);
+    for (int i0 = 0; i0 < nub; i0 += kSparseBlock, pos.advance(kSparseBlock, Nn)) {
       const int i = i0 + tid;
       const bool in = i < nub;
       const long long gid = g0 + i;
@@ -1858,8 +1912,8 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
 #pragma unroll
       for (int p = 0; p < C; ++p) u[p] = 0;
       if (in) {
-        rep = (int)(gid / Nn);
-        node = (int)(gid - (long long)rep * Nn);
+        rep = pos.rep;
+        node = pos.node;
 #pragma unroll
         for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
 #pragma unroll
@@ -1886,110 +1940,204 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
       if (tid == 0) {
         s_nact = 0;
         s_nheavy = 0;
+        s_next = 0;
       }
       __syncthreads();
       // 1. every unit of the chunk: finish of Td - 1 (launch start only),
-      //    quiescence test, rates, list of the units with lambda > 0
-      for (int i0 = 0; i0 < cn; i0 += kSparseBlock) {
-        const int i = i0 + tid;
-        const bool in = i < cn;
-        const long long gid = g0 + c0 + i;
+      //    quiescence test, rates; units with lambda > 0 go to the thread
+      //    list, or, expecting heavy_after transitions or more, straight to
+      //    a warp slot.  The next unit's loads are issued before this one is
+      //    processed, so that their latencies overlap.
+      {
+        int un[C];
+        double vn[NV > 0 ? NV : 1];
+        vn[0] = 0.0;
+#pragma unroll
+        for (int p = 0; p < C; ++p) un[p] = 0;
+        if (tid < cn) {
+          const long long gid = g0 + c0 + tid;
+#pragma unroll
+          for (int p = 0; p < C; ++p) un[p] = a.u[gid * C + p];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) vn[q] = a.v[gid * NV + q];
+        }
+        UnitPos pos;
+        pos.set(g0 + c0 + tid, Nn);
+#pragma unroll 1
+        for (int i0 = 0; i0 < cn; i0 += kSparseBlock, pos.advance(kSparseBlock, Nn)) {
+          const int i = i0 + tid;
+          const bool in = i < cn;
+          const long long gid = g0 + c0 + i;
+          int u[C];
+          double v[NV > 0 ? NV : 1];
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = un[p];
+#pragma unroll
+          for (int q = 0; q < (NV > 0 ? NV : 1); ++q) v[q] = vn[q];
+          if (i + kSparseBlock < cn) {
+#pragma unroll
+            for (int p = 0; p < C; ++p) un[p] = a.u[(gid + kSparseBlock) * C + p];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vn[q] = a.v[(gid + kSparseBlock) * NV + q];
+          }
+          int rep = 0, node = 0, code = 0;
+          if (in) {
+            rep = pos.rep;
+            node = pos.node;
+            if (fin_prev)
+              code = sparse_finish<KIND>(Td - 1, u, v, quiet, tb, a, rep, node, gid);
+            if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
+              double kf[NK], w[T];
+              M::prepare(v, tb.gdata, kf);
+              bool bad = false;
+#pragma unroll
+              for (int j = 0; j < T; ++j) {
+                w[j] = M::rate_k(j, u, kf, tb.gdata);
+                bad = bad || bad_rate(w[j]);
+              }
+              double lam = w[0];
+#pragma unroll
+              for (int j = 1; j < T; ++j) lam = lam + w[j];
+              if (bad) {
+                report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
+              } else if (gt0(lam)) {
+                int slot = kSparseHeavy;
+                if (!(lam < heavy_rate)) slot = atomicAdd(&s_nheavy, 1);
+                if (slot < kSparseHeavy) {
+                  HeavySlot<C, NK> &hs = s_heavy[slot];
+                  hs.t = (double)(Td - 1);
+#pragma unroll
+                  for (int q = 0; q < NK; ++q) hs.kf[q] = kf[q];
+                  hs.c = 0;
+                  hs.node = node;
+                  hs.rep = a.rep0 + rep;
+                  hs.code = c0 + i;  // the unit, until the warp reports
+#pragma unroll
+                  for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+                } else {
+                  s_act[atomicAdd(&s_nact, 1)] = c0 + i;
+                }
+              }
+            }
+          }
+          if (fin_prev && a.out.prev) {
+            const int m = a.rec[Td - 1 - a.t0];
+            if (m >= 0)
+              prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+          }
+        }
+      }
+      __syncthreads();
+      // 2. the thread list on the first list_warps warps (about two units
+      //    per lane), with lane refill: every round each busy lane takes one
+      //    draw of its unit, and a lane whose unit is done (or handed to a
+      //    warp slot after heavy_after draws) takes the next unit of the
+      //    list, so that the warps' lanes stay busy while the list lasts;
+      //    meanwhile the other warps run the warp slots filled in pass 1
+      const int na = s_nact;
+      const int n_direct = min(s_nheavy, kSparseHeavy);
+      const int list_warps = min(nwarps, (na + 63) >> 6);
+      if (warp >= list_warps) {
+        for (int h = warp - list_warps; h < n_direct; h += nwarps - list_warps) {
+          HeavySlot<C, NK> &hs = s_heavy[h];
+          const long long gid = g0 + hs.code;
+          __syncwarp();
+          ssa_warp<KIND>(hs, Tn, (uint32_t)Td, k0, k1, tb, fired, drawn);
+          if (lane == 0) {
+            if (hs.code) report(a.err, hs.code, hs.rep, hs.node, Td, -1);
+#pragma unroll
+            for (int p = 0; p < C; ++p) a.u[gid * C + p] = hs.u[p];
+          }
+          __syncwarp();
+        }
+      } else {
+        const long long Tkey = order_key(Tn);
+        bool busy = false, drained = false;
+        long long gid = 0;
+        int rep = 0, node = 0, nb = 0;
+        uint32_t tag = 0, c = 0;
         int u[C];
-        double v[NV > 0 ? NV : 1];
-        int rep = 0, node = 0, code = 0;
-        v[0] = 0.0;
+        double kf[NK], w[T];
+        double t = 0.0;
 #pragma unroll
         for (int p = 0; p < C; ++p) u[p] = 0;
-        if (in) {
-          rep = (int)(gid / Nn);
-          node = (int)(gid - (long long)rep * Nn);
 #pragma unroll
-          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+        for (int q = 0; q < NK; ++q) kf[q] = 0.0;
 #pragma unroll
-          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
-          if (fin_prev) code = sparse_finish<KIND>(Td - 1, u, v, quiet, tb, a, rep, node, gid);
-          if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
-            double kf[NK], w[T];
-            M::prepare(v, tb.gdata, kf);
-            bool bad = false;
+        for (int j = 0; j < T; ++j) w[j] = 0.0;
+        for (;;) {
+          if (!busy && !drained) {
+            const int i = atomicAdd(&s_next, 1);
+            if (i < na) {
+              gid = g0 + s_act[i];
+              rep = (int)(gid / Nn);
+              node = (int)(gid - (long long)rep * Nn);
+              tag = (SG_STREAM_SSA << 24) | (uint32_t)(a.rep0 + rep);
+              double v[NV > 0 ? NV : 1];
+              v[0] = 0.0;
 #pragma unroll
-            for (int j = 0; j < T; ++j) {
-              w[j] = M::rate_k(j, u, kf, tb.gdata);
-              bad = bad || bad_rate(w[j]);
-            }
-            double lam = w[0];
+              for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
 #pragma unroll
-            for (int j = 1; j < T; ++j) lam = lam + w[j];
-            if (bad) {
-              report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
-            } else if (gt0(lam)) {
-              s_act[atomicAdd(&s_nact, 1)] = c0 + i;
+              for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+              M::prepare(v, tb.gdata, kf);
+#pragma unroll
+              for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
+              t = (double)(Td - 1);
+              c = 0;
+              nb = 0;
+              busy = true;
+            } else {
+              drained = true;
             }
           }
-        }
-        if (fin_prev && a.out.prev) {
-          const int m = a.rec[Td - 1 - a.t0];
-          if (m >= 0)
-            prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
-        }
-      }
-      __syncthreads();
-      // 2. the listed units' SSA, one thread each
-      const int na = s_nact;
-      for (int i = tid; i < na; i += kSparseBlock) {
-        const long long gid = g0 + s_act[i];
-        const int rep = (int)(gid / Nn);
-        const int node = (int)(gid - (long long)rep * Nn);
-        const uint32_t tag = (SG_STREAM_SSA << 24) | (uint32_t)(a.rep0 + rep);
-        int u[C];
-        double v[NV > 0 ? NV : 1];
-        v[0] = 0.0;
-#pragma unroll
-        for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
-        double kf[NK], w[T];
-        M::prepare(v, tb.gdata, kf);
-#pragma unroll
-        for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
-        double t = (double)(Td - 1);
-        uint32_t c = 0;
-        int r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag, k0, k1,
-                                 a.heavy_after, tb, fired);
-        if (r == SSA_HEAVY) {
-          const int slot = atomicAdd(&s_nheavy, 1);
-          if (slot < kSparseHeavy) {
-            HeavySlot<C, NK> &hs = s_heavy[slot];
-            hs.t = t;
-#pragma unroll
-            for (int k = 0; k < NK; ++k) hs.kf[k] = kf[k];
-            hs.c = c;
-            hs.node = node;
-            hs.rep = a.rep0 + rep;
-            hs.code = (int32_t)(gid - g0);  // the unit, until the warp reports
-#pragma unroll
-            for (int p = 0; p < C; ++p) hs.u[p] = u[p];
-            drawn += c;
+          if (!__any_sync(0xffffffffu, busy)) break;
+          if (!busy) continue;
+          int r = ssa_step<KIND>(u, w, kf, t, c, Tkey, (uint32_t)node, (uint32_t)Td, tag, k0,
+                                 k1, nb == a.heavy_after, tb, fired);
+          if (r == SSA_STEP_FIRED) {
+            ++nb;
             continue;
           }
-          // no slot left: the thread finishes its unit itself
-          r = ssa_thread<KIND>(u, w, kf, t, c, Tn, (uint32_t)node, (uint32_t)Td, tag, k0, k1, -1,
-                               tb, fired);
-        }
-        drawn += c;
-        if (r < 0) report(a.err, r, a.rep0 + rep, node, Td, -1);
+          if (r == SSA_HEAVY) {
+            const int slot = atomicAdd(&s_nheavy, 1);
+            if (slot < kSparseHeavy) {
+              HeavySlot<C, NK> &hs = s_heavy[slot];
+              hs.t = t;
 #pragma unroll
-        for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+              for (int q = 0; q < NK; ++q) hs.kf[q] = kf[q];
+              hs.c = c;
+              hs.node = node;
+              hs.rep = a.rep0 + rep;
+              hs.code = (int32_t)(gid - g0);  // the unit, until the warp reports
+#pragma unroll
+              for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+              drawn += c;
+              busy = false;
+              continue;
+            }
+            // no slot left: this lane goes on with its unit (no hand-off)
+            nb = -(1 << 30);
+            continue;
+          }
+          // done or an error
+          drawn += c;
+          if (r < 0) report(a.err, r, a.rep0 + rep, node, Td, -1);
+#pragma unroll
+          for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+          busy = false;
+        }
       }
       __syncthreads();
-      // heavy units, one warp each
+      // the warp slots not run yet: all of them when every warp had list
+      // units, else those the thread list handed over
+      const int h0 = list_warps < nwarps ? n_direct : 0;
       const int nh = min(s_nheavy, kSparseHeavy);
-      for (int h = warp; h < nh; h += nwarps) {
+      for (int h = h0 + warp; h < nh; h += nwarps) {
         HeavySlot<C, NK> &hs = s_heavy[h];
         const long long gid = g0 + hs.code;  // the unit (ssa_warp sets the code)
         __syncwarp();
         ssa_warp<KIND>(hs, Tn, (uint32_t)Td, k0, k1, tb, fired, drawn);
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
           if (hs.code) report(a.err, hs.code, hs.rep, hs.node, Td, -1);
 #pragma unroll
           for (int p = 0; p < C; ++p) a.u[gid * C + p] = hs.u[p];
@@ -2000,53 +2148,100 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
     }
     // 3. every unit: E1 events of day Td in (time, type, list index) order,
     //    then (unless deferred to the next launch) the post time step and
-    //    recording of Td
+    //    recording of Td.  One word per unit (the day of its next E1 event)
+    //    decides whether it has events today; the next unit's loads are
+    //    issued before this one is processed.
     const bool fin = Td + 1 < a.T_end || a.finish_last;
-    for (int i0 = 0; i0 < nub; i0 += kSparseBlock) {
-      const int i = i0 + tid;
-      const bool in = i < nub;
-      const long long gid = g0 + i;
-      int u[C];
-      double v[NV > 0 ? NV : 1];
-      int rep = 0, node = 0, code = 0;
-      long long ecur = 0, eend = 0, ebase = 0;
-      bool has = false;
-      v[0] = 0.0;
+    const bool has_e1 = a.ev.e1_node_off != nullptr;
+    {
+      int nday_n = 0x7fffffff;
+      int un[C];
+      double vn[NV > 0 ? NV : 1];
+      vn[0] = 0.0;
 #pragma unroll
-      for (int p = 0; p < C; ++p) u[p] = 0;
-      if (in) {
-        rep = (int)(gid / Nn);
-        node = (int)(gid - (long long)rep * Nn);
-        if (a.ev.e1_node_off) {
-          const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
-          ebase = a.ev.e1_node_off[key];
-          eend = a.ev.e1_node_off[key + 1];
-          ecur = ebase + a.e1_cur[gid];
-          has = ecur < eend && a.ev.e1_day[ecur] == d;
-        }
-        if (has || fin) {
+      for (int p = 0; p < C; ++p) un[p] = 0;
+      if (tid < nub) {
+        if (has_e1) nday_n = a.e1_next[g0 + tid];
+        if (fin) {
 #pragma unroll
-          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+          for (int p = 0; p < C; ++p) un[p] = a.u[(g0 + tid) * C + p];
 #pragma unroll
-          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+          for (int q = 0; q < NV; ++q) vn[q] = a.v[(g0 + tid) * NV + q];
         }
       }
-      // E1 events, every lane with an event left taking its next one per
-      // round, applied in the thread or (kUrnWarp or more individuals
-      // drawn) by the whole warp; the loop is warp-uniform
-      {
-        const int grep = a.rep0 + rep;
-        const int lane = tid & 31;
-        bool pend = has;
-        while (__any_sync(0xffffffffu, pend)) {
-          E1Rec e;
-          bool heavy = false;
-          if (pend) {
-            if (ecur < eend && a.ev.e1_day[ecur] == d) {
-              e = load_e1(tb, a.ev, ecur, grep, k0, k1);
-              heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
-              if (!heavy) {
-                const int rc = apply_e1<C>(u, tb, e, grep, k0, k1);
+      UnitPos pos;
+      pos.set(g0 + tid, Nn);
+#pragma unroll 1
+      for (int i0 = 0; i0 < nub; i0 += kSparseBlock, pos.advance(kSparseBlock, Nn)) {
+        const int i = i0 + tid;
+        const bool in = i < nub;
+        const long long gid = g0 + i;
+        const int nday = nday_n;
+        int u[C];
+        double v[NV > 0 ? NV : 1];
+#pragma unroll
+        for (int p = 0; p < C; ++p) u[p] = un[p];
+#pragma unroll
+        for (int q = 0; q < (NV > 0 ? NV : 1); ++q) v[q] = vn[q];
+        if (i + kSparseBlock < nub) {
+          if (has_e1) nday_n = a.e1_next[gid + kSparseBlock];
+          if (fin) {
+#pragma unroll
+            for (int p = 0; p < C; ++p) un[p] = a.u[(gid + kSparseBlock) * C + p];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) vn[q] = a.v[(gid + kSparseBlock) * NV + q];
+          }
+        }
+        const int rep = in ? pos.rep : 0;
+        const int node = in ? pos.node : 0;
+        int code = 0;
+        const bool has = in && nday == d;
+        if (has && !fin) {
+          // only the units with events today need their counts
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+        }
+        // E1 events: every lane with an event left takes its next one per
+        // round, applied in the thread or (kUrnWarp or more individuals
+        // drawn) by the whole warp; the loop is warp-uniform
+        if (__any_sync(0xffffffffu, has)) {
+          const int grep = a.rep0 + rep;
+          long long ecur = 0, eend = 0, ebase = 0;
+          if (has) {
+            const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
+            ebase = a.ev.e1_node_off[key];
+            eend = a.ev.e1_node_off[key + 1];
+            ecur = ebase + a.e1_cur[gid];
+          }
+          bool pend = has;
+          while (__any_sync(0xffffffffu, pend)) {
+            E1Rec e;
+            bool heavy = false;
+            if (pend) {
+              if (ecur < eend && a.ev.e1_day[ecur] == d) {
+                e = load_e1(tb, a.ev, ecur, grep, k0, k1);
+                heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
+                if (!heavy) {
+                  const int rc = apply_e1<C>(u, tb, e, grep, k0, k1);
+                  if (rc) {
+                    code = rc;
+                    report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
+                    pend = false;
+                  } else {
+                    ++applied;
+                    ++ecur;
+                  }
+                }
+              } else {
+                pend = false;
+              }
+            }
+            unsigned hm = __ballot_sync(0xffffffffu, heavy);
+            while (hm) {
+              const int L = __ffs(hm) - 1;
+              hm &= hm - 1;
+              const int rc = apply_e1_warp<C>(u, tb, e, L, grep, k0, k1);
+              if (lane == L) {
                 if (rc) {
                   code = rc;
                   report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
@@ -2056,39 +2251,22 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
                   ++ecur;
                 }
               }
-            } else {
-              pend = false;
             }
           }
-          unsigned hm = __ballot_sync(0xffffffffu, heavy);
-          while (hm) {
-            const int L = __ffs(hm) - 1;
-            hm &= hm - 1;
-            const int rc = apply_e1_warp<C>(u, tb, e, L, grep, k0, k1);
-            if (lane == L) {
-              if (rc) {
-                code = rc;
-                report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
-                pend = false;
-              } else {
-                ++applied;
-                ++ecur;
-              }
-            }
-          }
-        }
-        if (has) {
+          if (has) {
 #pragma unroll
-          for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
-          a.e1_cur[gid] = (int32_t)(ecur - ebase);
+            for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+            a.e1_cur[gid] = (int32_t)(ecur - ebase);
+            a.e1_next[gid] = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
+          }
         }
-      }
-      if (in && fin && code == 0)
-        code = sparse_finish<KIND>(Td, u, v, quiet, tb, a, rep, node, gid);
-      if (fin && a.out.prev) {
-        const int m = a.rec[Td - a.t0];
-        if (m >= 0)
-          prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+        if (in && fin && code == 0)
+          code = sparse_finish<KIND>(Td, u, v, quiet, tb, a, rep, node, gid);
+        if (fin && a.out.prev) {
+          const int m = a.rec[Td - a.t0];
+          if (m >= 0)
+            prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+        }
       }
     }
     __syncthreads();
@@ -2106,6 +2284,21 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
       atomicAdd(&a.cnt->draws, drawn);
     }
     if (applied) atomicAdd(&a.cnt->events, applied);
+  }
+}
+
+// Day index of each unit's first E1 event (or 0x7fffffff), the sparse
+// schedule's per-unit test for "events today" (its E1 cursors start at 0).
+__global__ void k_e1_next_init(const int64_t *__restrict__ e1_node_off,
+                               const int32_t *__restrict__ e1_day, int Nn, int n_rep,
+                               int slots, int32_t *e1_next) {
+  const long long total = (long long)Nn * n_rep;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int rep = (int)(g / Nn), node = (int)(g - (long long)rep * Nn);
+    const long long key = (long long)(slots > 1 ? rep : 0) * Nn + node;
+    const long long b = e1_node_off[key], e = e1_node_off[key + 1];
+    e1_next[g] = b < e ? e1_day[b] : 0x7fffffff;
   }
 }
 
