@@ -208,6 +208,24 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Adds one recorded unit to the prevalence counters of `key` with its own
+// atomics (for units taken from a list, whose lanes are in no order).
+template <int C>
+__device__ __forceinline__ void prevalence_add_unit(const OutDev &o, long long key,
+                                                    const int *u) {
+  long long cs = 0, rk = 0;
+#pragma unroll
+  for (int p = 0; p < C; ++p) {
+    if ((o.cases >> p) & 1u) cs += u[p];
+    if ((o.at_risk >> p) & 1u) rk += u[p];
+  }
+  unsigned long long *q = o.prev + key * 4;
+  if (cs) atomicAdd(q, (unsigned long long)cs);
+  if (rk) atomicAdd(q + 1, (unsigned long long)rk);
+  if (cs > 0) atomicAdd(q + 2, 1ull);
+  if (rk > 0) atomicAdd(q + 3, 1ull);
+}
+
 // A grid barrier must wait for the slowest block's whole day; a wait longer
 // than this is taken as a failure (SG_ERR_TIMEOUT) instead of a hang.
 constexpr unsigned long long kGridWaitNs = 20ull * 1000 * 1000 * 1000;
@@ -1822,6 +1840,23 @@ __device__ __forceinline__ void load_ends(const DayArgs &a, const SgTables &tb, 
   for (int i = 0; i < 4; ++i) ld[i] = season_end_int(a.ldata[(long long)node * tb.n_ldata + i]);
 }
 
+// Recording of a unit whose post time step leaves it unchanged (tspan
+// slot m >= 0): dense U / V and the sparse entries.
+template <int C, int NV>
+__device__ __forceinline__ void record_unit(const DayArgs &a, int Nn, int m, int rep, int node,
+                                            const int *u, const double *v) {
+  const long long base = ((long long)rep * a.M + m) * Nn + node;
+  if (a.U) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) a.U[base * C + p] = u[p];
+  }
+  if (a.V) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) a.V[base * NV + q] = v[q];
+  }
+  record_sparse<C, NV>(a.out, m, rep, node, u, v);
+}
+
 // Post time step and recording of unit time Tf for one unit of the sparse
 // schedule (counts u, continuous state v, stored back); a quiescent unit's
 // post time step is skipped (phi stays +0).  Returns 0 or SG_ERR_PTS.
@@ -1879,8 +1914,9 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   using M = ModelTraits<KIND>;
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
   __shared__ int32_t s_act[kSparseChunk];
+  __shared__ int32_t s_nq[kSparseChunk];  // units of the chunk that are not quiescent
   __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
-  __shared__ int s_nact, s_nheavy, s_stop, s_next;
+  __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq;
   pdl_trigger();
   const int Nn = tb.n_nodes;
   const long long total = (long long)Nn * a.n_rep;
@@ -1941,89 +1977,108 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         s_nact = 0;
         s_nheavy = 0;
         s_next = 0;
+        s_nnq = 0;
       }
       __syncthreads();
-      // 1. every unit of the chunk: finish of Td - 1 (launch start only),
-      //    quiescence test, rates; units with lambda > 0 go to the thread
-      //    list, or, expecting heavy_after transitions or more, straight to
-      //    a warp slot.  The next unit's loads are issued before this one is
-      //    processed, so that their latencies overlap.
+      // 1a. every unit of the chunk, four per thread per step (their loads
+      //     issued together): a quiescent unit (no infected animal, phi ==
+      //     +0) has an empty day and, at the launch's start, only its record
+      //     of Td - 1 to write; the others are listed
+      const int m_prev = fin_prev ? a.rec[Td - 1 - a.t0] : -1;
       {
-        int un[C];
-        double vn[NV > 0 ? NV : 1];
-        vn[0] = 0.0;
-#pragma unroll
-        for (int p = 0; p < C; ++p) un[p] = 0;
-        if (tid < cn) {
-          const long long gid = g0 + c0 + tid;
-#pragma unroll
-          for (int p = 0; p < C; ++p) un[p] = a.u[gid * C + p];
-#pragma unroll
-          for (int q = 0; q < NV; ++q) vn[q] = a.v[gid * NV + q];
-        }
         UnitPos pos;
         pos.set(g0 + c0 + tid, Nn);
 #pragma unroll 1
-        for (int i0 = 0; i0 < cn; i0 += kSparseBlock, pos.advance(kSparseBlock, Nn)) {
-          const int i = i0 + tid;
-          const bool in = i < cn;
-          const long long gid = g0 + c0 + i;
-          int u[C];
-          double v[NV > 0 ? NV : 1];
+        for (int b0 = 0; b0 < cn; b0 += 4 * kSparseBlock) {
+          int uu[4][C];
+          double vv[4][NV > 0 ? NV : 1];
 #pragma unroll
-          for (int p = 0; p < C; ++p) u[p] = un[p];
+          for (int k = 0; k < 4; ++k) {
+            const int i = b0 + k * kSparseBlock + tid;
+            vv[k][0] = 0.0;
 #pragma unroll
-          for (int q = 0; q < (NV > 0 ? NV : 1); ++q) v[q] = vn[q];
-          if (i + kSparseBlock < cn) {
+            for (int p = 0; p < C; ++p) uu[k][p] = 0;
+            if (i < cn) {
+              const long long gid = g0 + c0 + i;
 #pragma unroll
-            for (int p = 0; p < C; ++p) un[p] = a.u[(gid + kSparseBlock) * C + p];
+              for (int p = 0; p < C; ++p) uu[k][p] = a.u[gid * C + p];
 #pragma unroll
-            for (int q = 0; q < NV; ++q) vn[q] = a.v[(gid + kSparseBlock) * NV + q];
-          }
-          int rep = 0, node = 0, code = 0;
-          if (in) {
-            rep = pos.rep;
-            node = pos.node;
-            if (fin_prev)
-              code = sparse_finish<KIND>(Td - 1, u, v, quiet, tb, a, rep, node, gid);
-            if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
-              double kf[NK], w[T];
-              M::prepare(v, tb.gdata, kf);
-              bool bad = false;
-#pragma unroll
-              for (int j = 0; j < T; ++j) {
-                w[j] = M::rate_k(j, u, kf, tb.gdata);
-                bad = bad || bad_rate(w[j]);
-              }
-              double lam = w[0];
-#pragma unroll
-              for (int j = 1; j < T; ++j) lam = lam + w[j];
-              if (bad) {
-                report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
-              } else if (gt0(lam)) {
-                int slot = kSparseHeavy;
-                if (!(lam < heavy_rate)) slot = atomicAdd(&s_nheavy, 1);
-                if (slot < kSparseHeavy) {
-                  HeavySlot<C, NK> &hs = s_heavy[slot];
-                  hs.t = (double)(Td - 1);
-#pragma unroll
-                  for (int q = 0; q < NK; ++q) hs.kf[q] = kf[q];
-                  hs.c = 0;
-                  hs.node = node;
-                  hs.rep = a.rep0 + rep;
-                  hs.code = c0 + i;  // the unit, until the warp reports
-#pragma unroll
-                  for (int p = 0; p < C; ++p) hs.u[p] = u[p];
-                } else {
-                  s_act[atomicAdd(&s_nact, 1)] = c0 + i;
-                }
-              }
+              for (int q = 0; q < NV; ++q) vv[k][q] = a.v[gid * NV + q];
             }
           }
-          if (fin_prev && a.out.prev) {
-            const int m = a.rec[Td - 1 - a.t0];
-            if (m >= 0)
-              prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = b0 + k * kSparseBlock + tid;
+            const bool in = i < cn;
+            const bool q0 = in && quiet && quiescent<KIND>(uu[k], vv[k]);
+            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = c0 + i;
+            if (m_prev >= 0) {
+              if (q0) record_unit<C, NV>(a, Nn, m_prev, pos.rep, pos.node, uu[k], vv[k]);
+              if (a.out.prev)
+                prevalence_add<C>(a.out, in ? (long long)pos.rep * a.M + m_prev : -1, q0,
+                                  uu[k]);
+            }
+            pos.advance(kSparseBlock, Nn);
+          }
+        }
+      }
+      __syncthreads();
+      // 1b. the listed units: finish of Td - 1 (launch start only), rates;
+      //     units with lambda > 0 go to the thread list, or, expecting
+      //     heavy_after transitions or more, straight to a warp slot
+      {
+        const int nq = s_nnq;
+#pragma unroll 1
+        for (int li = tid; li < nq; li += kSparseBlock) {
+          const int i = s_nq[li];
+          const long long gid = g0 + i;
+          const int rep = (int)(gid / Nn);
+          const int node = (int)(gid - (long long)rep * Nn);
+          int u[C];
+          double v[NV > 0 ? NV : 1];
+          v[0] = 0.0;
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+          int code = 0;
+          if (fin_prev) {
+            code = sparse_finish<KIND>(Td - 1, u, v, quiet, tb, a, rep, node, gid);
+            if (a.out.prev && m_prev >= 0 && code == 0)
+              prevalence_add_unit<C>(a.out, (long long)rep * a.M + m_prev, u);
+          }
+          if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
+            double kf[NK], w[T];
+            M::prepare(v, tb.gdata, kf);
+            bool bad = false;
+#pragma unroll
+            for (int j = 0; j < T; ++j) {
+              w[j] = M::rate_k(j, u, kf, tb.gdata);
+              bad = bad || bad_rate(w[j]);
+            }
+            double lam = w[0];
+#pragma unroll
+            for (int j = 1; j < T; ++j) lam = lam + w[j];
+            if (bad) {
+              report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
+            } else if (gt0(lam)) {
+              int slot = kSparseHeavy;
+              if (!(lam < heavy_rate)) slot = atomicAdd(&s_nheavy, 1);
+              if (slot < kSparseHeavy) {
+                HeavySlot<C, NK> &hs = s_heavy[slot];
+                hs.t = (double)(Td - 1);
+#pragma unroll
+                for (int q = 0; q < NK; ++q) hs.kf[q] = kf[q];
+                hs.c = 0;
+                hs.node = node;
+                hs.rep = a.rep0 + rep;
+                hs.code = i;  // the unit, until the warp reports
+#pragma unroll
+                for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+              } else {
+                s_act[atomicAdd(&s_nact, 1)] = i;
+              }
+            }
           }
         }
       }
@@ -2146,73 +2201,54 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
       }
       __syncthreads();
     }
-    // 3. every unit: E1 events of day Td in (time, type, list index) order,
-    //    then (unless deferred to the next launch) the post time step and
-    //    recording of Td.  One word per unit (the day of its next E1 event)
-    //    decides whether it has events today; the next unit's loads are
-    //    issued before this one is processed.
+    // 3. E1 events of day Td in (time, type, list index) order: a scan of
+    //    one word per unit (the day of its next E1 event) lists the units
+    //    with events today in shared memory (chunks of kSparseChunk units),
+    //    and the block applies the list, one unit per thread; then, unless
+    //    deferred to the next launch, the post time step and recording of
+    //    Td for every unit
     const bool fin = Td + 1 < a.T_end || a.finish_last;
-    const bool has_e1 = a.ev.e1_node_off != nullptr;
-    {
-      int nday_n = 0x7fffffff;
-      int un[C];
-      double vn[NV > 0 ? NV : 1];
-      vn[0] = 0.0;
-#pragma unroll
-      for (int p = 0; p < C; ++p) un[p] = 0;
-      if (tid < nub) {
-        if (has_e1) nday_n = a.e1_next[g0 + tid];
-        if (fin) {
-#pragma unroll
-          for (int p = 0; p < C; ++p) un[p] = a.u[(g0 + tid) * C + p];
-#pragma unroll
-          for (int q = 0; q < NV; ++q) vn[q] = a.v[(g0 + tid) * NV + q];
-        }
-      }
-      UnitPos pos;
-      pos.set(g0 + tid, Nn);
+    if (a.ev.e1_node_off != nullptr) {
+      for (int c0 = 0; c0 < nub; c0 += kSparseChunk) {
+        const int cn = min(kSparseChunk, nub - c0);
+        if (tid == 0) s_nact = 0;
+        __syncthreads();
+        int nday_n = tid < cn ? a.e1_next[g0 + c0 + tid] : 0x7fffffff;
 #pragma unroll 1
-      for (int i0 = 0; i0 < nub; i0 += kSparseBlock, pos.advance(kSparseBlock, Nn)) {
-        const int i = i0 + tid;
-        const bool in = i < nub;
-        const long long gid = g0 + i;
-        const int nday = nday_n;
-        int u[C];
-        double v[NV > 0 ? NV : 1];
-#pragma unroll
-        for (int p = 0; p < C; ++p) u[p] = un[p];
-#pragma unroll
-        for (int q = 0; q < (NV > 0 ? NV : 1); ++q) v[q] = vn[q];
-        if (i + kSparseBlock < nub) {
-          if (has_e1) nday_n = a.e1_next[gid + kSparseBlock];
-          if (fin) {
-#pragma unroll
-            for (int p = 0; p < C; ++p) un[p] = a.u[(gid + kSparseBlock) * C + p];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) vn[q] = a.v[(gid + kSparseBlock) * NV + q];
-          }
+        for (int i0 = 0; i0 < cn; i0 += kSparseBlock) {
+          const int i = i0 + tid;
+          const int nday = nday_n;
+          if (i + kSparseBlock < cn) nday_n = a.e1_next[g0 + c0 + i + kSparseBlock];
+          if (i < cn && nday == d) s_act[atomicAdd(&s_nact, 1)] = c0 + i;
         }
-        const int rep = in ? pos.rep : 0;
-        const int node = in ? pos.node : 0;
-        int code = 0;
-        const bool has = in && nday == d;
-        if (has && !fin) {
-          // only the units with events today need their counts
+        __syncthreads();
+        const int ne = s_nact;
+        // rounds of kSparseBlock list units; every thread of the block
+        // takes part in each round (the warp-uniform E1 loop)
+#pragma unroll 1
+        for (int r0 = 0; r0 < ne; r0 += kSparseBlock) {
+          const int li = r0 + tid;
+          const bool has = li < ne;
+          long long gid = 0, ecur = 0, eend = 0, ebase = 0;
+          int rep = 0, node = 0, code = 0;
+          int u[C];
 #pragma unroll
-          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
-        }
-        // E1 events: every lane with an event left takes its next one per
-        // round, applied in the thread or (kUrnWarp or more individuals
-        // drawn) by the whole warp; the loop is warp-uniform
-        if (__any_sync(0xffffffffu, has)) {
-          const int grep = a.rep0 + rep;
-          long long ecur = 0, eend = 0, ebase = 0;
+          for (int p = 0; p < C; ++p) u[p] = 0;
           if (has) {
+            gid = g0 + s_act[li];
+            rep = (int)(gid / Nn);
+            node = (int)(gid - (long long)rep * Nn);
             const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
             ebase = a.ev.e1_node_off[key];
             eend = a.ev.e1_node_off[key + 1];
             ecur = ebase + a.e1_cur[gid];
+#pragma unroll
+            for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
           }
+          const int grep = a.rep0 + rep;
+          // every lane with an event left takes its next one per round,
+          // applied in the thread or (kUrnWarp or more individuals drawn)
+          // by the whole warp
           bool pend = has;
           while (__any_sync(0xffffffffu, pend)) {
             E1Rec e;
@@ -2253,6 +2289,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
               }
             }
           }
+          (void)code;
           if (has) {
 #pragma unroll
             for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
@@ -2260,13 +2297,72 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
             a.e1_next[gid] = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
           }
         }
-        if (in && fin && code == 0)
-          code = sparse_finish<KIND>(Td, u, v, quiet, tb, a, rep, node, gid);
-        if (fin && a.out.prev) {
-          const int m = a.rec[Td - a.t0];
-          if (m >= 0)
-            prevalence_add<C>(a.out, in ? (long long)rep * a.M + m : -1, in && code == 0, u);
+        __syncthreads();
+      }
+    }
+    if (fin) {
+      // post time step and recording of Td: quiescent units are recorded
+      // by a scan (four per thread per step), the others listed (chunks of
+      // kSparseChunk units) and finished from the list
+      const int m_fin = a.rec[Td - a.t0];
+      for (int c0 = 0; c0 < nub; c0 += kSparseChunk) {
+        const int cn = min(kSparseChunk, nub - c0);
+        if (tid == 0) s_nnq = 0;
+        __syncthreads();
+        UnitPos pos;
+        pos.set(g0 + c0 + tid, Nn);
+#pragma unroll 1
+        for (int b0 = 0; b0 < cn; b0 += 4 * kSparseBlock) {
+          int uu[4][C];
+          double vv[4][NV > 0 ? NV : 1];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = b0 + k * kSparseBlock + tid;
+            vv[k][0] = 0.0;
+#pragma unroll
+            for (int p = 0; p < C; ++p) uu[k][p] = 0;
+            if (i < cn) {
+              const long long gid = g0 + c0 + i;
+#pragma unroll
+              for (int p = 0; p < C; ++p) uu[k][p] = a.u[gid * C + p];
+#pragma unroll
+              for (int q = 0; q < NV; ++q) vv[k][q] = a.v[gid * NV + q];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = b0 + k * kSparseBlock + tid;
+            const bool in = i < cn;
+            const bool q0 = in && quiet && quiescent<KIND>(uu[k], vv[k]);
+            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = c0 + i;
+            if (m_fin >= 0) {
+              if (q0) record_unit<C, NV>(a, Nn, m_fin, pos.rep, pos.node, uu[k], vv[k]);
+              if (a.out.prev)
+                prevalence_add<C>(a.out, in ? (long long)pos.rep * a.M + m_fin : -1, q0,
+                                  uu[k]);
+            }
+            pos.advance(kSparseBlock, Nn);
+          }
         }
+        __syncthreads();
+        const int nq = s_nnq;
+#pragma unroll 1
+        for (int li = tid; li < nq; li += kSparseBlock) {
+          const long long gid = g0 + s_nq[li];
+          const int rep = (int)(gid / Nn);
+          const int node = (int)(gid - (long long)rep * Nn);
+          int u[C];
+          double v[NV > 0 ? NV : 1];
+          v[0] = 0.0;
+#pragma unroll
+          for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+#pragma unroll
+          for (int q = 0; q < NV; ++q) v[q] = a.v[gid * NV + q];
+          const int code = sparse_finish<KIND>(Td, u, v, quiet, tb, a, rep, node, gid);
+          if (a.out.prev && m_fin >= 0 && code == 0)
+            prevalence_add_unit<C>(a.out, (long long)rep * a.M + m_fin, u);
+        }
+        __syncthreads();
       }
     }
     __syncthreads();
