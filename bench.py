@@ -377,7 +377,12 @@ def _fp64_roofline(w, aem, kt, fp64_fma_tflops):
     if w.kind not in table:
         return None
     per_nd, per_draw, per_fire = table[w.kind]
-    ops = (per_nd * kt["node_days"] + per_draw * kt["draws"] + per_fire * kt["reactions"])
+    # the day start's rates and the post time step count for the node-days
+    # that evaluate them (all of them on the thread-per-node schedule; the
+    # sparse-activity schedule skips quiescent node-days, whose rates are all
+    # zero and whose post time step changes nothing)
+    ops = (per_nd * kt["node_days_rated"] + per_draw * kt["draws"]
+           + per_fire * kt["reactions"])
     sec = kt["ms_ssa"] * 1e-3
     achieved = ops / sec / 1e12
     peak = fp64_fma_tflops / 2.0
@@ -389,8 +394,9 @@ def _fp64_roofline(w, aem, kt, fp64_fma_tflops):
                            f"(sg_fp64_fma_probe {fp64_fma_tflops:.4f} TFLOP/s / 2)",
             "ops_per_launch": ops / max(1, kt["launches_ssa"]),
             "ops_counted": "FP64 add, multiply, divide, conversion once each (oracle's "
-                           "definitions): per node-day / draw / transition "
-                           f"{per_nd} / {per_draw} / {per_fire}",
+                           "definitions): per node-day with its rates evaluated / draw / "
+                           f"transition {per_nd} / {per_draw} / {per_fire}",
+            "node_days_rated_fraction": kt["node_days_rated"] / max(1, kt["node_days"]),
             "avg_launch_ms": kt["ms_ssa"] / max(1, kt["launches_ssa"])}
 
 
@@ -466,7 +472,7 @@ def measure_gpu(w, args, stream, dev, steps, warmup, rep0=0, seed=None, tune=Tru
     model.set_kernel_timing(True)
     kt = {"ms_ssa": 0.0, "ms_e1": 0.0, "ms_e2": 0.0, "launches_ssa": 0,
           "launches_e1": 0, "launches_e2": 0, "draws": 0, "reactions": 0,
-          "node_days": 0}
+          "node_days": 0, "node_days_rated": 0}
     for _ in range(kps):
         flush.zero_()
         rc, st, er = step()

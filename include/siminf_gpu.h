@@ -169,6 +169,10 @@ typedef struct {
                              and uploading the events (0 when the plan of an
                              earlier run was reused)                        */
   double ms_host_total;   /* host time of the whole call                    */
+  int64_t node_days_rated;/* node-days whose transition rates were evaluated:
+                             all of them on the thread-per-node schedule, the
+                             non-quiescent ones on the sparse-activity schedule
+                             (see sg_set_tuning)                            */
 } sg_stats;
 
 /* Create a model from its tables (Sec. 3.2).  Validates the sizes against
@@ -310,7 +314,7 @@ int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total);
  * than heavy_after draws in a day is handed to one of the block's warps,
  * whose 32 lanes compute 32 draws' random numbers at once.  With
  * nodes_per_block > 128 (up to 2^22; the direct method on the built-in
- * kinds without emulator, persistent or fused schedules -- elsewhere it
+ * kinds without emulator or persistent schedule -- elsewhere it
  * means 128) the sparse-activity schedule runs instead: each block of 256
  * threads owns nodes_per_block pairs in device memory, skips the days that
  * are certainly empty (no infected animal and phi == +0, with finite model
@@ -319,7 +323,10 @@ int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total);
  * heavy_after draws to warps.  Results are identical for every setting (the
  * random stream is a function of replicate, node, day and draw index only);
  * only speed changes.  nodes_per_block <= 0 or heavy_after < 0 restore the
- * size-based defaults. */
+ * size-based defaults: the sparse-activity schedule with two blocks per SM
+ * and heavy_after 8 where it applies and the pairs exceed two full 128-pair
+ * blocks per SM, else 128 pairs per block (fewer for small problems, so
+ * that about two blocks per SM exist) and heavy_after 2. */
 int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 
 /* Autotuner: for each of nodes_per_block in {4, 8, 16, 32, 64, 128} x

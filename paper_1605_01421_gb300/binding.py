@@ -158,7 +158,8 @@ class Stats(ctypes.Structure):
                 ("ms_e2", ctypes.c_double), ("launches_ssa", ctypes.c_int64),
                 ("launches_e1", ctypes.c_int64), ("launches_e2", ctypes.c_int64),
                 ("ms_mlp", ctypes.c_double), ("launches_mlp", ctypes.c_int64),
-                ("ms_host_plan", ctypes.c_double), ("ms_host_total", ctypes.c_double)]
+                ("ms_host_plan", ctypes.c_double), ("ms_host_total", ctypes.c_double),
+                ("node_days_rated", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

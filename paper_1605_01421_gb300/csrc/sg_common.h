@@ -52,4 +52,5 @@ struct SgCounters {
   unsigned long long reactions;
   unsigned long long draws;
   unsigned long long events;
+  unsigned long long rated;  // node-days whose rates were evaluated (sparse schedule)
 };

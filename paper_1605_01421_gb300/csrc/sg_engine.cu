@@ -1447,10 +1447,25 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   // the sparse-activity schedule (nodes_per_block > kDayBlock) is for the
   // direct method on the built-in kinds with the day / E2 kernel pair;
   // elsewhere such a split falls back to full thread-per-node blocks
-  const bool sparse_ok = !aem && !m->emu_on && !m->fuse_e2 && !m->persistent &&
+  const bool sparse_ok = !aem && !m->emu_on && !m->persistent &&
                          (tb.kind == SG_SIR || tb.kind == SG_SIS || tb.kind == SG_SISE ||
                           tb.kind == SG_SISE3);
   if (da.npb > kDayBlock && !sparse_ok) da.npb = kDayBlock;
+  if (m->npb <= 0 && sparse_ok) {
+    // untuned: more units than two full thread-per-node blocks per SM take
+    // the sparse-activity schedule, two blocks per SM
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      sms = 152;
+    }
+    const long long units = (long long)Nn * n_rep;
+    if (units > 2LL * kDayBlock * sms) {
+      da.npb = (int32_t)((units + 2LL * sms - 1) / (2LL * sms));
+      if (m->heavy_after < 0) da.heavy_after = 8;
+    }
+  }
   {
     // a unit with no infected animal and phi == +0 has an empty day only
     // when every parameter is finite (0 times inf or NaN is not 0)
@@ -1587,6 +1602,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     stats->reactions = (int64_t)m->h_cnt->reactions;
     stats->events_applied = (int64_t)m->h_cnt->events;
     stats->node_days = (int64_t)Nn * n_rep * days;
+    // the sparse schedule evaluates the rates of non-quiescent node-days only
+    stats->node_days_rated =
+        da.npb > kDayBlock ? (int64_t)m->h_cnt->rated : stats->node_days;
     stats->kernel_launches = launches;
     stats->e2_waves = waves;
     stats->days = days;
@@ -1922,6 +1940,7 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
     stats->reactions = (int64_t)h_cnt.reactions;
     stats->draws = (int64_t)h_cnt.draws;
     stats->node_days = (int64_t)Nn * n_rep * days;
+    stats->node_days_rated = stats->node_days;
     stats->kernel_launches = launches;
     stats->days = days;
   }
@@ -1976,8 +1995,7 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
     }
     if (units > 2LL * kDayBlock * sms) sp.push_back(1024);
     const int k = m->tb.kind;
-    const bool sparse_ok = m->solver != SG_SOLVER_AEM && !m->emu_on && !m->fuse_e2 &&
-                           !m->persistent &&
+    const bool sparse_ok = m->solver != SG_SOLVER_AEM && !m->emu_on && !m->persistent &&
                            (k == SG_SIR || k == SG_SIS || k == SG_SISE || k == SG_SISE3);
     if (!sparse_ok) sp.clear();
     for (int32_t npb : sp)

@@ -1816,7 +1816,7 @@ k_days(const SgTables tb, const DayArgs a) {
 // thread-per-node schedule, so the results are identical.
 // ---------------------------------------------------------------------------
 constexpr int kSparseBlock = 256;   // threads of the sparse-schedule day kernel
-constexpr int kSparseChunk = 4096;  // units per pass through the active list
+constexpr int kSparseChunk = 8192;  // units per pass through the active list
 constexpr int kSparseHeavy = 64;    // warp hand-off slots per pass
 
 // A unit whose day is certainly empty: no infected animal and phi == +0
@@ -1913,8 +1913,9 @@ __global__ void __launch_bounds__(kSparseBlock)
 k_days_sparse(const SgTables tb, const DayArgs a) {
   using M = ModelTraits<KIND>;
   constexpr int C = M::C, T = M::T, NV = M::NV, NK = M::NK;
-  __shared__ int32_t s_act[kSparseChunk];
-  __shared__ int32_t s_nq[kSparseChunk];  // units of the chunk that are not quiescent
+  // lists of units of the current chunk (indices relative to the chunk)
+  __shared__ uint16_t s_act[kSparseChunk];
+  __shared__ uint16_t s_nq[kSparseChunk];  // units of the chunk that are not quiescent
   __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
   __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq;
   pdl_trigger();
@@ -1925,6 +1926,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const bool quiet = a.quiet != 0;
   const uint32_t k0 = a.k0, k1 = a.k1;
+  unsigned long long rated = 0;  // units whose rates this thread evaluated
   // a unit whose expected transitions in the day (lambda times one day) reach
   // this goes to a warp at once
   const double heavy_rate = (double)max(a.heavy_after, 1);
@@ -2011,7 +2013,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
             const int i = b0 + k * kSparseBlock + tid;
             const bool in = i < cn;
             const bool q0 = in && quiet && quiescent<KIND>(uu[k], vv[k]);
-            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = c0 + i;
+            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = (uint16_t)i;
             if (m_prev >= 0) {
               if (q0) record_unit<C, NV>(a, Nn, m_prev, pos.rep, pos.node, uu[k], vv[k]);
               if (a.out.prev)
@@ -2030,7 +2032,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         const int nq = s_nnq;
 #pragma unroll 1
         for (int li = tid; li < nq; li += kSparseBlock) {
-          const int i = s_nq[li];
+          const int i = c0 + s_nq[li];  // block-relative
           const long long gid = g0 + i;
           const int rep = (int)(gid / Nn);
           const int node = (int)(gid - (long long)rep * Nn);
@@ -2048,6 +2050,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
               prevalence_add_unit<C>(a.out, (long long)rep * a.M + m_prev, u);
           }
           if (code == 0 && !(quiet && quiescent<KIND>(u, v))) {
+            ++rated;
             double kf[NK], w[T];
             M::prepare(v, tb.gdata, kf);
             bool bad = false;
@@ -2076,7 +2079,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
 #pragma unroll
                 for (int p = 0; p < C; ++p) hs.u[p] = u[p];
               } else {
-                s_act[atomicAdd(&s_nact, 1)] = i;
+                s_act[atomicAdd(&s_nact, 1)] = (uint16_t)(i - c0);
               }
             }
           }
@@ -2124,7 +2127,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
           if (!busy && !drained) {
             const int i = atomicAdd(&s_next, 1);
             if (i < na) {
-              gid = g0 + s_act[i];
+              gid = g0 + c0 + s_act[i];
               rep = (int)(gid / Nn);
               node = (int)(gid - (long long)rep * Nn);
               tag = (SG_STREAM_SSA << 24) | (uint32_t)(a.rep0 + rep);
@@ -2213,13 +2216,17 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         const int cn = min(kSparseChunk, nub - c0);
         if (tid == 0) s_nact = 0;
         __syncthreads();
-        int nday_n = tid < cn ? a.e1_next[g0 + c0 + tid] : 0x7fffffff;
 #pragma unroll 1
-        for (int i0 = 0; i0 < cn; i0 += kSparseBlock) {
-          const int i = i0 + tid;
-          const int nday = nday_n;
-          if (i + kSparseBlock < cn) nday_n = a.e1_next[g0 + c0 + i + kSparseBlock];
-          if (i < cn && nday == d) s_act[atomicAdd(&s_nact, 1)] = c0 + i;
+        for (int b0 = 0; b0 < cn; b0 += 4 * kSparseBlock) {
+          int nday[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int i = b0 + k * kSparseBlock + tid;
+            nday[k] = i < cn ? a.e1_next[g0 + c0 + i] : 0x7fffffff;
+          }
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (nday[k] == d) s_act[atomicAdd(&s_nact, 1)] = (uint16_t)(b0 + k * kSparseBlock + tid);
         }
         __syncthreads();
         const int ne = s_nact;
@@ -2235,7 +2242,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
 #pragma unroll
           for (int p = 0; p < C; ++p) u[p] = 0;
           if (has) {
-            gid = g0 + s_act[li];
+            gid = g0 + c0 + s_act[li];
             rep = (int)(gid / Nn);
             node = (int)(gid - (long long)rep * Nn);
             const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
@@ -2334,7 +2341,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
             const int i = b0 + k * kSparseBlock + tid;
             const bool in = i < cn;
             const bool q0 = in && quiet && quiescent<KIND>(uu[k], vv[k]);
-            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = c0 + i;
+            if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = (uint16_t)i;
             if (m_fin >= 0) {
               if (q0) record_unit<C, NV>(a, Nn, m_fin, pos.rep, pos.node, uu[k], vv[k]);
               if (a.out.prev)
@@ -2348,7 +2355,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         const int nq = s_nnq;
 #pragma unroll 1
         for (int li = tid; li < nq; li += kSparseBlock) {
-          const long long gid = g0 + s_nq[li];
+          const long long gid = g0 + c0 + s_nq[li];
           const int rep = (int)(gid / Nn);
           const int node = (int)(gid - (long long)rep * Nn);
           int u[C];
@@ -2367,12 +2374,41 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
     }
     __syncthreads();
   }
+  if (a.e2_done) {
+    // the last block to finish a replicate's units runs its external
+    // transfers of T_end - 1 (counted per replicate, no block waits)
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    const long long g_hi = g0 + nub - 1;
+    for (int r = (int)(g0 / Nn); nub > 0 && (long long)r * Nn <= g_hi; ++r) {
+      if (tid == 0) {
+        const long long b_first = (long long)r * Nn / a.npb;
+        const long long b_last = ((long long)(r + 1) * Nn - 1) / a.npb;
+        const int old = atomicAdd(&a.e2_done[r], 1);
+        s_last = old == (int)(b_last - b_first);
+      }
+      __syncthreads();
+      if (s_last) {
+        __threadfence();
+        long long w0 = a.e2_wb, w1 = a.e2_we;
+        if (a.slots > 1) {
+          w0 = a.wave_off[(long long)a.e2_day_index * a.slots + r];
+          w1 = a.wave_off[(long long)a.e2_day_index * a.slots + r + 1];
+        }
+        e2_rep_block<C>(tb, a, r, a.T_end - 1, w0, w1);
+        if (tid == 0) a.e2_done[r] = 0;
+      }
+      __syncthreads();
+    }
+  }
   // one atomic per warp for the counters
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     fired += __shfl_down_sync(0xffffffffu, fired, off);
     drawn += __shfl_down_sync(0xffffffffu, drawn, off);
     applied += __shfl_down_sync(0xffffffffu, applied, off);
+    rated += __shfl_down_sync(0xffffffffu, rated, off);
   }
   if ((tid & 31) == 0) {
     if (drawn | fired) {
@@ -2380,6 +2416,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
       atomicAdd(&a.cnt->draws, drawn);
     }
     if (applied) atomicAdd(&a.cnt->events, applied);
+    if (rated) atomicAdd(&a.cnt->rated, rated);
   }
 }
 

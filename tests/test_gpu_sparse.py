@@ -179,9 +179,10 @@ def test_replicate_shards_on_the_sparse_schedule(orc, gpu):
     assert np.array_equal(Uo, U_all[1:3])
 
 
-def test_falls_back_where_the_schedule_does_not_apply(orc, gpu):
-    # the all events method and the fused external transfers take the
-    # thread-per-node kernel whatever the split (same results)
+def test_aem_fallback_and_fused_external_transfers(orc, gpu):
+    # the all events method takes the thread-per-node kernel whatever the
+    # split; with fused external transfers the sparse kernel's last block of
+    # each replicate runs them in its tail (same results either way)
     w = W.config_sise(n_nodes=900, days=40, gen_seed=48)
     w.solver = W.AEM
     _compare(orc, gpu, w, (2000, 2))
