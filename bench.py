@@ -369,10 +369,12 @@ def bench_reference(args):
     print(json.dumps(line))
 
 
-def _fp64_roofline(w, aem, kt, fp64_fma_tflops):
+def _fp64_roofline(w, aem, kt, fp64_fma_tflops, npb=None):
     """Algorithmic FP64 operations of the day kernel per second against the
     measured FP64 instruction rate (the FMA probe's flops / 2: one FMA lane
-    instruction = one operation here)."""
+    instruction = one operation here).  npb: the work split's nodes per
+    block (above 128 the sparse-activity kernel runs), None if the engine
+    chose it."""
     table = FP64_OPS_AEM if aem else FP64_OPS
     if w.kind not in table:
         return None
@@ -389,7 +391,12 @@ def _fp64_roofline(w, aem, kt, fp64_fma_tflops):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak,
             "kernel": ("k_days<aem> (channels + post time step + recording)" if aem
-                       else "k_days (SSA + E1 events + post time step + recording)"),
+                       else "k_days_sparse (quiescent units skipped; SSA + E1 events + "
+                            "post time step + recording)" if npb is not None and npb > 128
+                       else "k_days (SSA + E1 events + post time step + recording)"
+                       if npb is not None
+                       else "day kernel of the engine's default split (SSA + E1 events + "
+                            "post time step + recording)"),
             "peak_source": "measured: FP64 FMA lane instructions per second of this GPU "
                            f"(sg_fp64_fma_probe {fp64_fma_tflops:.4f} TFLOP/s / 2)",
             "ops_per_launch": ops / max(1, kt["launches_ssa"]),
@@ -480,7 +487,7 @@ def measure_gpu(w, args, stream, dev, steps, warmup, rep0=0, seed=None, tune=Tru
             kt[k] += st[k]
     model.set_kernel_timing(False)
     shares = {k: kt[f"ms_{k}"] for k in ("ssa", "e1", "e2")}
-    roof = _fp64_roofline(w, aem, kt, binding.fp64_fma_probe())
+    roof = _fp64_roofline(w, aem, kt, binding.fp64_fma_probe(), tuned[0] if tuned else None)
     if roof is not None:
         roof["kernel_ms_share"] = {k: v / max(1e-9, sum(shares.values()))
                                    for k, v in shares.items()}

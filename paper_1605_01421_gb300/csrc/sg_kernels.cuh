@@ -1891,6 +1891,149 @@ __device__ __forceinline__ int sparse_finish(int Tf, const int *u, double *v, bo
   return code;
 }
 
+// E1 events of day index d (unit time Td) of the unit of every lane with
+// `has`, in (time, type, list index) order, for the sparse schedule (state
+// in device memory).  Warp-uniform: all 32 lanes call it.  Every round each
+// lane with an event left takes its next one, applied in the thread or
+// (kUrnWarp or more individuals drawn) by the whole warp.  Returns the
+// lane's error code (0 if none).
+template <int C>
+__device__ __forceinline__ int sparse_e1(bool has, long long gid, int rep, int node, int Td,
+                                         int d, const SgTables &tb, const DayArgs &a,
+                                         uint32_t k0, uint32_t k1,
+                                         unsigned long long &applied) {
+  const int lane = threadIdx.x & 31;
+  const int Nn = tb.n_nodes;
+  long long ecur = 0, eend = 0, ebase = 0;
+  int code = 0;
+  int u[C];
+#pragma unroll
+  for (int p = 0; p < C; ++p) u[p] = 0;
+  if (has) {
+    const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
+    ebase = a.ev.e1_node_off[key];
+    eend = a.ev.e1_node_off[key + 1];
+    ecur = ebase + a.e1_cur[gid];
+#pragma unroll
+    for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
+  }
+  const int grep = a.rep0 + rep;
+  bool pend = has;
+  while (__any_sync(0xffffffffu, pend)) {
+    E1Rec e;
+    bool heavy = false;
+    if (pend) {
+      if (ecur < eend && a.ev.e1_day[ecur] == d) {
+        e = load_e1(tb, a.ev, ecur, grep, k0, k1);
+        heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
+        if (!heavy) {
+          const int rc = apply_e1<C>(u, tb, e, grep, k0, k1);
+          if (rc) {
+            code = rc;
+            report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
+            pend = false;
+          } else {
+            ++applied;
+            ++ecur;
+          }
+        }
+      } else {
+        pend = false;
+      }
+    }
+    unsigned hm = __ballot_sync(0xffffffffu, heavy);
+    while (hm) {
+      const int L = __ffs(hm) - 1;
+      hm &= hm - 1;
+      const int rc = apply_e1_warp<C>(u, tb, e, L, grep, k0, k1);
+      if (lane == L) {
+        if (rc) {
+          code = rc;
+          report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
+          pend = false;
+        } else {
+          ++applied;
+          ++ecur;
+        }
+      }
+    }
+  }
+  if (has) {
+#pragma unroll
+    for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
+    a.e1_cur[gid] = (int32_t)(ecur - ebase);
+    a.e1_next[gid] = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
+  }
+  return code;
+}
+
+// E1 events of day Td of the units marked in a chunk's bitmaps: units with
+// events today (e1bits) that took SSA draws (actbits) when `act`, else those
+// that did not.  A warp takes 32 words (1,024 units) at a time from *take,
+// counts the marked units of each word, and gives the k-th marked unit of
+// the take to lane k mod 32 in round k / 32 (word by a search over the
+// warp's prefix counts, bit by halving), so the lanes stay full however
+// sparse the marks are.  Warp-uniform; called by every lane of a warp.
+template <int C>
+__device__ __forceinline__ void sparse_e1_bits(const uint32_t *e1bits, const uint32_t *actbits,
+                                               bool act, int *take, int nw, long long gbase,
+                                               int Td, int d, const SgTables &tb,
+                                               const DayArgs &a, uint32_t k0, uint32_t k1,
+                                               unsigned long long &applied) {
+  const int lane = threadIdx.x & 31;
+  const int Nn = tb.n_nodes;
+  for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(take, 32);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= nw) break;
+    const int wi = g + lane;
+    uint32_t m = 0;
+    if (wi < nw) m = e1bits[wi] & (act ? actbits[wi] : ~actbits[wi]);
+    const int cnt = __popc(m);
+    int incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll 1
+    for (int r0 = 0; r0 < tot; r0 += 32) {
+      const int k = r0 + lane;
+      // the last word whose count starts at or below k
+      int w = 0;
+#pragma unroll
+      for (int sft = 16; sft > 0; sft >>= 1) {
+        const int e = __shfl_sync(0xffffffffu, excl, w + sft);
+        if (e <= k) w += sft;
+      }
+      uint32_t x = __shfl_sync(0xffffffffu, m, w);
+      int n = k - __shfl_sync(0xffffffffu, excl, w);
+      int pos = 0;
+#pragma unroll
+      for (int sft = 16; sft > 0; sft >>= 1) {
+        const int c = __popc(x & ((1u << sft) - 1u));
+        if (n >= c) {
+          n -= c;
+          x >>= sft;
+          pos += sft;
+        }
+      }
+      const bool has = k < tot;
+      long long gid = 0;
+      int rep = 0, node = 0;
+      if (has) {
+        gid = gbase + (long long)(g + w) * 32 + pos;
+        rep = (int)(gid / Nn);
+        node = (int)(gid - (long long)rep * Nn);
+      }
+      sparse_e1<C>(has, gid, rep, node, Td, d, tb, a, k0, k1, applied);
+    }
+  }
+}
+
 // (replicate, node) of a unit index, advanced by a stride without dividing
 // (the passes over a block's units step by kSparseBlock).
 struct UnitPos {
@@ -1917,7 +2060,9 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   __shared__ uint16_t s_act[kSparseChunk];
   __shared__ uint16_t s_nq[kSparseChunk];  // units of the chunk that are not quiescent
   __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
-  __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq;
+  __shared__ uint32_t s_actbits[kSparseChunk / 32];  // units taking SSA draws today
+  __shared__ uint32_t s_e1bits[kSparseChunk / 32];   // units with E1 events today
+  __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq, s_e1take, s_e1late;
   pdl_trigger();
   const int Nn = tb.n_nodes;
   const long long total = (long long)Nn * a.n_rep;
@@ -1925,6 +2070,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   const int nub = (int)max(0LL, min((long long)a.npb, total - g0));
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const bool quiet = a.quiet != 0;
+  const bool has_e1 = a.ev.e1_node_off != nullptr;
   const uint32_t k0 = a.k0, k1 = a.k1;
   unsigned long long rated = 0;  // units whose rates this thread evaluated
   // a unit whose expected transitions in the day (lambda times one day) reach
@@ -1980,7 +2126,10 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         s_nheavy = 0;
         s_next = 0;
         s_nnq = 0;
+        s_e1take = 0;
+        s_e1late = 0;
       }
+      for (int q = tid; q < kSparseChunk / 32; q += kSparseBlock) s_actbits[q] = 0u;
       __syncthreads();
       // 1a. every unit of the chunk, four per thread per step (their loads
       //     issued together): a quiescent unit (no infected animal, phi ==
@@ -1994,10 +2143,12 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         for (int b0 = 0; b0 < cn; b0 += 4 * kSparseBlock) {
           int uu[4][C];
           double vv[4][NV > 0 ? NV : 1];
+          int nday[4];
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int i = b0 + k * kSparseBlock + tid;
             vv[k][0] = 0.0;
+            nday[k] = -1;
 #pragma unroll
             for (int p = 0; p < C; ++p) uu[k][p] = 0;
             if (i < cn) {
@@ -2006,12 +2157,16 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
               for (int p = 0; p < C; ++p) uu[k][p] = a.u[gid * C + p];
 #pragma unroll
               for (int q = 0; q < NV; ++q) vv[k][q] = a.v[gid * NV + q];
+              if (has_e1) nday[k] = a.e1_next[gid];
             }
           }
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const int i = b0 + k * kSparseBlock + tid;
             const bool in = i < cn;
+            // a warp's 32 units of step k are one word of the bitmap
+            const uint32_t bw = __ballot_sync(0xffffffffu, nday[k] == d);
+            if (lane == 0) s_e1bits[(b0 + k * kSparseBlock) / 32 + warp] = bw;
             const bool q0 = in && quiet && quiescent<KIND>(uu[k], vv[k]);
             if (in && !q0) s_nq[atomicAdd(&s_nnq, 1)] = (uint16_t)i;
             if (m_prev >= 0) {
@@ -2065,6 +2220,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
             if (bad) {
               report(a.err, SG_ERR_RATE, a.rep0 + rep, node, Td, -1);
             } else if (gt0(lam)) {
+              atomicOr(&s_actbits[(i - c0) >> 5], 1u << ((i - c0) & 31));
               int slot = kSparseHeavy;
               if (!(lam < heavy_rate)) slot = atomicAdd(&s_nheavy, 1);
               if (slot < kSparseHeavy) {
@@ -2185,6 +2341,13 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
           busy = false;
         }
       }
+      // a warp with no SSA work left applies the E1 events of day Td of the
+      // chunk's units that take no draw today (1,024 units per take, their
+      // units with events compacted onto the lanes); the units that take
+      // draws come after the SSA (their events follow their day's
+      // transitions)
+      if (has_e1) sparse_e1_bits<C>(s_e1bits, s_actbits, false, &s_e1take, (cn + 31) >> 5,
+                                    g0 + c0, Td, d, tb, a, k0, k1, applied);
       __syncthreads();
       // the warp slots not run yet: all of them when every warp had list
       // units, else those the thread list handed over
@@ -2203,110 +2366,16 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         __syncwarp();
       }
       __syncthreads();
-    }
-    // 3. E1 events of day Td in (time, type, list index) order: a scan of
-    //    one word per unit (the day of its next E1 event) lists the units
-    //    with events today in shared memory (chunks of kSparseChunk units),
-    //    and the block applies the list, one unit per thread; then, unless
-    //    deferred to the next launch, the post time step and recording of
-    //    Td for every unit
-    const bool fin = Td + 1 < a.T_end || a.finish_last;
-    if (a.ev.e1_node_off != nullptr) {
-      for (int c0 = 0; c0 < nub; c0 += kSparseChunk) {
-        const int cn = min(kSparseChunk, nub - c0);
-        if (tid == 0) s_nact = 0;
-        __syncthreads();
-#pragma unroll 1
-        for (int b0 = 0; b0 < cn; b0 += 4 * kSparseBlock) {
-          int nday[4];
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const int i = b0 + k * kSparseBlock + tid;
-            nday[k] = i < cn ? a.e1_next[g0 + c0 + i] : 0x7fffffff;
-          }
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (nday[k] == d) s_act[atomicAdd(&s_nact, 1)] = (uint16_t)(b0 + k * kSparseBlock + tid);
-        }
-        __syncthreads();
-        const int ne = s_nact;
-        // rounds of kSparseBlock list units; every thread of the block
-        // takes part in each round (the warp-uniform E1 loop)
-#pragma unroll 1
-        for (int r0 = 0; r0 < ne; r0 += kSparseBlock) {
-          const int li = r0 + tid;
-          const bool has = li < ne;
-          long long gid = 0, ecur = 0, eend = 0, ebase = 0;
-          int rep = 0, node = 0, code = 0;
-          int u[C];
-#pragma unroll
-          for (int p = 0; p < C; ++p) u[p] = 0;
-          if (has) {
-            gid = g0 + c0 + s_act[li];
-            rep = (int)(gid / Nn);
-            node = (int)(gid - (long long)rep * Nn);
-            const long long key = (long long)(a.slots > 1 ? rep : 0) * Nn + node;
-            ebase = a.ev.e1_node_off[key];
-            eend = a.ev.e1_node_off[key + 1];
-            ecur = ebase + a.e1_cur[gid];
-#pragma unroll
-            for (int p = 0; p < C; ++p) u[p] = a.u[gid * C + p];
-          }
-          const int grep = a.rep0 + rep;
-          // every lane with an event left takes its next one per round,
-          // applied in the thread or (kUrnWarp or more individuals drawn)
-          // by the whole warp
-          bool pend = has;
-          while (__any_sync(0xffffffffu, pend)) {
-            E1Rec e;
-            bool heavy = false;
-            if (pend) {
-              if (ecur < eend && a.ev.e1_day[ecur] == d) {
-                e = load_e1(tb, a.ev, ecur, grep, k0, k1);
-                heavy = e1_draws<C>(u, tb, e) >= kUrnWarp;
-                if (!heavy) {
-                  const int rc = apply_e1<C>(u, tb, e, grep, k0, k1);
-                  if (rc) {
-                    code = rc;
-                    report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
-                    pend = false;
-                  } else {
-                    ++applied;
-                    ++ecur;
-                  }
-                }
-              } else {
-                pend = false;
-              }
-            }
-            unsigned hm = __ballot_sync(0xffffffffu, heavy);
-            while (hm) {
-              const int L = __ffs(hm) - 1;
-              hm &= hm - 1;
-              const int rc = apply_e1_warp<C>(u, tb, e, L, grep, k0, k1);
-              if (lane == L) {
-                if (rc) {
-                  code = rc;
-                  report(a.err, rc, grep, node, Td, a.ev.index[ecur]);
-                  pend = false;
-                } else {
-                  ++applied;
-                  ++ecur;
-                }
-              }
-            }
-          }
-          (void)code;
-          if (has) {
-#pragma unroll
-            for (int p = 0; p < C; ++p) a.u[gid * C + p] = u[p];
-            a.e1_cur[gid] = (int32_t)(ecur - ebase);
-            a.e1_next[gid] = ecur < eend ? a.ev.e1_day[ecur] : 0x7fffffff;
-          }
-        }
+      // 3. E1 events of day Td of the units that took draws today
+      if (has_e1) {
+        sparse_e1_bits<C>(s_e1bits, s_actbits, true, &s_e1late, (cn + 31) >> 5, g0 + c0, Td,
+                          d, tb, a, k0, k1, applied);
         __syncthreads();
       }
     }
+    // then, unless deferred to the next launch, the post time step and
+    // recording of Td for every unit
+    const bool fin = Td + 1 < a.T_end || a.finish_last;
     if (fin) {
       // post time step and recording of Td: quiescent units are recorded
       // by a scan (four per thread per step), the others listed (chunks of
