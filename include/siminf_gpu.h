@@ -320,19 +320,26 @@ int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total);
  * are certainly empty (no infected animal and phi == +0, with finite model
  * parameters), and runs the SSA of the pairs with a positive total rate from
  * a compact list, one thread each, handing those that need more than
- * heavy_after draws to warps.  Results are identical for every setting (the
+ * heavy_after draws to warps.  When nodes_per_block is also a multiple of
+ * the node count (every block holds whole replicates) the whole run is one
+ * launch: each block runs its replicates' external transfers itself and no
+ * block waits for another.  Results are identical for every setting (the
  * random stream is a function of replicate, node, day and draw index only);
  * only speed changes.  nodes_per_block <= 0 or heavy_after < 0 restore the
- * size-based defaults: the sparse-activity schedule with two blocks per SM
- * and heavy_after 8 where it applies and the pairs exceed two full 128-pair
- * blocks per SM, else 128 pairs per block (fewer for small problems, so
- * that about two blocks per SM exist) and heavy_after 2. */
+ * size-based defaults: where the sparse-activity schedule applies and the
+ * pairs exceed two full 128-pair blocks per SM, one replicate per block
+ * and heavy_after 16 when there are at least as many replicates as SMs
+ * (and more than 128 nodes), else two blocks per SM and heavy_after 8;
+ * otherwise 128 pairs per block (fewer for small problems, so that about
+ * two blocks per SM exist) and heavy_after 2. */
 int sg_set_tuning(sg_model *m, int32_t nodes_per_block, int32_t heavy_after);
 
 /* Autotuner: for each of nodes_per_block in {4, 8, 16, 32, 64, 128} x
  * heavy_after in {0, 1, 2, 4, 8}, and, where the sparse-activity schedule
- * applies, nodes_per_block = the pairs spread over 1, 2 or 4 blocks per SM
- * and 1,024 (when above 128) x heavy_after in {2, 8, 32, 128}, runs the given
+ * applies, nodes_per_block = the pairs spread over 1, 2 or 4 blocks per SM,
+ * 1,024, and one or two whole replicates (when above 128; replicates per
+ * block such that at least half a block per SM exists) x heavy_after in
+ * {2, 8, 16, 32, 128}, runs the given
  * workload (arguments as sg_run) once untimed (capturing its graph when
  * graphs are on) and twice timed, keeps the setting with the fastest timed
  * run in the model and reports it and its time (outputs may be NULL).  U and

@@ -1266,6 +1266,25 @@ static void enqueue_run(sg_model *m, const DayArgs &da0, const EvArgs &ea0, int3
     for (int32_t d = 0; d < days; ++d)
       waves += (int32_t)(P.e2_wave_off[(long long)(d + 1) * slots] -
                          P.e2_wave_off[(long long)d * slots]);
+  } else if (Nn > 0 && days > 0 && da.npb > kDayBlock && da.npb % Nn == 0 &&
+             m->tb.kind != SG_GENERIC && !da.aem_tau) {
+    // sparse schedule with whole replicates per block: every day in one
+    // launch, each block running its replicates' external transfers itself
+    // (no block waits for another)
+    DayArgs dr = da;
+    dr.T_begin = t0 + 1;
+    dr.T_end = t_end + 1;
+    dr.finish_first = 0;
+    dr.finish_last = 1;
+    dr.e2_inblock = 1;
+    {
+      LaunchTimer lt(m, st, 0);
+      launch_days_kind(m, dr, st);
+    }
+    ++launches;
+    for (int32_t d = 0; d < days; ++d)
+      waves += (int32_t)(P.e2_wave_off[(long long)(d + 1) * slots] -
+                         P.e2_wave_off[(long long)d * slots]);
   } else if (Nn > 0 && days > 0) {
     bool pending = false;  // the previous unit step still needs finishing
     int32_t d = 0;
@@ -1453,7 +1472,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   if (da.npb > kDayBlock && !sparse_ok) da.npb = kDayBlock;
   if (m->npb <= 0 && sparse_ok) {
     // untuned: more units than two full thread-per-node blocks per SM take
-    // the sparse-activity schedule, two blocks per SM
+    // the sparse-activity schedule: one replicate per block when there are
+    // at least as many replicates as SMs (every day in one launch), else
+    // the units spread over two blocks per SM
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -1462,8 +1483,9 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     }
     const long long units = (long long)Nn * n_rep;
     if (units > 2LL * kDayBlock * sms) {
-      da.npb = (int32_t)((units + 2LL * sms - 1) / (2LL * sms));
-      if (m->heavy_after < 0) da.heavy_after = 8;
+      const bool whole = n_rep >= sms && Nn > kDayBlock;
+      da.npb = whole ? Nn : (int32_t)((units + 2LL * sms - 1) / (2LL * sms));
+      if (m->heavy_after < 0) da.heavy_after = whole ? 16 : 8;
     }
   }
   {
@@ -1491,6 +1513,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
   da.e2_done = nullptr;
   da.grid_bar = nullptr;
   da.n_blocks = 0;
+  da.e2_inblock = 0;
   da.aem_a = aem ? m->aem_a.p : nullptr;
   da.aem_tau = aem ? m->aem_tau.p : nullptr;
   da.aem_cnt = aem ? m->aem_cnt.p : nullptr;
@@ -1916,6 +1939,7 @@ extern "C" int sg_run_noalloc(const sg_desc *d, const double *d_ldata, const int
       da.e2_done = nullptr;
       da.grid_bar = nullptr;
       da.n_blocks = 0;
+      da.e2_inblock = 0;
       const long long units = (long long)Nn * n_rep;
       const unsigned grid = (unsigned)std::max<long long>(1, (units + da.npb - 1) / da.npb);
       switch (k) {
@@ -1976,7 +2000,8 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
   // 4 and 8 nodes per block give every heavy node its own warp (workloads
   // where most node-days take thousands of draws); more than kDayBlock
   // selects the sparse-activity schedule: units spread over 1, 2 or 4
-  // blocks per SM, or fixed 1,024-unit blocks
+  // blocks per SM, fixed 1,024-unit blocks, or one or two whole replicates
+  // per block
   std::vector<std::pair<int32_t, int32_t>> cand;
   for (int32_t npb : {4, 8, 16, 32, 64, 128})
     for (int32_t h : {0, 1, 2, 4, 8}) cand.emplace_back(npb, h);
@@ -1994,12 +2019,19 @@ extern "C" int sg_autotune(sg_model *m, const int32_t *tspan, int32_t n_tspan, u
       if (b > kDayBlock && b <= (1 << 22)) sp.push_back((int32_t)b);
     }
     if (units > 2LL * kDayBlock * sms) sp.push_back(1024);
+    // whole replicates per block (one launch for every day, external
+    // transfers in the blocks) when that still gives half a block per SM
+    for (int per_block : {1, 2}) {
+      const long long b = (long long)m->tb.n_nodes * per_block;
+      if (b > kDayBlock && b <= (1 << 22) && (long long)n_rep / per_block >= sms / 2)
+        sp.push_back((int32_t)b);
+    }
     const int k = m->tb.kind;
     const bool sparse_ok = m->solver != SG_SOLVER_AEM && !m->emu_on && !m->persistent &&
                            (k == SG_SIR || k == SG_SIS || k == SG_SISE || k == SG_SISE3);
     if (!sparse_ok) sp.clear();
     for (int32_t npb : sp)
-      for (int32_t h : {2, 8, 32, 128}) cand.emplace_back(npb, h);
+      for (int32_t h : {2, 8, 16, 32, 128}) cand.emplace_back(npb, h);
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;

@@ -199,6 +199,11 @@ struct DayArgs {
   // (arrival count, generation); null: not persistent
   unsigned int *grid_bar;
   int32_t n_blocks;
+  // sparse schedule with every block holding whole replicates (nodes per
+  // block a multiple of the node count): each block runs its replicates'
+  // external transfers of every day itself, between the day's E1 events and
+  // its post time step, so one launch covers all days; 0: off
+  int32_t e2_inblock;
 };
 
 // %globaltimer (ns).
@@ -2118,7 +2123,12 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
     if (s_stop) break;
     const double Tn = (double)Td;
     const int d = Td - a.t0 - 1;
-    const bool fin_prev = Td == a.T_begin && a.finish_first;
+    // the post time step and recording of Td - 1 in this day's first
+    // passes: at a launch that finishes the previous one's last day, and on
+    // every day after the first when the block runs its replicates'
+    // external transfers itself
+    const bool fin_prev = (Td == a.T_begin && a.finish_first) ||
+                          (a.e2_inblock && Td > a.T_begin);
     for (int c0 = 0; c0 < nub; c0 += kSparseChunk) {
       const int cn = min(kSparseChunk, nub - c0);
       if (tid == 0) {
@@ -2242,12 +2252,6 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         }
       }
       __syncthreads();
-      // 2. the thread list on the first list_warps warps (about two units
-      //    per lane), with lane refill: every round each busy lane takes one
-      //    draw of its unit, and a lane whose unit is done (or handed to a
-      //    warp slot after heavy_after draws) takes the next unit of the
-      //    list, so that the warps' lanes stay busy while the list lasts;
-      //    meanwhile the other warps run the warp slots filled in pass 1
       const int na = s_nact;
       const int n_direct = min(s_nheavy, kSparseHeavy);
       const int list_warps = min(nwarps, (na + 63) >> 6);
@@ -2373,9 +2377,23 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         __syncthreads();
       }
     }
-    // then, unless deferred to the next launch, the post time step and
-    // recording of Td for every unit
-    const bool fin = Td + 1 < a.T_end || a.finish_last;
+    if (a.e2_inblock) {
+      // this block's replicates' external transfers of Td (the wave plan of
+      // day d; no other block touches their nodes)
+      for (long long r = g0 / Nn; nub > 0 && r * Nn < g0 + nub; ++r) {
+        const long long k = (long long)d * a.slots + (a.slots > 1 ? r : 0);
+        const long long w0 = a.wave_off[k], w1 = a.wave_off[k + 1];
+        if (w0 < w1) e2_rep_block<C>(tb, a, (int)r, Td, w0, w1);
+      }
+      // a failed transfer ends the run before the day's post time step
+      if (tid == 0) s_stop = *(volatile int32_t *)&a.err->code != 0;
+      __syncthreads();
+      if (s_stop) break;
+    }
+    // then, unless deferred to the next day's first passes or the next
+    // launch, the post time step and recording of Td for every unit
+    const bool fin = a.e2_inblock ? Td + 1 == a.T_end && a.finish_last
+                                  : Td + 1 < a.T_end || a.finish_last;
     if (fin) {
       // post time step and recording of Td: quiescent units are recorded
       // by a scan (four per thread per step), the others listed (chunks of

@@ -5,7 +5,8 @@ from a shared list) with the CPU oracle: bit-exact U and V, identical
 reaction counts and identical errors, for every built-in kind, with and
 without scheduled events, several replicates, ranges that need more than one
 pass through the list (more units per block than the list holds), blocks
-that hold a whole replicate or several, and every hand-off setting."""
+that hold a whole replicate or several (with the replicates' external
+transfers run by the block), and every hand-off setting."""
 import numpy as np
 import pytest
 
@@ -195,6 +196,39 @@ def test_aem_fallback_and_fused_external_transfers(orc, gpu):
     m.run(w.tspan, w.seed, 1, u0, v0, U, V)
     m.close()
     assert np.array_equal(U.cpu().numpy(), U0)
+
+
+@pytest.mark.parametrize("per_block,heavy", [(1, 8), (2, 0), (3, 1 << 20)])
+def test_whole_replicates_per_block(orc, gpu, per_block, heavy):
+    # nodes per block a multiple of the node count: one launch for every
+    # day, each block running its replicates' external transfers between the
+    # day's E1 events and its post time step (own events per replicate, and
+    # one list shared by the replicates)
+    w = W.config_batched(n_rep=5, n_nodes=700, days=50, gen_seed=49)
+    st = _compare(orc, gpu, w, (700 * per_block, heavy))
+    assert st["kernel_launches"] <= 5  # not two per day
+    w = W.config_sise3(n_nodes=400, days=90, gen_seed=5, n_rep=6)
+    _compare(orc, gpu, w, (400 * per_block, heavy))
+
+
+def test_whole_replicates_per_block_transfer_underflow(orc, gpu):
+    # an external transfer of more animals than the source holds, on day 2
+    # of replicate 1: the same error and no post time step of that day
+    rows = [(EXTERNAL, 1, 0, 1, 3, 0.0, 2, -1), (EXTERNAL, 2, 1, 0, 500, 0.0, 2, -1)]
+    u0 = [[40, 2], [30, 0]] + [[20, 1]] * 198
+    w = W.plain_model(W.SISE, u0, np.arange(0, 6), W.sise_gdata(), n_rep=3,
+                      events=W.make_events(rows))
+    code, U, V, R, err = orc.run(w)
+    assert code == -2 and err["event"] == 1 and err["day"] == 2
+    m = gpu.Model(w)
+    m.set_tuning(200, 2)
+    u0d, v0d, Ud, Vd = _dev(w)
+    rc, st, er = m.run(w.tspan, w.seed, 3, u0d, v0d, Ud, Vd, check=False)
+    assert rc == -2 and er["event"] == 1 and er["day"] == 2 and er["node"] == 1
+    m.set_events(W.make_events(rows[:1]))
+    rc, st, er = m.run(w.tspan, w.seed, 3, u0d, v0d, Ud, Vd, check=False)
+    assert rc == 0
+    m.close()
 
 
 def _dev(w, n_rep=None):
