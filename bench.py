@@ -274,24 +274,28 @@ def _kernel_sources_sha1():
 
 
 # Counters of one limited ncu capture of the day kernel on the batched
-# workload shortened to 8 days (256 replicates x 5,000 herds per launch, the
-# same launch as in the timed run); reported only while the kernel sources
-# hash to the captured ones (otherwise null).  The capture command:
-#   python bench.py --workload batched --days 8 --steps 1 --warmup 1
-#       --cpu-seconds 0 --e2e 0 --extras 0 --tuning <split>, under
+# workload shortened to 30 days (256 replicates x 5,000 herds, one replicate
+# per block: the whole run is one launch of the kernel, as in the timed
+# run); reported only while the kernel sources hash to the captured ones
+# (otherwise null).  DRAM bytes grow with the node-days a launch covers, so
+# the capture's bytes per node-day scale it to the timed launch.  The
+# capture command:
+#   python bench.py --workload batched --days 30 --steps 1 --warmup 1
+#       --cpu-seconds 0 --e2e 0 --extras 0 --tuning 5000,16, under
 #   ncu --section SpeedOfLight --section ComputeWorkloadAnalysis
 #       --section MemoryWorkloadAnalysis --section WarpStateStats
 #       --section SchedulerStats --section Occupancy --section LaunchStats
-#       --section InstructionStats --clock-control none -k regex:k_days -s 2 -c 2
+#       --metrics dram__bytes_read.sum,dram__bytes_write.sum
+#       --clock-control none -k regex:k_days_sparse -s 1 -c 1
 DAY_KERNEL_NCU = None
 
 
-def _day_kernel_ncu(w):
+def _day_kernel_ncu(w, node_days_per_launch):
     c = DAY_KERNEL_NCU
     if (c is None or not w.name.startswith("SISe3 256 replicates x 5000 nodes")
             or c["sources_sha1"] != _kernel_sources_sha1()):
         return None
-    return c
+    return dict(c, dram_bytes_per_launch=c["dram_bytes_per_node_day"] * node_days_per_launch)
 
 
 def max_over_ranks(total_ms, dist, device):
@@ -495,7 +499,7 @@ def measure_gpu(w, args, stream, dev, steps, warmup, rep0=0, seed=None, tune=Tru
         # its bound): bytes written per launch / launch time
         rec = (w.n_comp * 4 + w.n_v * 8) * w.n_nodes * n_rep * (M - 1) * kps
         roof["record_stream_gbs"] = rec / (kt["ms_ssa"] * 1e-3) / 1e9
-        ncu = _day_kernel_ncu(w)
+        ncu = _day_kernel_ncu(w, kt["node_days"] / max(1, kt["launches_ssa"]))
         roof["traffic"] = ncu["dram_bytes_per_launch"] if ncu else None
         roof["ncu"] = ncu
     out["roofline"] = roof

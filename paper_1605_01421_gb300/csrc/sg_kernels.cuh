@@ -2067,7 +2067,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
   __shared__ HeavySlot<C, NK> s_heavy[kSparseHeavy];
   __shared__ uint32_t s_actbits[kSparseChunk / 32];  // units taking SSA draws today
   __shared__ uint32_t s_e1bits[kSparseChunk / 32];   // units with E1 events today
-  __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq, s_e1take, s_e1late;
+  __shared__ int s_nact, s_nheavy, s_stop, s_next, s_nnq, s_e1take, s_e1late, s_nshort;
   pdl_trigger();
   const int Nn = tb.n_nodes;
   const long long total = (long long)Nn * a.n_rep;
@@ -2138,6 +2138,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         s_nnq = 0;
         s_e1take = 0;
         s_e1late = 0;
+        s_nshort = 0;
       }
       for (int q = tid; q < kSparseChunk / 32; q += kSparseBlock) s_actbits[q] = 0u;
       __syncthreads();
@@ -2244,6 +2245,11 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
                 hs.code = i;  // the unit, until the warp reports
 #pragma unroll
                 for (int p = 0; p < C; ++p) hs.u[p] = u[p];
+              } else if (lam < 2.0) {
+                // the thread list: units expecting two transitions or more
+                // from the front, the others from the back, so that the
+                // longer chains start first
+                s_act[kSparseChunk - 1 - atomicAdd(&s_nshort, 1)] = (uint16_t)(i - c0);
               } else {
                 s_act[atomicAdd(&s_nact, 1)] = (uint16_t)(i - c0);
               }
@@ -2252,7 +2258,8 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         }
       }
       __syncthreads();
-      const int na = s_nact;
+      const int n_long = s_nact;
+      const int na = n_long + s_nshort;
       const int n_direct = min(s_nheavy, kSparseHeavy);
       const int list_warps = min(nwarps, (na + 63) >> 6);
       if (warp >= list_warps) {
@@ -2287,7 +2294,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
           if (!busy && !drained) {
             const int i = atomicAdd(&s_next, 1);
             if (i < na) {
-              gid = g0 + c0 + s_act[i];
+              gid = g0 + c0 + s_act[i < n_long ? i : kSparseChunk - 1 - (i - n_long)];
               rep = (int)(gid / Nn);
               node = (int)(gid - (long long)rep * Nn);
               tag = (SG_STREAM_SSA << 24) | (uint32_t)(a.rep0 + rep);

@@ -123,6 +123,32 @@ def test_event_underflow_and_rate_errors(orc, gpu, tuning):
     m.close()
 
 
+@pytest.mark.parametrize("tuning", [(1000, 8), (300, 0), (2000, 1 << 20)])
+def test_sise3_rate_error_after_transitions_on_warps(orc, gpu, tuning):
+    # age class 2 has a negative upsilon and no susceptible animal: its
+    # infection rate is -0 until a recovery makes it negative, deep inside
+    # the SSA of heavy herds (several per warp) and of light ones
+    rng = np.random.default_rng(50)
+    n = 3000
+    u0 = np.zeros((n, 6), dtype=np.int32)
+    u0[:, 0] = rng.integers(0, 200, n)
+    u0[:, 1] = rng.integers(0, 3, n)
+    hot = rng.choice(n, 40, replace=False)
+    u0[hot, 2] = 0
+    u0[hot, 3] = rng.integers(100, 1500, hot.size)
+    g = W.sise3_gdata(upsilons=(0.0173, -0.01, 0.0173))
+    w = W.plain_model(W.SISE3, u0, np.arange(10, 16), g, seed=9, v0=np.ones((n, 1)))
+    code, U, V, R, err = orc.run(w)
+    assert code == -4
+    m = gpu.Model(w)
+    m.set_tuning(*tuning)
+    u0d, v0d, Ud, Vd = _dev(w)
+    rc, st, er = m.run(w.tspan, w.seed, 1, u0d, v0d, Ud, Vd, check=False)
+    m.close()
+    assert rc == -4 and er["day"] == err["day"]
+    assert er["node"] in set(hot.tolist())
+
+
 def test_draw_limit(orc, gpu):
     # node 1 needs more than 2^24 draws on its first day
     w = W.plain_model(W.SIS, [[10, 0], [1000, 1000], [5, 5]], np.arange(0, 3), [1e5, 1e5])
