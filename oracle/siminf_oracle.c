@@ -123,14 +123,17 @@ double oracle_u01(uint32_t a, uint32_t b)
 /* and log x = k ln2_hi + (f - (hfsq - (s (hfsq + R) + k ln2_lo))) with a   */
 /* Cody-Waite split of ln 2 whose high part has 33 significant bits, so     */
 /* k ln2_hi is exact.  |s| <= 0.1716, so ten terms leave a truncation       */
-/* error below 2^-54 relative.                                              */
+/* error below 2^-54 relative.  Every a + b c of the polynomial, hfsq + R,  */
+/* s (hfsq + R) + k ln2_lo and the final k ln2_hi + (...) is one fused      */
+/* multiply-add (C99 fma: a single rounding), the form with the fewest      */
+/* IEEE operations.                                                          */
 /* ------------------------------------------------------------------------ */
 
 double oracle_log(double x)
 {
     uint64_t bits;
     int k;
-    double m, f, hfsq, s, z, R, dk;
+    double m, f, hfsq, s, z, t, dk;
     const double ln2_hi = 0.6931471804855391;      /* 33 significant bits */
     const double ln2_lo = 7.440617110012397e-11;   /* ln 2 - ln2_hi      */
 
@@ -157,21 +160,22 @@ double oracle_log(double x)
     s = f / (2.0 + f);
     z = s * s;
     /* R(z) = z P(z), P(z) = sum_{j=1..10} c_j z^(j-1), c_j = 2 / (2 j + 1),
-     * in Estrin's scheme: pairs c_j + c_(j+1) z, combined with z^2, z^4, z^8 */
+     * in Estrin's scheme: pairs c_j + c_(j+1) z, combined with z^2, z^4, z^8;
+     * t = hfsq + R = hfsq + z P */
     {
         double z2 = z * z, z4 = z2 * z2, z8 = z4 * z4;
-        double p01 = 2.0 / 3.0 + (2.0 / 5.0) * z;
-        double p23 = 2.0 / 7.0 + (2.0 / 9.0) * z;
-        double p45 = 2.0 / 11.0 + (2.0 / 13.0) * z;
-        double p67 = 2.0 / 15.0 + (2.0 / 17.0) * z;
-        double p89 = 2.0 / 19.0 + (2.0 / 21.0) * z;
-        double q03 = p01 + z2 * p23;
-        double q47 = p45 + z2 * p67;
-        double P = (q03 + z4 * q47) + z8 * p89;
-        R = z * P;
+        double p01 = fma(2.0 / 5.0, z, 2.0 / 3.0);
+        double p23 = fma(2.0 / 9.0, z, 2.0 / 7.0);
+        double p45 = fma(2.0 / 13.0, z, 2.0 / 11.0);
+        double p67 = fma(2.0 / 17.0, z, 2.0 / 15.0);
+        double p89 = fma(2.0 / 21.0, z, 2.0 / 19.0);
+        double q03 = fma(z2, p23, p01);
+        double q47 = fma(z2, p67, p45);
+        double P = fma(z8, p89, fma(z4, q47, q03));
+        t = fma(z, P, hfsq);
     }
     dk = (double)k;
-    return dk * ln2_hi + (f - (hfsq - (s * (hfsq + R) + dk * ln2_lo)));
+    return fma(dk, ln2_hi, f - (hfsq - fma(s, t, dk * ln2_lo)));
 }
 
 /* ------------------------------------------------------------------------ */

@@ -88,8 +88,12 @@ __device__ __forceinline__ bool le_nonneg(double a, double b) {
 // evaluated as f - (h - s (h + R(s^2))) with h = f^2 / 2 and the atanh
 // Taylor polynomial R(z) = sum_{j=1}^{10} 2 z^j / (2 j + 1) in Estrin form;
 // k ln 2 is added through a split ln 2 = L_hi + L_lo whose high part has 33
-// significant bits (k L_hi exact).  Accuracy: within 1 ulp of the correctly
-// rounded logarithm.  Only positive finite arguments reach it here.
+// significant bits (k L_hi exact).  Every a + b c of the polynomial, h + R,
+// s (h + R) + k L_lo and k L_hi + (...) is one fused multiply-add (one
+// rounding): on GB300 each FP64 warp instruction occupies the
+// sub-partition's FP64 pipe for ~76 cycles, so the count of operations is
+// the cost.  Accuracy: within 1 ulp of the correctly rounded logarithm.
+// Only positive finite arguments reach it here.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double log_pos(double x) {
   long long bits = __double_as_longlong(x);
@@ -113,16 +117,16 @@ __device__ __forceinline__ double log_pos(double x) {
   // Estrin's scheme for z (c1 + c2 z + ... + c10 z^9): coefficient pairs,
   // then combined with z^2, z^4, z^8 (dependency depth 8 instead of 20)
   const double z2 = z * z, z4 = z2 * z2, z8 = z4 * z4;
-  const double p01 = 0x1.5555555555555p-1 + 0x1.999999999999ap-2 * z;
-  const double p23 = 0x1.2492492492492p-2 + 0x1.c71c71c71c71cp-3 * z;
-  const double p45 = 0x1.745d1745d1746p-3 + 0x1.3b13b13b13b14p-3 * z;
-  const double p67 = 0x1.1111111111111p-3 + 0x1.e1e1e1e1e1e1ep-4 * z;
-  const double p89 = 0x1.af286bca1af28p-4 + 0x1.8618618618618p-4 * z;
-  const double q03 = p01 + z2 * p23;
-  const double q47 = p45 + z2 * p67;
-  const double R = z * ((q03 + z4 * q47) + z8 * p89);
+  const double p01 = fma(0x1.999999999999ap-2, z, 0x1.5555555555555p-1);
+  const double p23 = fma(0x1.c71c71c71c71cp-3, z, 0x1.2492492492492p-2);
+  const double p45 = fma(0x1.3b13b13b13b14p-3, z, 0x1.745d1745d1746p-3);
+  const double p67 = fma(0x1.e1e1e1e1e1e1ep-4, z, 0x1.1111111111111p-3);
+  const double p89 = fma(0x1.8618618618618p-4, z, 0x1.af286bca1af28p-4);
+  const double q03 = fma(z2, p23, p01);
+  const double q47 = fma(z2, p67, p45);
+  const double hR = fma(z, fma(z8, p89, fma(z4, q47, q03)), h);  // h + R
   const double dk = (double)k;
-  return dk * 0x1.62e42fefp-1 + (f - (h - (s * (h + R) + dk * 0x1.473de6af278edp-34)));
+  return fma(dk, 0x1.62e42fefp-1, f - (h - fma(s, hR, dk * 0x1.473de6af278edp-34)));
 }
 
 // ---------------------------------------------------------------------------
