@@ -2284,6 +2284,12 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         int u[C];
         double kf[NK], w[T];
         double t = 0.0;
+        // draw buffer shared by the warp: after a refill with k busy lanes,
+        // the busy lane of rank r finds draw cb + j of its unit in lane
+        // r + j k (j < nbuf = 32 / k); bufE / bufR are this lane's entry
+        uint32_t cb = 0;
+        int nbuf = 0, rank = 0, kref = 1;
+        double bufE = 0.0, bufR = 0.0;
 #pragma unroll
         for (int p = 0; p < C; ++p) u[p] = 0;
 #pragma unroll
@@ -2310,15 +2316,77 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
               t = (double)(Td - 1);
               c = 0;
               nb = 0;
+              nbuf = 0;
               busy = true;
             } else {
               drained = true;
             }
           }
-          if (!__any_sync(0xffffffffu, busy)) break;
+          const unsigned bm = __ballot_sync(0xffffffffu, busy);
+          if (bm == 0u) break;
+          // a busy lane without its next draw buffered: every lane computes
+          // one draw (Philox, uniforms, logarithm) for the busy lanes, the
+          // draws c .. c + 32 / k - 1 of each, so that in the list's tail one
+          // logarithm sequence of the warp serves several rounds
+          if (__any_sync(0xffffffffu, busy && (nbuf == 0 || c - cb >= (uint32_t)nbuf))) {
+            const int k = __popc(bm);
+            const int per = 32 / k;
+            const int ro = lane % k, jo = lane / k;
+            // the busy lane of rank ro (the ro-th set bit of bm, by halving)
+            uint32_t x = bm;
+            int n = ro, owner = 0;
+#pragma unroll
+            for (int sft = 16; sft > 0; sft >>= 1) {
+              const int cnt = __popc(x & ((1u << sft) - 1u));
+              if (n >= cnt) {
+                n -= cnt;
+                x >>= sft;
+                owner += sft;
+              }
+            }
+            const uint32_t oc = __shfl_sync(0xffffffffu, c, owner);
+            const uint32_t on = (uint32_t)__shfl_sync(0xffffffffu, node, owner);
+            const uint32_t ot = __shfl_sync(0xffffffffu, tag, owner);
+            if (jo < per) {
+              const U4 xr = philox10(U4{oc + (uint32_t)jo, on, (uint32_t)Td, ot}, k0, k1);
+              bufE = -log_pos(u01_open(xr.x, xr.y));
+              bufR = u01_open(xr.z, xr.w);
+            }
+            kref = k;
+            cb = c;
+            nbuf = per;
+            rank = __popc(bm & ((1u << lane) - 1u));
+          }
+          const int src = (rank + (int)(c - cb) * kref) & 31;
+          const double E = __shfl_sync(0xffffffffu, bufE, src);
+          const double R2 = __shfl_sync(0xffffffffu, bufR, src);
           if (!busy) continue;
-          int r = ssa_step<KIND>(u, w, kf, t, c, Tkey, (uint32_t)node, (uint32_t)Td, tag, k0,
-                                 k1, nb == a.heavy_after, tb, fired);
+          // one draw: ssa_step's operations and order, with the draw's
+          // random numbers from the buffer
+          int r;
+          {
+            double lam = w[0];
+#pragma unroll
+            for (int j = 1; j < T; ++j) lam = lam + w[j];
+            if (!gt0(lam)) {
+              r = SSA_DONE;
+            } else if (c >= SG_MAX_DRAWS) {
+              r = SG_ERR_STEP_LIMIT;
+            } else if (nb == a.heavy_after) {
+              r = SSA_HEAVY;
+            } else {
+              ++c;
+              const double tt = t + E / lam;
+              if (order_key(tt) >= Tkey) {
+                r = SSA_DONE;
+              } else {
+                t = tt;
+                const int rc = fire<KIND>(u, w, lam * R2, kf, tb);
+                ++fired;
+                r = rc ? rc : SSA_STEP_FIRED;
+              }
+            }
+          }
           if (r == SSA_STEP_FIRED) {
             ++nb;
             continue;
