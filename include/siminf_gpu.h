@@ -328,7 +328,7 @@ int sg_set_replicate_range(sg_model *m, int32_t rep0, int32_t rep_total);
  * only speed changes.  nodes_per_block <= 0 or heavy_after < 0 restore the
  * size-based defaults: where the sparse-activity schedule applies and the
  * pairs exceed two full 128-pair blocks per SM, one replicate per block
- * and heavy_after 16 when there are at least as many replicates as SMs
+ * and heavy_after 32 when there are at least as many replicates as SMs
  * (and more than 128 nodes), else two blocks per SM and heavy_after 8;
  * otherwise 128 pairs per block (fewer for small problems, so that about
  * two blocks per SM exist) and heavy_after 2. */

@@ -1485,7 +1485,7 @@ extern "C" int sg_run(sg_model *m, const int32_t *tspan, int32_t n_tspan, uint64
     if (units > 2LL * kDayBlock * sms) {
       const bool whole = n_rep >= sms && Nn > kDayBlock;
       da.npb = whole ? Nn : (int32_t)((units + 2LL * sms - 1) / (2LL * sms));
-      if (m->heavy_after < 0) da.heavy_after = whole ? 16 : 8;
+      if (m->heavy_after < 0) da.heavy_after = whole ? 32 : 8;
     }
   }
   {
