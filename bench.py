@@ -287,7 +287,24 @@ def _kernel_sources_sha1():
 #       --section SchedulerStats --section Occupancy --section LaunchStats
 #       --metrics dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -k regex:k_days_sparse -s 1 -c 1
-DAY_KERNEL_NCU = None
+DAY_KERNEL_NCU = {
+    "sources_sha1": "7430c2ba135b4a4d98f42e9a449dc77bbbf37016",
+    "workload": "SISe3 256 replicates x 5000 nodes x 30 days, own events per replicate",
+    "tuning": [5000, 32],
+    "duration_us": 2289.9,
+    "dram_bytes_read": 2898760000,
+    "dram_bytes_write": 1507392000,
+    "dram_bytes_per_node_day": 114.74,
+    "algorithmic_bytes_per_node_day": 68,
+    "issue_active_pct": 19.06,
+    "fp64_pipe_active_pct": 14.54,
+    "warps_active_pct": 21.11,
+    "stall_barrier_per_issue": 8.00,
+    "stall_long_scoreboard_per_issue": 2.92,
+    "stall_wait_per_issue": 2.77,
+    "l1_hit_pct": 69.9,
+    "l2_hit_pct": 26.5,
+}
 
 
 def _day_kernel_ncu(w, node_days_per_launch):
