@@ -54,7 +54,7 @@ def test_sise3_with_all_event_types_and_replicates(orc, gpu, tuning):
     _compare(orc, gpu, w, tuning)
 
 
-@pytest.mark.parametrize("tuning", [(300, 0), (4500, 2)])
+@pytest.mark.parametrize("tuning", [(300, 0), (4500, 2), (4000, 2)])
 def test_sir_and_sis_without_events(orc, gpu, tuning):
     # no external transfers: whole runs of days inside one launch, the post
     # time step and recording of each day before the next day's SSA
@@ -162,9 +162,12 @@ def test_draw_limit(orc, gpu):
     m.close()
 
 
-def test_sparse_output_and_prevalence(orc, gpu):
+@pytest.mark.parametrize("tuning", [(700, 2), (1500, 32)])
+def test_sparse_output_and_prevalence(orc, gpu, tuning):
     # U_sparse / V_sparse and the prevalence counters from the sparse
-    # schedule equal the oracle's dense trajectory read at the pattern
+    # schedule equal the oracle's dense trajectory read at the pattern (also
+    # with one replicate per block, where each day's record is written by
+    # the next day's first passes)
     import torch
     from oracle import outputs
     w = W.config_batched(n_rep=2, n_nodes=1500, days=30, gen_seed=46)
@@ -179,7 +182,7 @@ def test_sparse_output_and_prevalence(orc, gpu):
     uval = torch.full((R, len(row)), -1, dtype=torch.int32, device="cuda")
     pout = torch.zeros((R, M, 4), dtype=torch.int64, device="cuda")
     m = gpu.Model(w)
-    m.set_tuning(700, 2)
+    m.set_tuning(*tuning)
     m.set_output(dense=False, n_tspan=M, u_pattern=up, u_values=uval,
                  prevalence=([1, 3, 5], list(range(6))), prev_out=pout)
     u0, v0, _, _ = _dev(w)
@@ -190,14 +193,15 @@ def test_sparse_output_and_prevalence(orc, gpu):
     assert np.array_equal(pout.cpu().numpy(), outputs.prevalence_counts(U0, [1, 3, 5], range(6)))
 
 
-def test_replicate_shards_on_the_sparse_schedule(orc, gpu):
+@pytest.mark.parametrize("tuning", [(1000, 0), (900, 8)])
+def test_replicate_shards_on_the_sparse_schedule(orc, gpu, tuning):
     import torch
     w = W.config_batched(n_rep=4, n_nodes=900, days=25, gen_seed=47)
     U_all, V_all, _ = gpu.simulate(w, tuning=(600, 2))
     s = W.replicate_range(w, 1, 2)
     m = gpu.Model(s)
     m.set_replicate_range(1, 4)
-    m.set_tuning(1000, 0)
+    m.set_tuning(*tuning)
     u0, v0, U, V = _dev(s)
     m.run(s.tspan, s.seed, 2, u0, v0, U, V)
     m.close()
