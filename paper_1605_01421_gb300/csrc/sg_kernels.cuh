@@ -404,6 +404,26 @@ __device__ void e2_rep_block(const SgTables &tb, const DayArgs &a, int rep, int 
 // target <= running sum of the positive rates (last positive one if rounding
 // leaves none), u += S[, n], and the rates that column n of G marks are
 // recomputed.  Returns 0 or SG_ERR_RATE.
+// u += S[, n] and the rates that column n of G marks recomputed; 0 or
+// SG_ERR_RATE.
+template <int KIND>
+__device__ __forceinline__ int apply_transition(int *u, double *w, int n, const double *kf,
+                                                const SgTables &tb) {
+  using M = ModelTraits<KIND>;
+#pragma unroll
+  for (int p = 0; p < M::C; ++p) u[p] += tb.S[n][p];
+  const uint32_t dep = tb.dep[n];
+  int code = 0;
+#pragma unroll
+  for (int k = 0; k < M::T; ++k) {
+    if ((dep >> k) & 1u) {
+      w[k] = M::rate_k(k, u, kf, tb.gdata);
+      if (bad_rate(w[k])) code = SG_ERR_RATE;
+    }
+  }
+  return code;
+}
+
 template <int KIND>
 __device__ __forceinline__ int fire(int *u, double *w, double target, const double *kf,
                                     const SgTables &tb) {
@@ -422,18 +442,33 @@ __device__ __forceinline__ int fire(int *u, double *w, double target, const doub
     }
   }
   if (n < 0) n = last;
+  return apply_transition<KIND>(u, w, n, kf, tb);
+}
+
+// Prefix sums P_j = (..(w_0 + w_1) + ..) + w_j of the rates in index order,
+// recomputed from index j0 on (the rates below j0 unchanged).  P_(T-1) is
+// lambda as the direct method sums it, and at every positive rate P_j is
+// the running sum of the positive rates that fire() forms (adding a zero
+// rate leaves a sum unchanged, and a sum of zeros plus w is w).
+template <int T>
+__device__ __forceinline__ void rate_prefix(const double *w, double *P, int j0) {
 #pragma unroll
-  for (int p = 0; p < M::C; ++p) u[p] += tb.S[n][p];
-  const uint32_t dep = tb.dep[n];
-  int code = 0;
+  for (int j = 0; j < T; ++j)
+    if (j >= j0) P[j] = j == 0 ? w[0] : P[j - 1] + w[j];
+}
+
+// fire()'s choice of transition from the prefix sums.
+template <int T>
+__device__ __forceinline__ int select_prefix(const double *w, const double *P, double target) {
+  int n = -1, last = -1;
 #pragma unroll
-  for (int k = 0; k < M::T; ++k) {
-    if ((dep >> k) & 1u) {
-      w[k] = M::rate_k(k, u, kf, tb.gdata);
-      if (bad_rate(w[k])) code = SG_ERR_RATE;
+  for (int j = 0; j < T; ++j) {
+    if (gt0(w[j])) {
+      if (n < 0) last = j;
+      if (n < 0 && le_nonneg(target, P[j])) n = j;
     }
   }
-  return code;
+  return n < 0 ? last : n;
 }
 
 enum { SSA_DONE = 0, SSA_HEAVY = 1 };
@@ -2290,6 +2325,9 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
         uint32_t cb = 0;
         int nbuf = 0, rank = 0, kref = 1;
         double bufE = 0.0, bufR = 0.0;
+        double P[T];  // prefix sums of w (rate_prefix)
+#pragma unroll
+        for (int j = 0; j < T; ++j) P[j] = 0.0;
 #pragma unroll
         for (int p = 0; p < C; ++p) u[p] = 0;
 #pragma unroll
@@ -2313,6 +2351,7 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
               M::prepare(v, tb.gdata, kf);
 #pragma unroll
               for (int j = 0; j < T; ++j) w[j] = M::rate_k(j, u, kf, tb.gdata);
+              rate_prefix<T>(w, P, 0);
               t = (double)(Td - 1);
               c = 0;
               nb = 0;
@@ -2362,12 +2401,11 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
           const double R2 = __shfl_sync(0xffffffffu, bufR, src);
           if (!busy) continue;
           // one draw: ssa_step's operations and order, with the draw's
-          // random numbers from the buffer
+          // random numbers from the buffer and lambda and the inversion's
+          // running sums from the kept prefix sums
           int r;
           {
-            double lam = w[0];
-#pragma unroll
-            for (int j = 1; j < T; ++j) lam = lam + w[j];
+            const double lam = P[T - 1];
             if (!gt0(lam)) {
               r = SSA_DONE;
             } else if (c >= SG_MAX_DRAWS) {
@@ -2381,7 +2419,9 @@ k_days_sparse(const SgTables tb, const DayArgs a) {
                 r = SSA_DONE;
               } else {
                 t = tt;
-                const int rc = fire<KIND>(u, w, lam * R2, kf, tb);
+                const int n = select_prefix<T>(w, P, lam * R2);
+                const int rc = apply_transition<KIND>(u, w, n, kf, tb);
+                rate_prefix<T>(w, P, __ffs(tb.dep[n]) - 1);
                 ++fired;
                 r = rc ? rc : SSA_STEP_FIRED;
               }
