@@ -288,22 +288,22 @@ def _kernel_sources_sha1():
 #       --metrics dram__bytes_read.sum,dram__bytes_write.sum
 #       --clock-control none -k regex:k_days_sparse -s 1 -c 1
 DAY_KERNEL_NCU = {
-    "sources_sha1": "7430c2ba135b4a4d98f42e9a449dc77bbbf37016",
+    "sources_sha1": "7c3a1bfdd76c0c8c69c09a955fc3d411772b05ab",
     "workload": "SISe3 256 replicates x 5000 nodes x 30 days, own events per replicate",
     "tuning": [5000, 32],
-    "duration_us": 2289.9,
-    "dram_bytes_read": 2898760000,
-    "dram_bytes_write": 1507392000,
-    "dram_bytes_per_node_day": 114.74,
+    "duration_us": 2249.0,
+    "dram_bytes_read": 2896477000,
+    "dram_bytes_write": 1507242000,
+    "dram_bytes_per_node_day": 114.68,
     "algorithmic_bytes_per_node_day": 68,
-    "issue_active_pct": 19.06,
-    "fp64_pipe_active_pct": 14.54,
+    "issue_active_pct": 19.23,
+    "fp64_pipe_active_pct": 14.09,
     "warps_active_pct": 21.11,
-    "stall_barrier_per_issue": 8.00,
-    "stall_long_scoreboard_per_issue": 2.92,
-    "stall_wait_per_issue": 2.77,
+    "stall_barrier_per_issue": 7.70,
+    "stall_long_scoreboard_per_issue": 3.10,
+    "stall_wait_per_issue": 2.75,
     "l1_hit_pct": 69.9,
-    "l2_hit_pct": 26.5,
+    "l2_hit_pct": 26.4,
 }
 
 
