@@ -241,6 +241,15 @@ def test_whole_replicates_per_block(orc, gpu, per_block, heavy):
     _compare(orc, gpu, w, (400 * per_block, heavy))
 
 
+@pytest.mark.parametrize("tuning", [(9000, 8), (18000, 2), (20000, 32)])
+def test_blocks_of_several_chunks(orc, gpu, tuning):
+    # more units per block than one chunk of the shared lists holds (8,192):
+    # each day runs the passes and the SSA chunk by chunk, with whole
+    # replicates per block (9,000 and 18,000) and without (20,000)
+    w = W.config_batched(n_rep=3, n_nodes=9000, days=20, gen_seed=51)
+    _compare(orc, gpu, w, tuning)
+
+
 def test_whole_replicates_per_block_transfer_underflow(orc, gpu):
     # an external transfer of more animals than the source holds, on day 2
     # of replicate 1: the same error and no post time step of that day
